@@ -1,0 +1,193 @@
+/*
+ * lbm.h - C ABI of the GB300 library for the D2Q9 lattice-Boltzmann step with
+ * moving rigid disks and the Galilean-invariant momentum-exchange force of
+ * Wen, Zhang, Tu, Wang and Fang, arXiv:1303.0625.
+ *
+ * The library owns every device buffer it allocates (populations, owner map,
+ * node flags, solid table, force history).  The caller owns every output
+ * buffer it passes in.  All entry points return an lbm_status and never abort
+ * or exit.  A context is not thread-safe; separate contexts are independent.
+ *
+ * Lattice conventions (Sec. III.C of the paper):
+ *   velocities e_0..e_8 = (0,0) (1,0) (0,1) (-1,0) (0,-1) (1,1) (-1,1) (-1,-1) (1,-1),
+ *   weights 4/9 (i=0), 1/9 (i=1..4), 1/36 (i=5..8);
+ *   node (x, y) sits at integer coordinates, 0 <= x < nx, 0 <= y < ny;
+ *   every 2-D field is row-major [ny][nx] (x fastest); populations are
+ *   [9][ny][nx].
+ * One step t -> t+1 (Eq. 1-3) records the force on every solid at t (Eq. 4-7
+ * plus the momentum of nodes that changed type), advects with half-way
+ * bounce-back, collides (BGK, Eq. 2 and Eq. 8), moves the solids and
+ * re-rasterises them (covered nodes give their momentum to the solid, fresh
+ * nodes are refilled by extrapolation, Sec. IV.B).
+ */
+#ifndef LBM_GB300_H
+#define LBM_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lbm_ctx lbm_ctx; /* opaque; owns all device state */
+
+typedef enum {
+    LBM_OK = 0,
+    LBM_EINVAL = 1,    /* bad argument or configuration; nothing changed */
+    LBM_ENOMEM = 2,    /* a device or host allocation failed */
+    LBM_ECUDA = 3,     /* a CUDA call failed; lbm_last_error has the text */
+    LBM_EUNSTABLE = 4, /* a non-finite or non-positive density was produced */
+    LBM_ETIMEOUT = 5,  /* a bounded device wait ran out */
+    LBM_ESTATE = 6,    /* call not valid in the current state (e.g. record gone) */
+} lbm_status;
+
+/* boundary kinds for bc_x / bc_y */
+enum {
+    LBM_PERIODIC = 0,
+    LBM_WALL = 1, /* half-way bounce-back wall half a spacing outside the first/last node */
+    LBM_OPEN = 2, /* x only: equilibrium Poiseuille inlet column x=0, copy outlet column x=nx-1 */
+};
+/* storage / arithmetic precision */
+enum {
+    LBM_FP64 = 0,     /* populations stored and computed in FP64 */
+    LBM_FP32_DEV = 1, /* stored as f_i - w_i in FP32, computed in FP32 */
+    LBM_FP16_DEV = 2, /* stored as f_i - w_i in FP16, computed in FP32 */
+};
+/* density used in the moving-wall term of the bounced population */
+enum { LBM_RHOW_CONST = 0 /* rho0 */, LBM_RHOW_LOCAL = 1 /* density of the fluid node */ };
+/* newborn-node refill (Sec. IV.B): A1 2nd-order, A2 linear, A3 neighbour average */
+enum { LBM_REFILL_A1 = 1, LBM_REFILL_A2 = 2, LBM_REFILL_A3 = 3 };
+/* solid motion */
+enum { LBM_PRESCRIBED = 0, LBM_FREE = 1 };
+/* force form: Eq. 4 (conventional) or Eq. 5 (Galilean invariant) */
+enum { LBM_CME = 0, LBM_GME = 1 };
+
+typedef struct {
+    int32_t nx, ny;        /* nodes; 4 <= nx, ny and nx * ny < 2^31 */
+    int32_t bc_x, bc_y;    /* LBM_PERIODIC | LBM_WALL | LBM_OPEN (x only) */
+    double tau;            /* BGK relaxation time (> 0.5); viscosity (tau - 1/2) / 3 */
+    double rho0;           /* initial density and rho_w in LBM_RHOW_CONST */
+    double u0[2];          /* initial uniform velocity (ignored when bc_x = LBM_OPEN) */
+    double wall_ux[2];     /* x-velocity of the y = -1/2 wall [0] and y = ny-1/2 wall [1] */
+    double body_force[2];  /* uniform body force on the fluid (Guo forcing); 0 = none */
+    double inflow_umax;    /* peak of the parabolic inlet profile for bc_x = LBM_OPEN */
+    double gravity[2];     /* gravity acting on free solids (net of buoyancy) */
+    double lub_range;      /* gap below which free solids repel; 0 = off */
+    int32_t precision;     /* LBM_FP64 | LBM_FP32_DEV | LBM_FP16_DEV */
+    int32_t rho_w_mode;    /* LBM_RHOW_CONST | LBM_RHOW_LOCAL */
+    int32_t refill;        /* LBM_REFILL_A1 (default) | A2 | A3 */
+    int32_t force_ring;    /* number of most recent steps whose forces stay on device (>= 1) */
+    int32_t device;        /* CUDA device ordinal */
+    int32_t reserved;      /* must be 0 */
+    void *stream;          /* cudaStream_t to run on; NULL = a stream the context creates */
+} lbm_config;
+
+typedef struct {
+    double cx, cy;   /* centre R at the current time, lattice units */
+    double r;        /* radius; nodes with (x-cx)^2 + (y-cy)^2 <= r^2 are solid */
+    double vx, vy;   /* translational velocity V */
+    double omega;    /* angular velocity (counter-clockwise positive) */
+    double rho_s;    /* solid density (used by LBM_FREE motion) */
+    int32_t motion;  /* LBM_PRESCRIBED: R(t) = R_add + V (t - t_add); LBM_FREE: Newton-Euler */
+    int32_t reserved;/* must be 0 */
+} lbm_disk;
+
+/* Fill *cfg with defaults: periodic 64x64, tau 0.8, rho0 1, FP32_DEV,
+ * RHOW_CONST, REFILL_A1, force_ring 256, device 0, own stream. */
+void lbm_config_default(lbm_config *cfg);
+
+/* Create a context: allocate the populations (two buffers), owner map, node
+ * flags and force history on cfg->device and set every population to the
+ * equilibrium of Eq. 8 at (rho0, u0) (the inlet profile for an open channel).
+ * On success *out owns the device memory until lbm_destroy.
+ * Errors: LBM_EINVAL (tau <= 0.5, sizes, enum values, reserved != 0),
+ * LBM_ENOMEM, LBM_ECUDA. */
+lbm_status lbm_create(const lbm_config *cfg, lbm_ctx **out);
+
+/* Release everything the context owns.  NULL is accepted. */
+lbm_status lbm_destroy(lbm_ctx *ctx);
+
+/* Add a rigid disk at the current time and rasterise it into the owner map
+ * (nodes it covers become solid; no momentum is booked for them).  Solid ids
+ * are 0, 1, ... in order of addition; where disks overlap the lowest id owns
+ * the node.  Errors: LBM_EINVAL (r <= 0, r >= min(nx, ny) / 2 - 4, centre not
+ * finite, rho_s <= 0 for a free disk, more than 65534 solids). */
+lbm_status lbm_add_solid(lbm_ctx *ctx, const lbm_disk *disk, int32_t *id_out);
+
+/* Enqueue nsteps steps on the context's stream; returns without waiting.
+ * Device errors from earlier work surface here or at the next call that
+ * waits.  nsteps >= 0. */
+lbm_status lbm_step(lbm_ctx *ctx, int64_t nsteps);
+
+/* Wait for all enqueued work; LBM_EUNSTABLE if any step produced a
+ * non-finite or non-positive density. */
+lbm_status lbm_sync(lbm_ctx *ctx);
+
+/* Copy the force records of steps first_step .. first_step+count-1 into out,
+ * laid out [count][nsolid][3] = (Fx, Fy, T) of the chosen form (Eq. 4 or
+ * Eq. 5, each summed by Eq. 6 and Eq. 7, plus the covered/fresh node
+ * momenta).  The record of step t is the force at time t, taken before the
+ * step t -> t+1 advects.  Records exist for the last force_ring steps taken;
+ * asking for older or future ones gives LBM_ESTATE.  on_device != 0: out is a
+ * device pointer and the copy is enqueued on the context's stream; otherwise
+ * out is host memory and the call waits. */
+lbm_status lbm_forces(lbm_ctx *ctx, int32_t form, int64_t first_step, int64_t count, double *out,
+                      int32_t on_device);
+
+/* Density and velocity of the current post-collision state, each [ny][nx]
+ * FP64; solid nodes are NaN.  With a body force the velocity is
+ * (sum_i e_i f_i - F/2) / rho.  on_device as for lbm_forces. */
+lbm_status lbm_fields(lbm_ctx *ctx, double *rho, double *ux, double *uy, int32_t on_device);
+
+/* Current populations as FP64 [9][ny][nx] (converted from the storage
+ * precision; the values at solid nodes are unspecified) / overwrite them
+ * (rounded to the storage precision).  on_device as for lbm_forces. */
+lbm_status lbm_get_populations(lbm_ctx *ctx, double *f, int32_t on_device);
+lbm_status lbm_set_populations(lbm_ctx *ctx, const double *f, int32_t on_device);
+
+/* Owner map [ny][nx]: -1 for fluid, else the id of the solid covering the
+ * node.  on_device as for lbm_forces. */
+lbm_status lbm_get_owner(lbm_ctx *ctx, int32_t *owner, int32_t on_device);
+
+/* Solid state at the current time, host [nsolid][5] = (x, y, vx, vy, omega).
+ * Waits for the stream. */
+lbm_status lbm_get_solids(lbm_ctx *ctx, double *state);
+
+/* Overwrite the state of solid id (x, y, vx, vy, omega); for a prescribed
+ * disk this also restarts its motion from the given position now.  The owner
+ * map is not re-rasterised until the next step. */
+lbm_status lbm_set_solid(lbm_ctx *ctx, int32_t id, const double *state);
+
+/* Fluid-solid links (x_f fluid, x_f + e_i solid, Eq. 6 summation set) as
+ * host rows (x_f, y_f, i, solid) in raster order of x_f then ascending i.
+ * Writes min(cap, total) rows and stores the total in *n_out. Waits. */
+lbm_status lbm_links(lbm_ctx *ctx, int64_t cap, int32_t *out, int64_t *n_out);
+
+/* Current time step and number of solids. */
+int64_t lbm_time(const lbm_ctx *ctx);
+int32_t lbm_nsolid(const lbm_ctx *ctx);
+
+/* Human-readable text of the last error on ctx (or of the last failed
+ * lbm_create when ctx is NULL).  Owned by the library. */
+const char *lbm_last_error(const lbm_ctx *ctx);
+const char *lbm_status_string(lbm_status st);
+
+/* Launch policy.  steps_per_graph > 1 captures that many steps into one CUDA
+ * graph and replays it; 0 or 1 launches each kernel directly (default 0). */
+lbm_status lbm_set_graph(lbm_ctx *ctx, int32_t steps_per_graph);
+
+/* Kernel timing: while enabled, every launch of the fused advection-collision
+ * kernel is bracketed by CUDA events on the context's stream (graphs are not
+ * used).  lbm_get_timing waits, then returns the summed duration in ms and the
+ * number of launches since timing was enabled. */
+lbm_status lbm_set_timing(lbm_ctx *ctx, int32_t enable);
+lbm_status lbm_get_timing(lbm_ctx *ctx, double *stream_collide_ms, int64_t *launches);
+
+/* Kernel launches issued by the library since creation (all kernels). */
+int64_t lbm_launch_count(const lbm_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBM_GB300_H */

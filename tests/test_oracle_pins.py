@@ -1,0 +1,424 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Each test compares the oracle with something other than itself: a closed
+form printed in the paper (Eq. 9, Eq. 10), a closed form of a textbook flow
+(Couette, Poiseuille), an exact invariant of the scheme (mass, momentum and
+angular-momentum bookkeeping), brute force on small inputs (rasterisation,
+link enumeration), or a polynomial that an extrapolation must reproduce.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+
+EX = np.array([0, 1, 0, -1, 0, 1, -1, -1, 1])
+EY = np.array([0, 0, 1, 0, -1, 1, 1, -1, -1])
+OPP = [0, 3, 4, 1, 2, 7, 8, 5, 6]
+# D2Q9 weights: the paper only calls them "weighting coefficients" (Sec. III.C);
+# these are the values for which its Eq. 10 cancellation holds.
+W = np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4)
+
+
+# ------------------------------------------------------------------ Eq. 8
+
+@pytest.mark.parametrize("rho,ux,uy", [(1.0, 0.0, 0.0), (1.03, 0.07, -0.02), (0.97, -0.1, 0.08)])
+def test_equilibrium_moments(rho, ux, uy):
+    """Eq. 8 must carry density rho, momentum rho u and momentum flux
+    rho/3 I + rho u u (the moments that make the LBE recover Navier-Stokes)."""
+    f = O.feq(rho, ux, uy)
+    assert f.sum() == pytest.approx(rho, abs=1e-15)
+    assert (EX * f).sum() == pytest.approx(rho * ux, abs=1e-15)
+    assert (EY * f).sum() == pytest.approx(rho * uy, abs=1e-15)
+    assert (EX * EX * f).sum() == pytest.approx(rho / 3 + rho * ux * ux, abs=1e-15)
+    assert (EY * EY * f).sum() == pytest.approx(rho / 3 + rho * uy * uy, abs=1e-15)
+    assert (EX * EY * f).sum() == pytest.approx(rho * ux * uy, abs=1e-15)
+
+
+# ------------------------------------------------------------- Eq. 9, 10
+
+VELS = [(0.03, -0.07), (0.1, 0.0), (0.0, -0.1), (-0.06, 0.05), (0.0, 0.0)]
+
+
+@pytest.mark.parametrize("v", VELS)
+@pytest.mark.parametrize("i", range(1, 9))
+def test_eq9_conventional_link_force(i, v):
+    """Eq. 9: in an equilibrium system moving with the boundary, the
+    conventional force on link i is 2 rho w_i e_i + 3 rho w_i [3 (e_i.v)^2 - v^2] e_i."""
+    rho = 1.02
+    f = O.feq(rho, *v)
+    lf = O.link_force(i, f[i], f[OPP[i]], *v)
+    ev = EX[i] * v[0] + EY[i] * v[1]
+    vv = v[0] ** 2 + v[1] ** 2
+    coef = 2 * rho * W[i] + 3 * rho * W[i] * (3 * ev * ev - vv)
+    assert lf[0] == pytest.approx(coef * EX[i], abs=1e-15)
+    assert lf[1] == pytest.approx(coef * EY[i], abs=1e-15)
+
+
+@pytest.mark.parametrize("v", VELS)
+@pytest.mark.parametrize("links", [(2, 5, 6), (1, 5, 8), (4, 7, 8), (3, 6, 7)])
+def test_eq10_galilean_invariant_sum(links, v):
+    """Eq. 10: over a symmetric link set ({2,5,6} and its rotations) the
+    Galilean-invariant force is sum 2 rho w_i e_i, independent of v."""
+    rho = 0.98
+    f = O.feq(rho, *v)
+    tot = np.zeros(2)
+    expect = np.zeros(2)
+    for i in links:
+        lf = O.link_force(i, f[i], f[OPP[i]], *v)
+        tot += lf[2:]
+        expect += 2 * rho * W[i] * np.array([EX[i], EY[i]])
+    assert np.allclose(tot, expect, atol=1e-15, rtol=0)
+    # |expect| = rho / 3 for these sets: the one-sided pressure of a flat wall
+    assert np.hypot(*expect) == pytest.approx(rho / 3, rel=1e-15)
+
+
+@pytest.mark.parametrize("i", range(1, 9))
+def test_galilean_form_equals_conventional_at_rest(i):
+    """Sec. III.B: with a motionless boundary Eq. 5 turns into Eq. 4."""
+    lf = O.link_force(i, 0.123, 0.071, 0.0, 0.0)
+    assert lf[2] == lf[0] and lf[3] == lf[1]
+
+
+# --------------------------------------------- thin plate, Fig. 1(b)
+
+def _plate_one_sided(o, nsolid_first, L, side_dirs, f):
+    """Sum of per-link forces over the plate links whose direction is in
+    side_dirs (one side of the plate), using the oracle's own link list."""
+    tot = np.zeros(4)
+    for xf, yf, i, s in o.links():
+        if s < nsolid_first or i not in side_dirs:
+            continue
+        st = o.solid_state(s)
+        rho_w = 1.0
+        fi = f[i, yf, xf]
+        fbb = fi - 6 * W[i] * rho_w * (EX[i] * st[2] + EY[i] * st[3])
+        tot += O.link_force(i, fi, fbb, st[2], st[3])
+    return tot
+
+
+@pytest.mark.parametrize("tau,L", [(0.6, 5), (1.2, 11), (0.8, 7)])
+@pytest.mark.parametrize("V", [0.02, 0.05, 0.1])
+def test_thin_plate_equilibrium(tau, L, V):
+    """Fig. 1(b) / Sec. III.C: a vertical plate and the fluid move together at
+    a horizontal speed V.  The state must stay exactly at equilibrium, the
+    Galilean-invariant one-sided force is rho L / 3 (error 0), and the
+    conventional one is too large by rho L V^2 (relative error 3 V^2),
+    independently of tau and of the plate length."""
+    nx, ny = 40, 32
+    o = O.Oracle(nx, ny, tau, u0=(V, 0.0))
+    x0, y0 = 12, 10
+    for k in range(L):  # one node per disk: radius 1/2 centred on a node
+        o.add_disk(x0, y0 + k, 0.5, V, 0.0)
+    steps = int(0.5 / V) - 1  # before the plate reaches the next column
+    o.step(steps)
+    f = o.get_f()
+    eq = O.feq(1.0, V, 0.0)
+    fluid = o.owner() < 0
+    assert np.abs(f[:, fluid] - eq[:, None]).max() < 1e-14
+    left = _plate_one_sided(o, 0, L, (1, 5, 8), f)
+    assert left[2] == pytest.approx(L / 3, rel=1e-13)          # Eq. 5: exact
+    assert abs(left[3]) < 1e-14
+    assert left[0] == pytest.approx(L / 3 + L * V * V, rel=1e-13)  # Eq. 4
+    assert (left[0] - L / 3) / (L / 3) == pytest.approx(3 * V * V, rel=1e-10)
+
+
+def test_thin_plate_stays_equilibrium_across_node_crossings():
+    """The uniformly moving plate keeps the fluid exactly uniform also when it
+    covers and uncovers nodes: refill A1 reproduces a uniform field."""
+    V = 0.1
+    o = O.Oracle(40, 24, 0.7, u0=(V, 0.0))
+    for k in range(6):
+        o.add_disk(10, 8 + k, 0.5, V, 0.0)
+    o.step(25)  # the plate crosses two nodes
+    f = o.get_f()
+    fluid = o.owner() < 0
+    eq = O.feq(1.0, V, 0.0)
+    assert np.abs(f[:, fluid] - eq[:, None]).max() < 1e-14
+
+
+# ------------------------------------------------------------ channel flows
+
+def test_couette_closed_form():
+    """Moving top wall U, resting bottom wall: u(y) = U (y + 1/2) / ny, which
+    half-way bounce-back with the moving-wall term reproduces exactly."""
+    ny, U = 16, 0.05
+    for tau in (0.6, 0.8):
+        o = O.Oracle(4, ny, tau, bc_y=O.WALL, wall_ux=(0.0, U))
+        o.step(30000 if tau < 0.7 else 15000, record=False)
+        rho, ux, uy = o.fields()
+        y = np.arange(ny)
+        assert np.abs(ux[:, 1] - U * (y + 0.5) / ny).max() < 1e-10
+        assert np.abs(uy).max() < 1e-13
+        assert np.abs(rho - 1.0).max() < 1e-11  # 3e4 steps of rounding
+
+
+def _poiseuille_error(tau, ny, g=1e-6):
+    nu = (tau - 0.5) / 3
+    o = O.Oracle(4, ny, tau, bc_y=O.WALL, body_force=(g, 0.0))
+    o.step(int(12 * ny * ny / nu), record=False)
+    _, ux, _ = o.fields()
+    y = np.arange(ny)
+    exact = g / (2 * nu) * (y + 0.5) * (ny - 0.5 - y)
+    return np.abs(ux[:, 1] - exact).max() / exact.max()
+
+
+def test_poiseuille_exact_at_magic_tau():
+    """Body-force Poiseuille flow between half-way bounce-back walls is exact
+    (to convergence) when (tau - 1/2)^2 = 3/16."""
+    assert _poiseuille_error(0.5 + math.sqrt(3) / 4, 8) < 1e-9
+
+
+def test_poiseuille_second_order():
+    """Away from that tau the wall-slip error shrinks as ny^-2."""
+    e8 = _poiseuille_error(0.8, 8)
+    e16 = _poiseuille_error(0.8, 16)
+    assert 1e-3 < e8 < 2e-2
+    assert e8 / e16 == pytest.approx(4.0, rel=0.05)
+
+
+# ------------------------------------------------------- bookkeeping
+
+def _perturbed(o, seed, amp=0.01, u=(0.0, 0.0)):
+    f = np.broadcast_to(O.feq(1.0, *u)[:, None, None], (9, o.ny, o.nx)).copy()
+    rng = np.random.default_rng(seed)
+    f *= 1 + rng.uniform(-amp, amp, size=f.shape)
+    o.set_f(f)
+
+
+def _fluid_momentum(o):
+    f = o.get_f()
+    fl = o.owner() < 0
+    return np.array([(EX[:, None] * f[:, fl]).sum(), (EY[:, None] * f[:, fl]).sum()]), f[:, fl].sum()
+
+
+@pytest.mark.parametrize("rho_w_mode", [O.RHOW_CONST, O.RHOW_LOCAL])
+def test_momentum_bookkeeping_moving_disks(rho_w_mode):
+    """The conventional form is exactly the fluid's momentum loss: over K
+    steps, P(K) - P(0) = -sum of the Eq. 4 records - momentum booked for the
+    next record (covered/fresh nodes).  Periodic domain, disks that translate
+    and rotate across node boundaries, perturbed initial state."""
+    o = O.Oracle(48, 40, 0.7, rho_w_mode=rho_w_mode)
+    o.add_disk(15.3, 12.1, 5.2, 0.09, 0.04, 0.01)
+    o.add_disk(31.7, 27.4, 6.1, -0.07, -0.08, -0.02)
+    _perturbed(o, 1)
+    p0, _ = _fluid_momentum(o)
+    rec = o.step(40)
+    p1, _ = _fluid_momentum(o)
+    booked = o.pending()
+    lost = rec[:, :, O.CME, :2].sum(axis=(0, 1)) + booked[:, :2].sum(axis=0)
+    assert np.abs((p1 - p0) + lost).max() < 1e-12
+
+
+def test_mass_conserved_with_resting_solids():
+    """Collision, advection and bounce-back at resting solids and walls
+    conserve mass exactly."""
+    o = O.Oracle(40, 30, 0.9, bc_y=O.WALL)
+    o.add_disk(20.4, 14.6, 6.3)
+    _perturbed(o, 2, amp=0.02, u=(0.03, 0.0))
+    _, m0 = _fluid_momentum(o)
+    o.step(60, record=False)
+    _, m1 = _fluid_momentum(o)
+    assert abs(m1 - m0) < 1e-11 * m0
+
+
+def test_angular_momentum_bookkeeping_rotating_disk():
+    """Eq. 7 with x_s on the link: for a rotating disk the torque of the
+    conventional form is exactly the fluid's loss of angular momentum about
+    R (advection and collision conserve it).  The perturbation stays clear of
+    the periodic boundary during the run."""
+    n = 64
+    o = O.Oracle(n, n, 0.75)
+    R = (32.0, 32.0)
+    o.add_disk(R[0], R[1], 7.5, 0.0, 0.0, 0.015)
+    f = np.broadcast_to(O.feq(1.0, 0.0, 0.0)[:, None, None], (9, n, n)).copy()
+    yy, xx = np.mgrid[0:n, 0:n]
+    near = (xx - R[0]) ** 2 + (yy - R[1]) ** 2 < 14 ** 2
+    rng = np.random.default_rng(3)
+    f[:, near] *= 1 + rng.uniform(-0.01, 0.01, size=(9, near.sum()))
+    o.set_f(f)
+
+    def ang(o):
+        f = o.get_f()
+        fl = o.owner() < 0
+        jx = (EX[:, None, None] * f).sum(0)
+        jy = (EY[:, None, None] * f).sum(0)
+        return ((xx - R[0]) * jy - (yy - R[1]) * jx)[fl].sum()
+
+    l0 = ang(o)
+    rec = o.step(8)
+    l1 = ang(o)
+    t_cme = rec[:, 0, O.CME, 2].sum()
+    assert abs((l1 - l0) + t_cme) < 1e-12
+    # the fluid resists the rotation: torque opposite to omega
+    assert rec[0, 0, O.CME, 2] < 0
+
+
+def test_translation_constant_rho_w_galilean_equals_conventional():
+    """Per link Eq. 5 - Eq. 4 = -6 w_i rho_w (e_i.v) v; with rho_w = rho0 and
+    pure translation these cancel over the entry/exit links of every lattice
+    line through a convex body, so the totals agree to rounding."""
+    o = O.Oracle(64, 48, 0.8, bc_y=O.WALL)
+    o.add_disk(30.3, 23.8, 8.4, 0.05, 0.02)
+    rec = o.step(30)
+    assert np.abs(rec[:, 0, O.GME, :2] - rec[:, 0, O.CME, :2]).max() < 1e-14
+
+
+# ----------------------------------------------- geometry and links
+
+def _brute_owner(nx, ny, disks, periodic=(True, True)):
+    """Owner map by brute force over every node and every disk, lowest id wins."""
+    owner = -np.ones((ny, nx), dtype=np.int32)
+    yy, xx = np.mgrid[0:ny, 0:nx].astype(float)
+    for s in reversed(range(len(disks))):
+        cx, cy, r = disks[s]
+        best = np.zeros((ny, nx), dtype=bool)
+        sx = (-1, 0, 1) if periodic[0] else (0,)
+        sy = (-1, 0, 1) if periodic[1] else (0,)
+        for ix in sx:
+            for iy in sy:
+                dx = xx + ix * nx - cx
+                dy = yy + iy * ny - cy
+                best |= dx * dx + dy * dy <= r * r
+        owner[best] = s
+    return owner
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_rasterisation_brute_force(seed):
+    rng = np.random.default_rng(seed)
+    nx, ny = 37, 29
+    disks = [(rng.uniform(0, nx), rng.uniform(0, ny), rng.uniform(1.5, 7)) for _ in range(5)]
+    o = O.Oracle(nx, ny, 0.8)
+    for d in disks:
+        o.add_disk(*d)
+    assert np.array_equal(o.owner(), _brute_owner(nx, ny, disks))
+
+
+def test_disk_node_count_gauss_circle():
+    """A disk of radius r centred on a node covers N(r) = #{(i, j): i^2 + j^2 <= r^2}
+    nodes (Gauss circle problem), e.g. N(12) = 441."""
+    o = O.Oracle(64, 64, 0.8)
+    o.add_disk(32, 32, 12)
+    assert (o.owner() == 0).sum() == 441
+    n5 = sum(1 for i in range(-5, 6) for j in range(-5, 6) if i * i + j * j <= 25)
+    o2 = O.Oracle(32, 32, 0.8)
+    o2.add_disk(10, 9, 5)
+    assert (o2.owner() == 0).sum() == n5 == 81
+
+
+@pytest.mark.parametrize("bc", [(O.PERIODIC, O.PERIODIC), (O.PERIODIC, O.WALL), (O.WALL, O.WALL)])
+def test_links_brute_force(bc):
+    rng = np.random.default_rng(11)
+    nx, ny = 33, 27
+    o = O.Oracle(nx, ny, 0.8, bc_x=bc[0], bc_y=bc[1])
+    for _ in range(4):
+        o.add_disk(rng.uniform(4, nx - 4), rng.uniform(4, ny - 4), rng.uniform(1.5, 5))
+    own = o.owner()
+    expect = []
+    for y in range(ny):
+        for x in range(nx):
+            if own[y, x] >= 0:
+                continue
+            for i in range(1, 9):
+                xb, yb = x + EX[i], y + EY[i]
+                if bc[0] == O.PERIODIC:
+                    xb %= nx
+                elif not 0 <= xb < nx:
+                    continue
+                if bc[1] == O.PERIODIC:
+                    yb %= ny
+                elif not 0 <= yb < ny:
+                    continue
+                if own[yb, xb] >= 0:
+                    expect.append((x, y, i, own[yb, xb]))
+    assert np.array_equal(o.links(), np.array(expect, dtype=np.int32).reshape(-1, 4))
+
+
+# ------------------------------------------------------ refill (Sec. IV.B)
+
+def _poly_field(nx, ny, degree, seed):
+    rng = np.random.default_rng(seed)
+    yy, xx = np.mgrid[0:ny, 0:nx].astype(float)
+    f = np.empty((9, ny, nx))
+    for j in range(9):
+        c = rng.uniform(-1, 1, size=6) * np.array([0.1, 1e-3, 1e-3, 1e-5, 1e-5, 1e-5])
+        f[j] = c[0] + c[1] * xx + c[2] * yy
+        if degree == 2:
+            f[j] += c[3] * xx * xx + c[4] * xx * yy + c[5] * yy * yy
+    return f
+
+
+@pytest.mark.parametrize("mode,degree", [(O.REFILL_A1, 2), (O.REFILL_A2, 1)])
+def test_refill_exact_for_polynomials(mode, degree):
+    """A1 (second-order extrapolation) reproduces any quadratic field, A2
+    (linear) any linear field, along every link direction and on average."""
+    nx = ny = 24
+    o = O.Oracle(nx, ny, 0.8, refill=mode)
+    f = _poly_field(nx, ny, degree, 5)
+    o.set_f(f)
+    for (x, y) in [(8, 9), (12, 12), (15, 7)]:
+        got = o.refill_probe(x, y)
+        assert np.abs(got - f[:, y, x]).max() < 1e-14
+
+
+def test_refill_a1_uses_only_old_fluid_nodes():
+    """Directions blocked by a solid within three nodes do not take part;
+    with every direction blocked A1 falls back to A2, then A3."""
+    nx = ny = 24
+    o = O.Oracle(nx, ny, 0.8)
+    f = _poly_field(nx, ny, 1, 9)
+    o.set_f(f)
+    o.add_disk(12, 15, 1.2)  # blocks the +y family at distance 2..4 from (12, 12)
+    got = o.refill_probe(12, 12)
+    assert np.abs(got - f[:, 12, 12]).max() < 1e-14  # linear field: still exact
+    # A3 for a quadratic field: plain average of the 8 neighbours
+    o3 = O.Oracle(nx, ny, 0.8, refill=O.REFILL_A3)
+    fq = _poly_field(nx, ny, 2, 4)
+    o3.set_f(fq)
+    got3 = o3.refill_probe(10, 10)
+    avg = np.mean([fq[:, 10 + EY[i], 10 + EX[i]] for i in range(1, 9)], axis=0)
+    assert np.abs(got3 - avg).max() < 1e-15
+
+
+# ------------------------------------------------------------- rigid body
+
+def test_free_disk_first_step_newton_euler():
+    """A free disk at rest, centred on a node, in fluid at rest feels no net
+    hydrodynamic force at t = 0, so one step gives V(1) = (1 - rho_f/rho_s) g
+    and R(1) = R(0) + V(1) / 2 (explicit Euler for V, trapezoid for R)."""
+    g = (0.0, -1e-4)
+    o = O.Oracle(48, 48, 0.8, gravity=g)
+    o.add_disk(24, 24, 6, rho_s=1.5, motion=O.FREE)
+    rec = o.step(1)
+    assert np.abs(rec[0, 0, O.GME]).max() < 1e-15
+    st = o.solid_state(0)
+    vy = (1 - 1 / 1.5) * g[1]
+    assert st[3] == pytest.approx(vy, rel=1e-14)
+    assert st[1] == pytest.approx(24 + 0.5 * vy, rel=1e-15)
+    assert abs(st[2]) < 1e-17 and abs(st[4]) < 1e-17  # rounding of the zero net force
+
+
+def test_lubrication_pair_symmetric():
+    """Two equal free disks with a gap s < zeta repel with
+    kappa ((zeta - s) / zeta)^2, kappa = net weight of one disk, equal and
+    opposite (mirror-symmetric set-up, no net fluid force at t = 0)."""
+    g = (0.0, -1e-5)
+    r, rho_s, zeta = 5.0, 1.5, 2.0
+    o = O.Oracle(64, 32, 0.8, lub_range=zeta, gravity=g)
+    gap = 1.0
+    xa, xb = 32 - (r + gap / 2), 32 + (r + gap / 2)
+    o.add_disk(xa, 16, r, rho_s=rho_s, motion=O.FREE)
+    o.add_disk(xb, 16, r, rho_s=rho_s, motion=O.FREE)
+    rec = o.step(1)
+    M = rho_s * math.pi * r * r
+    kappa = abs(1 - 1 / rho_s) * M * abs(g[1])
+    push = kappa * ((zeta - gap) / zeta) ** 2
+    va, vb = o.solid_state(0), o.solid_state(1)
+    fa = rec[0, 0, O.GME, 0]
+    fb = rec[0, 1, O.GME, 0]
+    assert fa == pytest.approx(-fb, abs=1e-15)
+    assert va[2] == pytest.approx((fa - push) / M, rel=1e-12, abs=1e-18)
+    assert vb[2] == pytest.approx((fb + push) / M, rel=1e-12, abs=1e-18)
+    assert va[2] == pytest.approx(-vb[2], rel=1e-12)
