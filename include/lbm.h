@@ -153,9 +153,10 @@ lbm_status lbm_get_owner(lbm_ctx *ctx, int32_t *owner, int32_t on_device);
  * Waits for the stream. */
 lbm_status lbm_get_solids(lbm_ctx *ctx, double *state);
 
-/* Overwrite the state of solid id (x, y, vx, vy, omega); for a prescribed
- * disk this also restarts its motion from the given position now.  The owner
- * map is not re-rasterised until the next step. */
+/* Set the velocity and angular velocity of solid id.  state = (x, y, vx,
+ * vy, omega) where (x, y) must equal the current centre exactly (positions
+ * cannot be changed; LBM_EINVAL otherwise).  A prescribed disk restarts its
+ * closed-form motion R(t) = R + V (t - now) from its current centre. */
 lbm_status lbm_set_solid(lbm_ctx *ctx, int32_t id, const double *state);
 
 /* Fluid-solid links (x_f fluid, x_f + e_i solid, Eq. 6 summation set) as

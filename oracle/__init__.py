@@ -143,6 +143,7 @@ class Oracle:
         if not self._h:
             raise ValueError("invalid oracle configuration")
         self.nx, self.ny = int(nx), int(ny)
+        self._radius = []
 
     def __del__(self):
         h = getattr(self, "_h", None)
@@ -159,6 +160,7 @@ class Oracle:
         return int(self._lib.ora_nsolid(self._h))
 
     def add_disk(self, cx, cy, r, vx=0.0, vy=0.0, omega=0.0, rho_s=1.0, motion=PRESCRIBED) -> int:
+        self._radius.append(float(r))
         return int(self._lib.ora_add_disk(self._h, cx, cy, r, vx, vy, omega, rho_s, int(motion)))
 
     def step(self, n: int = 1, record: bool = True):
@@ -197,6 +199,9 @@ class Oracle:
         out = np.empty(5)
         self._lib.ora_solid_state(self._h, int(s), _dp(out))
         return out
+
+    def solid_radius(self, s: int) -> float:
+        return float(self._radius[s])
 
     def set_solid_state(self, s: int, state) -> None:
         st = np.ascontiguousarray(state, dtype=np.float64)

@@ -684,6 +684,10 @@ void ora_set_solid_state(ora_sim *S, int s, const double *in)
     b->vx = in[2];
     b->vy = in[3];
     b->om = in[4];
+    /* prescribed motion restarts from here */
+    b->xa = b->x;
+    b->ya = b->y;
+    b->ta = S->t;
 }
 
 /* Enumerate the fluid-solid links in raster order of the fluid node and

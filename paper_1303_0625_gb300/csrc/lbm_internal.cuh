@@ -1,0 +1,223 @@
+// Internal definitions shared by the CUDA translation units of the library:
+// D2Q9 tables, storage precisions, the device-side parameter block and the
+// geometric helpers (disk boxes, inside test, periodic images).
+#pragma once
+
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "lbm.h"
+
+namespace gbm {
+
+constexpr uint16_t FLUID = 0xFFFFu;   // owner value of a fluid node
+constexpr int SOLID_BLOCK = 256;      // threads of the per-solid kernels
+constexpr int SC_BLOCK_X = 128;       // threads of the advection-collision kernel
+
+// D2Q9 velocities in the order of Sec. III.C of the paper:
+// (0,0) (1,0) (0,1) (-1,0) (0,-1) (1,1) (-1,1) (-1,-1) (1,-1)
+__host__ __device__ constexpr int cx(int i) {
+    return (i == 1 || i == 5 || i == 8) ? 1 : ((i == 3 || i == 6 || i == 7) ? -1 : 0);
+}
+__host__ __device__ constexpr int cy(int i) {
+    return (i == 2 || i == 5 || i == 6) ? 1 : ((i == 4 || i == 7 || i == 8) ? -1 : 0);
+}
+__host__ __device__ constexpr int opp(int i) {
+    return i == 0 ? 0 : (i <= 4 ? ((i + 1) & 3) + 1 : ((i - 3) & 3) + 5);
+}
+// lattice weights 4/9, 1/9, 1/36
+template <class C>
+__host__ __device__ constexpr C wgt(int i) {
+    return i == 0 ? C(4) / C(9) : (i <= 4 ? C(1) / C(9) : C(1) / C(36));
+}
+
+// Per-solid record on the device (array of structs, 160 bytes).
+struct DSolid {
+    double xa, ya;     // position when added (prescribed motion)
+    double x, y;       // centre R(t)
+    double xn, yn;     // centre R(t+1), written during the step
+    double vx, vy, om; // V(t), Omega(t)
+    double vxn, vyn, omn;
+    double r, rho_s;
+    double pend[3];    // momentum booked for the next force record
+    long long ta;      // time when added
+    int motion;
+    int pad;
+};
+
+struct Lattice {
+    int nx, ny, pitch; // pitch = elements per row of every 2-D plane
+    int bc_x, bc_y;
+    long long plane;   // ny * pitch
+};
+
+struct StepParams {
+    Lattice L;
+    void *f0, *f1;            // population buffers; buffer (t & 1) holds time t
+    uint16_t *owner, *prev, *flags;
+    DSolid *S;
+    int nsolid;
+    const int *moving;        // ids of solids that translate (or are free)
+    int nmoving;
+    double *ring;             // [ring_len][2][nsolid][3]
+    int ring_len;
+    long long *t;             // device step counter
+    int *status;              // bit 0: non-finite or non-positive density; bit 1: bad solid state
+    double tau, omega, rho0;
+    double wall_ux0, wall_ux1;
+    double body_x, body_y;
+    double umax;
+    double grav_x, grav_y, lub;
+    double u0x, u0y;
+    int rho_w_mode, refill, precision;
+};
+
+// ---------------------------------------------------------------- storage
+
+template <int P> struct Prec;
+template <> struct Prec<LBM_FP64> {
+    using S = double;
+    using C = double;
+    static constexpr bool dev = false;
+};
+template <> struct Prec<LBM_FP32_DEV> {
+    using S = float;
+    using C = float;
+    static constexpr bool dev = true;
+};
+template <> struct Prec<LBM_FP16_DEV> {
+    using S = __half;
+    using C = float;
+    static constexpr bool dev = true;
+};
+
+__device__ __forceinline__ double ld(const double *p) { return __ldg(p); }
+__device__ __forceinline__ float ld(const float *p) { return __ldg(p); }
+__device__ __forceinline__ float ld(const __half *p) { return __half2float(__ldg(p)); }
+__device__ __forceinline__ double ldc(const double *p) { return *p; }
+__device__ __forceinline__ float ldc(const float *p) { return *p; }
+__device__ __forceinline__ float ldc(const __half *p) { return __half2float(*p); }
+__device__ __forceinline__ void st(double *p, double v) { *p = v; }
+__device__ __forceinline__ void st(float *p, float v) { *p = v; }
+__device__ __forceinline__ void st(__half *p, float v) { *p = __float2half_rn(v); }
+__device__ __forceinline__ void st(float *p, double v) { *p = (float)v; }
+__device__ __forceinline__ void st(__half *p, double v) { *p = __double2half(v); }
+
+// Population i of cell k as an FP64 value f_i (undoing the deviation storage).
+template <int P>
+__device__ __forceinline__ double f64(const void *buf, long long plane, int i, long long k) {
+    using S = typename Prec<P>::S;
+    double v = (double)ldc(static_cast<const S *>(buf) + (long long)i * plane + k);
+    if (Prec<P>::dev) v += wgt<double>(i);
+    return v;
+}
+// Store an FP64 population value f_i into the storage precision.
+template <int P>
+__device__ __forceinline__ void put64(void *buf, long long plane, int i, long long k, double v) {
+    using S = typename Prec<P>::S;
+    if (Prec<P>::dev) v -= wgt<double>(i);
+    st(static_cast<S *>(buf) + (long long)i * plane + k, v);
+}
+
+// --------------------------------------------------------------- geometry
+
+struct Box {
+    int x0, y0, w, h;
+};
+
+// Nodes whose integer coordinates can be inside the disk, grown by g.
+__device__ __forceinline__ Box disk_box(double X, double Y, double r, int g) {
+    Box b;
+    b.x0 = (int)floor(__dsub_rn(X, r)) - g;
+    b.y0 = (int)floor(__dsub_rn(Y, r)) - g;
+    b.w = (int)ceil(__dadd_rn(X, r)) + g - b.x0 + 1;
+    b.h = (int)ceil(__dadd_rn(Y, r)) + g - b.y0 + 1;
+    return b;
+}
+
+// A solid whose centre is not finite (or absurdly far away) would give a
+// meaningless box; per-solid kernels skip it and raise status bit 1.
+__device__ __forceinline__ bool solid_ok(const DSolid &b) {
+    return fabs(b.x) < 1e9 && fabs(b.y) < 1e9 && fabs(b.xn) < 1e9 && fabs(b.yn) < 1e9 &&
+           b.r > 0.0 && b.r < 1e6;
+}
+
+__device__ __forceinline__ Box box_union(Box a, Box b) {
+    Box u;
+    u.x0 = min(a.x0, b.x0);
+    u.y0 = min(a.y0, b.y0);
+    u.w = max(a.x0 + a.w, b.x0 + b.w) - u.x0;
+    u.h = max(a.y0 + a.h, b.y0 + b.h) - u.y0;
+    return u;
+}
+
+// (i - X)^2 + (j - Y)^2 <= r^2, each operation rounded once (no contraction)
+__device__ __forceinline__ bool inside_disk(int i, int j, double X, double Y, double r) {
+    double dx = __dsub_rn((double)i, X), dy = __dsub_rn((double)j, Y);
+    return __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)) <= __dmul_rn(r, r);
+}
+
+// Map node coordinates into the domain; false beyond a non-periodic edge.
+__device__ __forceinline__ bool locate(const Lattice &L, int x, int y, int &xo, int &yo) {
+    if (L.bc_x == LBM_PERIODIC) {
+        x %= L.nx;
+        if (x < 0) x += L.nx;
+    } else if (x < 0 || x >= L.nx) {
+        return false;
+    }
+    if (L.bc_y == LBM_PERIODIC) {
+        y %= L.ny;
+        if (y < 0) y += L.ny;
+    } else if (y < 0 || y >= L.ny) {
+        return false;
+    }
+    xo = x;
+    yo = y;
+    return true;
+}
+
+// Separation reduced to the nearest periodic image.
+__device__ __forceinline__ double min_image(double d, int n, bool periodic) {
+    if (!periodic) return d;
+    double q = floor(__dadd_rn(__ddiv_rn(d, (double)n), 0.5));
+    return __dsub_rn(d, __dmul_rn((double)n, q));
+}
+
+// Velocity V + Omega x (p - R) of a solid at the point p; d = p - R.
+__device__ __forceinline__ void point_velocity(const Lattice &L, const double X, const double Y,
+                                               double vx, double vy, double om, double px,
+                                               double py, double &ux, double &uy, double &dx,
+                                               double &dy) {
+    dx = min_image(__dsub_rn(px, X), L.nx, L.bc_x == LBM_PERIODIC);
+    dy = min_image(__dsub_rn(py, Y), L.ny, L.bc_y == LBM_PERIODIC);
+    ux = vx - om * dy;
+    uy = vy + om * dx;
+}
+
+__device__ __forceinline__ long long cell_of(const Lattice &L, int x, int y) {
+    return (long long)y * L.pitch + x;
+}
+
+// ----------------------------------------------------------- launchers
+
+// k_stream_collide.cu
+cudaError_t launch_stream_collide(const StepParams &p, cudaStream_t st);
+// k_solids.cu
+cudaError_t launch_forces(const StepParams &p, cudaStream_t st);
+cudaError_t launch_remask(const StepParams &p, cudaStream_t st);
+cudaError_t launch_tick(const StepParams &p, cudaStream_t st);
+cudaError_t launch_init_populations(const StepParams &p, cudaStream_t st);
+cudaError_t launch_flags_all(const StepParams &p, cudaStream_t st);
+cudaError_t launch_stamp_solid(const StepParams &p, int id, cudaStream_t st);
+cudaError_t launch_export_populations(const StepParams &p, double *out, cudaStream_t st);
+cudaError_t launch_import_populations(const StepParams &p, const double *in, cudaStream_t st);
+cudaError_t launch_export_owner(const StepParams &p, int32_t *out, cudaStream_t st);
+cudaError_t launch_fields(const StepParams &p, double *rho, double *ux, double *uy,
+                          cudaStream_t st);
+cudaError_t launch_link_masks(const StepParams &p, uint8_t *mask, cudaStream_t st);
+// number of kernels launch_remask enqueues
+constexpr int REMASK_LAUNCHES = 5;
+
+}  // namespace gbm

@@ -1,0 +1,386 @@
+"""Python binding of the C ABI in include/lbm.h (argument marshalling only).
+
+Every function of the C library is exposed under its own name
+(``lbm_create``, ``lbm_step`` ...), plus a small ``Lattice`` convenience class
+that owns a context.  Device memory for results may be PyTorch CUDA tensors
+(pass ``on_device=True`` and a tensor); the library's own stream can be
+replaced by a PyTorch stream through ``stream=``.  No step of the method runs
+in Python: if the CUDA library cannot be loaded, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+import numpy as np
+
+from . import build as _build
+
+LBM_OK, LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA, LBM_EUNSTABLE, LBM_ETIMEOUT, LBM_ESTATE = range(7)
+LBM_PERIODIC, LBM_WALL, LBM_OPEN = 0, 1, 2
+LBM_FP64, LBM_FP32_DEV, LBM_FP16_DEV = 0, 1, 2
+LBM_RHOW_CONST, LBM_RHOW_LOCAL = 0, 1
+LBM_REFILL_A1, LBM_REFILL_A2, LBM_REFILL_A3 = 1, 2, 3
+LBM_PRESCRIBED, LBM_FREE = 0, 1
+LBM_CME, LBM_GME = 0, 1
+
+PRECISION_NAMES = {"fp64": LBM_FP64, "fp32": LBM_FP32_DEV, "fp16": LBM_FP16_DEV}
+
+
+class LBMError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"lbm status {status}: {msg}")
+        self.status = status
+
+
+class lbm_config(ctypes.Structure):
+    _fields_ = [
+        ("nx", ctypes.c_int32), ("ny", ctypes.c_int32),
+        ("bc_x", ctypes.c_int32), ("bc_y", ctypes.c_int32),
+        ("tau", ctypes.c_double), ("rho0", ctypes.c_double),
+        ("u0", ctypes.c_double * 2), ("wall_ux", ctypes.c_double * 2),
+        ("body_force", ctypes.c_double * 2), ("inflow_umax", ctypes.c_double),
+        ("gravity", ctypes.c_double * 2), ("lub_range", ctypes.c_double),
+        ("precision", ctypes.c_int32), ("rho_w_mode", ctypes.c_int32),
+        ("refill", ctypes.c_int32), ("force_ring", ctypes.c_int32),
+        ("device", ctypes.c_int32), ("reserved", ctypes.c_int32),
+        ("stream", ctypes.c_void_p),
+    ]
+
+
+class lbm_disk(ctypes.Structure):
+    _fields_ = [
+        ("cx", ctypes.c_double), ("cy", ctypes.c_double), ("r", ctypes.c_double),
+        ("vx", ctypes.c_double), ("vy", ctypes.c_double), ("omega", ctypes.c_double),
+        ("rho_s", ctypes.c_double), ("motion", ctypes.c_int32), ("reserved", ctypes.c_int32),
+    ]
+
+
+_lib = None
+_P = ctypes.c_void_p
+_D = ctypes.POINTER(ctypes.c_double)
+_I32 = ctypes.c_int32
+_I64 = ctypes.c_int64
+
+_SIGNATURES = {
+    "lbm_config_default": (None, [ctypes.POINTER(lbm_config)]),
+    "lbm_create": (_I32, [ctypes.POINTER(lbm_config), ctypes.POINTER(_P)]),
+    "lbm_destroy": (_I32, [_P]),
+    "lbm_add_solid": (_I32, [_P, ctypes.POINTER(lbm_disk), ctypes.POINTER(_I32)]),
+    "lbm_step": (_I32, [_P, _I64]),
+    "lbm_sync": (_I32, [_P]),
+    "lbm_forces": (_I32, [_P, _I32, _I64, _I64, _P, _I32]),
+    "lbm_fields": (_I32, [_P, _P, _P, _P, _I32]),
+    "lbm_get_populations": (_I32, [_P, _P, _I32]),
+    "lbm_set_populations": (_I32, [_P, _P, _I32]),
+    "lbm_get_owner": (_I32, [_P, _P, _I32]),
+    "lbm_get_solids": (_I32, [_P, _D]),
+    "lbm_set_solid": (_I32, [_P, _I32, _D]),
+    "lbm_links": (_I32, [_P, _I64, _P, ctypes.POINTER(_I64)]),
+    "lbm_time": (_I64, [_P]),
+    "lbm_nsolid": (_I32, [_P]),
+    "lbm_last_error": (ctypes.c_char_p, [_P]),
+    "lbm_status_string": (ctypes.c_char_p, [_I32]),
+    "lbm_set_graph": (_I32, [_P, _I32]),
+    "lbm_set_timing": (_I32, [_P, _I32]),
+    "lbm_get_timing": (_I32, [_P, _D, ctypes.POINTER(_I64)]),
+    "lbm_launch_count": (_I64, [_P]),
+}
+
+
+def header_symbols() -> list[str]:
+    """Names of the functions declared in include/lbm.h."""
+    with open(os.path.join(_build.INCLUDE, "lbm.h")) as fh:
+        text = fh.read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return re.findall(r"\b(lbm_[a-z_0-9]+)\s*\(", text)
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load liblbm_gb300.so (building it first if needed); raises if absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if build_if_missing:
+        path = _build.build()
+    if not os.path.exists(path):
+        raise RuntimeError(f"CUDA library {path} is missing; run the build first")
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in _SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(st: int, ctx=None):
+    if st != LBM_OK:
+        lib = load()
+        msg = lib.lbm_last_error(ctx).decode() if lib.lbm_last_error(ctx) else ""
+        raise LBMError(st, msg or lib.lbm_status_string(st).decode())
+
+
+def _ptr(a) -> int:
+    """Address of a numpy array or a torch tensor (contiguous)."""
+    if isinstance(a, np.ndarray):
+        assert a.flags.c_contiguous
+        return a.ctypes.data
+    assert a.is_contiguous()
+    return a.data_ptr()
+
+
+# ------------------------------------------------ same-name thin wrappers
+
+def lbm_config_default() -> lbm_config:
+    c = lbm_config()
+    load().lbm_config_default(ctypes.byref(c))
+    return c
+
+
+def lbm_create(cfg: lbm_config):
+    h = _P()
+    _check(load().lbm_create(ctypes.byref(cfg), ctypes.byref(h)))
+    return h
+
+
+def lbm_destroy(ctx):
+    _check(load().lbm_destroy(ctx))
+
+
+def lbm_add_solid(ctx, disk: lbm_disk) -> int:
+    out = _I32()
+    _check(load().lbm_add_solid(ctx, ctypes.byref(disk), ctypes.byref(out)), ctx)
+    return int(out.value)
+
+
+def lbm_step(ctx, n: int):
+    _check(load().lbm_step(ctx, int(n)), ctx)
+
+
+def lbm_sync(ctx):
+    _check(load().lbm_sync(ctx), ctx)
+
+
+def lbm_forces(ctx, form: int, first: int, count: int, out, on_device: bool = False):
+    _check(load().lbm_forces(ctx, int(form), int(first), int(count), _ptr(out), int(on_device)), ctx)
+
+
+def lbm_fields(ctx, rho, ux, uy, on_device: bool = False):
+    _check(load().lbm_fields(ctx, _ptr(rho), _ptr(ux), _ptr(uy), int(on_device)), ctx)
+
+
+def lbm_get_populations(ctx, f, on_device: bool = False):
+    _check(load().lbm_get_populations(ctx, _ptr(f), int(on_device)), ctx)
+
+
+def lbm_set_populations(ctx, f, on_device: bool = False):
+    _check(load().lbm_set_populations(ctx, _ptr(f), int(on_device)), ctx)
+
+
+def lbm_get_owner(ctx, owner, on_device: bool = False):
+    _check(load().lbm_get_owner(ctx, _ptr(owner), int(on_device)), ctx)
+
+
+def lbm_get_solids(ctx, out: np.ndarray):
+    _check(load().lbm_get_solids(ctx, out.ctypes.data_as(_D)), ctx)
+
+
+def lbm_set_solid(ctx, sid: int, state):
+    st = np.ascontiguousarray(state, dtype=np.float64)
+    _check(load().lbm_set_solid(ctx, int(sid), st.ctypes.data_as(_D)), ctx)
+
+
+def lbm_links(ctx, cap: int, out) -> int:
+    n = _I64()
+    _check(load().lbm_links(ctx, int(cap), _ptr(out) if cap else None, ctypes.byref(n)), ctx)
+    return int(n.value)
+
+
+def lbm_time(ctx) -> int:
+    return int(load().lbm_time(ctx))
+
+
+def lbm_nsolid(ctx) -> int:
+    return int(load().lbm_nsolid(ctx))
+
+
+def lbm_last_error(ctx=None) -> str:
+    r = load().lbm_last_error(ctx)
+    return r.decode() if r else ""
+
+
+def lbm_status_string(st: int) -> str:
+    return load().lbm_status_string(int(st)).decode()
+
+
+def lbm_set_graph(ctx, steps: int):
+    _check(load().lbm_set_graph(ctx, int(steps)), ctx)
+
+
+def lbm_set_timing(ctx, enable: bool):
+    _check(load().lbm_set_timing(ctx, int(bool(enable))), ctx)
+
+
+def lbm_get_timing(ctx):
+    ms = ctypes.c_double()
+    n = _I64()
+    _check(load().lbm_get_timing(ctx, ctypes.byref(ms), ctypes.byref(n)), ctx)
+    return float(ms.value), int(n.value)
+
+
+def lbm_launch_count(ctx) -> int:
+    return int(load().lbm_launch_count(ctx))
+
+
+# ----------------------------------------------------------- convenience
+
+def make_config(nx, ny, tau, *, rho0=1.0, u0=(0.0, 0.0), bc_x=LBM_PERIODIC, bc_y=LBM_PERIODIC,
+                wall_ux=(0.0, 0.0), body_force=(0.0, 0.0), inflow_umax=0.0, gravity=(0.0, 0.0),
+                lub_range=0.0, precision=LBM_FP64, rho_w_mode=LBM_RHOW_CONST,
+                refill=LBM_REFILL_A1, force_ring=256, device=0, stream=None) -> lbm_config:
+    c = lbm_config_default()
+    c.nx, c.ny, c.bc_x, c.bc_y = int(nx), int(ny), int(bc_x), int(bc_y)
+    c.tau, c.rho0 = float(tau), float(rho0)
+    c.u0[0], c.u0[1] = map(float, u0)
+    c.wall_ux[0], c.wall_ux[1] = map(float, wall_ux)
+    c.body_force[0], c.body_force[1] = map(float, body_force)
+    c.inflow_umax = float(inflow_umax)
+    c.gravity[0], c.gravity[1] = map(float, gravity)
+    c.lub_range = float(lub_range)
+    c.precision = PRECISION_NAMES.get(precision, precision) if isinstance(precision, str) else int(precision)
+    c.rho_w_mode, c.refill, c.force_ring = int(rho_w_mode), int(refill), int(force_ring)
+    c.device = int(device)
+    c.stream = stream
+    return c
+
+
+class Lattice:
+    """Owns one lbm_ctx.  Results come back as numpy arrays (host) unless a
+    torch tensor is passed to the *_into methods."""
+
+    def __init__(self, nx, ny, tau, **kw):
+        self.cfg = make_config(nx, ny, tau, **kw)
+        self.nx, self.ny = int(nx), int(ny)
+        self._h = lbm_create(self.cfg)
+
+    @classmethod
+    def from_workload(cls, w: dict, *, precision=LBM_FP64, add_solids=True, **kw):
+        """Build from a workload description (see the workloads package)."""
+        opts = dict(rho0=w.get("rho0", 1.0), u0=w.get("u0", (0.0, 0.0)), bc_x=w["bc_x"],
+                    bc_y=w["bc_y"], wall_ux=w.get("wall_ux", (0.0, 0.0)),
+                    body_force=w.get("body_force", (0.0, 0.0)),
+                    inflow_umax=w.get("inflow_umax", 0.0), gravity=w.get("gravity", (0.0, 0.0)),
+                    lub_range=w.get("lub_range", 0.0), rho_w_mode=w.get("rho_w_mode", 0),
+                    refill=w.get("refill", 1), precision=precision)
+        opts.update(kw)
+        lat = cls(w["nx"], w["ny"], w["tau"], **opts)
+        if add_solids:
+            for s in w["solids"]:
+                lat.add_disk(**s)
+        return lat
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lbm_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def handle(self):
+        return self._h
+
+    @property
+    def t(self) -> int:
+        return lbm_time(self._h)
+
+    @property
+    def nsolid(self) -> int:
+        return lbm_nsolid(self._h)
+
+    def add_disk(self, cx, cy, r, vx=0.0, vy=0.0, omega=0.0, rho_s=1.0, motion=LBM_PRESCRIBED):
+        d = lbm_disk(cx=cx, cy=cy, r=r, vx=vx, vy=vy, omega=omega, rho_s=rho_s, motion=motion)
+        return lbm_add_solid(self._h, d)
+
+    def step(self, n: int = 1):
+        lbm_step(self._h, n)
+
+    def sync(self):
+        lbm_sync(self._h)
+
+    def forces(self, first: int, count: int) -> np.ndarray:
+        """[count][nsolid][2 (Eq. 4, Eq. 5)][Fx, Fy, T] for steps first.. (host)."""
+        ns = self.nsolid
+        out = np.zeros((2, max(count, 0), ns, 3))
+        for form in (LBM_CME, LBM_GME):
+            buf = np.zeros((max(count, 0), ns, 3))
+            if count and ns:
+                lbm_forces(self._h, form, first, count, buf)
+            out[form] = buf
+        return np.ascontiguousarray(out.transpose(1, 2, 0, 3))
+
+    def step_record(self, n: int) -> np.ndarray:
+        t0 = self.t
+        self.step(n)
+        return self.forces(t0, n)
+
+    def fields(self):
+        rho = np.empty((self.ny, self.nx))
+        ux = np.empty_like(rho)
+        uy = np.empty_like(rho)
+        lbm_fields(self._h, rho, ux, uy)
+        return rho, ux, uy
+
+    def get_f(self) -> np.ndarray:
+        out = np.empty((9, self.ny, self.nx))
+        lbm_get_populations(self._h, out)
+        return out
+
+    def set_f(self, f: np.ndarray):
+        f = np.ascontiguousarray(f, dtype=np.float64)
+        assert f.shape == (9, self.ny, self.nx)
+        lbm_set_populations(self._h, f)
+
+    def owner(self) -> np.ndarray:
+        out = np.empty((self.ny, self.nx), dtype=np.int32)
+        lbm_get_owner(self._h, out)
+        return out
+
+    def solids(self) -> np.ndarray:
+        out = np.zeros((max(self.nsolid, 1), 5))
+        lbm_get_solids(self._h, out)
+        return out[: self.nsolid]
+
+    def set_solid_velocity(self, sid: int, vx: float, vy: float, omega: float):
+        st = self.solids()[sid].copy()
+        st[2:] = (vx, vy, omega)
+        lbm_set_solid(self._h, sid, st)
+
+    def links(self) -> np.ndarray:
+        n = lbm_links(self._h, 0, None)
+        out = np.zeros((max(n, 1), 4), dtype=np.int32)
+        lbm_links(self._h, n, out)
+        return out[:n]
+
+    def set_graph(self, steps: int):
+        lbm_set_graph(self._h, steps)
+
+    def set_timing(self, enable: bool):
+        lbm_set_timing(self._h, enable)
+
+    def timing(self):
+        return lbm_get_timing(self._h)
+
+    def launch_count(self) -> int:
+        return lbm_launch_count(self._h)
