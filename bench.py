@@ -1,0 +1,404 @@
+#!/usr/bin/env python
+"""Throughput of the full moving-solid D2Q9 step on one GB300.
+
+Workload (default): the precision-study domain, 8192 x 4096 fully periodic
+nodes, 2000 non-overlapping disks (radii uniform in 8..20, constant
+prescribed velocities with components uniform in +-0.05, seeded), tau drawn
+once in [0.55, 1.0].  One step = forces on every disk (conventional and
+Galilean-invariant momentum exchange, FP64 reduction) + fused
+advection/bounce-back/BGK collision + disk motion + re-rasterisation with
+covered/fresh node handling.
+
+Prints one JSON line.  ``value`` is MLUPS (lattice nodes updated per second,
+all nodes of the domain, summed over ranks) with every input resident in HBM;
+``e2e`` repeats the measurement through the C ABI with host buffers (initial
+populations uploaded from pinned host memory inside the timed region, force
+records read back to the host every 50 steps).  ``roofline`` relates the
+fused advection-collision kernel's algorithmic bytes to the measured HBM copy
+bandwidth.  ``--impl reference`` times the FP64 CPU oracle instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "MLUPS for stream+collide+GIMEM vs HBM roofline; time-to-drag at 1e-4 rel err"
+STORAGE_BYTES = {"fp64": 8, "fp32": 4, "fp16": 2}
+DTYPE = {"fp64": "f64", "fp32": "f32", "fp16": "f32"}
+FALLBACK_HBM_GBS = 6800.0
+CPU_CROP = (1024, 512)
+
+
+def parse():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=400)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--precision", choices=["fp32", "fp16", "fp64"], default="fp32")
+    ap.add_argument("--nx", type=int, default=8192)
+    ap.add_argument("--ny", type=int, default=4096)
+    ap.add_argument("--ndisk", type=int, default=2000)
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the e2e pass, the other precisions and the CPU baseline")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    return ap.parse_args()
+
+
+def workload(a):
+    import workloads as W
+    return W.precision_study(nx=a.nx, ny=a.ny, ndisk=a.ndisk)
+
+
+def workload_name(a):
+    return (f"precision-study domain {a.nx}x{a.ny} periodic, {a.ndisk} moving disks r 8-20, "
+            f"|v| components <= 0.05")
+
+
+# ------------------------------------------------------------ distributed
+
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, ws):
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ----------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while running."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, ValueError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx = float(parts[1])
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ----------------------------------------------------------------- helpers
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            return json.load(fh), "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": FALLBACK_HBM_GBS}, "fallback"
+
+
+def kernel_source_hash():
+    path = os.path.join(ROOT, "paper_1303_0625_gb300", "csrc", "k_stream_collide.cu")
+    with open(path, "rb") as fh:
+        return hashlib.sha256(fh.read()).hexdigest()[:16]
+
+
+def captured_traffic(precision, nx, ny):
+    """DRAM bytes per launch of the advection-collision kernel from the
+    committed ncu summary, if it was taken on the current kernel source."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as fh:
+            rec = json.load(fh).get(precision)
+    except (OSError, ValueError):
+        return None
+    if not rec or rec.get("kernel_sha256_16") != kernel_source_hash():
+        return None
+    # captured on a smaller domain: traffic scales with the node count
+    return rec["dram_bytes_per_launch"] * (nx * ny) / (rec["nx"] * rec["ny"])
+
+
+def algorithmic_bytes(precision, cells):
+    """Per launch of the advection-collision kernel: every node reads and
+    writes its nine populations once and reads its 2-byte flags word."""
+    return cells * (18 * STORAGE_BYTES[precision] + 2)
+
+
+# ------------------------------------------------------------ our path
+
+def run_ours(a, ws, rank, local):
+    import numpy as np
+    import torch
+
+    import paper_1303_0625_gb300 as G
+
+    torch.cuda.set_device(local)
+    stream = torch.cuda.Stream()
+    w = workload(a)
+    cells = w["nx"] * w["ny"]
+    peaks, peak_kind = measured_peaks()
+
+    def measure(precision, steps, warmup, sample_clocks):
+        lat = G.Lattice.from_workload(w, precision=G.PRECISION_NAMES[precision], device=local,
+                                      stream=stream.cuda_stream, force_ring=512)
+        variant = lat.autotune(4)  # picks the node width of the advection-collision kernel
+        lat.step(warmup)
+        lat.sync()
+        lat.set_timing(True)
+        launches0 = lat.launch_count()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        clocks = ClockSampler(local)
+        barrier(ws)
+        torch.cuda.synchronize()
+        if sample_clocks:
+            clocks.__enter__()
+            time.sleep(0.3)
+        e0.record(stream)
+        lat.step(steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if sample_clocks:
+            clocks.__exit__(None, None, None)
+        lat.sync()  # raises on an unstable run
+        ms = e0.elapsed_time(e1)
+        k1_ms, k1_n = lat.timing()
+        launches = lat.launch_count() - launches0
+        nfluid = int((lat.owner() < 0).sum())
+        lat.close()
+        return dict(ms=ms, k1_avg_ms=k1_ms / max(k1_n, 1), launches=launches, nfluid=nfluid,
+                    clocks=clocks.summary() if sample_clocks else None, variant=variant)
+
+    main = measure(a.precision, a.steps, a.warmup, rank == 0)
+    t_max = max_over_ranks(main["ms"], ws)
+    value = cells * a.steps * ws / (t_max / 1e3) / 1e6
+    bytes_launch = algorithmic_bytes(a.precision, cells)
+    achieved = bytes_launch / (main["k1_avg_ms"] / 1e3) / 1e9
+    peak = float(peaks.get("hbm_gbs", FALLBACK_HBM_GBS))
+    traffic = captured_traffic(a.precision, a.nx, a.ny)
+    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "traffic": traffic,
+                "kernel": "k_stream_collide", "peak_source": f"{peak_kind} hbm_gbs",
+                "algorithmic_bytes_per_launch": bytes_launch,
+                "bytes_per_node": 18 * STORAGE_BYTES[a.precision] + 2,
+                "avg_launch_ms": round(main["k1_avg_ms"], 5),
+                "kernel_variant": main["variant"],
+                "share_of_step": round(main["k1_avg_ms"] / (main["ms"] / a.steps), 4)}
+    line = {"metric": METRIC, "value": round(value, 1), "unit": "MLUPS", "n_gpus": ws,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": round(t_max / a.steps, 5),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": DTYPE[a.precision], "data": "synthetic",
+            "config": {"workload": workload_name(a), "nx": a.nx, "ny": a.ny, "disks": a.ndisk,
+                       "tau": round(w["tau"], 6), "precision": a.precision,
+                       "storage": {"fp64": "f64", "fp32": "f32 (f - w_i)",
+                                   "fp16": "f16 (f - w_i)"}[a.precision],
+                       "force_reduction": "f64, both forms every step",
+                       "l2": "inputs larger than L2 (populations "
+                             f"{2 * 9 * cells * STORAGE_BYTES[a.precision] / 1e9:.2f} GB)",
+                       "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
+                       "fluid_nodes": main["nfluid"]},
+            "roofline": roofline, "gpu_launches": main["launches"], "clocks": main["clocks"]}
+    if not a.no_extras and rank == 0:
+        line["e2e"] = run_e2e(a, w, local, stream)
+        modes = {}
+        for prec in ("fp16", "fp64", "fp32"):
+            if prec == a.precision:
+                continue
+            k = max(20, a.steps // 4) if prec != "fp64" else max(10, a.steps // 20)
+            m = measure(prec, k, 3, False)
+            b = algorithmic_bytes(prec, cells)
+            modes[prec] = {"mlups": round(cells * k / (m["ms"] / 1e3) / 1e6, 1), "steps": k,
+                           "kernel_gbs": round(b / (m["k1_avg_ms"] / 1e3) / 1e9, 1),
+                           "kernel_frac_of_hbm": round(b / (m["k1_avg_ms"] / 1e3) / 1e9 / peak, 4),
+                           "ms_per_step": round(m["ms"] / k, 5)}
+        line["modes"] = modes
+        line["cpu_baseline"] = run_cpu_baseline(a, w, a.cpu_seconds)
+    elif rank == 0:
+        line["e2e"] = None
+        line["cpu_baseline"] = None
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def run_e2e(a, w, local, stream):
+    """Same metric through the C ABI with host buffers: initial populations
+    from pinned host memory, force records read back every 50 steps."""
+    import numpy as np
+    import torch
+
+    import paper_1303_0625_gb300 as G
+    from paper_1303_0625_gb300 import lbm as L
+
+    nx, ny = w["nx"], w["ny"]
+    lat = G.Lattice.from_workload(w, precision=G.PRECISION_NAMES[a.precision], device=local,
+                                  stream=stream.cuda_stream, force_ring=512)
+    f0 = torch.empty((9, ny, nx), dtype=torch.float64, pin_memory=True)
+    lat.step(1)
+    L.lbm_get_populations(lat.handle, f0.numpy())  # a valid state to upload
+    ns = lat.nsolid
+    block = 50
+    out = torch.empty((2, block, ns, 3), dtype=torch.float64, pin_memory=True)
+    steps = a.steps
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    L.lbm_set_populations(lat.handle, f0.numpy())
+    t_start = lat.t
+    done = 0
+    while done < steps:
+        n = min(block, steps - done)
+        lat.step(n)
+        for form in (L.LBM_CME, L.LBM_GME):
+            L.lbm_forces(lat.handle, form, t_start + done, n, out[form].numpy())
+        done += n
+    lat.sync()
+    dt = time.perf_counter() - t0
+    lat.close()
+    h2d = 9 * nx * ny * 8
+    d2h = 2 * steps * ns * 3 * 8
+    return {"value": round(nx * ny * steps / dt / 1e6, 1), "unit": "MLUPS",
+            "h2d_bytes_per_step": int(h2d / steps), "d2h_bytes_per_step": int(d2h / steps),
+            "seconds": round(dt, 4),
+            "what": "C ABI with host buffers: FP64 initial populations uploaded from pinned host "
+                    "memory, both force forms copied to the host every 50 steps"}
+
+
+# ------------------------------------------------------------ CPU oracle
+
+def crop_workload(w):
+    import workloads as W
+    return W.crop_disks(w, *CPU_CROP)
+
+
+def run_cpu_baseline(a, w, seconds):
+    import oracle as O
+    c = crop_workload(w)
+    o = O.Oracle(c["nx"], c["ny"], c["tau"])
+    for s in c["solids"]:
+        o.add_disk(s["cx"], s["cy"], s["r"], s["vx"], s["vy"], s["omega"], s["rho_s"], s["motion"])
+    o.step(1)
+    n = 0
+    t0 = time.perf_counter()
+    while time.perf_counter() - t0 < seconds:
+        o.step(1)
+        n += 1
+    dt = time.perf_counter() - t0
+    return {"value": round(c["nx"] * c["ny"] * n / dt / 1e6, 3), "unit": "MLUPS", "cores": 1,
+            "kind": "oracle",
+            "sample": f"{n} steps of the {c['nx']}x{c['ny']} corner crop of the workload "
+                      f"({len(c['solids'])} disks lying wholly inside), FP64 oracle, one thread"}
+
+
+def run_reference(a, ws, rank):
+    if rank != 0:
+        return
+    w = workload(a)
+    c = crop_workload(w)
+    import oracle as O
+    o = O.Oracle(c["nx"], c["ny"], c["tau"])
+    for s in c["solids"]:
+        o.add_disk(s["cx"], s["cy"], s["r"], s["vx"], s["vy"], s["omega"], s["rho_s"], s["motion"])
+    o.step(a.warmup)
+    t0 = time.perf_counter()
+    o.step(a.steps)
+    dt = time.perf_counter() - t0
+    value = c["nx"] * c["ny"] * a.steps / dt / 1e6
+    sample = (f"each step: one FP64 oracle step of the {c['nx']}x{c['ny']} corner crop of the "
+              f"workload ({len(c['solids'])} disks lying wholly inside), one thread")
+    line = {"impl": "reference", "metric": METRIC, "value": round(value, 3), "unit": "MLUPS",
+            "n_gpus": ws, "steps": a.steps, "warmup": a.warmup,
+            "ms_per_step": round(dt / a.steps * 1e3, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": workload_name(a), "precision": "fp64 oracle",
+                       "crop": list(CPU_CROP)},
+            "cpu_baseline": {"value": round(value, 3), "unit": "MLUPS", "cores": 1,
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": round(value, 3), "unit": "MLUPS", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    a = parse()
+    ws, rank, local = dist_setup()
+    if a.impl == "reference":
+        run_reference(a, ws, rank)
+    else:
+        run_ours(a, ws, rank, local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -187,6 +187,19 @@ lbm_status lbm_get_timing(lbm_ctx *ctx, double *stream_collide_ms, int64_t *laun
 /* Kernel launches issued by the library since creation (all kernels). */
 int64_t lbm_launch_count(const lbm_ctx *ctx);
 
+/* Nodes per thread of the advection-collision kernel, as the width of one
+ * population word: 0 = 16 bytes (default), 1 = 8 bytes, 2 = 4 bytes.  Results
+ * are identical for every variant; only the speed differs.  LBM_EINVAL for
+ * other values. */
+lbm_status lbm_set_kernel_variant(lbm_ctx *ctx, int32_t variant);
+int32_t lbm_kernel_variant(const lbm_ctx *ctx);
+
+/* Autotuner: run 1 + steps real steps with each variant of the
+ * advection-collision kernel, timed with CUDA events, and keep the fastest
+ * (stored in *best when not NULL).  The simulation advances by 3 (1 + steps)
+ * steps; results do not depend on the variant.  Waits for the stream. */
+lbm_status lbm_autotune(lbm_ctx *ctx, int32_t steps, int32_t *best);
+
 #ifdef __cplusplus
 }
 #endif

@@ -106,6 +106,7 @@ typedef struct {
     int32_t *owner_prev;
     uint8_t *fresh;
     double *pending;  /* [nsolid][3] momentum booked for the next force record */
+    int raster_dirty; /* solids added since the owner map was last built */
 } ora_sim;
 
 /* ------------------------------------------------------------------ basics */
@@ -291,9 +292,18 @@ int ora_add_disk(ora_sim *S, double cx, double cy, double r, double vx, double v
     b->rho_s = rho_s;
     b->motion = motion;
     S->pending[3 * id] = S->pending[3 * id + 1] = S->pending[3 * id + 2] = 0.0;
+    S->raster_dirty = 1; /* rasterised before the owner map is next used */
+    return id;
+}
+
+/* Owner map of the current solids (added solids cover their nodes without
+ * booking any momentum). */
+static void ensure_raster(ora_sim *S)
+{
+    if (!S->raster_dirty) return;
     rasterise(S, S->owner);
     memcpy(S->owner_prev, S->owner, cells(S) * sizeof(int32_t));
-    return id;
+    S->raster_dirty = 0;
 }
 
 /* ------------------------------------------------------- 1. forces at t */
@@ -622,6 +632,7 @@ static void remask(ora_sim *S)
 void ora_step(ora_sim *S, int64_t n, double *rec)
 {
     double *r = (double *)malloc(((size_t)S->nsolid * 6 + 1) * sizeof(double));
+    ensure_raster(S);
     for (int64_t k = 0; k < n; k++) {
         record_forces(S, r);
         if (rec) memcpy(rec + (size_t)k * S->nsolid * 6, r, (size_t)S->nsolid * 6 * sizeof(double));
@@ -641,13 +652,18 @@ int ora_nsolid(const ora_sim *S) { return S->nsolid; }
 
 void ora_get_f(const ora_sim *S, double *out) { memcpy(out, S->f, 9 * cells(S) * sizeof(double)); }
 void ora_set_f(ora_sim *S, const double *in) { memcpy(S->f, in, 9 * cells(S) * sizeof(double)); }
-void ora_get_owner(const ora_sim *S, int32_t *out) { memcpy(out, S->owner, cells(S) * sizeof(int32_t)); }
+void ora_get_owner(ora_sim *S, int32_t *out)
+{
+    ensure_raster(S);
+    memcpy(out, S->owner, cells(S) * sizeof(int32_t));
+}
 
 /* density and velocity of the post-collision state; solid nodes get NaN.
  * With a body force the velocity is (sum e f~ - F/2) / rho. */
-void ora_fields(const ora_sim *S, double *rho, double *ux, double *uy)
+void ora_fields(ora_sim *S, double *rho, double *ux, double *uy)
 {
     const size_t N = cells(S);
+    ensure_raster(S);
     for (size_t k = 0; k < N; k++) {
         if (S->owner[k] >= 0) {
             rho[k] = ux[k] = uy[k] = NAN;
@@ -692,9 +708,10 @@ void ora_set_solid_state(ora_sim *S, int s, const double *in)
 
 /* Enumerate the fluid-solid links in raster order of the fluid node and
  * ascending direction.  Writes up to cap entries of (x_f, y_f, i, solid). */
-int64_t ora_links(const ora_sim *S, int64_t cap, int32_t *out)
+int64_t ora_links(ora_sim *S, int64_t cap, int32_t *out)
 {
     int64_t n = 0;
+    ensure_raster(S);
     for (int y = 0; y < S->c.ny; y++)
         for (int x = 0; x < S->c.nx; x++) {
             if (S->owner[at(S, x, y)] >= 0) continue;
@@ -719,6 +736,7 @@ int64_t ora_links(const ora_sim *S, int64_t cap, int32_t *out)
  * uncovered by solid s, given the current populations and owner map. */
 void ora_refill_probe(ora_sim *S, int x, int y, int s, double *out)
 {
+    ensure_raster(S);
     memset(S->fresh, 0, cells(S));
     S->fresh[at(S, x, y)] = 1;
     refill_node(S, x, y, s, out);

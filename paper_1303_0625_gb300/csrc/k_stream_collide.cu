@@ -1,11 +1,18 @@
 // Fused pull-advection + half-way bounce-back + BGK collision (Eq. 1-3, Eq. 8).
 //
-// One thread per node, x fastest, so every population plane is read and
-// written with consecutive addresses across a warp.  The nine pulls are issued
-// unconditionally (a bounced direction loads a neighbour that is later
-// discarded, which costs no extra DRAM traffic because that row is streamed
-// anyway); nodes next to a solid or a wall then take the rare path that
-// replaces the bounced populations by f~_opp(x) + 6 w_i rho_w (e_i . v).
+// Layout: SoA planes f_i[ny][pitch], x fastest, pitch a multiple of 64.
+// Every thread owns V consecutive nodes of one row, V chosen so that one
+// population of those nodes is 16 bytes (FP64: 2, FP32: 4, FP16: 8).  Each of
+// the nine pulls is one aligned 128-bit load from the source row (y - c_y);
+// the x-shifted pulls (c_x = +-1) take the missing neighbour element from the
+// adjacent lane with a warp shuffle (lanes 0 and 31 load it directly, wrapped
+// at the row ends), so DRAM sees each population plane read once, fully
+// coalesced.  Results go out as nine 128-bit stores (nodes in the row padding
+// store zeros).  Only the open inlet/outlet columns use a per-node path.
+//
+// Bounce-back: a node whose flags word has bit i set (x - e_i solid or
+// outside) replaces population i by f~_opp(x) + 6 w_i rho_w (e_i . v), v the
+// velocity of the wall or solid at x - e_i / 2.  Solid nodes store zeros.
 //
 // Storage: FP64 stores f_i; the deviation modes store f_i - w_i (FP32 or
 // FP16) and compute in FP32 entirely in deviation form, so that the small
@@ -18,68 +25,106 @@ namespace gbm {
 
 namespace {
 
-// Velocity of the wall or solid the population arriving at (x, y) along e_i
-// was bounced from (its source x - e_i is solid or outside the domain).
-__device__ __forceinline__ void source_velocity(const StepParams &p, int x, int y, int i,
-                                                double &vx, double &vy) {
+template <int P> struct Raw;
+template <> struct Raw<LBM_FP64> { using R = double; };
+template <> struct Raw<LBM_FP32_DEV> { using R = float; };
+template <> struct Raw<LBM_FP16_DEV> { using R = unsigned short; };
+
+template <int BYTES> struct Word;
+template <> struct Word<2> { using T = uint16_t; };
+template <> struct Word<4> { using T = uint32_t; };
+template <> struct Word<8> { using T = uint2; };
+template <> struct Word<16> { using T = uint4; };
+
+// V consecutive values of one population plane, loaded as one word
+template <class R, int V> union Pack {
+    typename Word<sizeof(R) * V>::T u;
+    R r[V];
+};
+template <int V> union FlagPack {
+    typename Word<2 * V>::T u;
+    uint16_t f[V];
+};
+
+__device__ __forceinline__ double cvt(double v) { return v; }
+__device__ __forceinline__ float cvt(float v) { return v; }
+__device__ __forceinline__ float cvt(unsigned short v) { return __half2float(__ushort_as_half(v)); }
+__device__ __forceinline__ void put(double &d, double v) { d = v; }
+__device__ __forceinline__ void put(float &d, float v) { d = v; }
+__device__ __forceinline__ void put(unsigned short &d, float v) {
+    d = __half_as_ushort(__float2half_rn(v));
+}
+
+__device__ __forceinline__ double shfl_up1(double v) { return __shfl_up_sync(0xffffffffu, v, 1); }
+__device__ __forceinline__ float shfl_up1(float v) { return __shfl_up_sync(0xffffffffu, v, 1); }
+__device__ __forceinline__ unsigned short shfl_up1(unsigned short v) {
+    return (unsigned short)__shfl_up_sync(0xffffffffu, (int)v, 1);
+}
+__device__ __forceinline__ double shfl_dn1(double v) { return __shfl_down_sync(0xffffffffu, v, 1); }
+__device__ __forceinline__ float shfl_dn1(float v) { return __shfl_down_sync(0xffffffffu, v, 1); }
+__device__ __forceinline__ unsigned short shfl_dn1(unsigned short v) {
+    return (unsigned short)__shfl_down_sync(0xffffffffu, (int)v, 1);
+}
+
+// Velocity of the wall or solid that population i arriving at (x, y) was
+// bounced from (its source x - e_i is solid or outside the domain).
+template <class C>
+__device__ __forceinline__ void source_velocity(const StepParams &p, int x, int y, int i, C &vx,
+                                                C &vy) {
     const Lattice &L = p.L;
-    int sx = x - cx(i), sy = y - cy(i);
-    vx = 0.0;
-    vy = 0.0;
+    const int sx = x - cx(i), sy = y - cy(i);
+    vx = 0;
+    vy = 0;
     if (L.bc_y == LBM_WALL && (sy < 0 || sy >= L.ny)) {
-        vx = sy < 0 ? p.wall_ux0 : p.wall_ux1;  // channel walls move along x
+        vx = (C)(sy < 0 ? p.wall_ux0 : p.wall_ux1);  // channel walls move along x
         return;
     }
     int xs, ys;
     if (!locate(L, sx, sy, xs, ys)) return;  // resting wall (or open column) in x
-    uint16_t s = p.owner[cell_of(L, xs, ys)];
+    const uint16_t s = p.owner[cell_of(L, xs, ys)];
     if (s == FLUID) return;
     const DSolid &b = p.S[s];
-    double dx, dy;
-    // boundary point halfway between x and x - e_i
-    point_velocity(L, b.x, b.y, b.vx, b.vy, b.om, (double)x - 0.5 * cx(i),
-                   (double)y - 0.5 * cy(i), vx, vy, dx, dy);
+    vx = pick<C>(b.vx, b.vxf);
+    vy = pick<C>(b.vy, b.vyf);
+    if (b.omf != 0.0f) {
+        const double om = b.om;
+        // boundary point halfway between x and x - e_i, relative to R
+        const C dx = (C)near_image((double)x - 0.5 * cx(i) - b.xw, L.nx, L.bc_x == LBM_PERIODIC);
+        const C dy = (C)near_image((double)y - 0.5 * cy(i) - b.yw, L.ny, L.bc_y == LBM_PERIODIC);
+        vx -= (C)om * dy;
+        vy += (C)om * dx;
+    }
 }
 
-// Post-collision populations (storage convention) of node (x, y).
-template <int P, bool FORCE, bool LOCAL>
-__device__ __forceinline__ void update_node(const StepParams &p,
-                                            const typename Prec<P>::S *__restrict__ fin, int x,
-                                            int y, uint16_t fl, typename Prec<P>::C (&out)[9]) {
+// Replace the bounced populations of node (x, y) (rare path).
+template <int P, bool LOCAL>
+__device__ __forceinline__ void bounce(const StepParams &p, const typename Raw<P>::R *fin, int x,
+                                    int y, uint16_t fl, typename Prec<P>::C (&g)[9]) {
     using C = typename Prec<P>::C;
     const Lattice &L = p.L;
-    const long long k = cell_of(L, x, y);
-    const bool per_x = L.bc_x == LBM_PERIODIC, per_y = L.bc_y == LBM_PERIODIC;
-    C g[9];
+    const int k = y * L.pitch + x;
+    const int plane = (int)L.plane;
+    C rho_w = pick<C>(p.rho0, p.rho0_f);
+    if (LOCAL) {
+        C s = 0;
 #pragma unroll
-    for (int i = 0; i < 9; i++) {
-        int xs = x - cx(i), ys = y - cy(i);
-        // wrap along periodic axes; clamp elsewhere (the value is then bounced)
-        if (xs < 0) xs = per_x ? xs + L.nx : 0;
-        if (xs >= L.nx) xs = per_x ? xs - L.nx : L.nx - 1;
-        if (ys < 0) ys = per_y ? ys + L.ny : 0;
-        if (ys >= L.ny) ys = per_y ? ys - L.ny : L.ny - 1;
-        g[i] = ld(fin + (long long)i * L.plane + cell_of(L, xs, ys));
+        for (int j = 0; j < 9; j++) s += cvt(fin[j * plane + k]);
+        rho_w = Prec<P>::dev ? (C)1 + s : s;
     }
-    if (fl & 0x1FEu) {
-        // half-way bounce-back with the moving-wall term
-        C rho_w = (C)p.rho0;
-        if (LOCAL) {
-            C s = 0;
 #pragma unroll
-            for (int j = 0; j < 9; j++) s += ld(fin + (long long)j * L.plane + k);
-            rho_w = Prec<P>::dev ? (C)1 + s : s;
-        }
-#pragma unroll
-        for (int i = 1; i < 9; i++) {
-            if (!((fl >> i) & 1u)) continue;
-            double vx, vy;
-            source_velocity(p, x, y, i, vx, vy);
-            C back = ld(fin + (long long)opp(i) * L.plane + k);
-            C ev = (C)(cx(i) * vx + cy(i) * vy);
-            g[i] = back + (C)6 * wgt<C>(i) * rho_w * ev;
-        }
+    for (int i = 1; i < 9; i++) {
+        if (!((fl >> i) & 1u)) continue;
+        C vx, vy;
+        source_velocity<C>(p, x, y, i, vx, vy);
+        const C back = cvt(fin[opp(i) * plane + k]);
+        g[i] = back + (C)6 * wgt<C>(i) * rho_w * ((C)cx(i) * vx + (C)cy(i) * vy);
     }
+}
+
+// BGK collision (with Guo forcing when FORCE) of one node in place.
+template <int P, bool FORCE>
+__device__ __forceinline__ void collide(const StepParams &p, typename Prec<P>::C (&g)[9]) {
+    using C = typename Prec<P>::C;
     C s0 = 0, jx = 0, jy = 0;
 #pragma unroll
     for (int i = 0; i < 9; i++) {
@@ -88,14 +133,13 @@ __device__ __forceinline__ void update_node(const StepParams &p,
         jy += (C)cy(i) * g[i];
     }
     const C rho = Prec<P>::dev ? (C)1 + s0 : s0;
-    const C Fx = (C)p.body_x, Fy = (C)p.body_y;
+    const C Fx = pick<C>(p.body_x, p.body_xf), Fy = pick<C>(p.body_y, p.body_yf);
     const C inv = (C)1 / rho;
     const C ux = FORCE ? (jx + (C)0.5 * Fx) * inv : jx * inv;
     const C uy = FORCE ? (jy + (C)0.5 * Fy) * inv : jy * inv;
     const C uu = ux * ux + uy * uy;
-    const C om = (C)p.omega;
-    if (!(rho > (C)0) || !(fabs((double)ux) < 1e30) || !(fabs((double)uy) < 1e30))
-        atomicOr(p.status, 1);
+    const C om = pick<C>(p.omega, p.omega_f);
+    if (!(rho > (C)0) || !(fabs(ux) < (C)1e30) || !(fabs(uy) < (C)1e30)) atomicOr(p.status, 1);
 #pragma unroll
     for (int i = 0; i < 9; i++) {
         const C eu = (C)cx(i) * ux + (C)cy(i) * uy;
@@ -109,25 +153,28 @@ __device__ __forceinline__ void update_node(const StepParams &p,
                  ((C)3 * (((C)cx(i) - ux) * Fx + ((C)cy(i) - uy) * Fy) +
                   (C)9 * eu * ((C)cx(i) * Fx + (C)cy(i) * Fy));
         }
-        out[i] = o;
+        g[i] = o;
     }
 }
 
+// Complete update of one node, with periodic wrap, bounce-back, walls and the
+// open inlet/outlet: used for the nodes the vector path leaves out (fluid
+// nodes next to a solid or wall, the first and last column).
 template <int P, bool FORCE, bool LOCAL>
-__global__ void __launch_bounds__(SC_BLOCK_X) k_stream_collide(const StepParams p) {
-    using S = typename Prec<P>::S;
+__device__ __noinline__ void update_node(const StepParams &p, const typename Raw<P>::R *fin,
+                                         typename Raw<P>::R *fout, int x, int y) {
     using C = typename Prec<P>::C;
+    using R = typename Raw<P>::R;
     const Lattice &L = p.L;
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    const int y = blockIdx.y;
-    if (x >= L.nx) return;
-    const long long t = *p.t;
-    const S *__restrict__ fin = static_cast<const S *>((t & 1) ? p.f1 : p.f0);
-    S *__restrict__ fout = static_cast<S *>((t & 1) ? p.f0 : p.f1);
-    const long long k = cell_of(L, x, y);
+    const int plane = (int)L.plane;
+    const int k = y * L.pitch + x;
     const uint16_t fl = p.flags[k];
-    if (fl & 1u) return;  // solid node: no populations
-    C out[9];
+    C g[9];
+    if (fl & 1u) {
+#pragma unroll
+        for (int i = 0; i < 9; i++) put(fout[i * plane + k], (C)0);
+        return;
+    }
     if (L.bc_x == LBM_OPEN && x == 0) {
         // equilibrium inlet with the parabolic profile
         const double h = (double)L.ny, yy = (double)y + 0.5;
@@ -137,32 +184,185 @@ __global__ void __launch_bounds__(SC_BLOCK_X) k_stream_collide(const StepParams 
         for (int i = 0; i < 9; i++) {
             const C eu = (C)cx(i) * u;
             const C poly = (C)3 * eu + (C)4.5 * eu * eu - (C)1.5 * u * u;
-            out[i] = Prec<P>::dev ? wgt<C>(i) * ((r - (C)1) + r * poly)
-                                  : r * wgt<C>(i) * ((C)1 + poly);
+            put(fout[i * plane + k], Prec<P>::dev ? wgt<C>(i) * ((r - (C)1) + r * poly)
+                                                  : r * wgt<C>(i) * ((C)1 + poly));
         }
-    } else if (L.bc_x == LBM_OPEN && x == L.nx - 1 && !(p.flags[k - 1] & 1u)) {
-        // outlet: copy of the updated column nx - 2
-        update_node<P, FORCE, LOCAL>(p, fin, x - 1, y, p.flags[k - 1], out);
-    } else {
-        update_node<P, FORCE, LOCAL>(p, fin, x, y, fl, out);
+        return;
     }
+    int xu = x;  // node whose update is computed
+    uint16_t flu = fl;
+    if (L.bc_x == LBM_OPEN && x == L.nx - 1 && !(p.flags[k - 1] & 1u)) {
+        xu = x - 1;  // outlet: copy of the updated column nx - 2
+        flu = p.flags[k - 1];
+    }
+    const bool per_x = L.bc_x == LBM_PERIODIC, per_y = L.bc_y == LBM_PERIODIC;
 #pragma unroll
-    for (int i = 0; i < 9; i++) st(fout + (long long)i * L.plane + k, out[i]);
+    for (int i = 0; i < 9; i++) {
+        int xs = xu - cx(i), ys = y - cy(i);
+        // wrap along periodic axes; clamp elsewhere (the value is then bounced)
+        if (xs < 0) xs = per_x ? xs + L.nx : 0;
+        if (xs >= L.nx) xs = per_x ? xs - L.nx : L.nx - 1;
+        if (ys < 0) ys = per_y ? ys + L.ny : 0;
+        if (ys >= L.ny) ys = per_y ? ys - L.ny : L.ny - 1;
+        g[i] = cvt(fin[i * plane + ys * L.pitch + xs]);
+    }
+    if (flu & 0x1FEu) bounce<P, LOCAL>(p, fin, xu, y, flu, g);
+    collide<P, FORCE>(p, g);
+#pragma unroll
+    for (int i = 0; i < 9; i++) {
+        R v;
+        put(v, g[i]);
+        fout[i * plane + k] = v;
+    }
 }
 
-template <int P, bool FORCE, bool LOCAL>
+template <int P, int V, bool FORCE, bool LOCAL>
+__global__ void __launch_bounds__(SC_BLOCK_X) k_stream_collide(const StepParams p) {
+    using R = typename Raw<P>::R;
+    using C = typename Prec<P>::C;
+    const Lattice &L = p.L;
+    const int lane = threadIdx.x & 31;
+    const int x0 = (blockIdx.x * SC_BLOCK_X + threadIdx.x) * V;
+    const int y = blockIdx.y;
+    const long long t = *p.t;
+    const R *__restrict__ fin = static_cast<const R *>((t & 1) ? p.f1 : p.f0);
+    R *__restrict__ fout = static_cast<R *>((t & 1) ? p.f0 : p.f1);
+    const int plane = (int)L.plane;
+    const int xl = min(x0, L.pitch - V);  // in-bounds load position for every lane
+    int ym = y - 1, yp = y + 1;
+    if (ym < 0) ym = L.bc_y == LBM_PERIODIC ? L.ny - 1 : 0;
+    if (yp >= L.ny) yp = L.bc_y == LBM_PERIODIC ? 0 : L.ny - 1;
+    const int rm = ym * L.pitch, r0 = y * L.pitch, rp = yp * L.pitch;
+#define SROW(i) (cy(i) == 1 ? rm : (cy(i) == -1 ? rp : r0))
+
+    Pack<R, V> raw[9];
+#pragma unroll
+    for (int i = 0; i < 9; i++)
+        raw[i].u = __ldg(reinterpret_cast<const typename Word<sizeof(R) * V>::T *>(
+            fin + i * plane + SROW(i) + xl));
+    FlagPack<V> fl;
+    fl.u = *reinterpret_cast<const typename Word<2 * V>::T *>(p.flags + r0 + xl);
+    // neighbour elements of the x-shifted pulls at the warp's ends; at the
+    // row ends they are wrong, but those columns take the per-node path
+    R hl[3] = {R(0), R(0), R(0)};
+    if (lane == 0) {
+        const int xh = max(x0 - 1, 0);
+        hl[0] = fin[1 * plane + SROW(1) + xh];
+        hl[1] = fin[5 * plane + SROW(5) + xh];
+        hl[2] = fin[8 * plane + SROW(8) + xh];
+    } else if (lane == 31) {
+        const int xh = min(x0 + V, L.pitch - 1);
+        hl[0] = fin[3 * plane + SROW(3) + xh];
+        hl[1] = fin[6 * plane + SROW(6) + xh];
+        hl[2] = fin[7 * plane + SROW(7) + xh];
+    }
+    R halo[9];
+#pragma unroll
+    for (int i = 0; i < 9; i++) {
+        halo[i] = R(0);
+        if (cx(i) == 1) halo[i] = shfl_up1(raw[i].r[V - 1]);
+        else if (cx(i) == -1) halo[i] = shfl_dn1(raw[i].r[0]);
+    }
+#undef SROW
+    if (x0 >= L.nx) return;
+    if (lane == 0) {
+        halo[1] = hl[0];
+        halo[5] = hl[1];
+        halo[8] = hl[2];
+    } else if (lane == 31) {
+        halo[3] = hl[0];
+        halo[6] = hl[1];
+        halo[7] = hl[2];
+    }
+#define PULL(i, j) \
+    cvt(cx(i) == 0 ? raw[i].r[j] \
+                   : (cx(i) == 1 ? ((j) == 0 ? halo[i] : raw[i].r[(j) - 1]) \
+                                 : ((j) == V - 1 ? halo[i] : raw[i].r[(j) + 1])))
+    // moments of every node from the pulled populations
+    C s0[V], ux[V], uy[V], rho[V];
+    uint32_t slow = 0;  // bit j: node j needs the per-node path
+#pragma unroll
+    for (int j = 0; j < V; j++) {
+        C a = 0, jx = 0, jy = 0;
+#pragma unroll
+        for (int i = 0; i < 9; i++) {
+            const C g = PULL(i, j);
+            a += g;
+            jx += (C)cx(i) * g;
+            jy += (C)cy(i) * g;
+        }
+        const C r = Prec<P>::dev ? (C)1 + a : a;
+        const C inv = (C)1 / r;
+        s0[j] = a;
+        rho[j] = r;
+        ux[j] = FORCE ? (jx + (C)0.5 * pick<C>(p.body_x, p.body_xf)) * inv : jx * inv;
+        uy[j] = FORCE ? (jy + (C)0.5 * pick<C>(p.body_y, p.body_yf)) * inv : jy * inv;
+        const uint16_t f = fl.f[j];
+        const int x = x0 + j;
+        if (!(f & 1u) && ((f & 0x1FEu) || x == 0 || x == L.nx - 1)) slow |= 1u << j;
+        else if (!(f & 1u) && x < L.nx &&
+                 (!(r > (C)0) || !(fabs(ux[j]) < (C)1e30) || !(fabs(uy[j]) < (C)1e30)))
+            atomicOr(p.status, 1);
+    }
+    // relax towards equilibrium, one population plane at a time
+    const C om = pick<C>(p.omega, p.omega_f);
+#pragma unroll
+    for (int i = 0; i < 9; i++) {
+        Pack<R, V> o;
+#pragma unroll
+        for (int j = 0; j < V; j++) {
+            const C g = PULL(i, j);
+            const C eu = (C)cx(i) * ux[j] + (C)cy(i) * uy[j];
+            const C uu = ux[j] * ux[j] + uy[j] * uy[j];
+            const C poly = (C)3 * eu + (C)4.5 * eu * eu - (C)1.5 * uu;
+            const C eq = Prec<P>::dev ? wgt<C>(i) * (s0[j] + rho[j] * poly)
+                                      : rho[j] * wgt<C>(i) * ((C)1 + poly);
+            C v = g - (g - eq) * om;
+            if (FORCE) {
+                const C Fx = pick<C>(p.body_x, p.body_xf), Fy = pick<C>(p.body_y, p.body_yf);
+                v += ((C)1 - (C)0.5 * om) * wgt<C>(i) *
+                     ((C)3 * (((C)cx(i) - ux[j]) * Fx + ((C)cy(i) - uy[j]) * Fy) +
+                      (C)9 * eu * ((C)cx(i) * Fx + (C)cy(i) * Fy));
+            }
+            put(o.r[j], (fl.f[j] & 1u) ? (C)0 : v);  // solid nodes store zeros
+        }
+        *reinterpret_cast<typename Word<sizeof(R) * V>::T *>(fout + i * plane + r0 + x0) = o.u;
+    }
+#undef PULL
+    // nodes next to a solid or a wall and the first/last column
+    while (slow) {
+        const int j = __ffs(slow) - 1;
+        slow &= slow - 1;
+        update_node<P, FORCE, LOCAL>(p, fin, fout, x0 + j, y);
+    }
+}
+
+template <int P, int V, bool FORCE, bool LOCAL>
 cudaError_t launch_sc(const StepParams &p, cudaStream_t st) {
-    dim3 grid((p.L.nx + SC_BLOCK_X - 1) / SC_BLOCK_X, p.L.ny);
-    k_stream_collide<P, FORCE, LOCAL><<<grid, SC_BLOCK_X, 0, st>>>(p);
+    dim3 grid((p.L.nx + SC_BLOCK_X * V - 1) / (SC_BLOCK_X * V), p.L.ny);
+    k_stream_collide<P, V, FORCE, LOCAL><<<grid, SC_BLOCK_X, 0, st>>>(p);
     return cudaGetLastError();
 }
 
-template <int P>
-cudaError_t launch_sc_p(const StepParams &p, cudaStream_t st) {
+template <int P, int V>
+cudaError_t launch_sc_v(const StepParams &p, cudaStream_t st) {
     const bool force = p.body_x != 0.0 || p.body_y != 0.0;
     const bool local = p.rho_w_mode == LBM_RHOW_LOCAL;
-    if (force) return local ? launch_sc<P, true, true>(p, st) : launch_sc<P, true, false>(p, st);
-    return local ? launch_sc<P, false, true>(p, st) : launch_sc<P, false, false>(p, st);
+    if (force)
+        return local ? launch_sc<P, V, true, true>(p, st) : launch_sc<P, V, true, false>(p, st);
+    return local ? launch_sc<P, V, false, true>(p, st) : launch_sc<P, V, false, false>(p, st);
+}
+
+// Node widths per thread: variant 0 = one 16-byte word per population,
+// variant 1 = 8 bytes, variant 2 = 4 bytes.
+template <int P>
+cudaError_t launch_sc_p(const StepParams &p, cudaStream_t st) {
+    constexpr int V16 = 16 / (int)sizeof(typename Raw<P>::R);
+    switch (p.sc_variant) {
+        case 1: return launch_sc_v<P, V16 / 2>(p, st);
+        case 2: return launch_sc_v<P, (V16 / 4 > 0 ? V16 / 4 : 1)>(p, st);
+        default: return launch_sc_v<P, V16>(p, st);
+    }
 }
 
 }  // namespace

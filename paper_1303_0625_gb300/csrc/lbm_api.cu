@@ -32,11 +32,14 @@ struct lbm_ctx {
     int ring_cap = 0;      // solids the ring was laid out for
     long long *t_d = nullptr;
     int *status_d = nullptr;
+    unsigned int *bar_d = nullptr;  // grid barrier of the per-solid kernel
+    bool record_ready = false;      // force record of time t and motion t -> t+1 computed
     int64_t t = 0;
     int64_t ring_base = 0; // first step whose force record is valid
     std::string err;
     // launch policy
     int graph_steps = 0;
+    int sc_variant = 0;
     cudaGraphExec_t gexec = nullptr;
     // timing
     bool timing = false;
@@ -95,7 +98,7 @@ StepParams params(const lbm_ctx *c) {
     p.moving = c->moving_d;
     p.nmoving = (int)c->moving.size();
     p.ring = c->ring;
-    p.ring_len = g.force_ring;
+    p.ring_len = g.force_ring + 1;  // one extra slot for the record computed ahead
     p.t = c->t_d;
     p.status = c->status_d;
     p.tau = g.tau;
@@ -114,6 +117,12 @@ StepParams params(const lbm_ctx *c) {
     p.rho_w_mode = g.rho_w_mode;
     p.refill = g.refill;
     p.precision = g.precision;
+    p.sc_variant = c->sc_variant;
+    p.omega_f = (float)(1.0 / g.tau);
+    p.body_xf = (float)g.body_force[0];
+    p.body_yf = (float)g.body_force[1];
+    p.rho0_f = (float)g.rho0;
+    p.bar = c->bar_d;
     return p;
 }
 
@@ -127,7 +136,7 @@ void release(lbm_ctx *c) {
     drop_graph(c);
     for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
     void *bufs[] = {c->f[0], c->f[1], c->owner, c->prev, c->flags, c->solids, c->moving_d,
-                    c->ring, c->t_d, c->status_d, c->scratch};
+                    c->ring, c->t_d, c->status_d, c->bar_d, c->scratch};
     for (void *b : bufs)
         if (b) cudaFree(b);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
@@ -166,9 +175,15 @@ lbm_status upload_moving(lbm_ctx *c) {
     return LBM_OK;
 }
 
-// One step t -> t+1 on the context's stream.
+// One step t -> t+1 on the context's stream: [forces at t, once] ->
+// advection-collision -> per-solid work (re-rasterisation, forces at t+1,
+// motion, t += 1).
 lbm_status enqueue_step(lbm_ctx *c, const StepParams &p, bool timed) {
-    CK(c, gbm::launch_forces(p, c->stream));
+    if (!c->record_ready && p.nsolid > 0) {
+        CK(c, gbm::launch_solids(p, 0, c->stream));
+        c->launches++;
+    }
+    c->record_ready = true;
     if (timed) {
         if (c->ev_used + 2 > c->ev.size()) {
             for (int k = 0; k < 2; k++) {
@@ -184,8 +199,13 @@ lbm_status enqueue_step(lbm_ctx *c, const StepParams &p, bool timed) {
         CK(c, cudaEventRecord(c->ev[c->ev_used + 1], c->stream));
         c->ev_used += 2;
     }
-    CK(c, gbm::launch_remask(p, c->stream));
-    c->launches += (p.nsolid > 0 ? 1 : 0) + 1 + (p.nmoving > 0 ? gbm::REMASK_LAUNCHES : 1);
+    if (p.nsolid > 0) {
+        const int mode = gbm::SOLIDS_ADVANCE | (p.nmoving > 0 ? gbm::SOLIDS_REMASK : 0);
+        CK(c, gbm::launch_solids(p, mode, c->stream));
+    } else {
+        CK(c, gbm::launch_tick(p, c->stream));
+    }
+    c->launches += 2;
     return LBM_OK;
 }
 
@@ -208,6 +228,11 @@ lbm_status check_status(lbm_ctx *c) {
     CK(c, cudaStreamSynchronize(c->stream));
     if (st & 1) return fail(c, LBM_EUNSTABLE, "non-finite or non-positive density produced");
     if (st & 2) return fail(c, LBM_EUNSTABLE, "a solid reached a non-finite state");
+    if (st & 4) {
+        // a grid barrier gave up: reset it so that later launches start clean
+        cudaMemsetAsync(c->bar_d, 0, 2 * sizeof(unsigned int), c->stream);
+        return fail(c, LBM_ETIMEOUT, "a grid-wide barrier of the per-solid kernel timed out");
+    }
     return LBM_OK;
 }
 
@@ -248,6 +273,8 @@ lbm_status lbm_create(const lbm_config *cfg, lbm_ctx **out) {
     if (g.refill < LBM_REFILL_A1 || g.refill > LBM_REFILL_A3)
         return fail(nullptr, LBM_EINVAL, "invalid refill");
     if (g.force_ring < 1) return fail(nullptr, LBM_EINVAL, "force_ring must be >= 1");
+    if (9ll * g.ny * ((g.nx + 63) / 64 * 64) >= (1ll << 31))
+        return fail(nullptr, LBM_EINVAL, "domain too large: 9 * ny * pitch must stay below 2^31");
     if (g.reserved != 0) return fail(nullptr, LBM_EINVAL, "reserved must be 0");
     if (g.bc_x == LBM_OPEN && g.bc_y != LBM_WALL)
         return fail(nullptr, LBM_EINVAL, "an open channel needs walls in y");
@@ -276,6 +303,8 @@ lbm_status lbm_create(const lbm_config *cfg, lbm_ctx **out) {
     if (e == cudaSuccess) e = cudaMalloc(&c->flags, plane * sizeof(uint16_t));
     if (e == cudaSuccess) e = cudaMalloc(&c->t_d, sizeof(long long));
     if (e == cudaSuccess) e = cudaMalloc(&c->status_d, sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc(&c->bar_d, 2 * sizeof(unsigned int));
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->bar_d, 0, 2 * sizeof(unsigned int), c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->owner, 0xFF, plane * sizeof(uint16_t), c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->prev, 0xFF, plane * sizeof(uint16_t), c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->t_d, 0, sizeof(long long), c->stream);
@@ -345,18 +374,24 @@ lbm_status lbm_add_solid(lbm_ctx *c, const lbm_disk *d, int32_t *id_out) {
         if (c->ring) CK(c, cudaFree(c->ring));
         c->ring = nullptr;
         c->ring_cap = 0;
-        CK(c, cudaMalloc(&c->ring, (size_t)g.force_ring * 2 * cap * 3 * sizeof(double)));
+        CK(c, cudaMalloc(&c->ring, (size_t)(g.force_ring + 1) * 2 * cap * 3 * sizeof(double)));
         c->ring_cap = cap;
     }
     DSolid s{};
     s.xa = s.x = s.xn = d->cx;
     s.ya = s.y = s.yn = d->cy;
+    s.xw = s.xnw = g.bc_x == LBM_PERIODIC ? d->cx - g.nx * std::floor(d->cx / g.nx) : d->cx;
+    s.yw = s.ynw = g.bc_y == LBM_PERIODIC ? d->cy - g.ny * std::floor(d->cy / g.ny) : d->cy;
     s.vx = s.vxn = d->vx;
     s.vy = s.vyn = d->vy;
     s.om = s.omn = d->omega;
     s.r = d->r;
     s.rho_s = d->rho_s;
     s.ta = c->t;
+    s.pend_t = -1;
+    s.vxf = (float)d->vx;
+    s.vyf = (float)d->vy;
+    s.omf = (float)d->omega;
     s.motion = d->motion;
     const int id = c->nsolid;
     CK(c, cudaMemcpyAsync(c->solids + id, &s, sizeof s, cudaMemcpyHostToDevice, c->stream));
@@ -369,6 +404,7 @@ lbm_status lbm_add_solid(lbm_ctx *c, const lbm_disk *d, int32_t *id_out) {
     c->launches += 2;
     CK(c, cudaStreamSynchronize(c->stream));
     c->ring_base = c->t;  // the record layout changed with nsolid
+    c->record_ready = false;
     if (id_out) *id_out = id;
     return LBM_OK;
 }
@@ -399,8 +435,7 @@ lbm_status lbm_step(lbm_ctx *c, int64_t n) {
                 CK(c, e);
             }
             CK(c, cudaGraphLaunch(c->gexec, c->stream));
-            c->launches += (int64_t)c->graph_steps *
-                           ((p.nsolid > 0 ? 1 : 0) + 1 + (p.nmoving > 0 ? gbm::REMASK_LAUNCHES : 1));
+            c->launches += 2 * (int64_t)c->graph_steps;
             done += c->graph_steps;
         }
     }
@@ -438,9 +473,10 @@ lbm_status lbm_forces(lbm_ctx *c, int32_t form, int64_t first, int64_t count, do
     if (ns > 0 && count > 0) {
         const size_t w = (size_t)ns * 3 * sizeof(double);
         int64_t k = 0;
+        const int64_t slots = c->cfg.force_ring + 1;
         while (k < count) {
-            const int64_t slot = (first + k) % c->cfg.force_ring;
-            int64_t run = c->cfg.force_ring - slot;
+            const int64_t slot = (first + k) % slots;
+            int64_t run = slots - slot;
             if (run > count - k) run = count - k;
             const double *src = c->ring + ((size_t)slot * 2 + form) * ns * 3;
             CK(c, cudaMemcpy2DAsync(out + (size_t)k * ns * 3, w, src, 2 * w, w, (size_t)run,
@@ -500,6 +536,7 @@ lbm_status lbm_set_populations(lbm_ctx *c, const double *f, int32_t on_device) {
     if (on_device) {
         CK(c, gbm::launch_import_populations(p, f, c->stream));
         c->launches++;
+        c->record_ready = false;
         return LBM_OK;
     }
     lbm_status st = ensure_scratch(c, n * sizeof(double));
@@ -507,6 +544,7 @@ lbm_status lbm_set_populations(lbm_ctx *c, const double *f, int32_t on_device) {
     CK(c, cudaMemcpyAsync(c->scratch, f, n * sizeof(double), cudaMemcpyHostToDevice, c->stream));
     CK(c, gbm::launch_import_populations(p, static_cast<const double *>(c->scratch), c->stream));
     c->launches++;
+    c->record_ready = false;
     CK(c, cudaStreamSynchronize(c->stream));
     return LBM_OK;
 }
@@ -565,8 +603,12 @@ lbm_status lbm_set_solid(lbm_ctx *c, int32_t id, const double *state) {
     s.vx = s.vxn = state[2];
     s.vy = s.vyn = state[3];
     s.om = s.omn = state[4];
+    s.vxf = (float)state[2];
+    s.vyf = (float)state[3];
+    s.omf = (float)state[4];
     CK(c, cudaMemcpyAsync(c->solids + id, &s, sizeof s, cudaMemcpyHostToDevice, c->stream));
     drop_graph(c);
+    c->record_ready = false;
     c->is_moving[id] = translates(s) ? 1 : 0;
     return upload_moving(c);
 }
@@ -661,5 +703,50 @@ lbm_status lbm_get_timing(lbm_ctx *c, double *ms, int64_t *launches) {
 }
 
 int64_t lbm_launch_count(const lbm_ctx *c) { return c ? c->launches : -1; }
+
+lbm_status lbm_set_kernel_variant(lbm_ctx *c, int32_t variant) {
+    if (!c || variant < 0 || variant > 2) return LBM_EINVAL;
+    drop_graph(c);
+    c->sc_variant = variant;
+    return LBM_OK;
+}
+
+int32_t lbm_kernel_variant(const lbm_ctx *c) { return c ? c->sc_variant : -1; }
+
+lbm_status lbm_autotune(lbm_ctx *c, int32_t steps, int32_t *best) {
+    if (!c || steps < 1) return LBM_EINVAL;
+    const bool was_timing = c->timing;
+    const double keep_ms = c->timed_ms;
+    const int64_t keep_n = c->timed_launches;
+    lbm_status st = harvest_timing(c);
+    if (st != LBM_OK) return st;
+    double best_ms = 0.0;
+    int best_v = 0;
+    for (int v = 0; v <= 2; v++) {
+        c->sc_variant = v;
+        drop_graph(c);
+        c->timing = true;
+        c->timed_ms = 0.0;
+        c->timed_launches = 0;
+        st = lbm_step(c, 1);  // first launch of a variant is not timed
+        if (st == LBM_OK) st = harvest_timing(c);
+        c->timed_ms = 0.0;
+        c->timed_launches = 0;
+        if (st == LBM_OK) st = lbm_step(c, steps);
+        if (st == LBM_OK) st = harvest_timing(c);
+        if (st != LBM_OK) return st;
+        const double ms = c->timed_ms / (c->timed_launches ? c->timed_launches : 1);
+        if (v == 0 || ms < best_ms) {
+            best_ms = ms;
+            best_v = v;
+        }
+    }
+    c->sc_variant = best_v;
+    c->timing = was_timing;
+    c->timed_ms = keep_ms;
+    c->timed_launches = keep_n;
+    if (best) *best = best_v;
+    return LBM_OK;
+}
 
 }  // extern "C"

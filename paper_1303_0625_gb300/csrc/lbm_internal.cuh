@@ -33,18 +33,21 @@ __host__ __device__ constexpr C wgt(int i) {
     return i == 0 ? C(4) / C(9) : (i <= 4 ? C(1) / C(9) : C(1) / C(36));
 }
 
-// Per-solid record on the device (array of structs, 160 bytes).
+// Per-solid record on the device (array of structs, 208 bytes).
 struct DSolid {
     double xa, ya;     // position when added (prescribed motion)
     double x, y;       // centre R(t)
     double xn, yn;     // centre R(t+1), written during the step
+    double xw, yw;     // R(t) reduced into the domain along periodic axes
+    double xnw, ynw;   // R(t+1) reduced likewise
     double vx, vy, om; // V(t), Omega(t)
     double vxn, vyn, omn;
     double r, rho_s;
-    double pend[3];    // momentum booked for the next force record
+    double pend[3];    // momentum booked by the node-type changes into time pend_t
+    long long pend_t;  // time whose force record carries pend
     long long ta;      // time when added
+    float vxf, vyf, omf;  // FP32 copies of vx, vy, om for the FP32 kernels
     int motion;
-    int pad;
 };
 
 struct Lattice {
@@ -61,7 +64,7 @@ struct StepParams {
     int nsolid;
     const int *moving;        // ids of solids that translate (or are free)
     int nmoving;
-    double *ring;             // [ring_len][2][nsolid][3]
+    double *ring;             // [ring_len][2][nsolid][3], slot = time % ring_len
     int ring_len;
     long long *t;             // device step counter
     int *status;              // bit 0: non-finite or non-positive density; bit 1: bad solid state
@@ -72,7 +75,14 @@ struct StepParams {
     double grav_x, grav_y, lub;
     double u0x, u0y;
     int rho_w_mode, refill, precision;
+    int sc_variant;           // node width per thread of the advection-collision kernel
+    float omega_f, body_xf, body_yf, rho0_f;  // FP32 copies for the FP32 kernels
+    unsigned int *bar;        // grid barrier of the per-solid kernel: {count, generation}
 };
+
+template <class C> __device__ __forceinline__ C pick(double d, float f);
+template <> __device__ __forceinline__ double pick<double>(double d, float) { return d; }
+template <> __device__ __forceinline__ float pick<float>(double, float f) { return f; }
 
 // ---------------------------------------------------------------- storage
 
@@ -178,6 +188,57 @@ __device__ __forceinline__ bool locate(const Lattice &L, int x, int y, int &xo, 
     return true;
 }
 
+// Coordinate reduced into [0, n) along a periodic axis.
+__device__ __forceinline__ double wrap_coord(double X, int n, bool periodic) {
+    if (!periodic) return X;
+    return X - (double)n * floor(X / (double)n);
+}
+
+// Separation from a centre already reduced into the domain to a point of the
+// domain, taken to the nearest periodic image by one conditional shift.
+__device__ __forceinline__ double near_image(double d, int n, bool periodic) {
+    if (periodic) {
+        if (d > 0.5 * n) d -= n;
+        else if (d < -0.5 * n) d += n;
+    }
+    return d;
+}
+
+// Inside test of node (i, j) for the disk (X, Y, r), decided exactly as the
+// FP64 expression (i - X)^2 + (j - Y)^2 <= r^2.  An FP32 evaluation relative to
+// the integer part of the centre settles every node farther than a relative
+// 1e-5 from the circle; the rest use the FP64 expression itself.
+struct DiskTest {
+    double X, Y, r;
+    int xi, yi;
+    float fx, fy, r2, margin;
+    __device__ __forceinline__ DiskTest(double X_, double Y_, double r_) : X(X_), Y(Y_), r(r_) {
+        const double fxd = floor(X), fyd = floor(Y);
+        xi = (int)fxd;
+        yi = (int)fyd;
+        fx = (float)(X - fxd);
+        fy = (float)(Y - fyd);
+        r2 = (float)(r * r);
+        margin = 1e-5f * r2 + 1e-5f;
+    }
+    __device__ __forceinline__ bool operator()(int i, int j) const {
+        const float dx = (float)(i - xi) - fx, dy = (float)(j - yi) - fy;
+        const float d2 = dx * dx + dy * dy;
+        if (d2 < r2 - margin) return true;
+        if (d2 > r2 + margin) return false;
+        return inside_disk(i, j, X, Y, r);
+    }
+};
+
+__device__ __forceinline__ void atomic_min_u16(uint16_t *a, uint16_t v) {
+    unsigned short old = *reinterpret_cast<volatile unsigned short *>(a);
+    while (v < old) {
+        unsigned short seen = atomicCAS(reinterpret_cast<unsigned short *>(a), old, v);
+        if (seen == old) break;
+        old = seen;
+    }
+}
+
 // Separation reduced to the nearest periodic image.
 __device__ __forceinline__ double min_image(double d, int n, bool periodic) {
     if (!periodic) return d;
@@ -204,9 +265,12 @@ __device__ __forceinline__ long long cell_of(const Lattice &L, int x, int y) {
 
 // k_stream_collide.cu
 cudaError_t launch_stream_collide(const StepParams &p, cudaStream_t st);
+// k_solid_step.cu: per-solid work of a step in one cooperative launch.
+// mode bits: SOLIDS_REMASK (re-rasterise the moving solids, t -> t+1),
+// SOLIDS_ADVANCE (forces at t+1 and t += 1; otherwise forces at t).
+constexpr int SOLIDS_REMASK = 1, SOLIDS_ADVANCE = 2;
+cudaError_t launch_solids(const StepParams &p, int mode, cudaStream_t st);
 // k_solids.cu
-cudaError_t launch_forces(const StepParams &p, cudaStream_t st);
-cudaError_t launch_remask(const StepParams &p, cudaStream_t st);
 cudaError_t launch_tick(const StepParams &p, cudaStream_t st);
 cudaError_t launch_init_populations(const StepParams &p, cudaStream_t st);
 cudaError_t launch_flags_all(const StepParams &p, cudaStream_t st);
@@ -217,7 +281,5 @@ cudaError_t launch_export_owner(const StepParams &p, int32_t *out, cudaStream_t 
 cudaError_t launch_fields(const StepParams &p, double *rho, double *ux, double *uy,
                           cudaStream_t st);
 cudaError_t launch_link_masks(const StepParams &p, uint8_t *mask, cudaStream_t st);
-// number of kernels launch_remask enqueues
-constexpr int REMASK_LAUNCHES = 5;
 
 }  // namespace gbm

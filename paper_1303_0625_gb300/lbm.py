@@ -86,6 +86,9 @@ _SIGNATURES = {
     "lbm_set_timing": (_I32, [_P, _I32]),
     "lbm_get_timing": (_I32, [_P, _D, ctypes.POINTER(_I64)]),
     "lbm_launch_count": (_I64, [_P]),
+    "lbm_set_kernel_variant": (_I32, [_P, _I32]),
+    "lbm_kernel_variant": (_I32, [_P]),
+    "lbm_autotune": (_I32, [_P, _I32, ctypes.POINTER(_I32)]),
 }
 
 
@@ -239,6 +242,20 @@ def lbm_launch_count(ctx) -> int:
     return int(load().lbm_launch_count(ctx))
 
 
+def lbm_set_kernel_variant(ctx, variant: int):
+    _check(load().lbm_set_kernel_variant(ctx, int(variant)), ctx)
+
+
+def lbm_kernel_variant(ctx) -> int:
+    return int(load().lbm_kernel_variant(ctx))
+
+
+def lbm_autotune(ctx, steps: int = 4) -> int:
+    best = _I32()
+    _check(load().lbm_autotune(ctx, int(steps), ctypes.byref(best)), ctx)
+    return int(best.value)
+
+
 # ----------------------------------------------------------- convenience
 
 def make_config(nx, ny, tau, *, rho0=1.0, u0=(0.0, 0.0), bc_x=LBM_PERIODIC, bc_y=LBM_PERIODIC,
@@ -384,3 +401,9 @@ class Lattice:
 
     def launch_count(self) -> int:
         return lbm_launch_count(self._h)
+
+    def set_kernel_variant(self, variant: int):
+        lbm_set_kernel_variant(self._h, variant)
+
+    def autotune(self, steps: int = 4) -> int:
+        return lbm_autotune(self._h, steps)

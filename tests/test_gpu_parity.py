@@ -165,7 +165,7 @@ def test_unstable_run_reports_status():
     LBM_EUNSTABLE by the next synchronising call (host-side check of a device
     flag; nothing faults)."""
     from paper_1303_0625_gb300 import lbm as L
-    w = _case(32, 32, 0.5001, [], u0=(0.9, 0.0))
+    w = _case(32, 32, 0.5001, _disks((16.0, 16.0, 4.0)), u0=(0.9, 0.0))
     g = make_gpu(w, "fp32")
     g.step(400)
     with pytest.raises(L.LBMError) as e:
