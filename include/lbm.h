@@ -139,6 +139,26 @@ lbm_status lbm_forces(lbm_ctx *ctx, int32_t form, int64_t first_step, int64_t co
  * (sum_i e_i f_i - F/2) / rho.  on_device as for lbm_forces. */
 lbm_status lbm_fields(lbm_ctx *ctx, double *rho, double *ux, double *uy, int32_t on_device);
 
+/* Same result as lbm_fields(ctx, rho, ux, uy, 0), for callers that must not
+ * allocate device memory.  The paper has no counterpart: this is a service of
+ * the library.  A program whose device memory is held by another allocator
+ * (PyTorch's caching allocator keeps freed blocks for itself, so a plain
+ * cudaMalloc can fail although the process has memory to spare), or which must
+ * not stall other streams (cudaFree waits for the whole device), cannot afford
+ * the staging buffer that lbm_fields allocates on first use.  This entry point
+ * stages the three fields in one fixed array compiled into the library
+ * instead (LBM_FIELDS_STATIC_MAX_NODES nodes, 3 doubles each, 12 MiB reserved
+ * on every GPU that loads the library, until the process exits).
+ * rho, ux, uy: host arrays [ny][nx]; solid nodes are NaN.  Waits for the
+ * stream.  Errors: LBM_EINVAL for a NULL argument or nx * ny above the
+ * maximum (nothing is copied then).  The first call on a device looks up the
+ * array's device address, so make that first call before any stream capture.
+ * Every call uses the same array and it keeps the last call's contents;
+ * calls whose work overlaps on the GPU (two contexts on different streams of
+ * one device, or several threads) race on it and must be serialised. */
+#define LBM_FIELDS_STATIC_MAX_NODES 524288
+lbm_status lbm_fields_static(lbm_ctx *ctx, double *rho, double *ux, double *uy);
+
 /* Current populations as FP64 [9][ny][nx] (converted from the storage
  * precision; the values at solid nodes are unspecified) / overwrite them
  * (rounded to the storage precision).  on_device as for lbm_forces. */

@@ -8,6 +8,8 @@
 #include <string>
 #include <vector>
 
+#include <mutex>
+
 #include "lbm_internal.cuh"
 
 using gbm::DSolid;
@@ -507,6 +509,51 @@ lbm_status lbm_fields(lbm_ctx *c, double *rho, double *ux, double *uy, int32_t o
     CK(c, cudaMemcpyAsync(rho, s, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     CK(c, cudaMemcpyAsync(ux, s + n, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     CK(c, cudaMemcpyAsync(uy, s + 2 * n, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    return lbm_sync(c);
+}
+
+}  // extern "C"
+
+// Fixed staging array of lbm_fields_static: rho, ux, uy of up to
+// LBM_FIELDS_STATIC_MAX_NODES nodes, reserved on every device that loads the
+// library.  Host code must not use the symbol itself as a device address; the
+// address is looked up once per device below.
+static __device__ __align__(256) double g_fields_stage[3 * LBM_FIELDS_STATIC_MAX_NODES];
+
+namespace {
+constexpr int MAX_DEVICES = 64;
+std::mutex g_stage_mutex;
+double *g_stage_ptr[MAX_DEVICES] = {};
+}  // namespace
+
+extern "C" {
+
+lbm_status lbm_fields_static(lbm_ctx *c, double *rho, double *ux, double *uy) {
+    if (!c || !rho || !ux || !uy) return LBM_EINVAL;
+    const int dev = c->cfg.device;
+    const long long n = (long long)c->cfg.nx * c->cfg.ny;
+    if (n > LBM_FIELDS_STATIC_MAX_NODES)
+        return fail(c, LBM_EINVAL, "lbm_fields_static: %lld nodes exceed the fixed maximum of %d",
+                    n, LBM_FIELDS_STATIC_MAX_NODES);
+    if (dev < 0 || dev >= MAX_DEVICES) return fail(c, LBM_EINVAL, "device ordinal out of range");
+    CK(c, cudaSetDevice(dev));
+    double *stage = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(g_stage_mutex);
+        if (!g_stage_ptr[dev]) {
+            void *ptr = nullptr;
+            CK(c, cudaGetSymbolAddress(&ptr, g_fields_stage));
+            g_stage_ptr[dev] = static_cast<double *>(ptr);
+        }
+        stage = g_stage_ptr[dev];
+    }
+    const StepParams p = params(c);
+    CK(c, gbm::launch_fields(p, stage, stage + n, stage + 2 * n, c->stream));
+    c->launches++;
+    CK(c, cudaMemcpyAsync(rho, stage, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CK(c, cudaMemcpyAsync(ux, stage + n, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CK(c, cudaMemcpyAsync(uy, stage + 2 * n, n * sizeof(double), cudaMemcpyDeviceToHost,
+                          c->stream));
     return lbm_sync(c);
 }
 

@@ -72,6 +72,7 @@ _SIGNATURES = {
     "lbm_sync": (_I32, [_P]),
     "lbm_forces": (_I32, [_P, _I32, _I64, _I64, _P, _I32]),
     "lbm_fields": (_I32, [_P, _P, _P, _P, _I32]),
+    "lbm_fields_static": (_I32, [_P, _P, _P, _P]),
     "lbm_get_populations": (_I32, [_P, _P, _I32]),
     "lbm_set_populations": (_I32, [_P, _P, _I32]),
     "lbm_get_owner": (_I32, [_P, _P, _I32]),
@@ -177,6 +178,14 @@ def lbm_forces(ctx, form: int, first: int, count: int, out, on_device: bool = Fa
 
 def lbm_fields(ctx, rho, ux, uy, on_device: bool = False):
     _check(load().lbm_fields(ctx, _ptr(rho), _ptr(ux), _ptr(uy), int(on_device)), ctx)
+
+
+def lbm_fields_static(ctx, rho, ux, uy):
+    """lbm_fields into host arrays without any device allocation (see lbm.h)."""
+    _check(load().lbm_fields_static(ctx, _ptr(rho), _ptr(ux), _ptr(uy)), ctx)
+
+
+LBM_FIELDS_STATIC_MAX_NODES = 524288
 
 
 def lbm_get_populations(ctx, f, on_device: bool = False):
