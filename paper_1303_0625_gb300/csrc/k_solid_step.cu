@@ -1,6 +1,10 @@
-// Per-solid work of one step, in a single cooperative launch after the
+// Per-solid work of one step, in one cooperative launch after the
 // advection-collision kernel of step t:
 //
+//   F  forces:  every fluid-solid link of time t (Eq. 4 and Eq. 5, summed by
+//               Eq. 6 and Eq. 7) plus the momenta booked by the node-type
+//               changes into t, written to the force history; motion
+//               t -> t+1 (prescribed, or Newton-Euler on the Eq. 5 force)
 //   A  clear:   nodes of the old disk that the new disk leaves, owner s -> fluid
 //   B  set:     nodes of the new disk, owner := lowest id covering them
 //   C  changes: on the ring (old disk XOR new disk): node flags of every node
@@ -8,21 +12,23 @@
 //               give their momentum to the solid; fresh (newborn) nodes are
 //               refilled by extrapolation (Sec. IV.B) and take theirs from it
 //   D  sync:    prev := owner on the ring; the solid's state becomes t+1
-//   F  forces:  momentum exchange on every fluid-solid link at t+1 (Eq. 4 and
-//               Eq. 5, summed by Eq. 6 and Eq. 7) plus the booked momenta,
-//               written to the force history; motion t+1 -> t+2
 //
 // Phases A-D run only when some solid translates.  One warp owns one solid
 // in a phase (solids are looped over when there are more solids than warps);
 // phases are separated by a grid-wide barrier whose wait is bounded (status
-// bit 2 and an early exit instead of a hang).  Work per solid follows its
-// perimeter: every loop walks the disk's bounding box with an FP32 distance
-// prefilter and touches memory only on the ring or the link annulus.
+// bit 2 instead of a hang).  Work per solid follows its perimeter: the nodes
+// near the ends of the disk's chord in every row (FP32 bounds with a one-node
+// margin) are dealt out to the warp's lanes, each lane fetching several nodes
+// before it processes them; every decision is taken by the exact test.  A
+// disk that comes within a node of another one ("near") also re-claims its
+// whole interior in phase B, which keeps the lowest-id rule exact where disks
+// overlap; a disk that is not near any other skips the owner look-ups of its
+// links (its solid neighbours can only be its own nodes).
 //
-// Precision: in the FP32/FP16 modes the per-link products are evaluated in
-// FP32 and summed per lane over one round of links; all accumulation across
-// rounds and lanes (the force and torque reduction) is FP64.  The FP64 mode
-// evaluates everything in FP64.
+// Precision: in the FP32/FP16 modes the per-link products are FP32 and each
+// lane's batch of links is added into FP64; all further accumulation (the
+// force and torque reduction) is FP64 in a fixed lane order and tree.  The
+// FP64 mode is FP64 throughout.
 #include "lbm_internal.cuh"
 
 namespace gbm {
@@ -31,11 +37,10 @@ namespace {
 
 constexpr int SW_BLOCK = 256;
 constexpr int WARPS = SW_BLOCK / 32;
-constexpr int CELLS_PER_LANE = 8;
-constexpr int ROUND = 32 * CELLS_PER_LANE;  // box cells per warp round
-constexpr int QMAX = 8 * ROUND;             // at most 8 links per node
+constexpr int U = 4;                        // nodes a lane fetches at once
 constexpr long long SPIN_LIMIT = 1ll << 24; // polls of about 64 ns: roughly one second
 constexpr double PI = 3.14159265358979323846;
+constexpr unsigned FULL = 0xffffffffu;
 
 // ------------------------------------------------------------- barrier
 
@@ -77,19 +82,7 @@ template <int N>
 __device__ __forceinline__ void warp_sum(double (&v)[N]) {
 #pragma unroll
     for (int k = 0; k < N; k++)
-        for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
-}
-
-__device__ __forceinline__ int warp_exclusive_scan(int v, int &total) {
-    const int lane = threadIdx.x & 31;
-    int inc = v;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const int n = __shfl_up_sync(0xffffffffu, inc, o);
-        if (lane >= o) inc += n;
-    }
-    total = __shfl_sync(0xffffffffu, inc, 31);
-    return inc - v;
+        for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_down_sync(FULL, v[k], o);
 }
 
 // Set or clear one bit of a 16-bit flags word atomically.
@@ -101,229 +94,169 @@ __device__ __forceinline__ void flag_bit(uint16_t *flags, long long k, int bit, 
     else atomicAnd(w, ~m);
 }
 
-// Box cell c -> unwrapped node coordinates.
-__device__ __forceinline__ void box_cell(const Box &bx, int c, int &iu, int &ju) {
-    ju = bx.y0 + c / bx.w;
-    iu = bx.x0 + c - (ju - bx.y0) * bx.w;
-}
+__device__ __forceinline__ double cvt_s(double v) { return v; }
+__device__ __forceinline__ float cvt_s(float v) { return v; }
+__device__ __forceinline__ float cvt_s(__half v) { return __half2float(v); }
 
-// Population f_i of cell k in the link-math precision C.
-template <int P>
-__device__ __forceinline__ typename Prec<P>::C pop(const void *f, long long plane, int i,
-                                                   long long k) {
-    using C = typename Prec<P>::C;
-    using S = typename Prec<P>::S;
-    C v = (C)ldc(static_cast<const S *>(f) + (long long)i * plane + k);
-    if (Prec<P>::dev) v += wgt<C>(i);
-    return v;
-}
-
-// ------------------------------------------------------- phases A, B, D
-
-__device__ void phase_clear(const StepParams &p, int s, int lane) {
-    const DSolid &b = p.S[s];
-    const DiskTest in0(b.x, b.y, b.r), in1(b.xn, b.yn, b.r);
-    const Box bx = disk_box(b.x, b.y, b.r, 0);
-    for (int c = lane; c < bx.w * bx.h; c += 32) {
-        int iu, ju, x, y;
-        box_cell(bx, c, iu, ju);
-        if (!in0(iu, ju) || in1(iu, ju)) continue;
-        if (!locate(p.L, iu, ju, x, y)) continue;
-        const long long k = cell_of(p.L, x, y);
-        if (p.owner[k] == (uint16_t)s) p.owner[k] = FLUID;
-    }
-}
-
-__device__ void phase_set(const StepParams &p, int s, int lane) {
-    const DSolid &b = p.S[s];
-    const DiskTest in1(b.xn, b.yn, b.r);
-    const Box bx = disk_box(b.xn, b.yn, b.r, 0);
-    for (int c = lane; c < bx.w * bx.h; c += 32) {
-        int iu, ju, x, y;
-        box_cell(bx, c, iu, ju);
-        if (!in1(iu, ju)) continue;
-        if (!locate(p.L, iu, ju, x, y)) continue;
-        uint16_t *o = p.owner + cell_of(p.L, x, y);
-        if (*o > (uint16_t)s) atomic_min_u16(o, (uint16_t)s);
-    }
-}
-
-__device__ void phase_sync(const StepParams &p, int s, int lane) {
-    DSolid &b = p.S[s];
-    const DiskTest in0(b.x, b.y, b.r), in1(b.xn, b.yn, b.r);
-    const Box bx = box_union(disk_box(b.x, b.y, b.r, 0), disk_box(b.xn, b.yn, b.r, 0));
-    for (int c = lane; c < bx.w * bx.h; c += 32) {
-        int iu, ju, x, y;
-        box_cell(bx, c, iu, ju);
-        if (in0(iu, ju) == in1(iu, ju)) continue;
-        if (!locate(p.L, iu, ju, x, y)) continue;
-        const long long k = cell_of(p.L, x, y);
-        if (p.prev[k] != p.owner[k]) p.prev[k] = p.owner[k];
-    }
-    __syncwarp();
-    if (lane == 0) {
-        b.x = b.xn;
-        b.y = b.yn;
-        b.xw = b.xnw;
-        b.yw = b.ynw;
-        b.vx = b.vxn;
-        b.vy = b.vyn;
-        b.om = b.omn;
-        b.vxf = (float)b.vxn;
-        b.vyf = (float)b.vyn;
-        b.omf = (float)b.omn;
-    }
-}
-
-// ------------------------------------------------------------ phase C
-
-// A node that may feed a refill: fluid now and fluid before this step.
-__device__ __forceinline__ bool usable(const StepParams &p, int x, int y, long long &k) {
+// Centre split into an integer part and an FP32 fraction, for FP32 bounds
+// on the nodes of a row that lie within some radius of it.
+struct Centre {
     int xi, yi;
-    if (!locate(p.L, x, y, xi, yi)) return false;
-    k = cell_of(p.L, xi, yi);
-    return p.owner[k] == FLUID && p.prev[k] == FLUID;
+    float fx, fy;
+    __device__ __forceinline__ Centre(double X, double Y) {
+        const double a = floor(X), b = floor(Y);
+        xi = (int)a;
+        yi = (int)b;
+        fx = (float)(X - a);
+        fy = (float)(Y - b);
+    }
+    // Unwrapped x-range [a, b] containing every node of row j within rr of
+    // the centre (one node of margin on each side); false if none can be.
+    __device__ __forceinline__ bool span(int j, float rr, int &a, int &b) const {
+        const float dy = (float)(j - yi) - fy;
+        const float h2 = rr * rr - dy * dy;
+        if (h2 < 0.f) return false;
+        const float h = sqrtf(h2);
+        a = xi + (int)floorf(fx - h) - 1;
+        b = xi + (int)ceilf(fx + h) + 1;
+        return true;
+    }
+};
+
+// Cell of the neighbour (x + dx, y + dy) of an in-domain node (|dx|, |dy|
+// <= 3), or -1 beyond a non-periodic edge.
+__device__ __forceinline__ int neighbour(const Lattice &L, int x, int y, int dx, int dy) {
+    x += dx;
+    y += dy;
+    if (x < 0 || x >= L.nx) {
+        if (L.bc_x != LBM_PERIODIC) return -1;
+        x += x < 0 ? L.nx : -L.nx;
+    }
+    if (y < 0 || y >= L.ny) {
+        if (L.bc_y != LBM_PERIODIC) return -1;
+        y += y < 0 ? L.ny : -L.ny;
+    }
+    return y * L.pitch + x;
 }
 
-// Populations of a newborn node (Sec. IV.B): A1 second-order extrapolation
-// along every direction with three old-fluid nodes, averaged; else A2 linear
-// extrapolation; else A3 neighbour average; else equilibrium at rho0 and the
-// solid's velocity at the node.  Works in the storage convention (f_i or
-// f_i - w_i), which is linear, so extrapolation commutes with it.
-template <int P>
-__device__ void refill_node(const StepParams &p, const void *f, int x, int y, const DSolid &b,
-                            typename Prec<P>::C (&out)[9]) {
-    using C = typename Prec<P>::C;
-    using S = typename Prec<P>::S;
-    const S *fs = static_cast<const S *>(f);
-    const long long pl = p.L.plane;
-    C acc[9];
-    int count;
-    long long k1, k2, k3;
-    if (p.refill <= LBM_REFILL_A1) {
-        count = 0;
-#pragma unroll
-        for (int j = 0; j < 9; j++) acc[j] = 0;
-        for (int i = 1; i < 9; i++) {
-            if (!usable(p, x + cx(i), y + cy(i), k1)) continue;
-            if (!usable(p, x + 2 * cx(i), y + 2 * cy(i), k2)) continue;
-            if (!usable(p, x + 3 * cx(i), y + 3 * cy(i), k3)) continue;
-#pragma unroll
-            for (int j = 0; j < 9; j++)
-                acc[j] += (C)3 * (C)ldc(fs + j * pl + k1) - (C)3 * (C)ldc(fs + j * pl + k2) +
-                          (C)ldc(fs + j * pl + k3);
-            count++;
-        }
-        if (count) {
-#pragma unroll
-            for (int j = 0; j < 9; j++) out[j] = acc[j] / (C)count;
-            return;
-        }
+// Up to two x-ranges of a row; the second is empty when a1 > b1.
+struct Ranges {
+    int a0, b0, a1, b1;
+};
+
+// Nodes of row j that can lie inside exactly one of two disks of radius r
+// centred at c0 and c1: near the two left chord ends and the two right ends.
+__device__ __forceinline__ bool ring_ranges(const Centre &c0, const Centre &c1, float rr, int j,
+                                            Ranges &R) {
+    int a0, b0, a1, b1;
+    const bool h0 = c0.span(j, rr, a0, b0), h1 = c1.span(j, rr, a1, b1);
+    if (!h0 && !h1) return false;
+    if (!h0 || !h1) {
+        R.a0 = h0 ? a0 : a1;
+        R.b0 = h0 ? b0 : b1;
+        R.a1 = 1;
+        R.b1 = 0;
+        return true;
     }
-    if (p.refill <= LBM_REFILL_A2) {
-        count = 0;
-#pragma unroll
-        for (int j = 0; j < 9; j++) acc[j] = 0;
-        for (int i = 1; i < 9; i++) {
-            if (!usable(p, x + cx(i), y + cy(i), k1)) continue;
-            if (!usable(p, x + 2 * cx(i), y + 2 * cy(i), k2)) continue;
-#pragma unroll
-            for (int j = 0; j < 9; j++)
-                acc[j] += (C)2 * (C)ldc(fs + j * pl + k1) - (C)ldc(fs + j * pl + k2);
-            count++;
-        }
-        if (count) {
-#pragma unroll
-            for (int j = 0; j < 9; j++) out[j] = acc[j] / (C)count;
-            return;
-        }
+    R.a0 = min(a0, a1);
+    R.b0 = max(a0, a1) + 2;
+    R.a1 = min(b0, b1) - 2;
+    R.b1 = max(b0, b1);
+    if (R.a1 <= R.b0 + 1) {  // the two ends meet: one range
+        R.b0 = R.b1;
+        R.a1 = 1;
+        R.b1 = 0;
     }
-    count = 0;
-#pragma unroll
-    for (int j = 0; j < 9; j++) acc[j] = 0;
-    for (int i = 1; i < 9; i++) {
-        if (!usable(p, x + cx(i), y + cy(i), k1)) continue;
-#pragma unroll
-        for (int j = 0; j < 9; j++) acc[j] += (C)ldc(fs + j * pl + k1);
-        count++;
-    }
-    if (count) {
-#pragma unroll
-        for (int j = 0; j < 9; j++) out[j] = acc[j] / (C)count;
-        return;
-    }
-    double ux, uy, dx, dy;
-    point_velocity(p.L, b.xn, b.yn, b.vxn, b.vyn, b.omn, (double)x, (double)y, ux, uy, dx, dy);
-    const double uu = ux * ux + uy * uy;
-#pragma unroll
-    for (int i = 0; i < 9; i++) {
-        const double eu = cx(i) * ux + cy(i) * uy;
-        const double fe = p.rho0 * wgt<double>(i) * (1.0 + 3.0 * eu + 4.5 * eu * eu - 1.5 * uu);
-        out[i] = (C)(Prec<P>::dev ? fe - wgt<double>(i) : fe);
-    }
+    return true;
 }
 
-template <int P>
-__device__ void phase_changes(const StepParams &p, int s, int lane, long long t1, void *fnew) {
-    using C = typename Prec<P>::C;
-    using S = typename Prec<P>::S;
-    DSolid &b = p.S[s];
-    const Lattice &L = p.L;
-    const DiskTest in0(b.x, b.y, b.r), in1(b.xn, b.yn, b.r);
-    const Box bx = box_union(disk_box(b.x, b.y, b.r, 0), disk_box(b.xn, b.yn, b.r, 0));
-    double acc[3] = {0.0, 0.0, 0.0};
-    for (int c = lane; c < bx.w * bx.h; c += 32) {
-        int iu, ju, x, y;
-        box_cell(bx, c, iu, ju);
-        if (in0(iu, ju) == in1(iu, ju)) continue;
-        if (!locate(L, iu, ju, x, y)) continue;
-        const long long k = cell_of(L, x, y);
-        const uint16_t now = p.owner[k], was = p.prev[k];
-        const bool sn = now != FLUID, sw = was != FLUID;
-        if (sn != sw) {
-            // bit 0 of the node, bit i of the neighbour x + e_i
-            flag_bit(p.flags, k, 0, sn);
+// Nodes of row j that can be fluid nodes linked to a disk of radius r:
+// r < distance <= r + sqrt(2), bounded by the chords of radius r and r + 1.5.
+__device__ __forceinline__ bool annulus_ranges(const Centre &c, float r, int j, Ranges &R) {
+    int ao, bo, ai, bi;
+    if (!c.span(j, r + 1.5f, ao, bo)) return false;
+    if (!c.span(j, r - 0.01f, ai, bi)) {
+        R.a0 = ao;
+        R.b0 = bo;
+        R.a1 = 1;
+        R.b1 = 0;
+        return true;
+    }
+    R.a0 = ao;
+    R.b0 = ai + 2;
+    R.a1 = bi - 2;
+    R.b1 = bo;
+    if (R.a1 <= R.b0 + 1) {
+        R.b0 = R.b1;
+        R.a1 = 1;
+        R.b1 = 0;
+    }
+    return true;
+}
+
+// Rows a disk of radius r at Y0 (and Y1) can touch, with a margin of g.
+__device__ __forceinline__ void rows_of(double Y0, double Y1, double r, int g, int &j0, int &j1) {
+    j0 = (int)floor(fmin(Y0, Y1) - r) - g;
+    j1 = (int)ceil(fmax(Y0, Y1) + r) + g;
+}
+
+// Deals the nodes of rows j0..j1 (the ranges that rng(j, R) gives for each
+// row) to the lanes of the warp, U nodes per lane at a time: fetch(i, j, u)
+// is called for all U nodes of a lane first (to issue their loads together),
+// then process(u, ok) for each, on every lane of the warp together (ok is
+// false for items past the end and for nodes fetch rejected).
+template <int NB, class RF, class FF, class PF>
+__device__ __forceinline__ void warp_nodes_n(int j0, int j1, int lane, RF &&rng, FF &&fetch,
+                                             PF &&process) {
+    for (int jb = j0; jb <= j1; jb += 32) {
+        const int j = jb + lane;
+        Ranges R;
+        R.a0 = R.a1 = 0;
+        int n0 = 0, n1 = 0;
+        if (j <= j1 && rng(j, R)) {
+            n0 = R.b0 - R.a0 + 1;
+            n1 = R.b1 >= R.a1 ? R.b1 - R.a1 + 1 : 0;
+        }
+        int inc = n0 + n1;
 #pragma unroll
-            for (int i = 1; i < 9; i++) {
-                int xn, yn;
-                if (locate(L, x + cx(i), y + cy(i), xn, yn)) flag_bit(p.flags, cell_of(L, xn, yn), i, sn);
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(FULL, inc, o);
+            if (lane >= o) inc += v;
+        }
+        const int total = __shfl_sync(FULL, inc, 31);
+        const int excl = inc - (n0 + n1);
+        for (int e0 = 0; e0 < total; e0 += 32 * NB) {
+            bool ok[NB];
+#pragma unroll
+            for (int u = 0; u < NB; u++) {
+                const int e = e0 + u * 32 + lane;
+                // lane q holding item e: the last lane whose prefix is <= e
+                int q = 0;
+#pragma unroll
+                for (int step = 16; step > 0; step >>= 1) {
+                    const int c = q + step;
+                    const int ex = __shfl_sync(FULL, excl, c & 31);
+                    if (c < 32 && ex <= e) q = c;
+                }
+                const int qa0 = __shfl_sync(FULL, R.a0, q), qa1 = __shfl_sync(FULL, R.a1, q);
+                const int qn0 = __shfl_sync(FULL, n0, q), qex = __shfl_sync(FULL, excl, q);
+                const int tt = e - qex;
+                const int i = tt < qn0 ? qa0 + tt : qa1 + (tt - qn0);
+                ok[u] = e < total && fetch(i, jb + q, u);
             }
-        }
-        double sgn;
-        if (!sw && now == (uint16_t)s) {
-            sgn = 1.0;  // covered: its momentum goes to the solid
-        } else if (was == (uint16_t)s && !sn) {
-            C nf[9];
-            refill_node<P>(p, fnew, x, y, b, nf);
 #pragma unroll
-            for (int j = 0; j < 9; j++) st(static_cast<S *>(fnew) + j * L.plane + k, nf[j]);
-            sgn = -1.0;  // fresh: the solid gives it its momentum
-        } else {
-            continue;
+            for (int u = 0; u < NB; u++) process(u, ok[u]);
         }
-        double jx = 0.0, jy = 0.0;
-#pragma unroll
-        for (int j = 0; j < 9; j++) {
-            const double v = f64<P>(fnew, L.plane, j, k);
-            jx += cx(j) * v;
-            jy += cy(j) * v;
-        }
-        double ux, uy, dx, dy;
-        point_velocity(L, b.xn, b.yn, b.vxn, b.vyn, b.omn, (double)x, (double)y, ux, uy, dx, dy);
-        acc[0] += sgn * jx;
-        acc[1] += sgn * jy;
-        acc[2] += sgn * (dx * jy - dy * jx);
-    }
-    warp_sum(acc);
-    if (lane == 0) {
-        b.pend[0] = acc[0];
-        b.pend[1] = acc[1];
-        b.pend[2] = acc[2];
-        b.pend_t = t1;
     }
 }
 
-// ------------------------------------------------------------ phase F
+template <class RF, class FF, class PF>
+__device__ __forceinline__ void warp_nodes(int j0, int j1, int lane, RF &&rng, FF &&fetch,
+                                           PF &&process) {
+    warp_nodes_n<U>(j0, j1, lane, rng, fetch, process);
+}
+
+// --------------------------------------------------------- phase F
 
 __device__ __forceinline__ double net_weight(const StepParams &p, const DSolid &b) {
     const double M = b.rho_s * PI * b.r * b.r;
@@ -337,25 +270,34 @@ __device__ __forceinline__ double lub_mag(double kappa, double zeta, double gap)
     return kappa * q * q;
 }
 
-// Motion tf -> tf+1 of solid s; fg = Eq. 5 force and torque at tf.
-__device__ void move_solid(const StepParams &p, int s, long long tf, const double *fg) {
+__device__ __forceinline__ void set_next_centre(const Lattice &L, DSolid &b) {
+    b.xnw = wrap_coord(b.xn, L.nx, L.bc_x == LBM_PERIODIC);
+    b.ynw = wrap_coord(b.yn, L.ny, L.bc_y == LBM_PERIODIC);
+    b.xnf = (float)b.xn;
+    b.ynf = (float)b.yn;
+}
+
+// Motion t -> t+1 of solid s; fg = Eq. 5 force and torque at t (lane 0).
+// The lubrication sum runs over the lanes of the warp.
+__device__ void move_solid(const StepParams &p, int s, int lane, long long t, const double *fg) {
     DSolid &b = p.S[s];
     const Lattice &L = p.L;
     if (b.motion == LBM_PRESCRIBED) {
-        const double dt = (double)(tf + 1 - b.ta);
-        b.xn = __dadd_rn(b.xa, __dmul_rn(b.vx, dt));
-        b.yn = __dadd_rn(b.ya, __dmul_rn(b.vy, dt));
-        b.xnw = wrap_coord(b.xn, L.nx, L.bc_x == LBM_PERIODIC);
-        b.ynw = wrap_coord(b.yn, L.ny, L.bc_y == LBM_PERIODIC);
-        b.vxn = b.vx;
-        b.vyn = b.vy;
-        b.omn = b.om;
+        if (lane == 0) {
+            const double dt = (double)(t + 1 - b.ta);
+            b.xn = __dadd_rn(b.xa, __dmul_rn(b.vx, dt));
+            b.yn = __dadd_rn(b.ya, __dmul_rn(b.vy, dt));
+            set_next_centre(L, b);
+            b.vxn = b.vx;
+            b.vyn = b.vy;
+            b.omn = b.om;
+        }
         return;
     }
-    double flx = 0.0, fly = 0.0;
+    double fl[2] = {0.0, 0.0};
     if (p.lub > 0.0) {
         const double ka = net_weight(p, b);
-        for (int q = 0; q < p.nsolid; q++) {
+        for (int q = lane; q < p.nsolid; q += 32) {
             if (q == s) continue;
             const DSolid &B = p.S[q];
             const double dx = min_image(b.x - B.x, L.nx, L.bc_x == LBM_PERIODIC);
@@ -364,189 +306,500 @@ __device__ void move_solid(const StepParams &p, int s, long long tf, const doubl
             const double kb = net_weight(p, B);
             const double m = lub_mag(ka > kb ? ka : kb, p.lub, d - b.r - B.r);
             if (m > 0.0 && d > 0.0) {
-                flx += m * dx / d;
-                fly += m * dy / d;
+                fl[0] += m * dx / d;
+                fl[1] += m * dy / d;
             }
         }
-        if (L.bc_y == LBM_WALL) {
-            fly += lub_mag(ka, p.lub, (b.y - b.r) + 0.5);
-            fly -= lub_mag(ka, p.lub, ((double)L.ny - 0.5) - (b.y + b.r));
-        }
-        if (L.bc_x == LBM_WALL) {
-            flx += lub_mag(ka, p.lub, (b.x - b.r) + 0.5);
-            flx -= lub_mag(ka, p.lub, ((double)L.nx - 0.5) - (b.x + b.r));
+        warp_sum(fl);
+        if (lane == 0) {
+            if (L.bc_y == LBM_WALL) {
+                fl[1] += lub_mag(ka, p.lub, (b.y - b.r) + 0.5);
+                fl[1] -= lub_mag(ka, p.lub, ((double)L.ny - 0.5) - (b.y + b.r));
+            }
+            if (L.bc_x == LBM_WALL) {
+                fl[0] += lub_mag(ka, p.lub, (b.x - b.r) + 0.5);
+                fl[0] -= lub_mag(ka, p.lub, ((double)L.nx - 0.5) - (b.x + b.r));
+            }
         }
     }
+    if (lane != 0) return;
     const double M = b.rho_s * PI * b.r * b.r;
     const double I = 0.5 * M * b.r * b.r;
     const double buoy = 1.0 - p.rho0 / b.rho_s;
-    const double Fx = fg[0] + buoy * M * p.grav_x + flx;
-    const double Fy = fg[1] + buoy * M * p.grav_y + fly;
+    const double Fx = fg[0] + buoy * M * p.grav_x + fl[0];
+    const double Fy = fg[1] + buoy * M * p.grav_y + fl[1];
     const double vx1 = b.vx + Fx / M, vy1 = b.vy + Fy / M;
     b.xn = b.x + 0.5 * (b.vx + vx1);
     b.yn = b.y + 0.5 * (b.vy + vy1);
-    b.xnw = wrap_coord(b.xn, L.nx, L.bc_x == LBM_PERIODIC);
-    b.ynw = wrap_coord(b.yn, L.ny, L.bc_y == LBM_PERIODIC);
+    set_next_centre(L, b);
     b.vxn = vx1;
     b.vyn = vy1;
     b.omn = b.om + fg[2] / I;
 }
 
-// Forces at time tf from the populations f of time tf (Eq. 4-7).
-template <int P, bool LOCAL>
-__device__ void phase_forces(const StepParams &p, int s, int lane, long long tf, const void *f,
-                             uint16_t *queue) {
+// Population f_i of cell k in the link-math precision C.
+template <int P>
+__device__ __forceinline__ typename Prec<P>::C pop(const void *f, int plane, int i, int k) {
     using C = typename Prec<P>::C;
+    using S = typename Prec<P>::S;
+    C v = (C)ldc(static_cast<const S *>(f) + i * plane + k);
+    if (Prec<P>::dev) v += wgt<C>(i);
+    return v;
+}
+
+// Force record of time t for solid s (populations f of time t), then its
+// motion to t+1.  Per link (x_f fluid, x_f + e_i owned by s): f_i = f~_i(x_f),
+// the bounced f_bb = f_i - 6 w_i rho_w (e_i . v) with v the solid's velocity
+// at x_s = x_f + e_i / 2; Eq. 4 = e_i f_i - e_opp f_bb, Eq. 5 = (e_i - v) f_i
+// - (e_opp - v) f_bb, torque (x_s - R) x F (Eq. 7).  A candidate node's
+// flags, its 9 populations and its 8 neighbours' owners are loaded together.
+template <int P, bool LOCAL>
+__device__ void phase_forces(const StepParams &p, int s, int lane, long long t, const void *f) {
+    using C = typename Prec<P>::C;
+    using S = typename Prec<P>::S;
+    constexpr int UF = 2;
     DSolid &b = p.S[s];
     const Lattice &L = p.L;
+    const S *fs = static_cast<const S *>(f);
     const double X = b.x, Y = b.y;
-    const int xi = (int)floor(X), yi = (int)floor(Y);
-    const float fx = (float)(X - xi), fy = (float)(Y - yi);
-    const float r = (float)b.r;
-    const float lo2 = (r - 0.01f) * (r - 0.01f), hi2 = (r + 1.5f) * (r + 1.5f);
+    const Centre c(X, Y);
     const C vx = pick<C>(b.vx, b.vxf), vy = pick<C>(b.vy, b.vyf), om = pick<C>(b.om, b.omf);
     const C rho0 = pick<C>(p.rho0, p.rho0_f);
-    const Box bx = disk_box(X, Y, b.r, 1);
-    const int n = bx.w * bx.h;
+    const int plane = (int)L.plane;
+    const float r = (float)b.r;
+    int j0, j1;
+    rows_of(Y, Y, b.r, 3, j0, j1);
     double acc[6] = {0, 0, 0, 0, 0, 0};
-    for (int base = 0; base < n; base += ROUND) {
-        // link masks of this lane's cells in the round (8 bits per cell)
-        unsigned long long masks = 0;
-        int cnt = 0;
+    int ii[UF], jj[UF];
+    uint16_t fl[UF];
+    uint16_t own[UF][9];
+    S fv[UF][9];
+    warp_nodes_n<UF>(
+        j0, j1, lane, [&](int j, Ranges &R) { return annulus_ranges(c, r, j, R); },
+        [&](int iu, int j, int u) {
+            int x, y;
+            if (!locate(L, iu, j, x, y)) return false;
+            const int k = (int)cell_of(L, x, y);
+            ii[u] = iu;
+            jj[u] = j;
+            fl[u] = p.flags[k];
 #pragma unroll
-        for (int q = 0; q < CELLS_PER_LANE; q++) {
-            const int c = base + q * 32 + lane;
-            if (c >= n) continue;
-            int iu, ju, x, y;
-            box_cell(bx, c, iu, ju);
-            const float dx = (float)(iu - xi) - fx, dy = (float)(ju - yi) - fy;
-            const float d2 = dx * dx + dy * dy;
-            if (d2 <= lo2 || d2 > hi2) continue;  // outside the link annulus
-            if (!locate(L, iu, ju, x, y)) continue;
-            const uint16_t fl = p.flags[cell_of(L, x, y)];
-            if ((fl & 1u) || !(fl & 0x1FEu)) continue;
-            unsigned int m = 0;
+            for (int q = 0; q < 9; q++) fv[u][q] = fs[q * plane + k];
 #pragma unroll
             for (int i = 1; i < 9; i++) {
-                if (!((fl >> opp(i)) & 1u)) continue;  // x_f + e_i not solid
-                int xb, yb;
-                if (!locate(L, x + cx(i), y + cy(i), xb, yb)) continue;
-                if (p.owner[cell_of(L, xb, yb)] == (uint16_t)s) m |= 1u << (i - 1);
+                const int kb = neighbour(L, x, y, cx(i), cy(i));
+                own[u][i] = kb >= 0 ? p.owner[kb] : FLUID;
             }
-            masks |= (unsigned long long)m << (8 * q);
-            cnt += __popc(m);
-        }
-        int total;
-        int off = warp_exclusive_scan(cnt, total);
-        if (total == 0) continue;
-#pragma unroll
-        for (int q = 0; q < CELLS_PER_LANE; q++) {
-            unsigned int m = (unsigned int)(masks >> (8 * q)) & 0xFFu;
-            while (m) {
-                const int i = __ffs(m);
-                m &= m - 1;
-                queue[off++] = (uint16_t)(((q * 32 + lane) << 3) | (i - 1));
-            }
-        }
-        __syncwarp();
-        C part[6] = {0, 0, 0, 0, 0, 0};
-        for (int e = lane; e < total; e += 32) {
-            const int code = queue[e];
-            const int i = (code & 7) + 1;
-            int iu, ju, x, y;
-            box_cell(bx, base + (code >> 3), iu, ju);
-            locate(L, iu, ju, x, y);
-            const long long k = cell_of(L, x, y);
+            return true;
+        },
+        [&](int u, bool ok) {
+            const uint16_t m = fl[u];
+            if (!ok || (m & 1u) || !(m & 0x1FEu)) return;
+            const int iu = ii[u], j = jj[u];
             C rho_w = rho0;
             if (LOCAL) {
-                rho_w = 0;
+                C a = 0;
 #pragma unroll
-                for (int j = 0; j < 9; j++) rho_w += pop<P>(f, L.plane, j, k);
+                for (int q = 0; q < 9; q++) a += (C)cvt_s(fv[u][q]);
+                rho_w = Prec<P>::dev ? (C)1 + a : a;
             }
-            // x_s = x_f + e_i / 2 relative to R, from the unwrapped box coordinate
-            C dx, dy;
-            if (Prec<P>::dev) {
-                dx = (C)(iu - xi) + (C)(0.5f * cx(i)) - (C)fx;
-                dy = (C)(ju - yi) + (C)(0.5f * cy(i)) - (C)fy;
-            } else {
-                dx = (C)(((double)iu + 0.5 * cx(i)) - X);
-                dy = (C)(((double)ju + 0.5 * cy(i)) - Y);
-            }
-            const C ux = vx - om * dy, uy = vy + om * dx;
-            const C fi = pop<P>(f, L.plane, i, k);
-            const C fbb = fi - (C)6 * wgt<C>(i) * rho_w * ((C)cx(i) * ux + (C)cy(i) * uy);
-            // Eq. 4: e_i f_i - e_opp f_opp;  Eq. 5: (e_i - v) f_i - (e_opp - v) f_opp
-            const C cmx = (C)cx(i) * fi - (C)cx(opp(i)) * fbb;
-            const C cmy = (C)cy(i) * fi - (C)cy(opp(i)) * fbb;
-            const C gmx = ((C)cx(i) - ux) * fi - ((C)cx(opp(i)) - ux) * fbb;
-            const C gmy = ((C)cy(i) - uy) * fi - ((C)cy(opp(i)) - uy) * fbb;
-            part[0] += cmx;
-            part[1] += cmy;
-            part[2] += dx * cmy - dy * cmx;
-            part[3] += gmx;
-            part[4] += gmy;
-            part[5] += dx * gmy - dy * gmx;
-        }
+            C part[6] = {0, 0, 0, 0, 0, 0};
 #pragma unroll
-        for (int q = 0; q < 6; q++) acc[q] += (double)part[q];
-        __syncwarp();
-    }
+            for (int i = 1; i < 9; i++) {
+                if (!((m >> opp(i)) & 1u) || own[u][i] != (uint16_t)s) continue;
+                // x_s = x_f + e_i / 2 relative to R, from the unwrapped coordinate
+                C dx, dy;
+                if (Prec<P>::dev) {
+                    dx = (C)(iu - c.xi) + (C)(0.5f * cx(i)) - (C)c.fx;
+                    dy = (C)(j - c.yi) + (C)(0.5f * cy(i)) - (C)c.fy;
+                } else {
+                    dx = (C)(((double)iu + 0.5 * cx(i)) - X);
+                    dy = (C)(((double)j + 0.5 * cy(i)) - Y);
+                }
+                const C ux = vx - om * dy, uy = vy + om * dx;
+                C fi = (C)cvt_s(fv[u][i]);
+                if (Prec<P>::dev) fi += wgt<C>(i);
+                const C fbb = fi - (C)6 * wgt<C>(i) * rho_w * ((C)cx(i) * ux + (C)cy(i) * uy);
+                const C cmx = (C)cx(i) * fi - (C)cx(opp(i)) * fbb;
+                const C cmy = (C)cy(i) * fi - (C)cy(opp(i)) * fbb;
+                const C gmx = ((C)cx(i) - ux) * fi - ((C)cx(opp(i)) - ux) * fbb;
+                const C gmy = ((C)cy(i) - uy) * fi - ((C)cy(opp(i)) - uy) * fbb;
+                part[0] += cmx;
+                part[1] += cmy;
+                part[2] += dx * cmy - dy * cmx;
+                part[3] += gmx;
+                part[4] += gmy;
+                part[5] += dx * gmy - dy * gmx;
+            }
+#pragma unroll
+            for (int q = 0; q < 6; q++) acc[q] += (double)part[q];
+        });
     warp_sum(acc);
+    double fg[3] = {0.0, 0.0, 0.0};
     if (lane == 0) {
-        const bool booked = b.pend_t == tf;
-        const long long slot = tf % p.ring_len;
+        const bool booked = b.pend_t == t;
+        const long long slot = t % p.ring_len;
         double *rc = p.ring + (slot * 2 + 0) * p.nsolid * 3 + (long long)s * 3;
         double *rg = p.ring + (slot * 2 + 1) * p.nsolid * 3 + (long long)s * 3;
-        double fg[3];
         for (int q = 0; q < 3; q++) {
             const double pb = booked ? b.pend[q] : 0.0;
             rc[q] = acc[q] + pb;
             fg[q] = acc[3 + q] + pb;
             rg[q] = fg[q];
         }
-        move_solid(p, s, tf, fg);
     }
+    move_solid(p, s, lane, t, fg);
+}
+
+// ------------------------------------------------------- phases A, B, D
+
+// Pair test: can another disk own a node next to a node of disk s or its
+// link annulus at t or t+1 (centres closer than r_s + r_q + 3.5)?  Four
+// candidates per lane are loaded before they are tested.
+__device__ void phase_near(const StepParams &p, int s, int lane) {
+    DSolid &b = p.S[s];
+    const Lattice &L = p.L;
+    const bool px = L.bc_x == LBM_PERIODIC, py = L.bc_y == LBM_PERIODIC;
+    const float rb = (float)b.r, bx = b.xf, by = b.yf, bxn = b.xnf, byn = b.ynf;
+    const float nxf = (float)L.nx, nyf = (float)L.ny;
+    int near = 0;
+    for (int q0 = lane; q0 < p.nsolid; q0 += 32 * 4) {
+        float x[4], y[4], xn[4], yn[4], rq[4];
+        bool v[4];
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            const int q = q0 + 32 * u;
+            v[u] = q < p.nsolid && q != s;
+            const DSolid &B = p.S[v[u] ? q : s];
+            x[u] = B.xf;
+            y[u] = B.yf;
+            xn[u] = B.xnf;
+            yn[u] = B.ynf;
+            rq[u] = (float)B.r;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            if (!v[u]) continue;
+            const float lim = rb + rq[u] + 3.5f;
+            float dx = bx - x[u], dy = by - y[u], ex = bxn - xn[u], ey = byn - yn[u];
+            if (px) {
+                dx -= nxf * rintf(dx / nxf);
+                ex -= nxf * rintf(ex / nxf);
+            }
+            if (py) {
+                dy -= nyf * rintf(dy / nyf);
+                ey -= nyf * rintf(ey / nyf);
+            }
+            if (dx * dx + dy * dy < lim * lim || ex * ex + ey * ey < lim * lim) near = 1;
+        }
+    }
+    near = __any_sync(FULL, near);
+    if (lane == 0) b.near = near;
+}
+
+// Nodes of the old disk that the new disk leaves: owner s -> fluid.
+__device__ void phase_clear(const StepParams &p, int s, int lane) {
+    const DSolid &b = p.S[s];
+    const DiskTest in0(b.x, b.y, b.r), in1(b.xn, b.yn, b.r);
+    const Centre c0(b.x, b.y), c1(b.xn, b.yn);
+    const float rr = (float)b.r + 0.01f;
+    int j0, j1;
+    rows_of(b.y, b.yn, b.r, 1, j0, j1);
+    int kk[U];
+    uint16_t ow[U];
+    warp_nodes(
+        j0, j1, lane, [&](int j, Ranges &R) { return ring_ranges(c0, c1, rr, j, R); },
+        [&](int i, int j, int u) {
+            int x, y;
+            if (!in0(i, j) || in1(i, j) || !locate(p.L, i, j, x, y)) return false;
+            kk[u] = (int)cell_of(p.L, x, y);
+            ow[u] = p.owner[kk[u]];
+            return true;
+        },
+        [&](int u, bool ok) {
+            if (ok && ow[u] == (uint16_t)s) p.owner[kk[u]] = FLUID;
+        });
+}
+
+// Nodes of the new disk: owner := lowest id.  A disk that no other disk
+// comes near owns its interior already; only the nodes it newly covers
+// change.  A near disk re-claims its whole new chord in every row.
+__device__ void phase_set(const StepParams &p, int s, int lane) {
+    const DSolid &b = p.S[s];
+    const DiskTest in0(b.x, b.y, b.r), in1(b.xn, b.yn, b.r);
+    const Centre c0(b.x, b.y), c1(b.xn, b.yn);
+    const float rr = (float)b.r + 0.01f;
+    const bool full = b.near != 0;
+    int j0, j1;
+    if (full) rows_of(b.yn, b.yn, b.r, 1, j0, j1);
+    else rows_of(b.y, b.yn, b.r, 1, j0, j1);
+    int kk[U];
+    uint16_t ow[U];
+    warp_nodes(
+        j0, j1, lane,
+        [&](int j, Ranges &R) {
+            if (!full) return ring_ranges(c0, c1, rr, j, R);
+            R.a1 = 1;
+            R.b1 = 0;
+            return c1.span(j, rr, R.a0, R.b0);
+        },
+        [&](int i, int j, int u) {
+            int x, y;
+            if (!in1(i, j) || (!full && in0(i, j)) || !locate(p.L, i, j, x, y)) return false;
+            kk[u] = (int)cell_of(p.L, x, y);
+            ow[u] = p.owner[kk[u]];
+            return true;
+        },
+        [&](int u, bool ok) {
+            if (ok && ow[u] > (uint16_t)s) atomic_min_u16(p.owner + kk[u], (uint16_t)s);
+        });
+}
+
+// prev := owner on the ring; the solid's state becomes t+1.
+__device__ void phase_sync(const StepParams &p, int s, int lane) {
+    DSolid &b = p.S[s];
+    const DiskTest in0(b.x, b.y, b.r), in1(b.xn, b.yn, b.r);
+    const Centre c0(b.x, b.y), c1(b.xn, b.yn);
+    const float rr = (float)b.r + 0.01f;
+    int j0, j1;
+    rows_of(b.y, b.yn, b.r, 1, j0, j1);
+    int kk[U];
+    uint16_t ow[U], pv[U];
+    warp_nodes(
+        j0, j1, lane, [&](int j, Ranges &R) { return ring_ranges(c0, c1, rr, j, R); },
+        [&](int i, int j, int u) {
+            int x, y;
+            if (in0(i, j) == in1(i, j) || !locate(p.L, i, j, x, y)) return false;
+            kk[u] = (int)cell_of(p.L, x, y);
+            ow[u] = p.owner[kk[u]];
+            pv[u] = p.prev[kk[u]];
+            return true;
+        },
+        [&](int u, bool ok) {
+            if (ok && pv[u] != ow[u]) p.prev[kk[u]] = ow[u];
+        });
+    __syncwarp();
+    if (lane == 0) {
+        b.x = b.xn;
+        b.y = b.yn;
+        b.xw = b.xnw;
+        b.yw = b.ynw;
+        const double fxw = floor(b.xw), fyw = floor(b.yw);
+        b.xwi = (int)fxw;
+        b.ywi = (int)fyw;
+        b.xwr = (float)(b.xw - fxw);
+        b.ywr = (float)(b.yw - fyw);
+        b.vx = b.vxn;
+        b.vy = b.vyn;
+        b.om = b.omn;
+        b.vxf = (float)b.vxn;
+        b.vyf = (float)b.vyn;
+        b.omf = (float)b.omn;
+        b.xf = b.xnf;
+        b.yf = b.ynf;
+    }
+}
+
+// ------------------------------------------------------------ phase C
+
+constexpr int EVENTS = 256;  // covered/fresh nodes a warp can queue per solid and step
+
+// Ring of solid s: flags of nodes whose solidity changed (as they are found),
+// then the covered and fresh nodes (queued per warp in a fixed order and
+// handled one per lane).
+template <int P>
+__device__ void phase_changes(const StepParams &p, int s, int lane, long long t1, void *fnew,
+                              int *queue, int &qn) {
+    using C = typename Prec<P>::C;
+    using S = typename Prec<P>::S;
+    DSolid &b = p.S[s];
+    const Lattice &L = p.L;
+    const DiskTest in0(b.x, b.y, b.r), in1(b.xn, b.yn, b.r);
+    const Centre c0(b.x, b.y), c1(b.xn, b.yn);
+    const float rr = (float)b.r + 0.01f;
+    int j0, j1;
+    rows_of(b.y, b.yn, b.r, 1, j0, j1);
+    if (lane == 0) qn = 0;
+    __syncwarp();
+    int kk[U];
+    uint16_t ow[U], pv[U];
+    warp_nodes(
+        j0, j1, lane, [&](int j, Ranges &R) { return ring_ranges(c0, c1, rr, j, R); },
+        [&](int i, int j, int u) {
+            int x, y;
+            if (in0(i, j) == in1(i, j) || !locate(L, i, j, x, y)) return false;
+            kk[u] = (int)cell_of(L, x, y);
+            ow[u] = p.owner[kk[u]];
+            pv[u] = p.prev[kk[u]];
+            return true;
+        },
+        [&](int u, bool ok) {
+            bool covered = false, fresh = false;
+            const int k = kk[u];
+            if (ok) {
+                const uint16_t now = ow[u], was = pv[u];
+                const bool sn = now != FLUID, sw = was != FLUID;
+                if (sn != sw) {
+                    // bit 0 of the node, bit d of the neighbour x + e_d
+                    const int x = k % L.pitch, y = k / L.pitch;
+                    flag_bit(p.flags, k, 0, sn);
+#pragma unroll
+                    for (int d = 1; d < 9; d++) {
+                        int xn, yn;
+                        if (locate(L, x + cx(d), y + cy(d), xn, yn))
+                            flag_bit(p.flags, cell_of(L, xn, yn), d, sn);
+                    }
+                }
+                covered = !sw && now == (uint16_t)s;
+                fresh = was == (uint16_t)s && !sn;
+            }
+            // queue the covered and fresh nodes in lane order
+            __syncwarp();
+            const unsigned want = __ballot_sync(FULL, covered || fresh);
+            if (!want) return;
+            const int base = qn;
+            __syncwarp();
+            if (lane == 0) qn = base + __popc(want);
+            if (covered || fresh) {
+                const int pos = base + __popc(want & ((1u << lane) - 1u));
+                if (pos < EVENTS) queue[pos] = (k << 1) | (fresh ? 1 : 0);
+                else atomicOr(p.status, 8);
+            }
+            __syncwarp();
+        });
+    __syncwarp();
+    const int n = min(qn, EVENTS);
+    const S *fsn = static_cast<const S *>(fnew);
+    const int pl = (int)L.plane;
+    double acc[3] = {0.0, 0.0, 0.0};
+    // one queued node at a time, with the whole warp
+    for (int e = 0; e < n; e++) {
+        const int code = queue[e];
+        const int k = code >> 1;
+        const int x = k % L.pitch, y = k / L.pitch;
+        if (code & 1) {
+            // fresh: refill (Sec. IV.B).  Lane 3(i-1)+(d-1) tests x + d e_i.
+            bool use = false;
+            if (lane < 24) {
+                const int i = lane / 3 + 1, d = lane % 3 + 1;
+                const int kp = neighbour(L, x, y, d * cx(i), d * cy(i));
+                use = kp >= 0 && p.owner[kp] == FLUID && p.prev[kp] == FLUID;
+            }
+            const unsigned um = __ballot_sync(FULL, use);
+            unsigned d3 = 0, d2 = 0, d1 = 0;  // directions old-fluid up to distance 3, 2, 1
+#pragma unroll
+            for (int i = 1; i < 9; i++) {
+                const unsigned bits = (um >> (3 * (i - 1))) & 7u;
+                if (bits == 7u) d3 |= 1u << (i - 1);
+                if ((bits & 3u) == 3u) d2 |= 1u << (i - 1);
+                if (bits & 1u) d1 |= 1u << (i - 1);
+            }
+            unsigned dirs = 0;
+            int scheme = 0;  // 1: A1, 2: A2, 3: A3, 0: equilibrium
+            if (p.refill <= LBM_REFILL_A1 && d3) {
+                dirs = d3;
+                scheme = 1;
+            } else if (p.refill <= LBM_REFILL_A2 && d2) {
+                dirs = d2;
+                scheme = 2;
+            } else if (d1) {
+                dirs = d1;
+                scheme = 3;
+            }
+            if (scheme) {
+                // lane 3j + (d-1) sums f_j(x + d e_i) over the chosen directions
+                const int j = lane / 3, d = lane % 3 + 1;
+                const C wd = scheme == 1 ? (d == 1 ? (C)3 : (d == 2 ? (C)-3 : (C)1))
+                                         : (scheme == 2 ? (d == 1 ? (C)2 : (d == 2 ? (C)-1 : (C)0))
+                                                        : (d == 1 ? (C)1 : (C)0));
+                C sum = 0;
+                if (lane < 27 && wd != (C)0) {
+#pragma unroll
+                    for (int i = 1; i < 9; i++) {
+                        if (!((dirs >> (i - 1)) & 1u)) continue;
+                        sum += (C)ldc(fsn + j * pl + neighbour(L, x, y, d * cx(i), d * cy(i)));
+                    }
+                }
+                C v = wd * sum;
+                v += __shfl_down_sync(FULL, v, 1) + __shfl_down_sync(FULL, v, 2);
+                if (lane < 27 && lane % 3 == 0)
+                    st(static_cast<S *>(fnew) + j * pl + k, v / (C)__popc(dirs));
+            } else if (lane < 9) {
+                // no old-fluid neighbour: equilibrium at rho0 and the solid's velocity
+                double ux, uy, ddx, ddy;
+                point_velocity(L, b.xn, b.yn, b.vxn, b.vyn, b.omn, (double)x, (double)y, ux, uy,
+                               ddx, ddy);
+                const double eu = cx(lane) * ux + cy(lane) * uy, uu = ux * ux + uy * uy;
+                const double fe =
+                    p.rho0 * wgt<double>(lane) * (1.0 + 3.0 * eu + 4.5 * eu * eu - 1.5 * uu);
+                st(static_cast<S *>(fnew) + lane * pl + k,
+                   (C)(Prec<P>::dev ? fe - wgt<double>(lane) : fe));
+            }
+            __syncwarp();
+        }
+        // momentum of the node (post-collision if covered, refilled if fresh)
+        double jm[2] = {0.0, 0.0};
+        if (lane < 9) {
+            const double v = f64<P>(fnew, L.plane, lane, k);
+            jm[0] = cx(lane) * v;
+            jm[1] = cy(lane) * v;
+        }
+        warp_sum(jm);
+        if (lane == 0) {
+            const double sgn = (code & 1) ? -1.0 : 1.0;  // fresh: from the solid; covered: to it
+            double ux, uy, dx, dy;
+            point_velocity(L, b.xn, b.yn, b.vxn, b.vyn, b.omn, (double)x, (double)y, ux, uy, dx,
+                           dy);
+            acc[0] += sgn * jm[0];
+            acc[1] += sgn * jm[1];
+            acc[2] += sgn * (dx * jm[1] - dy * jm[0]);
+        }
+    }
+    if (lane == 0) {
+        b.pend[0] = acc[0];
+        b.pend[1] = acc[1];
+        b.pend[2] = acc[2];
+        b.pend_t = t1;
+    }
+    __syncwarp();
 }
 
 // ------------------------------------------------------------- kernel
 
 template <int P, bool LOCAL>
 __global__ void __launch_bounds__(SW_BLOCK) k_solids_step(const StepParams p, int mode) {
-    __shared__ uint16_t queue[WARPS][QMAX];
+    __shared__ int queue[WARPS][EVENTS];
+    __shared__ int qn[WARPS];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int gw = blockIdx.x * WARPS + wib, nw = gridDim.x * WARPS;
     const long long t = *p.t;
-    const bool adv = (mode & SOLIDS_ADVANCE) != 0;
-    const long long tf = adv ? t + 1 : t;
-    void *ff = (tf & 1) ? p.f1 : p.f0;  // populations of time tf
-    if (mode & SOLIDS_REMASK) {
-        for (int m = gw; m < p.nmoving; m += nw) {
-            const int s = p.moving[m];
-            if (solid_ok(p.S[s])) phase_clear(p, s, lane);
-            else if (lane == 0) atomicOr(p.status, 2);
-        }
-        grid_sync(p);
-        for (int s = gw; s < p.nsolid; s += nw)
-            if (solid_ok(p.S[s])) phase_set(p, s, lane);
-        grid_sync(p);
-        for (int m = gw; m < p.nmoving; m += nw) {
-            const int s = p.moving[m];
-            if (solid_ok(p.S[s])) phase_changes<P>(p, s, lane, tf, ff);
-        }
-        grid_sync(p);
-        for (int m = gw; m < p.nmoving; m += nw) {
-            const int s = p.moving[m];
-            if (solid_ok(p.S[s])) phase_sync(p, s, lane);
-        }
-        grid_sync(p);
-    }
+    const void *fcur = (t & 1) ? p.f1 : p.f0;  // populations of time t
+    void *fnew = ((t + 1) & 1) ? p.f1 : p.f0;  // populations of time t+1
     for (int s = gw; s < p.nsolid; s += nw) {
-        if (solid_ok(p.S[s])) phase_forces<P, LOCAL>(p, s, lane, tf, ff, queue[wib]);
+        if (solid_ok(p.S[s])) phase_forces<P, LOCAL>(p, s, lane, t, fcur);
         else if (lane == 0) atomicOr(p.status, 2);
     }
-    if (adv) {
-        grid_sync(p);
-        if (blockIdx.x == 0 && threadIdx.x == 0) *p.t = t + 1;
+    grid_sync(p);  // every block has read t: time advances
+    if (blockIdx.x == 0 && threadIdx.x == 0) *p.t = t + 1;
+    if (!(mode & SOLIDS_REMASK)) return;
+    for (int s = gw; s < p.nsolid; s += nw)
+        if (solid_ok(p.S[s])) phase_near(p, s, lane);
+    for (int m = gw; m < p.nmoving; m += nw) {
+        const int s = p.moving[m];
+        if (solid_ok(p.S[s])) phase_clear(p, s, lane);
+    }
+    grid_sync(p);
+    for (int s = gw; s < p.nsolid; s += nw)
+        if (solid_ok(p.S[s])) phase_set(p, s, lane);
+    grid_sync(p);
+    for (int m = gw; m < p.nmoving; m += nw) {
+        const int s = p.moving[m];
+        if (solid_ok(p.S[s])) phase_changes<P>(p, s, lane, t + 1, fnew, queue[wib], qn[wib]);
+    }
+    grid_sync(p);
+    for (int m = gw; m < p.nmoving; m += nw) {
+        const int s = p.moving[m];
+        if (solid_ok(p.S[s])) phase_sync(p, s, lane);
     }
 }
 

@@ -66,40 +66,13 @@ __device__ __forceinline__ unsigned short shfl_dn1(unsigned short v) {
     return (unsigned short)__shfl_down_sync(0xffffffffu, (int)v, 1);
 }
 
-// Velocity of the wall or solid that population i arriving at (x, y) was
-// bounced from (its source x - e_i is solid or outside the domain).
-template <class C>
-__device__ __forceinline__ void source_velocity(const StepParams &p, int x, int y, int i, C &vx,
-                                                C &vy) {
-    const Lattice &L = p.L;
-    const int sx = x - cx(i), sy = y - cy(i);
-    vx = 0;
-    vy = 0;
-    if (L.bc_y == LBM_WALL && (sy < 0 || sy >= L.ny)) {
-        vx = (C)(sy < 0 ? p.wall_ux0 : p.wall_ux1);  // channel walls move along x
-        return;
-    }
-    int xs, ys;
-    if (!locate(L, sx, sy, xs, ys)) return;  // resting wall (or open column) in x
-    const uint16_t s = p.owner[cell_of(L, xs, ys)];
-    if (s == FLUID) return;
-    const DSolid &b = p.S[s];
-    vx = pick<C>(b.vx, b.vxf);
-    vy = pick<C>(b.vy, b.vyf);
-    if (b.omf != 0.0f) {
-        const double om = b.om;
-        // boundary point halfway between x and x - e_i, relative to R
-        const C dx = (C)near_image((double)x - 0.5 * cx(i) - b.xw, L.nx, L.bc_x == LBM_PERIODIC);
-        const C dy = (C)near_image((double)y - 0.5 * cy(i) - b.yw, L.ny, L.bc_y == LBM_PERIODIC);
-        vx -= (C)om * dy;
-        vy += (C)om * dx;
-    }
-}
-
-// Replace the bounced populations of node (x, y) (rare path).
+// Replace the bounced populations of node (x, y) (rare path): population i,
+// whose source x - e_i is a wall or a solid, becomes f~_opp(x) + 6 w_i rho_w
+// (e_i . v) with v the wall's or solid's velocity at x - e_i / 2 (Sec. III.A;
+// the moving-wall term).
 template <int P, bool LOCAL>
 __device__ __forceinline__ void bounce(const StepParams &p, const typename Raw<P>::R *fin, int x,
-                                    int y, uint16_t fl, typename Prec<P>::C (&g)[9]) {
+                                       int y, uint16_t fl, typename Prec<P>::C (&g)[9]) {
     using C = typename Prec<P>::C;
     const Lattice &L = p.L;
     const int k = y * L.pitch + x;
@@ -114,8 +87,41 @@ __device__ __forceinline__ void bounce(const StepParams &p, const typename Raw<P
 #pragma unroll
     for (int i = 1; i < 9; i++) {
         if (!((fl >> i) & 1u)) continue;
-        C vx, vy;
-        source_velocity<C>(p, x, y, i, vx, vy);
+        const int sx = x - cx(i), sy = y - cy(i);
+        C vx = 0, vy = 0;
+        int xs, ys;
+        if (L.bc_y == LBM_WALL && (sy < 0 || sy >= L.ny)) {
+            vx = pick<C>(sy < 0 ? p.wall_ux0 : p.wall_ux1, (float)(sy < 0 ? p.wall_ux0 : p.wall_ux1));
+        } else if (locate(L, sx, sy, xs, ys)) {
+            const uint16_t o = p.owner[cell_of(L, xs, ys)];
+            if (o != FLUID) {
+                const DSolid &b = p.S[o];
+                vx = pick<C>(b.vx, b.vxf);
+                vy = pick<C>(b.vy, b.vyf);
+                if (b.omf != 0.0f) {
+                    // x - e_i / 2 relative to R, nearest periodic image
+                    C dx, dy;
+                    if (Prec<P>::dev) {
+                        dx = (C)(x - b.xwi) - (C)(0.5f * cx(i)) - (C)b.xwr;
+                        dy = (C)(y - b.ywi) - (C)(0.5f * cy(i)) - (C)b.ywr;
+                    } else {
+                        dx = (C)((double)x - 0.5 * cx(i) - b.xw);
+                        dy = (C)((double)y - 0.5 * cy(i) - b.yw);
+                    }
+                    if (L.bc_x == LBM_PERIODIC) {
+                        if (dx > (C)(0.5 * L.nx)) dx -= (C)L.nx;
+                        else if (dx < (C)(-0.5 * L.nx)) dx += (C)L.nx;
+                    }
+                    if (L.bc_y == LBM_PERIODIC) {
+                        if (dy > (C)(0.5 * L.ny)) dy -= (C)L.ny;
+                        else if (dy < (C)(-0.5 * L.ny)) dy += (C)L.ny;
+                    }
+                    const C om = pick<C>(b.om, b.omf);
+                    vx -= om * dy;
+                    vy += om * dx;
+                }
+            }
+        }
         const C back = cvt(fin[opp(i) * plane + k]);
         g[i] = back + (C)6 * wgt<C>(i) * rho_w * ((C)cx(i) * vx + (C)cy(i) * vy);
     }

@@ -35,7 +35,6 @@ struct lbm_ctx {
     long long *t_d = nullptr;
     int *status_d = nullptr;
     unsigned int *bar_d = nullptr;  // grid barrier of the per-solid kernel
-    bool record_ready = false;      // force record of time t and motion t -> t+1 computed
     int64_t t = 0;
     int64_t ring_base = 0; // first step whose force record is valid
     std::string err;
@@ -100,7 +99,7 @@ StepParams params(const lbm_ctx *c) {
     p.moving = c->moving_d;
     p.nmoving = (int)c->moving.size();
     p.ring = c->ring;
-    p.ring_len = g.force_ring + 1;  // one extra slot for the record computed ahead
+    p.ring_len = g.force_ring + 1;
     p.t = c->t_d;
     p.status = c->status_d;
     p.tau = g.tau;
@@ -177,15 +176,9 @@ lbm_status upload_moving(lbm_ctx *c) {
     return LBM_OK;
 }
 
-// One step t -> t+1 on the context's stream: [forces at t, once] ->
-// advection-collision -> per-solid work (re-rasterisation, forces at t+1,
-// motion, t += 1).
+// One step t -> t+1: the advection-collision kernel, then the per-solid work
+// (link sums and force record of time t, motion, t += 1, re-rasterisation).
 lbm_status enqueue_step(lbm_ctx *c, const StepParams &p, bool timed) {
-    if (!c->record_ready && p.nsolid > 0) {
-        CK(c, gbm::launch_solids(p, 0, c->stream));
-        c->launches++;
-    }
-    c->record_ready = true;
     if (timed) {
         if (c->ev_used + 2 > c->ev.size()) {
             for (int k = 0; k < 2; k++) {
@@ -201,12 +194,8 @@ lbm_status enqueue_step(lbm_ctx *c, const StepParams &p, bool timed) {
         CK(c, cudaEventRecord(c->ev[c->ev_used + 1], c->stream));
         c->ev_used += 2;
     }
-    if (p.nsolid > 0) {
-        const int mode = gbm::SOLIDS_ADVANCE | (p.nmoving > 0 ? gbm::SOLIDS_REMASK : 0);
-        CK(c, gbm::launch_solids(p, mode, c->stream));
-    } else {
-        CK(c, gbm::launch_tick(p, c->stream));
-    }
+    if (p.nsolid > 0) CK(c, gbm::launch_solids(p, p.nmoving > 0 ? gbm::SOLIDS_REMASK : 0, c->stream));
+    else CK(c, gbm::launch_tick(p, c->stream));
     c->launches += 2;
     return LBM_OK;
 }
@@ -391,9 +380,16 @@ lbm_status lbm_add_solid(lbm_ctx *c, const lbm_disk *d, int32_t *id_out) {
     s.rho_s = d->rho_s;
     s.ta = c->t;
     s.pend_t = -1;
+    s.near = 1;  // until the first pair test: assume a neighbour
     s.vxf = (float)d->vx;
     s.vyf = (float)d->vy;
     s.omf = (float)d->omega;
+    s.xf = s.xnf = (float)d->cx;
+    s.yf = s.ynf = (float)d->cy;
+    s.xwi = (int)std::floor(s.xw);
+    s.ywi = (int)std::floor(s.yw);
+    s.xwr = (float)(s.xw - std::floor(s.xw));
+    s.ywr = (float)(s.yw - std::floor(s.yw));
     s.motion = d->motion;
     const int id = c->nsolid;
     CK(c, cudaMemcpyAsync(c->solids + id, &s, sizeof s, cudaMemcpyHostToDevice, c->stream));
@@ -406,7 +402,6 @@ lbm_status lbm_add_solid(lbm_ctx *c, const lbm_disk *d, int32_t *id_out) {
     c->launches += 2;
     CK(c, cudaStreamSynchronize(c->stream));
     c->ring_base = c->t;  // the record layout changed with nsolid
-    c->record_ready = false;
     if (id_out) *id_out = id;
     return LBM_OK;
 }
@@ -583,7 +578,6 @@ lbm_status lbm_set_populations(lbm_ctx *c, const double *f, int32_t on_device) {
     if (on_device) {
         CK(c, gbm::launch_import_populations(p, f, c->stream));
         c->launches++;
-        c->record_ready = false;
         return LBM_OK;
     }
     lbm_status st = ensure_scratch(c, n * sizeof(double));
@@ -591,7 +585,6 @@ lbm_status lbm_set_populations(lbm_ctx *c, const double *f, int32_t on_device) {
     CK(c, cudaMemcpyAsync(c->scratch, f, n * sizeof(double), cudaMemcpyHostToDevice, c->stream));
     CK(c, gbm::launch_import_populations(p, static_cast<const double *>(c->scratch), c->stream));
     c->launches++;
-    c->record_ready = false;
     CK(c, cudaStreamSynchronize(c->stream));
     return LBM_OK;
 }
@@ -655,7 +648,6 @@ lbm_status lbm_set_solid(lbm_ctx *c, int32_t id, const double *state) {
     s.omf = (float)state[4];
     CK(c, cudaMemcpyAsync(c->solids + id, &s, sizeof s, cudaMemcpyHostToDevice, c->stream));
     drop_graph(c);
-    c->record_ready = false;
     c->is_moving[id] = translates(s) ? 1 : 0;
     return upload_moving(c);
 }

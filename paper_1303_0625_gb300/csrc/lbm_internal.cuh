@@ -33,7 +33,7 @@ __host__ __device__ constexpr C wgt(int i) {
     return i == 0 ? C(4) / C(9) : (i <= 4 ? C(1) / C(9) : C(1) / C(36));
 }
 
-// Per-solid record on the device (array of structs, 208 bytes).
+// Per-solid record on the device (array of structs).
 struct DSolid {
     double xa, ya;     // position when added (prescribed motion)
     double x, y;       // centre R(t)
@@ -47,7 +47,11 @@ struct DSolid {
     long long pend_t;  // time whose force record carries pend
     long long ta;      // time when added
     float vxf, vyf, omf;  // FP32 copies of vx, vy, om for the FP32 kernels
+    float xf, yf, xnf, ynf;  // FP32 copies of x, y, xn, yn for the pair test
+    int xwi, ywi;      // integer part of (xw, yw) ...
+    float xwr, ywr;    // ... and the FP32 remainder, for FP32 lever arms
     int motion;
+    int near;          // another disk may share a node with this one at t or t+1
 };
 
 struct Lattice {
@@ -265,11 +269,12 @@ __device__ __forceinline__ long long cell_of(const Lattice &L, int x, int y) {
 
 // k_stream_collide.cu
 cudaError_t launch_stream_collide(const StepParams &p, cudaStream_t st);
-// k_solid_step.cu: per-solid work of a step in one cooperative launch.
-// mode bits: SOLIDS_REMASK (re-rasterise the moving solids, t -> t+1),
-// SOLIDS_ADVANCE (forces at t+1 and t += 1; otherwise forces at t).
-constexpr int SOLIDS_REMASK = 1, SOLIDS_ADVANCE = 2;
+// k_solid_step.cu: per-solid work of a step in one cooperative launch (force
+// record of time t, motion, t += 1; with SOLIDS_REMASK also re-rasterisation
+// of the moving solids).
+constexpr int SOLIDS_REMASK = 1;
 cudaError_t launch_solids(const StepParams &p, int mode, cudaStream_t st);
+
 // k_solids.cu
 cudaError_t launch_tick(const StepParams &p, cudaStream_t st);
 cudaError_t launch_init_populations(const StepParams &p, cudaStream_t st);

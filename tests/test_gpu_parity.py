@@ -129,7 +129,8 @@ def test_graph_replay_matches_direct_launches():
     g2.set_graph(8)
     a = g1.step_record(40)
     b = g2.step_record(40)
-    assert np.array_equal(a, b)
+    # the link sums are FP64 atomics, whose order differs between runs
+    assert np.abs(a - b).max() <= 1e-13 * np.abs(a).max()
     assert np.array_equal(g1.get_f(), g2.get_f())
 
 
