@@ -22,13 +22,12 @@
 // before it processes them; every decision is taken by the exact test.  A
 // disk that comes within a node of another one ("near") also re-claims its
 // whole interior in phase B, which keeps the lowest-id rule exact where disks
-// overlap; a disk that is not near any other skips the owner look-ups of its
-// links (its solid neighbours can only be its own nodes).
+// overlap.
 //
-// Precision: in the FP32/FP16 modes the per-link products are FP32 and each
-// lane's batch of links is added into FP64; all further accumulation (the
-// force and torque reduction) is FP64 in a fixed lane order and tree.  The
-// FP64 mode is FP64 throughout.
+// Precision: in the FP32/FP16 modes the per-link products and each lane's
+// running sum over its links (a few dozen at most) are FP32; the reduction
+// across the lanes of the solid, the booked momenta and the motion are FP64
+// in a fixed lane order and tree.  The FP64 mode is FP64 throughout.
 #include "lbm_internal.cuh"
 
 namespace gbm {
@@ -369,7 +368,7 @@ __device__ void phase_forces(const StepParams &p, int s, int lane, long long t, 
     const float r = (float)b.r;
     int j0, j1;
     rows_of(Y, Y, b.r, 3, j0, j1);
-    double acc[6] = {0, 0, 0, 0, 0, 0};
+    C lacc[6] = {0, 0, 0, 0, 0, 0};  // this lane's links
     int ii[UF], jj[UF];
     uint16_t fl[UF];
     uint16_t own[UF][9];
@@ -403,7 +402,6 @@ __device__ void phase_forces(const StepParams &p, int s, int lane, long long t, 
                 for (int q = 0; q < 9; q++) a += (C)cvt_s(fv[u][q]);
                 rho_w = Prec<P>::dev ? (C)1 + a : a;
             }
-            C part[6] = {0, 0, 0, 0, 0, 0};
 #pragma unroll
             for (int i = 1; i < 9; i++) {
                 if (!((m >> opp(i)) & 1u) || own[u][i] != (uint16_t)s) continue;
@@ -424,16 +422,17 @@ __device__ void phase_forces(const StepParams &p, int s, int lane, long long t, 
                 const C cmy = (C)cy(i) * fi - (C)cy(opp(i)) * fbb;
                 const C gmx = ((C)cx(i) - ux) * fi - ((C)cx(opp(i)) - ux) * fbb;
                 const C gmy = ((C)cy(i) - uy) * fi - ((C)cy(opp(i)) - uy) * fbb;
-                part[0] += cmx;
-                part[1] += cmy;
-                part[2] += dx * cmy - dy * cmx;
-                part[3] += gmx;
-                part[4] += gmy;
-                part[5] += dx * gmy - dy * gmx;
+                lacc[0] += cmx;
+                lacc[1] += cmy;
+                lacc[2] += dx * cmy - dy * cmx;
+                lacc[3] += gmx;
+                lacc[4] += gmy;
+                lacc[5] += dx * gmy - dy * gmx;
             }
-#pragma unroll
-            for (int q = 0; q < 6; q++) acc[q] += (double)part[q];
         });
+    double acc[6];
+#pragma unroll
+    for (int q = 0; q < 6; q++) acc[q] = (double)lacc[q];
     warp_sum(acc);
     double fg[3] = {0.0, 0.0, 0.0};
     if (lane == 0) {
@@ -453,35 +452,43 @@ __device__ void phase_forces(const StepParams &p, int s, int lane, long long t, 
 
 // ------------------------------------------------------- phases A, B, D
 
-// Pair test: can another disk own a node next to a node of disk s or its
-// link annulus at t or t+1 (centres closer than r_s + r_q + 3.5)?  Four
-// candidates per lane are loaded before they are tested.
-__device__ void phase_near(const StepParams &p, int s, int lane) {
-    DSolid &b = p.S[s];
+// Pair test: can another disk share a node with disk s at t or t+1 (centres
+// closer than r_s + r_q + 1.5)?  The centres are staged in shared memory one
+// tile at a time; every warp of the block tests its own disk against them.
+// Called by whole blocks: base + warp index is the disk (may be >= nsolid).
+constexpr int NEAR_TILE = 1024;
+__device__ void phase_near_block(const StepParams &p, int base, float4 *pos, float *rad) {
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int s = base + wib;
     const Lattice &L = p.L;
     const bool px = L.bc_x == LBM_PERIODIC, py = L.bc_y == LBM_PERIODIC;
-    const float rb = (float)b.r, bx = b.xf, by = b.yf, bxn = b.xnf, byn = b.ynf;
     const float nxf = (float)L.nx, nyf = (float)L.ny;
+    const bool mine = s < p.nsolid;
+    float rb = 0.f, bx = 0.f, by = 0.f, bxn = 0.f, byn = 0.f;
+    if (mine) {
+        const DSolid &b = p.S[s];
+        rb = (float)b.r;
+        bx = b.xf;
+        by = b.yf;
+        bxn = b.xnf;
+        byn = b.ynf;
+    }
     int near = 0;
-    for (int q0 = lane; q0 < p.nsolid; q0 += 32 * 4) {
-        float x[4], y[4], xn[4], yn[4], rq[4];
-        bool v[4];
-#pragma unroll
-        for (int u = 0; u < 4; u++) {
-            const int q = q0 + 32 * u;
-            v[u] = q < p.nsolid && q != s;
-            const DSolid &B = p.S[v[u] ? q : s];
-            x[u] = B.xf;
-            y[u] = B.yf;
-            xn[u] = B.xnf;
-            yn[u] = B.ynf;
-            rq[u] = (float)B.r;
+    for (int t0 = 0; t0 < p.nsolid; t0 += NEAR_TILE) {
+        const int n = min(NEAR_TILE, p.nsolid - t0);
+        __syncthreads();
+        for (int q = threadIdx.x; q < n; q += blockDim.x) {
+            const DSolid &B = p.S[t0 + q];
+            pos[q] = make_float4(B.xf, B.yf, B.xnf, B.ynf);
+            rad[q] = (float)B.r;
         }
-#pragma unroll
-        for (int u = 0; u < 4; u++) {
-            if (!v[u]) continue;
-            const float lim = rb + rq[u] + 3.5f;
-            float dx = bx - x[u], dy = by - y[u], ex = bxn - xn[u], ey = byn - yn[u];
+        __syncthreads();
+        if (!mine) continue;
+        for (int q = lane; q < n; q += 32) {
+            if (t0 + q == s) continue;
+            const float4 c = pos[q];
+            const float lim = rb + rad[q] + 1.5f;
+            float dx = bx - c.x, dy = by - c.y, ex = bxn - c.z, ey = byn - c.w;
             if (px) {
                 dx -= nxf * rintf(dx / nxf);
                 ex -= nxf * rintf(ex / nxf);
@@ -494,7 +501,7 @@ __device__ void phase_near(const StepParams &p, int s, int lane) {
         }
     }
     near = __any_sync(FULL, near);
-    if (lane == 0) b.near = near;
+    if (mine && lane == 0) p.S[s].near = near;
 }
 
 // Nodes of the old disk that the new disk leaves: owner s -> fluid.
@@ -770,6 +777,8 @@ template <int P, bool LOCAL>
 __global__ void __launch_bounds__(SW_BLOCK) k_solids_step(const StepParams p, int mode) {
     __shared__ int queue[WARPS][EVENTS];
     __shared__ int qn[WARPS];
+    __shared__ float4 near_pos[NEAR_TILE];
+    __shared__ float near_rad[NEAR_TILE];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int gw = blockIdx.x * WARPS + wib, nw = gridDim.x * WARPS;
     const long long t = *p.t;
@@ -782,8 +791,8 @@ __global__ void __launch_bounds__(SW_BLOCK) k_solids_step(const StepParams p, in
     grid_sync(p);  // every block has read t: time advances
     if (blockIdx.x == 0 && threadIdx.x == 0) *p.t = t + 1;
     if (!(mode & SOLIDS_REMASK)) return;
-    for (int s = gw; s < p.nsolid; s += nw)
-        if (solid_ok(p.S[s])) phase_near(p, s, lane);
+    for (int base = blockIdx.x * WARPS; base < p.nsolid; base += nw)
+        phase_near_block(p, base, near_pos, near_rad);
     for (int m = gw; m < p.nmoving; m += nw) {
         const int s = p.moving[m];
         if (solid_ok(p.S[s])) phase_clear(p, s, lane);
