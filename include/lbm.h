@@ -45,7 +45,9 @@ typedef enum {
 enum {
     LBM_PERIODIC = 0,
     LBM_WALL = 1, /* half-way bounce-back wall half a spacing outside the first/last node */
-    LBM_OPEN = 2, /* x only: equilibrium Poiseuille inlet column x=0, copy outlet column x=nx-1 */
+    LBM_OPEN = 2, /* x only: parabolic velocity inlet column x=0 (peak inflow_umax), pressure
+                   * outlet column x=nx-1 (density rho0), both by non-equilibrium
+                   * extrapolation from the inner neighbour column */
 };
 /* storage / arithmetic precision */
 enum {
@@ -208,9 +210,10 @@ lbm_status lbm_get_timing(lbm_ctx *ctx, double *stream_collide_ms, int64_t *laun
 int64_t lbm_launch_count(const lbm_ctx *ctx);
 
 /* Nodes per thread of the advection-collision kernel, as the width of one
- * population word: 0 = 16 bytes (default), 1 = 8 bytes, 2 = 4 bytes.  Results
- * are identical for every variant; only the speed differs.  LBM_EINVAL for
- * other values. */
+ * population word: 0 = 16 bytes (default), 1 = 8 bytes, 2 = 4 bytes.  Every
+ * variant evaluates the same expressions; the compiler may fuse multiply-adds
+ * differently in each, so results agree to the storage precision's rounding
+ * (not always bit for bit).  LBM_EINVAL for other values. */
 lbm_status lbm_set_kernel_variant(lbm_ctx *ctx, int32_t variant);
 int32_t lbm_kernel_variant(const lbm_ctx *ctx);
 
@@ -219,6 +222,91 @@ int32_t lbm_kernel_variant(const lbm_ctx *ctx);
  * (stored in *best when not NULL).  The simulation advances by 3 (1 + steps)
  * steps; results do not depend on the variant.  Waits for the stream. */
 lbm_status lbm_autotune(lbm_ctx *ctx, int32_t steps, int32_t *best);
+
+/* ------------------------------------------------------------------ batches
+ *
+ * A batch runs many independent domains ("cases", e.g. a sweep of channels
+ * with one fixed cylinder each) as one set of launches per step: one
+ * advection-collision launch over the tiles of every active case, one launch
+ * for the force records of every solid of every active case, and every
+ * `every` steps one launch that tests convergence and retires cases.  The
+ * method is the paper's (Eq. 1-8) applied to each case on its own; batching
+ * is an execution scheme the paper does not have.  Each case is an lbm_ctx
+ * that the batch owns; its results are read through the lbm_ctx calls above.
+ *
+ * Limits: every case has the same precision, rho_w_mode and device; solids
+ * in a batch rest (zero velocity, prescribed), so no node changes type. */
+typedef struct lbm_batch lbm_batch; /* opaque; owns its cases */
+
+/* case states */
+enum {
+    LBM_CASE_ACTIVE = 0,    /* still stepping */
+    LBM_CASE_CONVERGED = 1, /* drag moved by less than tol (relative) over `every` steps */
+    LBM_CASE_CAPPED = 2,    /* reached max_steps without converging */
+    LBM_CASE_UNSTABLE = 3,  /* a status bit was raised or the drag became non-finite */
+};
+
+/* Create ncase cases from configs[0..ncase-1] (lbm_create's rules for each;
+ * precision, rho_w_mode and device equal for all, else LBM_EINVAL).  The
+ * batch runs on configs[0].stream (or a stream it creates); the other
+ * configs' stream fields are ignored.  Convergence defaults: every = 100,
+ * tol = 1e-7, max_steps = 2000000. */
+lbm_status lbm_batch_create(const lbm_config *configs, int32_t ncase, lbm_batch **out);
+lbm_status lbm_batch_destroy(lbm_batch *b);
+
+/* Number of cases, and a borrowed handle of case k (valid until
+ * lbm_batch_destroy).  Reading calls (lbm_forces, lbm_fields, lbm_time,
+ * lbm_get_populations, lbm_get_owner, lbm_get_solids, lbm_links) and
+ * lbm_set_populations work on it; calls that step it or change its solids
+ * return LBM_EINVAL (use the lbm_batch_* calls). */
+int32_t lbm_batch_size(const lbm_batch *b);
+lbm_status lbm_batch_case(lbm_batch *b, int32_t k, lbm_ctx **ctx);
+
+/* Add a resting disk (vx = vy = omega = 0, LBM_PRESCRIBED; else LBM_EINVAL)
+ * to case k; lbm_add_solid's rules otherwise.  Its id within the case is
+ * stored in *id when not NULL. */
+lbm_status lbm_batch_add_solid(lbm_batch *b, int32_t k, const lbm_disk *d, int32_t *id);
+
+/* Convergence test: every `every` steps of the batch (>= 1), an active case
+ * whose drag D (x component of the Eq. 5 force summed over its solids, from
+ * its latest record) satisfies |D - D_prev| < tol |D|, D_prev being the drag
+ * at the previous test, becomes LBM_CASE_CONVERGED and stops stepping; one
+ * that has run max_steps steps becomes LBM_CASE_CAPPED.  A case without
+ * solids has D = 0 and never converges.  The drag history restarts. */
+lbm_status lbm_batch_set_convergence(lbm_batch *b, int32_t every, double tol, int64_t max_steps);
+
+/* Advance every active case by up to `steps` steps (fewer when all cases
+ * retire first; the test runs whenever the batch has done `every` steps since
+ * the previous one).  *nactive (when not NULL) receives the number of active
+ * cases afterwards.  Waits for the stream. */
+lbm_status lbm_batch_run(lbm_batch *b, int64_t steps, int32_t *nactive);
+
+/* Per-case results after the last lbm_batch_run, host arrays of ncase (any
+ * may be NULL): state (LBM_CASE_*), steps run, drag at the latest test (NaN
+ * before the first). */
+lbm_status lbm_batch_state(lbm_batch *b, int32_t *state, int64_t *steps, double *drag);
+
+/* Launch policy.  variant as for lbm_set_kernel_variant; persistent = 1 runs
+ * the fused kernel as one resident block per slot walking the tile list, 0
+ * as one block per tile.  graph = 1 captures the `every` steps between two
+ * tests (and the test) into one CUDA graph (default 1). */
+lbm_status lbm_batch_set_launch(lbm_batch *b, int32_t variant, int32_t persistent, int32_t graph);
+lbm_status lbm_batch_get_launch(const lbm_batch *b, int32_t *variant, int32_t *persistent);
+
+/* Autotuner: run 1 + steps real steps with each (variant, persistent) pair,
+ * timing the fused kernel with CUDA events, and keep the fastest (stored in
+ * best[0..1] when not NULL).  The batch advances by 6 (1 + steps) steps and
+ * the drag history restarts.  Waits for the stream. */
+lbm_status lbm_batch_autotune(lbm_batch *b, int32_t steps, int32_t *best);
+
+/* Timing of the fused kernel as for lbm_set_timing / lbm_get_timing. */
+lbm_status lbm_batch_set_timing(lbm_batch *b, int32_t enable);
+lbm_status lbm_batch_get_timing(lbm_batch *b, double *stream_collide_ms, int64_t *launches);
+
+/* Kernel launches issued by the batch (all kernels), and the text of its
+ * last error (owned by the library). */
+int64_t lbm_batch_launch_count(const lbm_batch *b);
+const char *lbm_batch_last_error(const lbm_batch *b);
 
 #ifdef __cplusplus
 }

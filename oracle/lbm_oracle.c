@@ -45,7 +45,16 @@
  *     -rho u of its refilled populations; torque about R(t+1);
  *   - refill: A1 = 3 f(x+e) - 3 f(x+2e) + f(x+3e) along every direction whose
  *     three nodes are old fluid; else A2 = 2 f(x+e) - f(x+2e); else A3 =
- *     neighbour average; else equilibrium at rho0 and the solid velocity.
+ *     neighbour average; else equilibrium at rho0 and the solid velocity;
+ *   - open channel (bc_x = ORA_OPEN, not part of the paper's method): after
+ *     collision the inlet column x = 0 and the outlet column x = nx-1 take the
+ *     non-equilibrium extrapolation of their inner neighbour n (x = 1 and
+ *     x = nx-2): f_b = feq(rho_b, u_b) + (f_n - feq(rho_n, u_n)), with f_n
+ *     post-collision and rho_n, u_n its moments; the inlet imposes the
+ *     parabolic velocity u_b = (u_in(y), 0) with rho_b = rho_n, the outlet
+ *     the density rho_b = rho0 with u_b = u_n.  Where the neighbour is solid
+ *     the inlet is feq(rho0, u_in) and the outlet updates as a node whose
+ *     outside neighbours are a resting wall.
  */
 #include <math.h>
 #include <stdint.h>
@@ -65,7 +74,7 @@ static const double W[9] = {4.0 / 9.0,  1.0 / 9.0,  1.0 / 9.0,  1.0 / 9.0, 1.0 /
 
 #define ORA_PERIODIC 0
 #define ORA_WALL 1
-#define ORA_OPEN 2 /* x only: equilibrium Poiseuille inlet at x=0, copy outlet at x=nx-1 */
+#define ORA_OPEN 2 /* x only: Poiseuille velocity inlet at x=0, pressure outlet at x=nx-1 */
 
 #define ORA_PRESCRIBED 0
 #define ORA_FREE 1
@@ -396,6 +405,30 @@ static void advect(ora_sim *S)
 
 /* ------------------------------------------------------ 3. collision */
 
+/* Open column x = b from its inner neighbour x = n (both fluid), after the
+ * neighbour's collision: non-equilibrium extrapolation.  The neighbour's
+ * density and velocity are those of its collision (pre-collision moments,
+ * half the body force in u).  inlet: velocity (u_in(y), 0) with the
+ * neighbour's density; outlet: density rho0 with the neighbour's velocity. */
+static void open_column(ora_sim *S, int b, int n, int y, int inlet)
+{
+    const ora_config *c = &S->c;
+    double rho = 0.0, jx = 0.0, jy = 0.0;
+    for (int i = 0; i < 9; i++) {
+        double g = *F(S, S->g, i, n, y);
+        rho += g;
+        jx += EX[i] * g;
+        jy += EY[i] * g;
+    }
+    double ux = (jx + 0.5 * c->body_fx) / rho, uy = (jy + 0.5 * c->body_fy) / rho;
+    double eq_n[9], eq_b[9];
+    ora_feq(rho, ux, uy, eq_n);
+    if (inlet) ora_feq(rho, inlet_ux(c, y), 0.0, eq_b);
+    else ora_feq(c->rho0, ux, uy, eq_b);
+    for (int i = 0; i < 9; i++)
+        *F(S, S->f, i, b, y) = eq_b[i] + (*F(S, S->f, i, n, y) - eq_n[i]);
+}
+
 static void collide(ora_sim *S)
 {
     const ora_config *c = &S->c;
@@ -428,12 +461,16 @@ static void collide(ora_sim *S)
     if (c->bc_x == ORA_OPEN) {
         for (int y = 0; y < c->ny; y++) {
             double eq[9];
-            ora_feq(c->rho0, inlet_ux(c, y), 0.0, eq);
-            if (S->owner[at(S, 0, y)] < 0)
-                for (int i = 0; i < 9; i++) *F(S, S->f, i, 0, y) = eq[i];
+            if (S->owner[at(S, 0, y)] < 0) {
+                if (S->owner[at(S, 1, y)] < 0) {
+                    open_column(S, 0, 1, y, 1);
+                } else {
+                    ora_feq(c->rho0, inlet_ux(c, y), 0.0, eq);
+                    for (int i = 0; i < 9; i++) *F(S, S->f, i, 0, y) = eq[i];
+                }
+            }
             if (S->owner[at(S, c->nx - 1, y)] < 0 && S->owner[at(S, c->nx - 2, y)] < 0)
-                for (int i = 0; i < 9; i++)
-                    *F(S, S->f, i, c->nx - 1, y) = *F(S, S->f, i, c->nx - 2, y);
+                open_column(S, c->nx - 1, c->nx - 2, y, 0);
         }
     }
 }

@@ -7,4 +7,4 @@ in ``csrc/``, C ABI in ``include/lbm.h``); ``lbm`` is its Python binding.
 """
 from . import build  # noqa: F401
 from .lbm import *  # noqa: F401,F403
-from .lbm import Lattice, load  # noqa: F401
+from .lbm import Batch, Lattice, load  # noqa: F401

@@ -836,7 +836,197 @@ cudaError_t launch_sw(const StepParams &p, int mode, cudaStream_t st) {
                                        dim3(SW_BLOCK), args, 0, st);
 }
 
+// ------------------------------------------------------------- batch
+
+// Force records of a batch of independent domains whose solids rest: one
+// warp per (case, solid) item of the active list, phase F only.  The last
+// block to finish (a ticket, no waiting) advances the step counter of every
+// active case, after every block has read it.
+template <int P, bool LOCAL>
+__global__ void __launch_bounds__(SW_BLOCK)
+    k_solids_batch(const StepParams *__restrict__ cases, const int2 *__restrict__ items,
+                   const int *__restrict__ nitems, const int *__restrict__ active,
+                   const int *__restrict__ nactive, unsigned int *ticket) {
+    __shared__ bool last;
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int gw = blockIdx.x * WARPS + wib, nw = gridDim.x * WARPS;
+    const int n = *nitems;
+    for (int k = gw; k < n; k += nw) {
+        const int2 it = items[k];
+        const StepParams &p = cases[it.x];
+        const long long t = *p.t;
+        const void *fcur = (t & 1) ? p.f1 : p.f0;
+        if (solid_ok(p.S[it.y])) phase_forces<P, LOCAL>(p, it.y, lane, t, fcur);
+        else if (lane == 0) atomicOr(p.status, 2);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    const int na = *nactive;
+    for (int a = threadIdx.x; a < na; a += blockDim.x) *cases[active[a]].t += 1;
+    if (threadIdx.x == 0) *ticket = 0;
+}
+
+template <int P, bool LOCAL>
+cudaError_t launch_sb(const BatchLaunch &b, cudaStream_t st) {
+    static int per_sm = -1, sms = 0;
+    if (per_sm < 0) {
+        int dev = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e == cudaSuccess)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_solids_batch<P, LOCAL>,
+                                                              SW_BLOCK, 0);
+        if (e != cudaSuccess) return e;
+    }
+    int blocks = (b.max_items + WARPS - 1) / WARPS;
+    if (blocks > per_sm * sms) blocks = per_sm * sms;
+    if (blocks < 1) blocks = 1;
+    k_solids_batch<P, LOCAL><<<blocks, SW_BLOCK, 0, st>>>(b.cases, b.items, b.nitems, b.active,
+                                                          b.nactive, b.ticket);
+    return cudaGetLastError();
+}
+
+// Convergence test and list rebuild, one block.  Case states: 0 active,
+// 1 converged, 2 step cap reached, 3 unstable (a status bit raised, or a
+// non-finite drag).  The drag of a case is the x component of the Eq. 5
+// force summed over its solids in the latest record; it has converged when
+// it moved by less than tol relative since the previous test.  Modes:
+// BATCH_TEST tests and rebuilds the lists if a case retired; BATCH_REBUILD
+// keeps the states, clears the drag history and rebuilds the lists;
+// BATCH_GATHER only copies the step counters.  Every mode copies them.
+constexpr int CV_BLOCK = 1024;
+__global__ void __launch_bounds__(CV_BLOCK)
+    k_batch_converge(BatchLaunch b, int ncase, double tol, long long max_steps, int mode,
+                     int *state, double *drag, long long *steps, int *toff, int *ioff,
+                     int tile_w) {
+    __shared__ int changed;
+    __shared__ int wsum[3][CV_BLOCK / 32];
+    __shared__ int carry[3];
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    if (tid == 0) {
+        changed = mode == BATCH_REBUILD;
+        carry[0] = carry[1] = carry[2] = 0;
+    }
+    __syncthreads();
+    for (int c = tid; c < ncase; c += CV_BLOCK) {
+        const StepParams &p = b.cases[c];
+        const long long t = *p.t;
+        steps[c] = t;
+        if (mode == BATCH_GATHER) continue;
+        if (mode == BATCH_REBUILD) {
+            drag[c] = __longlong_as_double(0x7ff8000000000000ll);  // no history
+            continue;
+        }
+        if (state[c] != 0) continue;
+        int ns = 0;
+        if (*p.status != 0) ns = 3;
+        double D = 0.0;
+        if (ns == 0 && p.nsolid > 0 && t >= 1) {
+            const long long slot = (t - 1) % p.ring_len;
+            const double *rg = p.ring + (slot * 2 + 1) * p.nsolid * 3;
+            for (int s = 0; s < p.nsolid; s++) D += rg[s * 3];
+            const double prev = drag[c];
+            drag[c] = D;
+            if (!isfinite(D)) ns = 3;
+            else if (isfinite(prev) && fabs(D - prev) < tol * fabs(D)) ns = 1;
+        }
+        if (ns == 0 && t >= max_steps) ns = 2;
+        if (ns != 0) {
+            state[c] = ns;
+            changed = 1;
+        }
+    }
+    __syncthreads();
+    if (!changed) return;
+    // exclusive scans of (active, tiles, items) over the cases, in chunks
+    for (int base = 0; base < ncase; base += CV_BLOCK) {
+        const int c = base + tid;
+        int v[3] = {0, 0, 0};
+        if (c < ncase && state[c] == 0) {
+            const Lattice &L = b.cases[c].L;
+            v[0] = 1;
+            v[1] = (L.nx + tile_w - 1) / tile_w * L.ny;
+            v[2] = b.cases[c].nsolid;
+        }
+        int inc[3];
+#pragma unroll
+        for (int q = 0; q < 3; q++) {
+            inc[q] = v[q];
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int u = __shfl_up_sync(FULL, inc[q], o);
+                if (lane >= o) inc[q] += u;
+            }
+            if (lane == 31) wsum[q][wid] = inc[q];
+        }
+        __syncthreads();
+        if (wid == 0) {
+#pragma unroll
+            for (int q = 0; q < 3; q++) {
+                int w = wsum[q][lane];
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int u = __shfl_up_sync(FULL, w, o);
+                    if (lane >= o) w += u;
+                }
+                wsum[q][lane] = w;  // inclusive over warps
+            }
+        }
+        __syncthreads();
+        int ex[3];
+#pragma unroll
+        for (int q = 0; q < 3; q++) ex[q] = carry[q] + (wid ? wsum[q][wid - 1] : 0) + inc[q] - v[q];
+        if (v[0]) {
+            b.active[ex[0]] = c;
+            toff[c] = ex[1];
+            ioff[c] = ex[2];
+        }
+        __syncthreads();
+        if (tid == 0)
+            for (int q = 0; q < 3; q++) carry[q] += wsum[q][CV_BLOCK / 32 - 1];
+        __syncthreads();
+    }
+    const int na = carry[0];
+    if (tid == 0) {
+        *b.nactive = na;
+        *b.ntiles = carry[1];
+        *b.nitems = carry[2];
+    }
+    int4 *tiles = b.tiles;
+    int2 *items = b.items;
+    for (int a = 0; a < na; a++) {
+        const int c = b.active[a];
+        const Lattice &L = b.cases[c].L;
+        const int nbx = (L.nx + tile_w - 1) / tile_w, nt = nbx * L.ny, o = toff[c];
+        for (int k = tid; k < nt; k += CV_BLOCK) tiles[o + k] = make_int4(c, k % nbx, k / nbx, 0);
+        const int ns = b.cases[c].nsolid, oi = ioff[c];
+        for (int s = tid; s < ns; s += CV_BLOCK) items[oi + s] = make_int2(c, s);
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_solids_batch(const BatchLaunch &b, cudaStream_t st) {
+    if (b.precision == LBM_FP64)
+        return b.local ? launch_sb<LBM_FP64, true>(b, st) : launch_sb<LBM_FP64, false>(b, st);
+    if (b.precision == LBM_FP32_DEV)
+        return b.local ? launch_sb<LBM_FP32_DEV, true>(b, st) : launch_sb<LBM_FP32_DEV, false>(b, st);
+    return b.local ? launch_sb<LBM_FP16_DEV, true>(b, st) : launch_sb<LBM_FP16_DEV, false>(b, st);
+}
+
+cudaError_t launch_batch_converge(const BatchLaunch &b, const BatchState &s, int mode,
+                                  cudaStream_t st) {
+    k_batch_converge<<<1, CV_BLOCK, 0, st>>>(b, s.ncase, s.tol, s.max_steps, mode,
+                                             s.state, s.drag, s.steps, s.toff, s.ioff,
+                                             tile_nodes(b.precision, b.variant));
+    return cudaGetLastError();
+}
 
 cudaError_t launch_solids(const StepParams &p, int mode, cudaStream_t st) {
     if (p.nsolid == 0) return cudaSuccess;

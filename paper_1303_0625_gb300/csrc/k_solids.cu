@@ -59,10 +59,13 @@ __global__ void k_init_populations(const StepParams p) {
     }
 }
 
+// Flags of every node; the row padding (nx <= x < pitch) is marked solid, so
+// that the advection-collision kernel stores zeros there and never sends a
+// padding node down the per-node path.
 __global__ void k_flags_all(const StepParams p) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
-    if (x >= p.L.nx) return;
-    p.flags[cell_of(p.L, x, y)] = node_flags(p.L, p.owner, x, y);
+    if (x >= p.L.pitch) return;
+    p.flags[cell_of(p.L, x, y)] = x < p.L.nx ? node_flags(p.L, p.owner, x, y) : (uint16_t)1u;
 }
 
 __global__ void __launch_bounds__(SOLID_BLOCK) k_stamp(const StepParams p, int s) {
@@ -162,6 +165,7 @@ __global__ void k_link_masks(const StepParams p, uint8_t *mask) {
     mask[(long long)y * L.nx + x] = m;
 }
 
+// covers the row padding too: (nx + 127) / 128 * 128 >= pitch = (nx + 63) / 64 * 64
 dim3 cell_grid(const Lattice &L) { return dim3((L.nx + 127) / 128, L.ny); }
 
 }  // namespace

@@ -181,24 +181,34 @@ __device__ __noinline__ void update_node(const StepParams &p, const typename Raw
         for (int i = 0; i < 9; i++) put(fout[i * plane + k], (C)0);
         return;
     }
-    if (L.bc_x == LBM_OPEN && x == 0) {
-        // equilibrium inlet with the parabolic profile
-        const double h = (double)L.ny, yy = (double)y + 0.5;
-        const C u = (C)(4.0 * p.umax * yy * (h - yy) / (h * h));
-        const C r = (C)p.rho0;
-#pragma unroll
-        for (int i = 0; i < 9; i++) {
-            const C eu = (C)cx(i) * u;
-            const C poly = (C)3 * eu + (C)4.5 * eu * eu - (C)1.5 * u * u;
-            put(fout[i * plane + k], Prec<P>::dev ? wgt<C>(i) * ((r - (C)1) + r * poly)
-                                                  : r * wgt<C>(i) * ((C)1 + poly));
-        }
-        return;
-    }
-    int xu = x;  // node whose update is computed
+    // open columns: the update of the inner neighbour n, then the
+    // non-equilibrium extrapolation f_b = f_n + feq(rho_b, u_b) - feq(rho_n, u_n)
+    // (inlet: u_b = (u_in(y), 0), rho_b = rho_n; outlet: rho_b = rho0, u_b = u_n)
+    C u_in = 0;
+    int open = 0;  // 1 inlet, 2 outlet
+    int xu = x;    // node whose update is computed
     uint16_t flu = fl;
-    if (L.bc_x == LBM_OPEN && x == L.nx - 1 && !(p.flags[k - 1] & 1u)) {
-        xu = x - 1;  // outlet: copy of the updated column nx - 2
+    if (L.bc_x == LBM_OPEN && x == 0) {
+        const double h = (double)L.ny, yy = (double)y + 0.5;
+        u_in = (C)(4.0 * p.umax * yy * (h - yy) / (h * h));
+        if (p.flags[k + 1] & 1u) {
+            // solid neighbour: equilibrium inlet at rho0
+            const C r = (C)p.rho0;
+#pragma unroll
+            for (int i = 0; i < 9; i++) {
+                const C eu = (C)cx(i) * u_in;
+                const C poly = (C)3 * eu + (C)4.5 * eu * eu - (C)1.5 * u_in * u_in;
+                put(fout[i * plane + k], Prec<P>::dev ? wgt<C>(i) * ((r - (C)1) + r * poly)
+                                                      : r * wgt<C>(i) * ((C)1 + poly));
+            }
+            return;
+        }
+        open = 1;
+        xu = 1;
+        flu = p.flags[k + 1];
+    } else if (L.bc_x == LBM_OPEN && x == L.nx - 1 && !(p.flags[k - 1] & 1u)) {
+        open = 2;
+        xu = x - 1;
         flu = p.flags[k - 1];
     }
     const bool per_x = L.bc_x == LBM_PERIODIC, per_y = L.bc_y == LBM_PERIODIC;
@@ -213,7 +223,36 @@ __device__ __noinline__ void update_node(const StepParams &p, const typename Raw
         g[i] = cvt(fin[i * plane + ys * L.pitch + xs]);
     }
     if (flu & 0x1FEu) bounce<P, LOCAL>(p, fin, xu, y, flu, g);
+    C rn = 0, uxn = 0, uyn = 0;  // moments of the neighbour's collision
+    if (open) {
+        C s0 = 0, jx = 0, jy = 0;
+#pragma unroll
+        for (int i = 0; i < 9; i++) {
+            s0 += g[i];
+            jx += (C)cx(i) * g[i];
+            jy += (C)cy(i) * g[i];
+        }
+        rn = Prec<P>::dev ? (C)1 + s0 : s0;
+        if (FORCE) {
+            jx += (C)0.5 * pick<C>(p.body_x, p.body_xf);
+            jy += (C)0.5 * pick<C>(p.body_y, p.body_yf);
+        }
+        uxn = jx / rn;
+        uyn = jy / rn;
+    }
     collide<P, FORCE>(p, g);
+    if (open) {
+        const C ub = open == 1 ? u_in : uxn, vb = open == 1 ? (C)0 : uyn;
+        const C rb = open == 1 ? rn : pick<C>(p.rho0, p.rho0_f);
+        const C uun = uxn * uxn + uyn * uyn, uub = ub * ub + vb * vb;
+#pragma unroll
+        for (int i = 0; i < 9; i++) {
+            const C en = (C)cx(i) * uxn + (C)cy(i) * uyn, eb = (C)cx(i) * ub + (C)cy(i) * vb;
+            const C pn = (C)3 * en + (C)4.5 * en * en - (C)1.5 * uun;
+            const C pb = (C)3 * eb + (C)4.5 * eb * eb - (C)1.5 * uub;
+            g[i] += wgt<C>(i) * ((rb - rn) + rb * pb - rn * pn);
+        }
+    }
 #pragma unroll
     for (int i = 0; i < 9; i++) {
         R v;
@@ -222,14 +261,15 @@ __device__ __noinline__ void update_node(const StepParams &p, const typename Raw
     }
 }
 
+// One tile: row y, nodes bx * SC_BLOCK_X * V .. + SC_BLOCK_X * V - 1 (the
+// whole block works on the same tile).
 template <int P, int V, bool FORCE, bool LOCAL>
-__global__ void __launch_bounds__(SC_BLOCK_X) k_stream_collide(const StepParams p) {
+__device__ __forceinline__ void sc_tile(const StepParams &p, int bx, int y) {
     using R = typename Raw<P>::R;
     using C = typename Prec<P>::C;
     const Lattice &L = p.L;
     const int lane = threadIdx.x & 31;
-    const int x0 = (blockIdx.x * SC_BLOCK_X + threadIdx.x) * V;
-    const int y = blockIdx.y;
+    const int x0 = (bx * SC_BLOCK_X + threadIdx.x) * V;
     const long long t = *p.t;
     const R *__restrict__ fin = static_cast<const R *>((t & 1) ? p.f1 : p.f0);
     R *__restrict__ fout = static_cast<R *>((t & 1) ? p.f0 : p.f1);
@@ -344,6 +384,35 @@ __global__ void __launch_bounds__(SC_BLOCK_X) k_stream_collide(const StepParams 
 }
 
 template <int P, int V, bool FORCE, bool LOCAL>
+__global__ void __launch_bounds__(SC_BLOCK_X) k_stream_collide(const StepParams p) {
+    sc_tile<P, V, FORCE, LOCAL>(p, blockIdx.x, blockIdx.y);
+}
+
+// Batch of independent domains: persistent blocks walk the list of active
+// tiles {case, x block, row} of all cases (case-major), each tile with its
+// own case's parameters and step counter.
+template <int P, int V, bool FORCE, bool LOCAL>
+__global__ void __launch_bounds__(SC_BLOCK_X, 6)
+    k_stream_collide_batch(const StepParams *__restrict__ cases, const int4 *__restrict__ tiles,
+                           const int *__restrict__ ntiles) {
+    const int n = *ntiles;
+    for (int k = blockIdx.x; k < n; k += gridDim.x) {
+        const int4 tl = tiles[k];
+        sc_tile<P, V, FORCE, LOCAL>(cases[tl.x], tl.y, tl.z);
+    }
+}
+
+// The same tiles with one block per tile (grid = capacity of the list).
+template <int P, int V, bool FORCE, bool LOCAL>
+__global__ void __launch_bounds__(SC_BLOCK_X)
+    k_stream_collide_tiles(const StepParams *__restrict__ cases, const int4 *__restrict__ tiles,
+                           const int *__restrict__ ntiles) {
+    if ((int)blockIdx.x >= *ntiles) return;
+    const int4 tl = tiles[blockIdx.x];
+    sc_tile<P, V, FORCE, LOCAL>(cases[tl.x], tl.y, tl.z);
+}
+
+template <int P, int V, bool FORCE, bool LOCAL>
 cudaError_t launch_sc(const StepParams &p, cudaStream_t st) {
     dim3 grid((p.L.nx + SC_BLOCK_X * V - 1) / (SC_BLOCK_X * V), p.L.ny);
     k_stream_collide<P, V, FORCE, LOCAL><<<grid, SC_BLOCK_X, 0, st>>>(p);
@@ -371,7 +440,59 @@ cudaError_t launch_sc_p(const StepParams &p, cudaStream_t st) {
     }
 }
 
+template <int P, int V, bool FORCE, bool LOCAL>
+cudaError_t launch_scb(const BatchLaunch &b, cudaStream_t st) {
+    static int per_sm = -1, sms = 0;
+    if (per_sm < 0) {
+        int dev = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e == cudaSuccess)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                &per_sm, k_stream_collide_batch<P, V, FORCE, LOCAL>, SC_BLOCK_X, 0);
+        if (e != cudaSuccess) return e;
+    }
+    if (b.persistent)
+        k_stream_collide_batch<P, V, FORCE, LOCAL>
+            <<<per_sm * sms, SC_BLOCK_X, 0, st>>>(b.cases, b.tiles, b.ntiles);
+    else if (b.max_tiles > 0)
+        k_stream_collide_tiles<P, V, FORCE, LOCAL>
+            <<<b.max_tiles, SC_BLOCK_X, 0, st>>>(b.cases, b.tiles, b.ntiles);
+    return cudaGetLastError();
+}
+
+template <int P, int V>
+cudaError_t launch_scb_v(const BatchLaunch &b, cudaStream_t st) {
+    if (b.force)
+        return b.local ? launch_scb<P, V, true, true>(b, st) : launch_scb<P, V, true, false>(b, st);
+    return b.local ? launch_scb<P, V, false, true>(b, st) : launch_scb<P, V, false, false>(b, st);
+}
+
+template <int P>
+cudaError_t launch_scb_p(const BatchLaunch &b, cudaStream_t st) {
+    constexpr int V16 = 16 / (int)sizeof(typename Raw<P>::R);
+    switch (b.variant) {
+        case 1: return launch_scb_v<P, V16 / 2>(b, st);
+        case 2: return launch_scb_v<P, (V16 / 4 > 0 ? V16 / 4 : 1)>(b, st);
+        default: return launch_scb_v<P, V16>(b, st);
+    }
+}
+
 }  // namespace
+
+int tile_nodes(int precision, int variant) {
+    const int v16 = precision == LBM_FP64 ? 2 : (precision == LBM_FP32_DEV ? 4 : 8);
+    const int v = variant == 1 ? v16 / 2 : (variant == 2 ? (v16 / 4 > 0 ? v16 / 4 : 1) : v16);
+    return SC_BLOCK_X * v;
+}
+
+cudaError_t launch_stream_collide_batch(const BatchLaunch &b, cudaStream_t st) {
+    switch (b.precision) {
+        case LBM_FP64: return launch_scb_p<LBM_FP64>(b, st);
+        case LBM_FP32_DEV: return launch_scb_p<LBM_FP32_DEV>(b, st);
+        default: return launch_scb_p<LBM_FP16_DEV>(b, st);
+    }
+}
 
 cudaError_t launch_stream_collide(const StepParams &p, cudaStream_t st) {
     switch (p.precision) {

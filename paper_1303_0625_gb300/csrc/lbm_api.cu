@@ -52,6 +52,8 @@ struct lbm_ctx {
     // staging buffer for host transfers
     void *scratch = nullptr;
     size_t scratch_bytes = 0;
+    // set when the context is a case of a batch (stepped by the batch only)
+    const lbm_batch *batch = nullptr;
 };
 
 namespace {
@@ -289,6 +291,8 @@ lbm_status lbm_create(const lbm_config *cfg, lbm_ctx **out) {
     const size_t plane = (size_t)g.ny * c->pitch;
     cudaError_t e = cudaSuccess;
     for (int b = 0; b < 2 && e == cudaSuccess; b++) e = cudaMalloc(&c->f[b], 9 * plane * c->elem);
+    for (int b = 0; b < 2 && e == cudaSuccess; b++)  // row padding stays zero
+        e = cudaMemsetAsync(c->f[b], 0, 9 * plane * c->elem, c->stream);
     if (e == cudaSuccess) e = cudaMalloc(&c->owner, plane * sizeof(uint16_t));
     if (e == cudaSuccess) e = cudaMalloc(&c->prev, plane * sizeof(uint16_t));
     if (e == cudaSuccess) e = cudaMalloc(&c->flags, plane * sizeof(uint16_t));
@@ -319,6 +323,7 @@ lbm_status lbm_create(const lbm_config *cfg, lbm_ctx **out) {
 
 lbm_status lbm_destroy(lbm_ctx *ctx) {
     if (!ctx) return LBM_OK;
+    if (ctx->batch) return fail(ctx, LBM_EINVAL, "a case of a batch is destroyed with its batch");
     cudaSetDevice(ctx->cfg.device);
     cudaStreamSynchronize(ctx->stream);
     release(ctx);
@@ -327,6 +332,7 @@ lbm_status lbm_destroy(lbm_ctx *ctx) {
 
 lbm_status lbm_add_solid(lbm_ctx *c, const lbm_disk *d, int32_t *id_out) {
     if (!c || !d) return LBM_EINVAL;
+    if (c->batch) return fail(c, LBM_EINVAL, "add solids to a batch case with lbm_batch_add_solid");
     const lbm_config &g = c->cfg;
     const double rmax = 0.5 * (g.nx < g.ny ? g.nx : g.ny) - 4.0;
     if (!(d->r > 0.0) || !(d->r < rmax))
@@ -408,6 +414,7 @@ lbm_status lbm_add_solid(lbm_ctx *c, const lbm_disk *d, int32_t *id_out) {
 
 lbm_status lbm_step(lbm_ctx *c, int64_t n) {
     if (!c || n < 0) return LBM_EINVAL;
+    if (c->batch) return fail(c, LBM_EINVAL, "a case of a batch is stepped by lbm_batch_run");
     CK(c, cudaSetDevice(c->cfg.device));
     const StepParams p = params(c);
     int64_t done = 0;
@@ -629,6 +636,7 @@ lbm_status lbm_get_solids(lbm_ctx *c, double *state) {
 
 lbm_status lbm_set_solid(lbm_ctx *c, int32_t id, const double *state) {
     if (!c || !state || id < 0 || id >= c->nsolid) return LBM_EINVAL;
+    if (c->batch) return fail(c, LBM_EINVAL, "solids of a batch case rest");
     for (int k = 0; k < 5; k++)
         if (!std::isfinite(state[k])) return fail(c, LBM_EINVAL, "non-finite solid state");
     CK(c, cudaSetDevice(c->cfg.device));
@@ -754,6 +762,7 @@ int32_t lbm_kernel_variant(const lbm_ctx *c) { return c ? c->sc_variant : -1; }
 
 lbm_status lbm_autotune(lbm_ctx *c, int32_t steps, int32_t *best) {
     if (!c || steps < 1) return LBM_EINVAL;
+    if (c->batch) return fail(c, LBM_EINVAL, "a case of a batch is tuned by lbm_batch_autotune");
     const bool was_timing = c->timing;
     const double keep_ms = c->timed_ms;
     const int64_t keep_n = c->timed_launches;
@@ -786,6 +795,537 @@ lbm_status lbm_autotune(lbm_ctx *c, int32_t steps, int32_t *best) {
     c->timed_launches = keep_n;
     if (best) *best = best_v;
     return LBM_OK;
+}
+
+}  // extern "C"
+
+// ====================================================================== batch
+//
+// A batch owns ncase ordinary contexts (its cases) that share one stream, and
+// steps all of them with three kernels: the fused advection-collision kernel
+// over the list of active tiles {case, x block, row}, the force kernel over
+// the list of active (case, solid) items (which also advances the step
+// counters), and every `every` steps the convergence kernel, which retires
+// cases and rebuilds both lists on the device, so that a captured graph of
+// `every` steps stays valid while cases retire.
+
+struct lbm_batch {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    std::vector<lbm_ctx *> cases;
+    int precision = 0, rho_w_mode = 0;
+    bool force = false;
+    // launch policy
+    int variant = 0;
+    bool persistent = true, graph = true;
+    // convergence test
+    int every = 100;
+    double tol = 1e-7;
+    int64_t max_steps = 2000000;
+    int since_test = 0;  // batch steps since the last test
+    // device tables
+    bool dirty = true;  // parameters or lists must be rebuilt before stepping
+    StepParams *cases_d = nullptr;
+    int4 *tiles_d = nullptr;
+    int2 *items_d = nullptr;
+    int *counts_d = nullptr;  // {ntiles, nitems, nactive}
+    int *active_d = nullptr;
+    unsigned int *ticket_d = nullptr;
+    int *state_d = nullptr;
+    double *drag_d = nullptr;
+    long long *steps_d = nullptr;
+    int *toff_d = nullptr, *ioff_d = nullptr;
+    long long tile_cap = 0, item_cap = 0;
+    int max_tiles = 0, max_items = 0;
+    int *nactive_h = nullptr;  // pinned
+    // host copies of the per-case results
+    std::vector<int32_t> state;
+    std::vector<long long> steps;
+    std::vector<double> drag;
+    cudaGraphExec_t gexec = nullptr;
+    // timing of the fused kernel
+    bool timing = false;
+    std::vector<cudaEvent_t> ev;
+    size_t ev_used = 0;
+    double timed_ms = 0.0;
+    int64_t timed_launches = 0;
+    int64_t launches = 0;
+    std::string err;
+};
+
+namespace {
+
+lbm_status bfail(lbm_batch *b, lbm_status st, const char *fmt, ...) __attribute__((format(printf, 3, 4)));
+lbm_status bfail(lbm_batch *b, lbm_status st, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (b) b->err = buf;
+    else g_create_error = buf;
+    return st;
+}
+
+#define BCK(b, call)                                                                        \
+    do {                                                                                    \
+        cudaError_t e_ = (call);                                                            \
+        if (e_ != cudaSuccess)                                                              \
+            return bfail((b), e_ == cudaErrorMemoryAllocation ? LBM_ENOMEM : LBM_ECUDA,     \
+                         "%s failed: %s", #call, cudaGetErrorString(e_));                  \
+    } while (0)
+
+gbm::BatchLaunch blaunch(const lbm_batch *b) {
+    gbm::BatchLaunch l{};
+    l.cases = b->cases_d;
+    l.tiles = b->tiles_d;
+    l.ntiles = b->counts_d;
+    l.items = b->items_d;
+    l.nitems = b->counts_d + 1;
+    l.active = b->active_d;
+    l.nactive = b->counts_d + 2;
+    l.ticket = b->ticket_d;
+    l.precision = b->precision;
+    l.variant = b->variant;
+    l.force = b->force;
+    l.local = b->rho_w_mode == LBM_RHOW_LOCAL;
+    l.max_items = b->max_items;
+    l.max_tiles = b->max_tiles;
+    l.persistent = b->persistent;
+    return l;
+}
+
+gbm::BatchState bstate(const lbm_batch *b) {
+    gbm::BatchState s{};
+    s.ncase = (int)b->cases.size();
+    s.tol = b->tol;
+    s.max_steps = b->max_steps;
+    s.state = b->state_d;
+    s.drag = b->drag_d;
+    s.steps = b->steps_d;
+    s.toff = b->toff_d;
+    s.ioff = b->ioff_d;
+    return s;
+}
+
+void bdrop_graph(lbm_batch *b) {
+    if (b->gexec) cudaGraphExecDestroy(b->gexec);
+    b->gexec = nullptr;
+}
+
+void brelease(lbm_batch *b) {
+    if (!b) return;
+    bdrop_graph(b);
+    for (cudaEvent_t e : b->ev) cudaEventDestroy(e);
+    for (lbm_ctx *c : b->cases) {
+        c->batch = nullptr;
+        release(c);
+    }
+    void *bufs[] = {b->cases_d, b->tiles_d, b->items_d, b->counts_d, b->active_d, b->ticket_d,
+                    b->state_d, b->drag_d, b->steps_d, b->toff_d, b->ioff_d};
+    for (void *p : bufs)
+        if (p) cudaFree(p);
+    if (b->nactive_h) cudaFreeHost(b->nactive_h);
+    if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
+    delete b;
+}
+
+// Upload the case parameters and rebuild the lists (clears the drag history).
+lbm_status bprepare(lbm_batch *b) {
+    if (!b->dirty) return LBM_OK;
+    bdrop_graph(b);
+    const int w = gbm::tile_nodes(b->precision, b->variant);
+    const int wmin = gbm::tile_nodes(b->precision, 2);
+    long long tiles = 0, tiles_min = 0, items = 0;
+    std::vector<StepParams> hp(b->cases.size());
+    for (size_t k = 0; k < b->cases.size(); k++) {
+        const lbm_ctx *c = b->cases[k];
+        tiles += (long long)((c->cfg.nx + w - 1) / w) * c->cfg.ny;
+        tiles_min += (long long)((c->cfg.nx + wmin - 1) / wmin) * c->cfg.ny;
+        items += c->nsolid;
+        hp[k] = params(c);
+        hp[k].sc_variant = b->variant;
+    }
+    if (tiles_min >= (1ll << 31) || items >= (1ll << 31))
+        return bfail(b, LBM_EINVAL, "batch too large: %lld tiles", tiles_min);
+    BCK(b, cudaStreamSynchronize(b->stream));
+    if (tiles_min > b->tile_cap) {
+        if (b->tiles_d) BCK(b, cudaFree(b->tiles_d));
+        b->tiles_d = nullptr;
+        b->tile_cap = 0;
+        BCK(b, cudaMalloc(&b->tiles_d, (size_t)tiles_min * sizeof(int4)));
+        b->tile_cap = tiles_min;
+    }
+    if (items > b->item_cap || !b->items_d) {
+        if (b->items_d) BCK(b, cudaFree(b->items_d));
+        b->items_d = nullptr;
+        b->item_cap = 0;
+        const long long cap = items > 0 ? items : 1;
+        BCK(b, cudaMalloc(&b->items_d, (size_t)cap * sizeof(int2)));
+        b->item_cap = cap;
+    }
+    b->max_tiles = (int)tiles;
+    b->max_items = (int)items;
+    BCK(b, cudaMemcpyAsync(b->cases_d, hp.data(), hp.size() * sizeof(StepParams),
+                           cudaMemcpyHostToDevice, b->stream));
+    BCK(b, gbm::launch_batch_converge(blaunch(b), bstate(b), gbm::BATCH_REBUILD, b->stream));
+    b->launches++;
+    BCK(b, cudaMemcpyAsync(b->nactive_h, b->counts_d + 2, sizeof(int), cudaMemcpyDeviceToHost,
+                           b->stream));
+    BCK(b, cudaStreamSynchronize(b->stream));  // hp must outlive the copy
+    b->since_test = 0;
+    b->dirty = false;
+    return LBM_OK;
+}
+
+lbm_status benqueue_step(lbm_batch *b, const gbm::BatchLaunch &l, bool timed) {
+    if (timed) {
+        if (b->ev_used + 2 > b->ev.size()) {
+            for (int k = 0; k < 2; k++) {
+                cudaEvent_t e;
+                BCK(b, cudaEventCreate(&e));
+                b->ev.push_back(e);
+            }
+        }
+        BCK(b, cudaEventRecord(b->ev[b->ev_used], b->stream));
+    }
+    BCK(b, gbm::launch_stream_collide_batch(l, b->stream));
+    if (timed) {
+        BCK(b, cudaEventRecord(b->ev[b->ev_used + 1], b->stream));
+        b->ev_used += 2;
+    }
+    BCK(b, gbm::launch_solids_batch(l, b->stream));
+    b->launches += 2;
+    return LBM_OK;
+}
+
+lbm_status bharvest(lbm_batch *b) {
+    if (b->ev_used == 0) return LBM_OK;
+    BCK(b, cudaStreamSynchronize(b->stream));
+    for (size_t k = 0; k + 1 < b->ev_used; k += 2) {
+        float ms = 0.f;
+        BCK(b, cudaEventElapsedTime(&ms, b->ev[k], b->ev[k + 1]));
+        b->timed_ms += ms;
+        b->timed_launches++;
+    }
+    b->ev_used = 0;
+    return LBM_OK;
+}
+
+// Step counters, states and drags to the host; the cases' clocks follow.
+lbm_status bgather(lbm_batch *b) {
+    const size_t n = b->cases.size();
+    lbm_status st = bprepare(b);  // the kernel reads the uploaded case parameters
+    if (st != LBM_OK) return st;
+    BCK(b, gbm::launch_batch_converge(blaunch(b), bstate(b), gbm::BATCH_GATHER, b->stream));
+    b->launches++;
+    BCK(b, cudaMemcpyAsync(b->state.data(), b->state_d, n * sizeof(int), cudaMemcpyDeviceToHost,
+                           b->stream));
+    BCK(b, cudaMemcpyAsync(b->steps.data(), b->steps_d, n * sizeof(long long),
+                           cudaMemcpyDeviceToHost, b->stream));
+    BCK(b, cudaMemcpyAsync(b->drag.data(), b->drag_d, n * sizeof(double), cudaMemcpyDeviceToHost,
+                           b->stream));
+    BCK(b, cudaStreamSynchronize(b->stream));
+    for (size_t k = 0; k < n; k++) b->cases[k]->t = b->steps[k];
+    return LBM_OK;
+}
+
+// `n` steps of every active case, without a convergence test.
+lbm_status bsteps(lbm_batch *b, int64_t n) {
+    const gbm::BatchLaunch l = blaunch(b);
+    for (int64_t k = 0; k < n; k++) {
+        lbm_status st = benqueue_step(b, l, b->timing);
+        if (st != LBM_OK) return st;
+        if (b->timing && b->ev_used >= 8192) {
+            st = bharvest(b);
+            if (st != LBM_OK) return st;
+        }
+    }
+    return LBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+lbm_status lbm_batch_create(const lbm_config *configs, int32_t ncase, lbm_batch **out) {
+    if (!configs || !out || ncase < 1) return bfail(nullptr, LBM_EINVAL, "bad batch arguments");
+    *out = nullptr;
+    for (int k = 1; k < ncase; k++)
+        if (configs[k].precision != configs[0].precision ||
+            configs[k].rho_w_mode != configs[0].rho_w_mode ||
+            configs[k].device != configs[0].device)
+            return bfail(nullptr, LBM_EINVAL,
+                         "case %d: precision, rho_w_mode and device must match case 0", k);
+    if (cudaSetDevice(configs[0].device) != cudaSuccess)
+        return bfail(nullptr, LBM_ECUDA, "cannot select device %d", configs[0].device);
+    lbm_batch *b = new (std::nothrow) lbm_batch;
+    if (!b) return bfail(nullptr, LBM_ENOMEM, "host allocation failed");
+    b->device = configs[0].device;
+    b->precision = configs[0].precision;
+    b->rho_w_mode = configs[0].rho_w_mode;
+    if (configs[0].stream) {
+        b->stream = static_cast<cudaStream_t>(configs[0].stream);
+    } else {
+        if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            brelease(b);
+            return bfail(nullptr, LBM_ECUDA, "stream creation failed");
+        }
+        b->own_stream = true;
+    }
+    b->cases.reserve(ncase);
+    for (int k = 0; k < ncase; k++) {
+        lbm_config g = configs[k];
+        g.stream = b->stream;
+        lbm_ctx *c = nullptr;
+        lbm_status st = lbm_create(&g, &c);
+        if (st != LBM_OK) {
+            const std::string why = g_create_error;
+            brelease(b);
+            return bfail(nullptr, st, "case %d: %s", k, why.c_str());
+        }
+        c->batch = b;
+        b->cases.push_back(c);
+        if (g.body_force[0] != 0.0 || g.body_force[1] != 0.0) b->force = true;
+    }
+    const size_t n = (size_t)ncase;
+    cudaError_t e = cudaMalloc(&b->cases_d, n * sizeof(StepParams));
+    if (e == cudaSuccess) e = cudaMalloc(&b->counts_d, 3 * sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc(&b->active_d, n * sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc(&b->ticket_d, sizeof(unsigned int));
+    if (e == cudaSuccess) e = cudaMalloc(&b->state_d, n * sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc(&b->drag_d, n * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&b->steps_d, n * sizeof(long long));
+    if (e == cudaSuccess) e = cudaMalloc(&b->toff_d, n * sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc(&b->ioff_d, n * sizeof(int));
+    if (e == cudaSuccess) e = cudaMallocHost(&b->nactive_h, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->ticket_d, 0, sizeof(unsigned int), b->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->state_d, 0, n * sizeof(int), b->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->counts_d, 0, 3 * sizeof(int), b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) {
+        brelease(b);
+        return bfail(nullptr, e == cudaErrorMemoryAllocation ? LBM_ENOMEM : LBM_ECUDA,
+                     "lbm_batch_create: %s", cudaGetErrorString(e));
+    }
+    b->state.assign(n, LBM_CASE_ACTIVE);
+    b->steps.assign(n, 0);
+    b->drag.assign(n, std::nan(""));
+    *out = b;
+    return LBM_OK;
+}
+
+lbm_status lbm_batch_destroy(lbm_batch *b) {
+    if (!b) return LBM_OK;
+    cudaSetDevice(b->device);
+    cudaStreamSynchronize(b->stream);
+    brelease(b);
+    return LBM_OK;
+}
+
+int32_t lbm_batch_size(const lbm_batch *b) { return b ? (int32_t)b->cases.size() : -1; }
+
+lbm_status lbm_batch_case(lbm_batch *b, int32_t k, lbm_ctx **ctx) {
+    if (!b || !ctx || k < 0 || k >= (int32_t)b->cases.size()) return LBM_EINVAL;
+    *ctx = b->cases[k];
+    return LBM_OK;
+}
+
+lbm_status lbm_batch_add_solid(lbm_batch *b, int32_t k, const lbm_disk *d, int32_t *id) {
+    if (!b || !d || k < 0 || k >= (int32_t)b->cases.size()) return LBM_EINVAL;
+    if (d->vx != 0.0 || d->vy != 0.0 || d->omega != 0.0 || d->motion != LBM_PRESCRIBED)
+        return bfail(b, LBM_EINVAL, "solids of a batch rest (zero velocity, prescribed)");
+    lbm_ctx *c = b->cases[k];
+    BCK(b, cudaSetDevice(b->device));
+    bdrop_graph(b);
+    c->batch = nullptr;
+    lbm_status st = lbm_add_solid(c, d, id);
+    c->batch = b;
+    if (st != LBM_OK) return bfail(b, st, "case %d: %s", k, c->err.c_str());
+    b->dirty = true;
+    return LBM_OK;
+}
+
+lbm_status lbm_batch_set_convergence(lbm_batch *b, int32_t every, double tol, int64_t max_steps) {
+    if (!b || every < 1 || !(tol >= 0.0) || !std::isfinite(tol) || max_steps < 0)
+        return LBM_EINVAL;
+    b->every = every;
+    b->tol = tol;
+    b->max_steps = max_steps;
+    b->dirty = true;
+    bdrop_graph(b);
+    return LBM_OK;
+}
+
+lbm_status lbm_batch_run(lbm_batch *b, int64_t steps, int32_t *nactive) {
+    if (!b || steps < 0) return LBM_EINVAL;
+    BCK(b, cudaSetDevice(b->device));
+    lbm_status st = bprepare(b);
+    if (st != LBM_OK) return st;
+    int64_t done = 0;
+    int na = *b->nactive_h;
+    while (done < steps && na > 0) {
+        int64_t chunk = b->every - b->since_test;
+        if (chunk > steps - done) chunk = steps - done;
+        if (b->graph && !b->timing && chunk == b->every) {
+            if (!b->gexec) {
+                cudaGraph_t g;
+                const int64_t before = b->launches;
+                BCK(b, cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+                st = bsteps(b, chunk);
+                cudaError_t e = st == LBM_OK ? gbm::launch_batch_converge(
+                                                   blaunch(b), bstate(b), gbm::BATCH_TEST, b->stream)
+                                             : cudaSuccess;
+                cudaError_t e2 = cudaStreamEndCapture(b->stream, &g);
+                b->launches = before;  // counted when the graph is launched
+                if (st != LBM_OK) return st;
+                BCK(b, e);
+                BCK(b, e2);
+                e = cudaGraphInstantiate(&b->gexec, g, 0);
+                cudaGraphDestroy(g);
+                BCK(b, e);
+            }
+            BCK(b, cudaGraphLaunch(b->gexec, b->stream));
+            b->launches += 2 * chunk + 1;
+        } else {
+            st = bsteps(b, chunk);
+            if (st != LBM_OK) return st;
+            if (b->since_test + chunk == b->every) {
+                BCK(b, gbm::launch_batch_converge(blaunch(b), bstate(b), gbm::BATCH_TEST,
+                                                  b->stream));
+                b->launches++;
+            }
+        }
+        done += chunk;
+        b->since_test = (int)((b->since_test + chunk) % b->every);
+        if (b->since_test == 0) {
+            BCK(b, cudaMemcpyAsync(b->nactive_h, b->counts_d + 2, sizeof(int),
+                                   cudaMemcpyDeviceToHost, b->stream));
+            BCK(b, cudaStreamSynchronize(b->stream));
+            na = *b->nactive_h;
+        }
+    }
+    st = bharvest(b);
+    if (st == LBM_OK) st = bgather(b);
+    if (st != LBM_OK) return st;
+    if (nactive) {
+        int32_t a = 0;
+        for (int32_t s : b->state) a += s == LBM_CASE_ACTIVE;
+        *nactive = a;
+    }
+    return LBM_OK;
+}
+
+lbm_status lbm_batch_state(lbm_batch *b, int32_t *state, int64_t *steps, double *drag) {
+    if (!b) return LBM_EINVAL;
+    BCK(b, cudaSetDevice(b->device));
+    lbm_status st = bgather(b);
+    if (st != LBM_OK) return st;
+    for (size_t k = 0; k < b->cases.size(); k++) {
+        if (state) state[k] = b->state[k];
+        if (steps) steps[k] = b->steps[k];
+        if (drag) drag[k] = b->drag[k];
+    }
+    return LBM_OK;
+}
+
+lbm_status lbm_batch_set_launch(lbm_batch *b, int32_t variant, int32_t persistent, int32_t graph) {
+    if (!b || variant < 0 || variant > 2) return LBM_EINVAL;
+    if (variant != b->variant || (persistent != 0) != b->persistent) b->dirty = true;
+    b->variant = variant;
+    b->persistent = persistent != 0;
+    b->graph = graph != 0;
+    bdrop_graph(b);
+    return LBM_OK;
+}
+
+lbm_status lbm_batch_get_launch(const lbm_batch *b, int32_t *variant, int32_t *persistent) {
+    if (!b) return LBM_EINVAL;
+    if (variant) *variant = b->variant;
+    if (persistent) *persistent = b->persistent ? 1 : 0;
+    return LBM_OK;
+}
+
+lbm_status lbm_batch_set_timing(lbm_batch *b, int32_t enable) {
+    if (!b) return LBM_EINVAL;
+    BCK(b, cudaSetDevice(b->device));
+    lbm_status st = bharvest(b);
+    if (st != LBM_OK) return st;
+    if (enable && !b->timing) {
+        b->timed_ms = 0.0;
+        b->timed_launches = 0;
+    }
+    b->timing = enable != 0;
+    return LBM_OK;
+}
+
+lbm_status lbm_batch_get_timing(lbm_batch *b, double *ms, int64_t *launches) {
+    if (!b) return LBM_EINVAL;
+    BCK(b, cudaSetDevice(b->device));
+    lbm_status st = bharvest(b);
+    if (st != LBM_OK) return st;
+    if (ms) *ms = b->timed_ms;
+    if (launches) *launches = b->timed_launches;
+    return LBM_OK;
+}
+
+lbm_status lbm_batch_autotune(lbm_batch *b, int32_t steps, int32_t *best) {
+    if (!b || steps < 1) return LBM_EINVAL;
+    BCK(b, cudaSetDevice(b->device));
+    lbm_status st = bharvest(b);
+    if (st != LBM_OK) return st;
+    const bool was_timing = b->timing;
+    const double keep_ms = b->timed_ms;
+    const int64_t keep_n = b->timed_launches;
+    double best_ms = 0.0;
+    int best_v = 0, best_p = 1;
+    bool first = true;
+    for (int v = 0; v <= 2; v++) {
+        for (int pers = 1; pers >= 0; pers--) {
+            if (v != b->variant || (pers != 0) != b->persistent) b->dirty = true;
+            b->variant = v;
+            b->persistent = pers != 0;
+            st = bprepare(b);
+            if (st != LBM_OK) return st;
+            b->timing = true;
+            st = bsteps(b, 1);  // the first launch of a kernel is not timed
+            if (st == LBM_OK) st = bharvest(b);
+            b->timed_ms = 0.0;
+            b->timed_launches = 0;
+            if (st == LBM_OK) st = bsteps(b, steps);
+            if (st == LBM_OK) st = bharvest(b);
+            if (st != LBM_OK) return st;
+            const double ms = b->timed_ms / (b->timed_launches ? b->timed_launches : 1);
+            if (first || ms < best_ms) {
+                best_ms = ms;
+                best_v = v;
+                best_p = pers;
+                first = false;
+            }
+        }
+    }
+    b->dirty = true;
+    b->variant = best_v;
+    b->persistent = best_p != 0;
+    b->timing = was_timing;
+    b->timed_ms = keep_ms;
+    b->timed_launches = keep_n;
+    bdrop_graph(b);
+    st = bprepare(b);  // rebuild for the chosen tiles; the drag history restarts
+    if (st == LBM_OK) st = bgather(b);
+    if (st != LBM_OK) return st;
+    if (best) {
+        best[0] = best_v;
+        best[1] = best_p;
+    }
+    return LBM_OK;
+}
+
+int64_t lbm_batch_launch_count(const lbm_batch *b) { return b ? b->launches : -1; }
+
+const char *lbm_batch_last_error(const lbm_batch *b) {
+    return b ? b->err.c_str() : g_create_error.c_str();
 }
 
 }  // extern "C"

@@ -267,13 +267,55 @@ __device__ __forceinline__ long long cell_of(const Lattice &L, int x, int y) {
 
 // ----------------------------------------------------------- launchers
 
+// Device tables of a batch of independent domains (k_stream_collide.cu and
+// k_solid_step.cu).
+struct BatchLaunch {
+    const StepParams *cases;  // [ncase], device
+    int4 *tiles;              // active tiles {case, x block, row, 0}, device
+    int *ntiles;              // device
+    int2 *items;              // active (case, local solid) pairs, device
+    int *nitems;              // device
+    int *active;              // active case ids, device
+    int *nactive;             // device
+    unsigned int *ticket;     // last-block ticket of the batch force kernel, device
+    int precision, variant;
+    bool force, local;
+    int max_items;            // capacity of items (all solids of all cases)
+    int max_tiles;            // capacity of tiles (all tiles of all cases)
+    bool persistent;          // fused kernel: persistent blocks, else one block per tile
+};
+
+// Per-case convergence bookkeeping of a batch (device arrays of ncase).
+struct BatchState {
+    int ncase;
+    double tol;
+    long long max_steps;
+    int *state;               // 0 active, 1 converged, 2 step cap, 3 unstable
+    double *drag;             // drag at the previous test (NaN: none yet)
+    long long *steps;         // step counter of each case at the last test
+    int *toff, *ioff;         // offsets of each active case in the tile and item lists
+};
+
 // k_stream_collide.cu
 cudaError_t launch_stream_collide(const StepParams &p, cudaStream_t st);
+cudaError_t launch_stream_collide_batch(const BatchLaunch &b, cudaStream_t st);
+int tile_nodes(int precision, int variant);  // nodes along x of one tile
 // k_solid_step.cu: per-solid work of a step in one cooperative launch (force
 // record of time t, motion, t += 1; with SOLIDS_REMASK also re-rasterisation
 // of the moving solids).
 constexpr int SOLIDS_REMASK = 1;
 cudaError_t launch_solids(const StepParams &p, int mode, cudaStream_t st);
+// batch: force record of every resting solid of every active case, t += 1
+cudaError_t launch_solids_batch(const BatchLaunch &b, cudaStream_t st);
+// batch: BATCH_TEST retires the active cases whose drag (Eq. 5 Fx summed
+// over the case's solids) moved by less than tol relative since the previous
+// test, or that reached max_steps or became unstable, and rebuilds the active
+// case, item and tile lists when any case retired; BATCH_REBUILD clears the
+// drag history and rebuilds the lists; BATCH_GATHER copies the step counters
+// (all modes do).
+constexpr int BATCH_TEST = 0, BATCH_REBUILD = 1, BATCH_GATHER = 2;
+cudaError_t launch_batch_converge(const BatchLaunch &b, const BatchState &s, int mode,
+                                  cudaStream_t st);
 
 // k_solids.cu
 cudaError_t launch_tick(const StepParams &p, cudaStream_t st);

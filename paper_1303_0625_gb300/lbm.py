@@ -90,6 +90,21 @@ _SIGNATURES = {
     "lbm_set_kernel_variant": (_I32, [_P, _I32]),
     "lbm_kernel_variant": (_I32, [_P]),
     "lbm_autotune": (_I32, [_P, _I32, ctypes.POINTER(_I32)]),
+    "lbm_batch_create": (_I32, [ctypes.POINTER(lbm_config), _I32, ctypes.POINTER(_P)]),
+    "lbm_batch_destroy": (_I32, [_P]),
+    "lbm_batch_size": (_I32, [_P]),
+    "lbm_batch_case": (_I32, [_P, _I32, ctypes.POINTER(_P)]),
+    "lbm_batch_add_solid": (_I32, [_P, _I32, ctypes.POINTER(lbm_disk), ctypes.POINTER(_I32)]),
+    "lbm_batch_set_convergence": (_I32, [_P, _I32, ctypes.c_double, _I64]),
+    "lbm_batch_run": (_I32, [_P, _I64, ctypes.POINTER(_I32)]),
+    "lbm_batch_state": (_I32, [_P, _P, _P, _P]),
+    "lbm_batch_set_launch": (_I32, [_P, _I32, _I32, _I32]),
+    "lbm_batch_get_launch": (_I32, [_P, ctypes.POINTER(_I32), ctypes.POINTER(_I32)]),
+    "lbm_batch_autotune": (_I32, [_P, _I32, _P]),
+    "lbm_batch_set_timing": (_I32, [_P, _I32]),
+    "lbm_batch_get_timing": (_I32, [_P, _D, ctypes.POINTER(_I64)]),
+    "lbm_batch_launch_count": (_I64, [_P]),
+    "lbm_batch_last_error": (ctypes.c_char_p, [_P]),
 }
 
 
@@ -265,6 +280,95 @@ def lbm_autotune(ctx, steps: int = 4) -> int:
     return int(best.value)
 
 
+# ------------------------------------------------------------- batches
+
+LBM_CASE_ACTIVE, LBM_CASE_CONVERGED, LBM_CASE_CAPPED, LBM_CASE_UNSTABLE = range(4)
+
+
+def _bcheck(st: int, b=None):
+    if st != LBM_OK:
+        lib = load()
+        r = lib.lbm_batch_last_error(b)
+        raise LBMError(st, (r.decode() if r else "") or lib.lbm_status_string(st).decode())
+
+
+def lbm_batch_create(configs) -> ctypes.c_void_p:
+    arr = (lbm_config * len(configs))(*configs)
+    h = _P()
+    _bcheck(load().lbm_batch_create(arr, len(configs), ctypes.byref(h)))
+    return h
+
+
+def lbm_batch_destroy(b):
+    _bcheck(load().lbm_batch_destroy(b), b)
+
+
+def lbm_batch_size(b) -> int:
+    return int(load().lbm_batch_size(b))
+
+
+def lbm_batch_case(b, k: int):
+    h = _P()
+    _bcheck(load().lbm_batch_case(b, int(k), ctypes.byref(h)), b)
+    return h
+
+
+def lbm_batch_add_solid(b, k: int, disk: lbm_disk) -> int:
+    out = _I32()
+    _bcheck(load().lbm_batch_add_solid(b, int(k), ctypes.byref(disk), ctypes.byref(out)), b)
+    return int(out.value)
+
+
+def lbm_batch_set_convergence(b, every: int, tol: float, max_steps: int):
+    _bcheck(load().lbm_batch_set_convergence(b, int(every), float(tol), int(max_steps)), b)
+
+
+def lbm_batch_run(b, steps: int) -> int:
+    na = _I32()
+    _bcheck(load().lbm_batch_run(b, int(steps), ctypes.byref(na)), b)
+    return int(na.value)
+
+
+def lbm_batch_state(b, state, steps, drag):
+    _bcheck(load().lbm_batch_state(b, _ptr(state), _ptr(steps), _ptr(drag)), b)
+
+
+def lbm_batch_set_launch(b, variant: int, persistent: bool, graph: bool = True):
+    _bcheck(load().lbm_batch_set_launch(b, int(variant), int(bool(persistent)), int(bool(graph))), b)
+
+
+def lbm_batch_get_launch(b):
+    v, p = _I32(), _I32()
+    _bcheck(load().lbm_batch_get_launch(b, ctypes.byref(v), ctypes.byref(p)), b)
+    return int(v.value), int(p.value)
+
+
+def lbm_batch_autotune(b, steps: int = 4):
+    best = np.zeros(2, dtype=np.int32)
+    _bcheck(load().lbm_batch_autotune(b, int(steps), _ptr(best)), b)
+    return int(best[0]), int(best[1])
+
+
+def lbm_batch_set_timing(b, enable: bool):
+    _bcheck(load().lbm_batch_set_timing(b, int(bool(enable))), b)
+
+
+def lbm_batch_get_timing(b):
+    ms = ctypes.c_double()
+    n = _I64()
+    _bcheck(load().lbm_batch_get_timing(b, ctypes.byref(ms), ctypes.byref(n)), b)
+    return float(ms.value), int(n.value)
+
+
+def lbm_batch_launch_count(b) -> int:
+    return int(load().lbm_batch_launch_count(b))
+
+
+def lbm_batch_last_error(b=None) -> str:
+    r = load().lbm_batch_last_error(b)
+    return r.decode() if r else ""
+
+
 # ----------------------------------------------------------- convenience
 
 def make_config(nx, ny, tau, *, rho0=1.0, u0=(0.0, 0.0), bc_x=LBM_PERIODIC, bc_y=LBM_PERIODIC,
@@ -313,9 +417,9 @@ class Lattice:
         return lat
 
     def close(self):
-        if getattr(self, "_h", None):
+        if getattr(self, "_h", None) and not getattr(self, "_borrowed", False):
             lbm_destroy(self._h)
-            self._h = None
+        self._h = None
 
     def __del__(self):
         try:
@@ -416,3 +520,142 @@ class Lattice:
 
     def autotune(self, steps: int = 4) -> int:
         return lbm_autotune(self._h, steps)
+
+
+class Batch:
+    """Owns an lbm_batch: many independent domains stepped together.  Case k
+    is read through ``case(k)``, a Lattice view on the batch's context."""
+
+    def __init__(self, configs):
+        self.configs = list(configs)
+        self._h = lbm_batch_create(self.configs)
+        self._views = {}
+
+    @classmethod
+    def from_workloads(cls, ws, *, precision=LBM_FP32_DEV, force_ring=4, **kw):
+        cfgs = []
+        for w in ws:
+            opts = dict(rho0=w.get("rho0", 1.0), u0=w.get("u0", (0.0, 0.0)), bc_x=w["bc_x"],
+                        bc_y=w["bc_y"], wall_ux=w.get("wall_ux", (0.0, 0.0)),
+                        body_force=w.get("body_force", (0.0, 0.0)),
+                        inflow_umax=w.get("inflow_umax", 0.0),
+                        rho_w_mode=w.get("rho_w_mode", 0), refill=w.get("refill", 1),
+                        precision=precision, force_ring=force_ring)
+            opts.update(kw)
+            cfgs.append(make_config(w["nx"], w["ny"], w["tau"], **opts))
+        b = cls(cfgs)
+        for k, w in enumerate(ws):
+            for d in w["solids"]:
+                b.add_disk(k, d["cx"], d["cy"], d["r"])
+        return b
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lbm_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __len__(self):
+        return len(self.configs)
+
+    @property
+    def handle(self):
+        return self._h
+
+    def add_disk(self, k: int, cx, cy, r) -> int:
+        return lbm_batch_add_solid(self._h, k, lbm_disk(cx=cx, cy=cy, r=r))
+
+    def set_convergence(self, every=100, tol=1e-7, max_steps=2_000_000):
+        lbm_batch_set_convergence(self._h, every, tol, max_steps)
+
+    def run(self, steps: int) -> int:
+        """Advance the active cases by up to ``steps``; returns the active count."""
+        return lbm_batch_run(self._h, steps)
+
+    def state(self):
+        n = len(self)
+        st = np.zeros(n, dtype=np.int32)
+        steps = np.zeros(n, dtype=np.int64)
+        drag = np.zeros(n)
+        lbm_batch_state(self._h, st, steps, drag)
+        return st, steps, drag
+
+    def case(self, k: int) -> "Lattice":
+        if k not in self._views:
+            v = Lattice.__new__(Lattice)
+            v.cfg = self.configs[k]
+            v.nx, v.ny = int(v.cfg.nx), int(v.cfg.ny)
+            v._h = lbm_batch_case(self._h, k)
+            v._borrowed = True
+            self._views[k] = v
+        return self._views[k]
+
+    def set_launch(self, variant: int, persistent: bool = True, graph: bool = True):
+        lbm_batch_set_launch(self._h, variant, persistent, graph)
+
+    def launch(self):
+        return lbm_batch_get_launch(self._h)
+
+    def autotune(self, steps: int = 4, cache: str | None = None):
+        """Fastest (variant, persistent) of the fused kernel for this batch.
+        With ``cache`` (a JSON file), a result stored under the same key (GPU
+        name, precision and the batch's size classes) is reused without
+        timing, and a new result is stored."""
+        key = None
+        if cache:
+            import json
+            key = _tune_key(self.configs)
+            try:
+                with open(cache) as fh:
+                    table = json.load(fh)
+            except (OSError, ValueError):
+                table = {}
+            if key in table:
+                v, p = table[key]
+                self.set_launch(int(v), bool(p))
+                return int(v), int(p)
+        best = lbm_batch_autotune(self._h, steps)
+        if cache:
+            import json
+            try:
+                with open(cache) as fh:
+                    table = json.load(fh)
+            except (OSError, ValueError):
+                table = {}
+            table[key] = list(best)
+            with open(cache, "w") as fh:
+                json.dump(table, fh, indent=1, sort_keys=True)
+        return best
+
+    def set_timing(self, enable: bool):
+        lbm_batch_set_timing(self._h, enable)
+
+    def timing(self):
+        return lbm_batch_get_timing(self._h)
+
+    def launch_count(self) -> int:
+        return lbm_batch_launch_count(self._h)
+
+
+def _tune_key(configs) -> str:
+    """Autotuner cache key: device name, precision, and the number of cases
+    per size class (x extent rounded up to a power of two, total nodes to a
+    power of four)."""
+    import math
+    try:
+        import torch
+        dev = torch.cuda.get_device_name(int(configs[0].device)) if torch.cuda.is_available() else "cpu"
+    except Exception:
+        dev = "unknown"
+    classes = {}
+    for c in configs:
+        k = f"x{1 << max(0, math.ceil(math.log2(c.nx)))}"
+        classes[k] = classes.get(k, 0) + 1
+    cells = sum(int(c.nx) * int(c.ny) for c in configs)
+    parts = ",".join(f"{k}:{v}" for k, v in sorted(classes.items()))
+    return f"{dev}|p{int(configs[0].precision)}|{parts}|n4^{round(math.log(max(cells, 1), 4))}"

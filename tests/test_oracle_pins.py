@@ -178,6 +178,43 @@ def test_poiseuille_second_order():
     assert e8 / e16 == pytest.approx(4.0, rel=0.05)
 
 
+def _open_channel(ny, nx=24, umax=1e-3):
+    """Empty channel, parabolic velocity inlet and pressure outlet, at the
+    tau where half-way bounce-back walls are exact; run to steady state."""
+    tau = 0.5 + math.sqrt(3) / 4
+    nu = (tau - 0.5) / 3
+    o = O.Oracle(nx, ny, tau, bc_x=O.OPEN, bc_y=O.WALL, inflow_umax=umax)
+    o.step(int(12 * ny * ny / nu), record=False)
+    rho, ux, uy = o.fields()
+    o.step(200, record=False)
+    drift = np.abs(o.fields()[1] - ux).max() / umax
+    y = np.arange(ny) + 0.5
+    shape = 4 * y * (ny - y) / ny**2
+    xm = nx // 2
+    amp = (ux[:, xm] * shape).sum() / (shape * shape).sum()  # least-squares parabola
+    return dict(drift=drift, prof=np.abs(ux[:, xm] / umax - shape).max(),
+                parab=np.abs(ux[:, xm] - amp * shape).max() / umax,
+                dpdx=np.polyfit(np.arange(2, nx - 2), rho.mean(axis=0)[2:nx - 2], 1)[0] / 3,
+                shear=-8 * nu * amp / ny**2, rho_out=np.abs(rho[:, -1] - 1.0).max())
+
+
+def test_open_channel_velocity_inlet_pressure_outlet():
+    """Open channel (not part of the paper's method; the boundary of the
+    cylinder sweep): non-equilibrium extrapolation at both ends.  The flow
+    reaches a steady state; the bulk profile is a parabola whose amplitude
+    differs from the inlet's by a second-order inlet defect (ratio 4 between
+    ny = 8 and 16); the pressure drop balances the bulk profile's wall shear
+    (dp/dx = -8 rho nu u_max / ny^2); the outlet column holds rho0."""
+    a, b = _open_channel(8), _open_channel(16)
+    for r in (a, b):
+        assert r["drift"] < 1e-9
+        assert r["parab"] < 1e-4
+        assert r["dpdx"] / r["shear"] == pytest.approx(1.0, abs=2e-3)
+        assert r["rho_out"] < 1e-14
+    assert a["prof"] < 0.03
+    assert a["prof"] / b["prof"] == pytest.approx(4.0, rel=0.1)
+
+
 # ------------------------------------------------------- bookkeeping
 
 def _perturbed(o, seed, amp=0.01, u=(0.0, 0.0)):

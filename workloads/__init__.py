@@ -129,6 +129,48 @@ def sedimentation(nx=2048, ny=8192, ndisk=200, *, r=10.0, density_ratio=1.5, g=1
                 rho_w_mode=RHOW_CONST, refill=1, solids=solids)
 
 
+def cylinder_sweep(ncase=512, *, seed_offset=3, nx_range=(128, 1024), ny_range=(64, 512),
+                   re_range=(1.0, 100.0), tau=0.6, umax_cap=0.1):
+    """Sweep of independent channels with one fixed cylinder each.
+
+    Per case: nx uniform in nx_range, ny uniform among the even values of
+    ny_range (the pair drawn again while the disk would come closer than 4
+    nodes to the inlet, nx/4 - ny/10 < 4; ``shape_redraws`` counts those
+    draws), a disk of radius ny/10 at (nx/4, ny/2 + U[-2, 2]), bounce-back
+    walls in y, an equilibrium Poiseuille inlet at x = 0 and a copy outlet.
+    Re = U_mean d / nu with d = 2 r and nu = (tau - 1/2) / 3 is drawn
+    uniformly from re_range and drawn again while the inlet peak
+    1.5 U_mean would exceed umax_cap (low Mach number); ``redraws`` counts the
+    extra draws.  Returns a list of case descriptions.
+    """
+    rng = np.random.default_rng(BASE_SEED + seed_offset)
+    nu = (tau - 0.5) / 3.0
+    out = []
+    for _ in range(ncase):
+        shape_redraws = -1
+        while True:
+            shape_redraws += 1
+            nx = int(rng.integers(nx_range[0], nx_range[1] + 1))
+            ny = 2 * int(rng.integers(ny_range[0] // 2, ny_range[1] // 2 + 1))
+            if nx / 4.0 - ny / 10.0 >= 4.0:
+                break
+        r = ny / 10.0
+        cy = ny / 2.0 + float(rng.uniform(-2.0, 2.0))
+        redraws = -1
+        while True:
+            redraws += 1
+            re = float(rng.uniform(*re_range))
+            umax = 1.5 * re * nu / (2.0 * r)
+            if umax <= umax_cap:
+                break
+        out.append(dict(nx=nx, ny=ny, tau=float(tau), rho0=1.0, bc_x=OPEN, bc_y=WALL,
+                        u0=(0.0, 0.0), wall_ux=(0.0, 0.0), body_force=(0.0, 0.0),
+                        inflow_umax=umax, re=re, redraws=redraws,
+                        shape_redraws=shape_redraws, rho_w_mode=RHOW_CONST,
+                        refill=1, solids=[_disk(nx / 4.0, cy, r)]))
+    return out
+
+
 def crop_disks(cfg, nx, ny):
     """Copy of a periodic workload restricted to the disks whose whole extent
     (plus a 2-node gap) lies inside [0, nx) x [0, ny)."""
