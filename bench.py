@@ -52,6 +52,9 @@ def parse():
                     help="skip the e2e pass, the other precisions and the CPU baseline")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--batch-steps", type=int, default=1000)
+    ap.add_argument("--batch-cases", type=int, default=512)
+    ap.add_argument("--batch-only", action="store_true",
+                    help="measure only the cylinder-sweep batch and print its record")
     ap.add_argument("--batch-warmup", type=int, default=100)
     return ap.parse_args()
 
@@ -171,9 +174,12 @@ def measured_peaks():
 
 
 def kernel_source_hash():
-    path = os.path.join(ROOT, "paper_1303_0625_gb300", "csrc", "k_stream_collide.cu")
-    with open(path, "rb") as fh:
-        return hashlib.sha256(fh.read()).hexdigest()[:16]
+    """Hash of the single-domain advection-collision kernel's sources."""
+    h = hashlib.sha256()
+    for name in ("k_stream_collide.cu", "k_stream_collide.cuh"):
+        with open(os.path.join(ROOT, "paper_1303_0625_gb300", "csrc", name), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
 
 
 def captured_traffic(precision, nx, ny):
@@ -308,7 +314,7 @@ def run_batch(a, local, stream, peak):
     import paper_1303_0625_gb300 as G
     import workloads as W
 
-    ws = W.cylinder_sweep(512)
+    ws = W.cylinder_sweep(a.batch_cases)
     cells = np.array([w["nx"] * w["ny"] for w in ws], dtype=np.int64)
     t0 = time.time()
     b = G.Batch.from_workloads(ws, precision=G.LBM_FP32_DEV, force_ring=4, device=local,
@@ -341,8 +347,8 @@ def run_batch(a, local, stream, peak):
     live = cells[(s3 - s2) > 0]
     bytes_launch = float(live.sum()) * (18 * 4 + 2)
     gbs = bytes_launch / (k_ms / max(k_n, 1) / 1e3) / 1e9 if k_n else 0.0
-    out = {"workload": "cylinder sweep: 512 channels, nx 128..1024, ny 64..512 (even), one "
-                       "fixed disk r = ny/10, Poiseuille inlet, Re 1..100, tau 0.6, fp32",
+    out = {"workload": f"cylinder sweep: {len(ws)} channels, nx 128..1024, ny 64..512 (even), "
+                       "one fixed disk r = ny/10, Poiseuille inlet, Re 1..100, tau 0.6, fp32",
            "cases": len(ws), "cells": int(cells.sum()), "setup_s": round(setup_s, 2),
            "kernel_variant": variant, "persistent": bool(persistent),
            "steps": steps, "ms": round(ms, 3), "ms_per_step": round(ms / steps, 5),
@@ -456,6 +462,13 @@ def main():
     ws, rank, local = dist_setup()
     if a.impl == "reference":
         run_reference(a, ws, rank)
+    elif a.batch_only:
+        import torch
+        torch.cuda.set_device(local)
+        peaks, _ = measured_peaks()
+        rec = run_batch(a, local, torch.cuda.Stream(), float(peaks.get("hbm_gbs", FALLBACK_HBM_GBS)))
+        if rank == 0:
+            print(json.dumps(rec), flush=True)
     else:
         run_ours(a, ws, rank, local)
     if ws > 1:

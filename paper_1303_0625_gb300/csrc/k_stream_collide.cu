@@ -1,415 +1,25 @@
-// Fused pull-advection + half-way bounce-back + BGK collision (Eq. 1-3, Eq. 8).
-//
-// Layout: SoA planes f_i[ny][pitch], x fastest, pitch a multiple of 64.
-// Every thread owns V consecutive nodes of one row, V chosen so that one
-// population of those nodes is 16 bytes (FP64: 2, FP32: 4, FP16: 8).  Each of
-// the nine pulls is one aligned 128-bit load from the source row (y - c_y);
-// the x-shifted pulls (c_x = +-1) take the missing neighbour element from the
-// adjacent lane with a warp shuffle (lanes 0 and 31 load it directly, wrapped
-// at the row ends), so DRAM sees each population plane read once, fully
-// coalesced.  Results go out as nine 128-bit stores (nodes in the row padding
-// store zeros).  Only the open inlet/outlet columns use a per-node path.
-//
-// Bounce-back: a node whose flags word has bit i set (x - e_i solid or
-// outside) replaces population i by f~_opp(x) + 6 w_i rho_w (e_i . v), v the
-// velocity of the wall or solid at x - e_i / 2.  Solid nodes store zeros.
-//
-// Storage: FP64 stores f_i; the deviation modes store f_i - w_i (FP32 or
-// FP16) and compute in FP32 entirely in deviation form, so that the small
-// deviations keep their relative precision:
-//   drho = sum d_i,  rho = 1 + drho,  rho u = sum e_i d_i,
-//   deq_i = w_i (drho + rho (3 e.u + 4.5 (e.u)^2 - 1.5 u.u)).
-#include "lbm_internal.cuh"
+// Fused pull-advection + half-way bounce-back + BGK collision (Eq. 1-3, Eq. 8)
+// on one domain: one block per tile (row y, SC_BLOCK_X * V nodes); and the
+// open-channel columns pass.  The device code is in k_stream_collide.cuh.
+#include "k_stream_collide.cuh"
 
 namespace gbm {
 
 namespace {
-
-template <int P> struct Raw;
-template <> struct Raw<LBM_FP64> { using R = double; };
-template <> struct Raw<LBM_FP32_DEV> { using R = float; };
-template <> struct Raw<LBM_FP16_DEV> { using R = unsigned short; };
-
-template <int BYTES> struct Word;
-template <> struct Word<2> { using T = uint16_t; };
-template <> struct Word<4> { using T = uint32_t; };
-template <> struct Word<8> { using T = uint2; };
-template <> struct Word<16> { using T = uint4; };
-
-// V consecutive values of one population plane, loaded as one word
-template <class R, int V> union Pack {
-    typename Word<sizeof(R) * V>::T u;
-    R r[V];
-};
-template <int V> union FlagPack {
-    typename Word<2 * V>::T u;
-    uint16_t f[V];
-};
-
-__device__ __forceinline__ double cvt(double v) { return v; }
-__device__ __forceinline__ float cvt(float v) { return v; }
-__device__ __forceinline__ float cvt(unsigned short v) { return __half2float(__ushort_as_half(v)); }
-__device__ __forceinline__ void put(double &d, double v) { d = v; }
-__device__ __forceinline__ void put(float &d, float v) { d = v; }
-__device__ __forceinline__ void put(unsigned short &d, float v) {
-    d = __half_as_ushort(__float2half_rn(v));
-}
-
-__device__ __forceinline__ double shfl_up1(double v) { return __shfl_up_sync(0xffffffffu, v, 1); }
-__device__ __forceinline__ float shfl_up1(float v) { return __shfl_up_sync(0xffffffffu, v, 1); }
-__device__ __forceinline__ unsigned short shfl_up1(unsigned short v) {
-    return (unsigned short)__shfl_up_sync(0xffffffffu, (int)v, 1);
-}
-__device__ __forceinline__ double shfl_dn1(double v) { return __shfl_down_sync(0xffffffffu, v, 1); }
-__device__ __forceinline__ float shfl_dn1(float v) { return __shfl_down_sync(0xffffffffu, v, 1); }
-__device__ __forceinline__ unsigned short shfl_dn1(unsigned short v) {
-    return (unsigned short)__shfl_down_sync(0xffffffffu, (int)v, 1);
-}
-
-// Replace the bounced populations of node (x, y) (rare path): population i,
-// whose source x - e_i is a wall or a solid, becomes f~_opp(x) + 6 w_i rho_w
-// (e_i . v) with v the wall's or solid's velocity at x - e_i / 2 (Sec. III.A;
-// the moving-wall term).
-template <int P, bool LOCAL>
-__device__ __forceinline__ void bounce(const StepParams &p, const typename Raw<P>::R *fin, int x,
-                                       int y, uint16_t fl, typename Prec<P>::C (&g)[9]) {
-    using C = typename Prec<P>::C;
-    const Lattice &L = p.L;
-    const int k = y * L.pitch + x;
-    const int plane = (int)L.plane;
-    C rho_w = pick<C>(p.rho0, p.rho0_f);
-    if (LOCAL) {
-        C s = 0;
-#pragma unroll
-        for (int j = 0; j < 9; j++) s += cvt(fin[j * plane + k]);
-        rho_w = Prec<P>::dev ? (C)1 + s : s;
-    }
-#pragma unroll
-    for (int i = 1; i < 9; i++) {
-        if (!((fl >> i) & 1u)) continue;
-        const int sx = x - cx(i), sy = y - cy(i);
-        C vx = 0, vy = 0;
-        int xs, ys;
-        if (L.bc_y == LBM_WALL && (sy < 0 || sy >= L.ny)) {
-            vx = pick<C>(sy < 0 ? p.wall_ux0 : p.wall_ux1, (float)(sy < 0 ? p.wall_ux0 : p.wall_ux1));
-        } else if (locate(L, sx, sy, xs, ys)) {
-            const uint16_t o = p.owner[cell_of(L, xs, ys)];
-            if (o != FLUID) {
-                const DSolid &b = p.S[o];
-                vx = pick<C>(b.vx, b.vxf);
-                vy = pick<C>(b.vy, b.vyf);
-                if (b.omf != 0.0f) {
-                    // x - e_i / 2 relative to R, nearest periodic image
-                    C dx, dy;
-                    if (Prec<P>::dev) {
-                        dx = (C)(x - b.xwi) - (C)(0.5f * cx(i)) - (C)b.xwr;
-                        dy = (C)(y - b.ywi) - (C)(0.5f * cy(i)) - (C)b.ywr;
-                    } else {
-                        dx = (C)((double)x - 0.5 * cx(i) - b.xw);
-                        dy = (C)((double)y - 0.5 * cy(i) - b.yw);
-                    }
-                    if (L.bc_x == LBM_PERIODIC) {
-                        if (dx > (C)(0.5 * L.nx)) dx -= (C)L.nx;
-                        else if (dx < (C)(-0.5 * L.nx)) dx += (C)L.nx;
-                    }
-                    if (L.bc_y == LBM_PERIODIC) {
-                        if (dy > (C)(0.5 * L.ny)) dy -= (C)L.ny;
-                        else if (dy < (C)(-0.5 * L.ny)) dy += (C)L.ny;
-                    }
-                    const C om = pick<C>(b.om, b.omf);
-                    vx -= om * dy;
-                    vy += om * dx;
-                }
-            }
-        }
-        const C back = cvt(fin[opp(i) * plane + k]);
-        g[i] = back + (C)6 * wgt<C>(i) * rho_w * ((C)cx(i) * vx + (C)cy(i) * vy);
-    }
-}
-
-// BGK collision (with Guo forcing when FORCE) of one node in place.
-template <int P, bool FORCE>
-__device__ __forceinline__ void collide(const StepParams &p, typename Prec<P>::C (&g)[9]) {
-    using C = typename Prec<P>::C;
-    C s0 = 0, jx = 0, jy = 0;
-#pragma unroll
-    for (int i = 0; i < 9; i++) {
-        s0 += g[i];
-        jx += (C)cx(i) * g[i];
-        jy += (C)cy(i) * g[i];
-    }
-    const C rho = Prec<P>::dev ? (C)1 + s0 : s0;
-    const C Fx = pick<C>(p.body_x, p.body_xf), Fy = pick<C>(p.body_y, p.body_yf);
-    const C inv = (C)1 / rho;
-    const C ux = FORCE ? (jx + (C)0.5 * Fx) * inv : jx * inv;
-    const C uy = FORCE ? (jy + (C)0.5 * Fy) * inv : jy * inv;
-    const C uu = ux * ux + uy * uy;
-    const C om = pick<C>(p.omega, p.omega_f);
-    if (!(rho > (C)0) || !(fabs(ux) < (C)1e30) || !(fabs(uy) < (C)1e30)) atomicOr(p.status, 1);
-#pragma unroll
-    for (int i = 0; i < 9; i++) {
-        const C eu = (C)cx(i) * ux + (C)cy(i) * uy;
-        const C poly = (C)3 * eu + (C)4.5 * eu * eu - (C)1.5 * uu;
-        C eq;
-        if (Prec<P>::dev) eq = wgt<C>(i) * (s0 + rho * poly);  // f_eq - w_i
-        else eq = rho * wgt<C>(i) * ((C)1 + poly);
-        C o = g[i] - (g[i] - eq) * om;
-        if (FORCE) {
-            o += ((C)1 - (C)0.5 * om) * wgt<C>(i) *
-                 ((C)3 * (((C)cx(i) - ux) * Fx + ((C)cy(i) - uy) * Fy) +
-                  (C)9 * eu * ((C)cx(i) * Fx + (C)cy(i) * Fy));
-        }
-        g[i] = o;
-    }
-}
-
-// Complete update of one node, with periodic wrap, bounce-back, walls and the
-// open inlet/outlet: used for the nodes the vector path leaves out (fluid
-// nodes next to a solid or wall, the first and last column).
-template <int P, bool FORCE, bool LOCAL>
-__device__ __noinline__ void update_node(const StepParams &p, const typename Raw<P>::R *fin,
-                                         typename Raw<P>::R *fout, int x, int y) {
-    using C = typename Prec<P>::C;
-    using R = typename Raw<P>::R;
-    const Lattice &L = p.L;
-    const int plane = (int)L.plane;
-    const int k = y * L.pitch + x;
-    const uint16_t fl = p.flags[k];
-    C g[9];
-    if (fl & 1u) {
-#pragma unroll
-        for (int i = 0; i < 9; i++) put(fout[i * plane + k], (C)0);
-        return;
-    }
-    // open columns: the update of the inner neighbour n, then the
-    // non-equilibrium extrapolation f_b = f_n + feq(rho_b, u_b) - feq(rho_n, u_n)
-    // (inlet: u_b = (u_in(y), 0), rho_b = rho_n; outlet: rho_b = rho0, u_b = u_n)
-    C u_in = 0;
-    int open = 0;  // 1 inlet, 2 outlet
-    int xu = x;    // node whose update is computed
-    uint16_t flu = fl;
-    if (L.bc_x == LBM_OPEN && x == 0) {
-        const double h = (double)L.ny, yy = (double)y + 0.5;
-        u_in = (C)(4.0 * p.umax * yy * (h - yy) / (h * h));
-        if (p.flags[k + 1] & 1u) {
-            // solid neighbour: equilibrium inlet at rho0
-            const C r = (C)p.rho0;
-#pragma unroll
-            for (int i = 0; i < 9; i++) {
-                const C eu = (C)cx(i) * u_in;
-                const C poly = (C)3 * eu + (C)4.5 * eu * eu - (C)1.5 * u_in * u_in;
-                put(fout[i * plane + k], Prec<P>::dev ? wgt<C>(i) * ((r - (C)1) + r * poly)
-                                                      : r * wgt<C>(i) * ((C)1 + poly));
-            }
-            return;
-        }
-        open = 1;
-        xu = 1;
-        flu = p.flags[k + 1];
-    } else if (L.bc_x == LBM_OPEN && x == L.nx - 1 && !(p.flags[k - 1] & 1u)) {
-        open = 2;
-        xu = x - 1;
-        flu = p.flags[k - 1];
-    }
-    const bool per_x = L.bc_x == LBM_PERIODIC, per_y = L.bc_y == LBM_PERIODIC;
-#pragma unroll
-    for (int i = 0; i < 9; i++) {
-        int xs = xu - cx(i), ys = y - cy(i);
-        // wrap along periodic axes; clamp elsewhere (the value is then bounced)
-        if (xs < 0) xs = per_x ? xs + L.nx : 0;
-        if (xs >= L.nx) xs = per_x ? xs - L.nx : L.nx - 1;
-        if (ys < 0) ys = per_y ? ys + L.ny : 0;
-        if (ys >= L.ny) ys = per_y ? ys - L.ny : L.ny - 1;
-        g[i] = cvt(fin[i * plane + ys * L.pitch + xs]);
-    }
-    if (flu & 0x1FEu) bounce<P, LOCAL>(p, fin, xu, y, flu, g);
-    C rn = 0, uxn = 0, uyn = 0;  // moments of the neighbour's collision
-    if (open) {
-        C s0 = 0, jx = 0, jy = 0;
-#pragma unroll
-        for (int i = 0; i < 9; i++) {
-            s0 += g[i];
-            jx += (C)cx(i) * g[i];
-            jy += (C)cy(i) * g[i];
-        }
-        rn = Prec<P>::dev ? (C)1 + s0 : s0;
-        if (FORCE) {
-            jx += (C)0.5 * pick<C>(p.body_x, p.body_xf);
-            jy += (C)0.5 * pick<C>(p.body_y, p.body_yf);
-        }
-        uxn = jx / rn;
-        uyn = jy / rn;
-    }
-    collide<P, FORCE>(p, g);
-    if (open) {
-        const C ub = open == 1 ? u_in : uxn, vb = open == 1 ? (C)0 : uyn;
-        const C rb = open == 1 ? rn : pick<C>(p.rho0, p.rho0_f);
-        const C uun = uxn * uxn + uyn * uyn, uub = ub * ub + vb * vb;
-#pragma unroll
-        for (int i = 0; i < 9; i++) {
-            const C en = (C)cx(i) * uxn + (C)cy(i) * uyn, eb = (C)cx(i) * ub + (C)cy(i) * vb;
-            const C pn = (C)3 * en + (C)4.5 * en * en - (C)1.5 * uun;
-            const C pb = (C)3 * eb + (C)4.5 * eb * eb - (C)1.5 * uub;
-            g[i] += wgt<C>(i) * ((rb - rn) + rb * pb - rn * pn);
-        }
-    }
-#pragma unroll
-    for (int i = 0; i < 9; i++) {
-        R v;
-        put(v, g[i]);
-        fout[i * plane + k] = v;
-    }
-}
-
-// One tile: row y, nodes bx * SC_BLOCK_X * V .. + SC_BLOCK_X * V - 1 (the
-// whole block works on the same tile).
-template <int P, int V, bool FORCE, bool LOCAL>
-__device__ __forceinline__ void sc_tile(const StepParams &p, int bx, int y) {
-    using R = typename Raw<P>::R;
-    using C = typename Prec<P>::C;
-    const Lattice &L = p.L;
-    const int lane = threadIdx.x & 31;
-    const int x0 = (bx * SC_BLOCK_X + threadIdx.x) * V;
-    const long long t = *p.t;
-    const R *__restrict__ fin = static_cast<const R *>((t & 1) ? p.f1 : p.f0);
-    R *__restrict__ fout = static_cast<R *>((t & 1) ? p.f0 : p.f1);
-    const int plane = (int)L.plane;
-    const int xl = min(x0, L.pitch - V);  // in-bounds load position for every lane
-    int ym = y - 1, yp = y + 1;
-    if (ym < 0) ym = L.bc_y == LBM_PERIODIC ? L.ny - 1 : 0;
-    if (yp >= L.ny) yp = L.bc_y == LBM_PERIODIC ? 0 : L.ny - 1;
-    const int rm = ym * L.pitch, r0 = y * L.pitch, rp = yp * L.pitch;
-#define SROW(i) (cy(i) == 1 ? rm : (cy(i) == -1 ? rp : r0))
-
-    Pack<R, V> raw[9];
-#pragma unroll
-    for (int i = 0; i < 9; i++)
-        raw[i].u = __ldg(reinterpret_cast<const typename Word<sizeof(R) * V>::T *>(
-            fin + i * plane + SROW(i) + xl));
-    FlagPack<V> fl;
-    fl.u = *reinterpret_cast<const typename Word<2 * V>::T *>(p.flags + r0 + xl);
-    // neighbour elements of the x-shifted pulls at the warp's ends; at the
-    // row ends they are wrong, but those columns take the per-node path
-    R hl[3] = {R(0), R(0), R(0)};
-    if (lane == 0) {
-        const int xh = max(x0 - 1, 0);
-        hl[0] = fin[1 * plane + SROW(1) + xh];
-        hl[1] = fin[5 * plane + SROW(5) + xh];
-        hl[2] = fin[8 * plane + SROW(8) + xh];
-    } else if (lane == 31) {
-        const int xh = min(x0 + V, L.pitch - 1);
-        hl[0] = fin[3 * plane + SROW(3) + xh];
-        hl[1] = fin[6 * plane + SROW(6) + xh];
-        hl[2] = fin[7 * plane + SROW(7) + xh];
-    }
-    R halo[9];
-#pragma unroll
-    for (int i = 0; i < 9; i++) {
-        halo[i] = R(0);
-        if (cx(i) == 1) halo[i] = shfl_up1(raw[i].r[V - 1]);
-        else if (cx(i) == -1) halo[i] = shfl_dn1(raw[i].r[0]);
-    }
-#undef SROW
-    if (x0 >= L.nx) return;
-    if (lane == 0) {
-        halo[1] = hl[0];
-        halo[5] = hl[1];
-        halo[8] = hl[2];
-    } else if (lane == 31) {
-        halo[3] = hl[0];
-        halo[6] = hl[1];
-        halo[7] = hl[2];
-    }
-#define PULL(i, j) \
-    cvt(cx(i) == 0 ? raw[i].r[j] \
-                   : (cx(i) == 1 ? ((j) == 0 ? halo[i] : raw[i].r[(j) - 1]) \
-                                 : ((j) == V - 1 ? halo[i] : raw[i].r[(j) + 1])))
-    // moments of every node from the pulled populations
-    C s0[V], ux[V], uy[V], rho[V];
-    uint32_t slow = 0;  // bit j: node j needs the per-node path
-#pragma unroll
-    for (int j = 0; j < V; j++) {
-        C a = 0, jx = 0, jy = 0;
-#pragma unroll
-        for (int i = 0; i < 9; i++) {
-            const C g = PULL(i, j);
-            a += g;
-            jx += (C)cx(i) * g;
-            jy += (C)cy(i) * g;
-        }
-        const C r = Prec<P>::dev ? (C)1 + a : a;
-        const C inv = (C)1 / r;
-        s0[j] = a;
-        rho[j] = r;
-        ux[j] = FORCE ? (jx + (C)0.5 * pick<C>(p.body_x, p.body_xf)) * inv : jx * inv;
-        uy[j] = FORCE ? (jy + (C)0.5 * pick<C>(p.body_y, p.body_yf)) * inv : jy * inv;
-        const uint16_t f = fl.f[j];
-        const int x = x0 + j;
-        if (!(f & 1u) && ((f & 0x1FEu) || x == 0 || x == L.nx - 1)) slow |= 1u << j;
-        else if (!(f & 1u) && x < L.nx &&
-                 (!(r > (C)0) || !(fabs(ux[j]) < (C)1e30) || !(fabs(uy[j]) < (C)1e30)))
-            atomicOr(p.status, 1);
-    }
-    // relax towards equilibrium, one population plane at a time
-    const C om = pick<C>(p.omega, p.omega_f);
-#pragma unroll
-    for (int i = 0; i < 9; i++) {
-        Pack<R, V> o;
-#pragma unroll
-        for (int j = 0; j < V; j++) {
-            const C g = PULL(i, j);
-            const C eu = (C)cx(i) * ux[j] + (C)cy(i) * uy[j];
-            const C uu = ux[j] * ux[j] + uy[j] * uy[j];
-            const C poly = (C)3 * eu + (C)4.5 * eu * eu - (C)1.5 * uu;
-            const C eq = Prec<P>::dev ? wgt<C>(i) * (s0[j] + rho[j] * poly)
-                                      : rho[j] * wgt<C>(i) * ((C)1 + poly);
-            C v = g - (g - eq) * om;
-            if (FORCE) {
-                const C Fx = pick<C>(p.body_x, p.body_xf), Fy = pick<C>(p.body_y, p.body_yf);
-                v += ((C)1 - (C)0.5 * om) * wgt<C>(i) *
-                     ((C)3 * (((C)cx(i) - ux[j]) * Fx + ((C)cy(i) - uy[j]) * Fy) +
-                      (C)9 * eu * ((C)cx(i) * Fx + (C)cy(i) * Fy));
-            }
-            put(o.r[j], (fl.f[j] & 1u) ? (C)0 : v);  // solid nodes store zeros
-        }
-        *reinterpret_cast<typename Word<sizeof(R) * V>::T *>(fout + i * plane + r0 + x0) = o.u;
-    }
-#undef PULL
-    // nodes next to a solid or a wall and the first/last column
-    while (slow) {
-        const int j = __ffs(slow) - 1;
-        slow &= slow - 1;
-        update_node<P, FORCE, LOCAL>(p, fin, fout, x0 + j, y);
-    }
-}
 
 template <int P, int V, bool FORCE, bool LOCAL>
 __global__ void __launch_bounds__(SC_BLOCK_X) k_stream_collide(const StepParams p) {
     sc_tile<P, V, FORCE, LOCAL>(p, blockIdx.x, blockIdx.y);
 }
 
-// Batch of independent domains: persistent blocks walk the list of active
-// tiles {case, x block, row} of all cases (case-major), each tile with its
-// own case's parameters and step counter.
-template <int P, int V, bool FORCE, bool LOCAL>
-__global__ void __launch_bounds__(SC_BLOCK_X, 6)
-    k_stream_collide_batch(const StepParams *__restrict__ cases, const int4 *__restrict__ tiles,
-                           const int *__restrict__ ntiles) {
-    const int n = *ntiles;
-    for (int k = blockIdx.x; k < n; k += gridDim.x) {
-        const int4 tl = tiles[k];
-        sc_tile<P, V, FORCE, LOCAL>(cases[tl.x], tl.y, tl.z);
-    }
-}
-
-// The same tiles with one block per tile (grid = capacity of the list).
-template <int P, int V, bool FORCE, bool LOCAL>
-__global__ void __launch_bounds__(SC_BLOCK_X)
-    k_stream_collide_tiles(const StepParams *__restrict__ cases, const int4 *__restrict__ tiles,
-                           const int *__restrict__ ntiles) {
-    if ((int)blockIdx.x >= *ntiles) return;
-    const int4 tl = tiles[blockIdx.x];
-    sc_tile<P, V, FORCE, LOCAL>(cases[tl.x], tl.y, tl.z);
+// Open-channel columns of every row, on the populations of t+1.
+template <int P, bool FORCE>
+__global__ void k_open_columns(const StepParams p) {
+    using R = typename Raw<P>::R;
+    const int y = blockIdx.x * blockDim.x + threadIdx.x;
+    if (y >= p.L.ny) return;
+    const long long t = *p.t;
+    open_row<P, FORCE>(p, static_cast<R *>((t & 1) ? p.f0 : p.f1), y);
 }
 
 template <int P, int V, bool FORCE, bool LOCAL>
@@ -440,59 +50,7 @@ cudaError_t launch_sc_p(const StepParams &p, cudaStream_t st) {
     }
 }
 
-template <int P, int V, bool FORCE, bool LOCAL>
-cudaError_t launch_scb(const BatchLaunch &b, cudaStream_t st) {
-    static int per_sm = -1, sms = 0;
-    if (per_sm < 0) {
-        int dev = 0;
-        cudaError_t e = cudaGetDevice(&dev);
-        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (e == cudaSuccess)
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                &per_sm, k_stream_collide_batch<P, V, FORCE, LOCAL>, SC_BLOCK_X, 0);
-        if (e != cudaSuccess) return e;
-    }
-    if (b.persistent)
-        k_stream_collide_batch<P, V, FORCE, LOCAL>
-            <<<per_sm * sms, SC_BLOCK_X, 0, st>>>(b.cases, b.tiles, b.ntiles);
-    else if (b.max_tiles > 0)
-        k_stream_collide_tiles<P, V, FORCE, LOCAL>
-            <<<b.max_tiles, SC_BLOCK_X, 0, st>>>(b.cases, b.tiles, b.ntiles);
-    return cudaGetLastError();
-}
-
-template <int P, int V>
-cudaError_t launch_scb_v(const BatchLaunch &b, cudaStream_t st) {
-    if (b.force)
-        return b.local ? launch_scb<P, V, true, true>(b, st) : launch_scb<P, V, true, false>(b, st);
-    return b.local ? launch_scb<P, V, false, true>(b, st) : launch_scb<P, V, false, false>(b, st);
-}
-
-template <int P>
-cudaError_t launch_scb_p(const BatchLaunch &b, cudaStream_t st) {
-    constexpr int V16 = 16 / (int)sizeof(typename Raw<P>::R);
-    switch (b.variant) {
-        case 1: return launch_scb_v<P, V16 / 2>(b, st);
-        case 2: return launch_scb_v<P, (V16 / 4 > 0 ? V16 / 4 : 1)>(b, st);
-        default: return launch_scb_v<P, V16>(b, st);
-    }
-}
-
 }  // namespace
-
-int tile_nodes(int precision, int variant) {
-    const int v16 = precision == LBM_FP64 ? 2 : (precision == LBM_FP32_DEV ? 4 : 8);
-    const int v = variant == 1 ? v16 / 2 : (variant == 2 ? (v16 / 4 > 0 ? v16 / 4 : 1) : v16);
-    return SC_BLOCK_X * v;
-}
-
-cudaError_t launch_stream_collide_batch(const BatchLaunch &b, cudaStream_t st) {
-    switch (b.precision) {
-        case LBM_FP64: return launch_scb_p<LBM_FP64>(b, st);
-        case LBM_FP32_DEV: return launch_scb_p<LBM_FP32_DEV>(b, st);
-        default: return launch_scb_p<LBM_FP16_DEV>(b, st);
-    }
-}
 
 cudaError_t launch_stream_collide(const StepParams &p, cudaStream_t st) {
     switch (p.precision) {
@@ -500,6 +58,26 @@ cudaError_t launch_stream_collide(const StepParams &p, cudaStream_t st) {
         case LBM_FP32_DEV: return launch_sc_p<LBM_FP32_DEV>(p, st);
         default: return launch_sc_p<LBM_FP16_DEV>(p, st);
     }
+}
+
+cudaError_t launch_open_columns(const StepParams &p, cudaStream_t st) {
+    if (p.L.bc_x != LBM_OPEN) return cudaSuccess;
+    const bool force = p.body_x != 0.0 || p.body_y != 0.0;
+    const dim3 grid((p.L.ny + 127) / 128);
+    switch (p.precision) {
+        case LBM_FP64:
+            if (force) k_open_columns<LBM_FP64, true><<<grid, 128, 0, st>>>(p);
+            else k_open_columns<LBM_FP64, false><<<grid, 128, 0, st>>>(p);
+            break;
+        case LBM_FP32_DEV:
+            if (force) k_open_columns<LBM_FP32_DEV, true><<<grid, 128, 0, st>>>(p);
+            else k_open_columns<LBM_FP32_DEV, false><<<grid, 128, 0, st>>>(p);
+            break;
+        default:
+            if (force) k_open_columns<LBM_FP16_DEV, true><<<grid, 128, 0, st>>>(p);
+            else k_open_columns<LBM_FP16_DEV, false><<<grid, 128, 0, st>>>(p);
+    }
+    return cudaGetLastError();
 }
 
 }  // namespace gbm

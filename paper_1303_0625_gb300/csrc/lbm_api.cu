@@ -196,6 +196,10 @@ lbm_status enqueue_step(lbm_ctx *c, const StepParams &p, bool timed) {
         CK(c, cudaEventRecord(c->ev[c->ev_used + 1], c->stream));
         c->ev_used += 2;
     }
+    if (p.L.bc_x == LBM_OPEN) {
+        CK(c, gbm::launch_open_columns(p, c->stream));
+        c->launches++;
+    }
     if (p.nsolid > 0) CK(c, gbm::launch_solids(p, p.nmoving > 0 ? gbm::SOLIDS_REMASK : 0, c->stream));
     else CK(c, gbm::launch_tick(p, c->stream));
     c->launches += 2;
@@ -439,7 +443,7 @@ lbm_status lbm_step(lbm_ctx *c, int64_t n) {
                 CK(c, e);
             }
             CK(c, cudaGraphLaunch(c->gexec, c->stream));
-            c->launches += 2 * (int64_t)c->graph_steps;
+            c->launches += (c->cfg.bc_x == LBM_OPEN ? 3 : 2) * (int64_t)c->graph_steps;
             done += c->graph_steps;
         }
     }
@@ -816,6 +820,7 @@ struct lbm_batch {
     std::vector<lbm_ctx *> cases;
     int precision = 0, rho_w_mode = 0;
     bool force = false;
+    bool open = false;  // some case is an open channel
     // launch policy
     int variant = 0;
     bool persistent = true, graph = true;
@@ -995,6 +1000,10 @@ lbm_status benqueue_step(lbm_batch *b, const gbm::BatchLaunch &l, bool timed) {
         BCK(b, cudaEventRecord(b->ev[b->ev_used + 1], b->stream));
         b->ev_used += 2;
     }
+    if (b->open) {
+        BCK(b, gbm::launch_open_batch(l, (int)b->cases.size(), b->stream));
+        b->launches++;
+    }
     BCK(b, gbm::launch_solids_batch(l, b->stream));
     b->launches += 2;
     return LBM_OK;
@@ -1088,6 +1097,7 @@ lbm_status lbm_batch_create(const lbm_config *configs, int32_t ncase, lbm_batch 
         c->batch = b;
         b->cases.push_back(c);
         if (g.body_force[0] != 0.0 || g.body_force[1] != 0.0) b->force = true;
+        if (g.bc_x == LBM_OPEN) b->open = true;
     }
     const size_t n = (size_t)ncase;
     cudaError_t e = cudaMalloc(&b->cases_d, n * sizeof(StepParams));
@@ -1187,7 +1197,7 @@ lbm_status lbm_batch_run(lbm_batch *b, int64_t steps, int32_t *nactive) {
                 BCK(b, e);
             }
             BCK(b, cudaGraphLaunch(b->gexec, b->stream));
-            b->launches += 2 * chunk + 1;
+            b->launches += (b->open ? 3 : 2) * chunk + 1;
         } else {
             st = bsteps(b, chunk);
             if (st != LBM_OK) return st;

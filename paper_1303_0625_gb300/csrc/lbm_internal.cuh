@@ -298,7 +298,12 @@ struct BatchState {
 
 // k_stream_collide.cu
 cudaError_t launch_stream_collide(const StepParams &p, cudaStream_t st);
+// open channel: columns 0 and nx-1 of the populations just written (t+1)
+cudaError_t launch_open_columns(const StepParams &p, cudaStream_t st);
+
+// k_stream_collide_batch.cu
 cudaError_t launch_stream_collide_batch(const BatchLaunch &b, cudaStream_t st);
+cudaError_t launch_open_batch(const BatchLaunch &b, int ncase, cudaStream_t st);
 int tile_nodes(int precision, int variant);  // nodes along x of one tile
 // k_solid_step.cu: per-solid work of a step in one cooperative launch (force
 // record of time t, motion, t += 1; with SOLIDS_REMASK also re-rasterisation
