@@ -320,7 +320,7 @@ def run_batch(a, local, stream, peak):
     b = G.Batch.from_workloads(ws, precision=G.LBM_FP32_DEV, force_ring=4, device=local,
                                stream=stream.cuda_stream)
     setup_s = time.time() - t0
-    variant, persistent = b.autotune(4)
+    variant, tile_rows, persistent = b.autotune(4)
     b.set_convergence(every=100, tol=1e-7, max_steps=2_000_000)
     b.run(a.batch_warmup)
     steps = a.batch_steps
@@ -350,7 +350,7 @@ def run_batch(a, local, stream, peak):
     out = {"workload": f"cylinder sweep: {len(ws)} channels, nx 128..1024, ny 64..512 (even), "
                        "one fixed disk r = ny/10, Poiseuille inlet, Re 1..100, tau 0.6, fp32",
            "cases": len(ws), "cells": int(cells.sum()), "setup_s": round(setup_s, 2),
-           "kernel_variant": variant, "persistent": bool(persistent),
+           "kernel_variant": variant, "tile_rows": tile_rows, "persistent": bool(persistent),
            "steps": steps, "ms": round(ms, 3), "ms_per_step": round(ms / steps, 5),
            "mlups": round(updates / (ms / 1e3) / 1e6, 1), "active_after": active,
            "converged": int((st == G.LBM_CASE_CONVERGED).sum()), "gpu_launches": launches,

@@ -286,17 +286,23 @@ lbm_status lbm_batch_run(lbm_batch *b, int64_t steps, int32_t *nactive);
  * before the first). */
 lbm_status lbm_batch_state(lbm_batch *b, int32_t *state, int64_t *steps, double *drag);
 
-/* Launch policy.  variant as for lbm_set_kernel_variant; persistent = 1 runs
- * the fused kernel as one resident block per slot walking the tile list, 0
- * as one block per tile.  graph = 1 captures the `every` steps between two
- * tests (and the test) into one CUDA graph (default 1). */
-lbm_status lbm_batch_set_launch(lbm_batch *b, int32_t variant, int32_t persistent, int32_t graph);
-lbm_status lbm_batch_get_launch(const lbm_batch *b, int32_t *variant, int32_t *persistent);
+/* Launch policy.  Tiles of the fused kernel are tile_rows rows (1..64) of
+ * 128 threads x the nodes per thread of `variant` (as for
+ * lbm_set_kernel_variant).  persistent = 1 runs the fused kernel as resident
+ * blocks walking the tile list, 0 as one block per tile (default).  graph = 1
+ * captures the `every` steps between two tests (and the test) into one CUDA
+ * graph (default 1).  Defaults: variant 0, 1 row, per-tile blocks. */
+lbm_status lbm_batch_set_launch(lbm_batch *b, int32_t variant, int32_t tile_rows,
+                                int32_t persistent, int32_t graph);
+lbm_status lbm_batch_get_launch(const lbm_batch *b, int32_t *variant, int32_t *tile_rows,
+                                int32_t *persistent);
 
-/* Autotuner: run 1 + steps real steps with each (variant, persistent) pair,
- * timing the fused kernel with CUDA events, and keep the fastest (stored in
- * best[0..1] when not NULL).  The batch advances by 6 (1 + steps) steps and
- * the drag history restarts.  Waits for the stream. */
+/* Autotuner: run 1 + steps real steps with each of LBM_BATCH_TUNE_SHAPES
+ * launch shapes (variant, rows per tile, persistent), timing the fused
+ * kernel with CUDA events, and keep the fastest (stored in best[0..2] when
+ * not NULL).  The batch advances by LBM_BATCH_TUNE_SHAPES (1 + steps) steps
+ * and the drag history restarts.  Waits for the stream. */
+#define LBM_BATCH_TUNE_SHAPES 10
 lbm_status lbm_batch_autotune(lbm_batch *b, int32_t steps, int32_t *best);
 
 /* Timing of the fused kernel as for lbm_set_timing / lbm_get_timing. */

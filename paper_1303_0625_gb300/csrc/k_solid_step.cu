@@ -203,11 +203,12 @@ __device__ __forceinline__ void rows_of(double Y0, double Y1, double r, int g, i
 // row) to the lanes of the warp, U nodes per lane at a time: fetch(i, j, u)
 // is called for all U nodes of a lane first (to issue their loads together),
 // then process(u, ok) for each, on every lane of the warp together (ok is
-// false for items past the end and for nodes fetch rejected).
+// false for items past the end and for nodes fetch rejected).  With nw > 1
+// warps sharing the rows, this warp (wi) takes the 32-row blocks wi, wi + nw ...
 template <int NB, class RF, class FF, class PF>
 __device__ __forceinline__ void warp_nodes_n(int j0, int j1, int lane, RF &&rng, FF &&fetch,
-                                             PF &&process) {
-    for (int jb = j0; jb <= j1; jb += 32) {
+                                             PF &&process, int wi = 0, int nw = 1) {
+    for (int jb = j0 + 32 * wi; jb <= j1; jb += 32 * nw) {
         const int j = jb + lane;
         Ranges R;
         R.a0 = R.a1 = 0;
@@ -353,11 +354,12 @@ __device__ __forceinline__ typename Prec<P>::C pop(const void *f, int plane, int
 // - (e_opp - v) f_bb, torque (x_s - R) x F (Eq. 7).  A candidate node's
 // flags, its 9 populations and its 8 neighbours' owners are loaded together.
 template <int P, bool LOCAL>
-__device__ void phase_forces(const StepParams &p, int s, int lane, long long t, const void *f) {
+__device__ void forces_sum(const StepParams &p, int s, int lane, const void *f, int wi, int nw,
+                           double (&acc)[6]) {
     using C = typename Prec<P>::C;
     using S = typename Prec<P>::S;
     constexpr int UF = 2;
-    DSolid &b = p.S[s];
+    const DSolid &b = p.S[s];
     const Lattice &L = p.L;
     const S *fs = static_cast<const S *>(f);
     const double X = b.x, Y = b.y;
@@ -429,11 +431,19 @@ __device__ void phase_forces(const StepParams &p, int s, int lane, long long t, 
                 lacc[4] += gmy;
                 lacc[5] += dx * gmy - dy * gmx;
             }
-        });
-    double acc[6];
+        },
+        wi, nw);
 #pragma unroll
     for (int q = 0; q < 6; q++) acc[q] = (double)lacc[q];
     warp_sum(acc);
+}
+
+// Force record of time t of solid s from its link sums acc (lane 0: Eq. 4
+// force and torque, then Eq. 5), plus the momentum booked into t; then its
+// motion to t+1.
+__device__ void record_forces(const StepParams &p, int s, int lane, long long t,
+                              const double (&acc)[6]) {
+    const DSolid &b = p.S[s];
     double fg[3] = {0.0, 0.0, 0.0};
     if (lane == 0) {
         const bool booked = b.pend_t == t;
@@ -448,6 +458,13 @@ __device__ void phase_forces(const StepParams &p, int s, int lane, long long t, 
         }
     }
     move_solid(p, s, lane, t, fg);
+}
+
+template <int P, bool LOCAL>
+__device__ void phase_forces(const StepParams &p, int s, int lane, long long t, const void *f) {
+    double acc[6];
+    forces_sum<P, LOCAL>(p, s, lane, f, 0, 1, acc);
+    record_forces(p, s, lane, t, acc);
 }
 
 // ------------------------------------------------------- phases A, B, D
@@ -839,7 +856,7 @@ cudaError_t launch_sw(const StepParams &p, int mode, cudaStream_t st) {
 // ------------------------------------------------------------- batch
 
 // Force records of a batch of independent domains whose solids rest: one
-// warp per (case, solid) item of the active list, phase F only.  The last
+// block per (case, solid) item of the active list, phase F only.  The last
 // block to finish (a ticket, no waiting) advances the step counter of every
 // active case, after every block has read it.
 template <int P, bool LOCAL>
@@ -848,16 +865,33 @@ __global__ void __launch_bounds__(SW_BLOCK)
                    const int *__restrict__ nitems, const int *__restrict__ active,
                    const int *__restrict__ nactive, unsigned int *ticket) {
     __shared__ bool last;
+    __shared__ double part[WARPS][6];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    const int gw = blockIdx.x * WARPS + wib, nw = gridDim.x * WARPS;
     const int n = *nitems;
-    for (int k = gw; k < n; k += nw) {
+    // one block per item: the warps share the disk's rows, then warp 0 adds
+    // their sums in warp order
+    for (int k = blockIdx.x; k < n; k += gridDim.x) {
         const int2 it = items[k];
         const StepParams &p = cases[it.x];
         const long long t = *p.t;
         const void *fcur = (t & 1) ? p.f1 : p.f0;
-        if (solid_ok(p.S[it.y])) phase_forces<P, LOCAL>(p, it.y, lane, t, fcur);
-        else if (lane == 0) atomicOr(p.status, 2);
+        if (!solid_ok(p.S[it.y])) {
+            if (threadIdx.x == 0) atomicOr(p.status, 2);
+            continue;
+        }
+        double acc[6];
+        forces_sum<P, LOCAL>(p, it.y, lane, fcur, wib, WARPS, acc);
+        if (lane == 0)
+            for (int q = 0; q < 6; q++) part[wib][q] = acc[q];
+        __syncthreads();
+        if (wib == 0) {
+            double tot[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+            if (lane == 0)
+                for (int w = 0; w < WARPS; w++)
+                    for (int q = 0; q < 6; q++) tot[q] += part[w][q];
+            record_forces(p, it.y, lane, t, tot);
+        }
+        __syncthreads();
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -884,7 +918,7 @@ cudaError_t launch_sb(const BatchLaunch &b, cudaStream_t st) {
                                                               SW_BLOCK, 0);
         if (e != cudaSuccess) return e;
     }
-    int blocks = (b.max_items + WARPS - 1) / WARPS;
+    int blocks = b.max_items;
     if (blocks > per_sm * sms) blocks = per_sm * sms;
     if (blocks < 1) blocks = 1;
     k_solids_batch<P, LOCAL><<<blocks, SW_BLOCK, 0, st>>>(b.cases, b.items, b.nitems, b.active,
@@ -904,7 +938,7 @@ constexpr int CV_BLOCK = 1024;
 __global__ void __launch_bounds__(CV_BLOCK)
     k_batch_converge(BatchLaunch b, int ncase, double tol, long long max_steps, int mode,
                      int *state, double *drag, long long *steps, int *toff, int *ioff,
-                     int tile_w) {
+                     int tile_w, int tile_h) {
     __shared__ int changed;
     __shared__ int wsum[3][CV_BLOCK / 32];
     __shared__ int carry[3];
@@ -951,7 +985,7 @@ __global__ void __launch_bounds__(CV_BLOCK)
         if (c < ncase && state[c] == 0) {
             const Lattice &L = b.cases[c].L;
             v[0] = 1;
-            v[1] = (L.nx + tile_w - 1) / tile_w * L.ny;
+            v[1] = (L.nx + tile_w - 1) / tile_w * ((L.ny + tile_h - 1) / tile_h);
             v[2] = b.cases[c].nsolid;
         }
         int inc[3];
@@ -1003,8 +1037,10 @@ __global__ void __launch_bounds__(CV_BLOCK)
     for (int a = 0; a < na; a++) {
         const int c = b.active[a];
         const Lattice &L = b.cases[c].L;
-        const int nbx = (L.nx + tile_w - 1) / tile_w, nt = nbx * L.ny, o = toff[c];
-        for (int k = tid; k < nt; k += CV_BLOCK) tiles[o + k] = make_int4(c, k % nbx, k / nbx, 0);
+        const int nbx = (L.nx + tile_w - 1) / tile_w, nby = (L.ny + tile_h - 1) / tile_h;
+        const int nt = nbx * nby, o = toff[c];
+        for (int k = tid; k < nt; k += CV_BLOCK)
+            tiles[o + k] = make_int4(c, k % nbx, (k / nbx) * tile_h, 0);
         const int ns = b.cases[c].nsolid, oi = ioff[c];
         for (int s = tid; s < ns; s += CV_BLOCK) items[oi + s] = make_int2(c, s);
     }
@@ -1024,7 +1060,7 @@ cudaError_t launch_batch_converge(const BatchLaunch &b, const BatchState &s, int
                                   cudaStream_t st) {
     k_batch_converge<<<1, CV_BLOCK, 0, st>>>(b, s.ncase, s.tol, s.max_steps, mode,
                                              s.state, s.drag, s.steps, s.toff, s.ioff,
-                                             tile_nodes(b.precision, b.variant));
+                                             tile_nodes(b.precision, b.variant), b.tile_h);
     return cudaGetLastError();
 }
 

@@ -9,7 +9,7 @@ namespace {
 
 template <int P, int V, bool FORCE, bool LOCAL>
 __global__ void __launch_bounds__(SC_BLOCK_X) k_stream_collide(const StepParams p) {
-    sc_tile<P, V, FORCE, LOCAL>(p, blockIdx.x, blockIdx.y);
+    sc_tile<P, V, FORCE, LOCAL, false>(p, blockIdx.x, blockIdx.y);
 }
 
 // Open-channel columns of every row, on the populations of t+1.

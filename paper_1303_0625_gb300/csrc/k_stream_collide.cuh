@@ -13,8 +13,9 @@
 // at the row ends), so DRAM sees each population plane read once, fully
 // coalesced.  Results go out as nine 128-bit stores (nodes in the row padding
 // store zeros).  Nodes next to a solid or a wall and the first and last
-// column take a per-node path; the columns of an open channel are replaced
-// afterwards by a separate pass (open_row).
+// column take a per-node path, which in the batch kernels (OPEN) also
+// computes the columns of an open channel; the single-domain kernel leaves
+// those to a separate pass (open_row), to keep its per-node path small.
 //
 // Bounce-back: a node whose flags word has bit i set (x - e_i solid or
 // outside) replaces population i by f~_opp(x) + 6 w_i rho_w (e_i . v), v the
@@ -170,11 +171,73 @@ __device__ __forceinline__ void collide(const StepParams &p, typename Prec<P>::C
     }
 }
 
+// Inlet profile of an open channel at row y: u_in = 4 umax y' (ny - y') / ny^2,
+// y' = y + 1/2 (walls at y = -1/2 and ny - 1/2).
+template <class C>
+__device__ __forceinline__ C inlet_ux(const StepParams &p, int y) {
+    const double h = (double)p.L.ny, yy = (double)y + 0.5;
+    return (C)(4.0 * p.umax * yy * (h - yy) / (h * h));
+}
+
+// feq(rho0, (u_in, 0)) into g (deviation form in the deviation modes).
+template <int P>
+__device__ __forceinline__ void inlet_equilibrium(const StepParams &p, typename Prec<P>::C u_in,
+                                                  typename Prec<P>::C (&g)[9]) {
+    using C = typename Prec<P>::C;
+    const C r = pick<C>(p.rho0, p.rho0_f);
+#pragma unroll
+    for (int i = 0; i < 9; i++) {
+        const C eu = (C)cx(i) * u_in;
+        const C poly = (C)3 * eu + (C)4.5 * eu * eu - (C)1.5 * u_in * u_in;
+        g[i] = Prec<P>::dev ? wgt<C>(i) * ((r - (C)1) + r * poly) : r * wgt<C>(i) * ((C)1 + poly);
+    }
+}
+
+// Non-equilibrium extrapolation onto an open column from the post-collision
+// populations g of its inner neighbour n, in place: g + feq(rho_b, u_b) -
+// feq(rho_n, u_n), with rho_n, u_n the neighbour's density and velocity (BGK
+// keeps rho and rho u; Guo forcing adds F to rho u).  Inlet: u_b = (u_in, 0),
+// rho_b = rho_n; outlet: rho_b = rho0, u_b = u_n.
+template <int P, bool FORCE>
+__device__ __forceinline__ void extrapolate_open(const StepParams &p, bool inlet,
+                                                 typename Prec<P>::C u_in,
+                                                 typename Prec<P>::C (&g)[9]) {
+    using C = typename Prec<P>::C;
+    C s0 = 0, jx = 0, jy = 0;
+#pragma unroll
+    for (int i = 0; i < 9; i++) {
+        s0 += g[i];
+        jx += (C)cx(i) * g[i];
+        jy += (C)cy(i) * g[i];
+    }
+    const C rn = Prec<P>::dev ? (C)1 + s0 : s0;
+    if (FORCE) {
+        jx -= (C)0.5 * pick<C>(p.body_x, p.body_xf);
+        jy -= (C)0.5 * pick<C>(p.body_y, p.body_yf);
+    }
+    const C uxn = jx / rn, uyn = jy / rn;
+    const C ub = inlet ? u_in : uxn, vb = inlet ? (C)0 : uyn;
+    const C rb = inlet ? rn : pick<C>(p.rho0, p.rho0_f);
+    const C uun = uxn * uxn + uyn * uyn, uub = ub * ub + vb * vb;
+#pragma unroll
+    for (int i = 0; i < 9; i++) {
+        const C en = (C)cx(i) * uxn + (C)cy(i) * uyn, eb = (C)cx(i) * ub + (C)cy(i) * vb;
+        const C pn = (C)3 * en + (C)4.5 * en * en - (C)1.5 * uun;
+        const C pb = (C)3 * eb + (C)4.5 * eb * eb - (C)1.5 * uub;
+        g[i] += wgt<C>(i) * ((rb - rn) + rb * pb - rn * pn);
+    }
+}
+
 // Complete update of one node, with periodic wrap, bounce-back and walls
 // (beyond a non-periodic edge: a resting wall): used for the nodes the vector
 // path leaves out (fluid nodes next to a solid or wall, the first and last
-// column).
-template <int P, bool FORCE, bool LOCAL>
+// column).  With OPEN, the columns of an open channel are computed here too:
+// the update of the inner neighbour (x = 1 or nx - 2, recomputed from fin)
+// followed by the non-equilibrium extrapolation; next to a solid neighbour
+// the inlet is feq(rho0, u_in) and the outlet updates as a walled node.
+// Without OPEN they update as walled nodes and a later pass (open_col)
+// replaces them.
+template <int P, bool FORCE, bool LOCAL, bool OPEN>
 __device__ __noinline__ void update_node(const StepParams &p, const typename Raw<P>::R *fin,
                                          typename Raw<P>::R *fout, int x, int y) {
     using C = typename Prec<P>::C;
@@ -189,10 +252,28 @@ __device__ __noinline__ void update_node(const StepParams &p, const typename Raw
         for (int i = 0; i < 9; i++) put(fout[i * plane + k], (C)0);
         return;
     }
+    int xu = x;  // node whose update is computed
+    uint16_t flu = fl;
+    bool open = false;
+    C u_in = 0;
+    if (OPEN && L.bc_x == LBM_OPEN && (x == 0 || x == L.nx - 1)) {
+        const uint16_t fln = p.flags[x == 0 ? k + 1 : k - 1];
+        if (x == 0) u_in = inlet_ux<C>(p, y);
+        if (!(fln & 1u)) {
+            open = true;
+            xu = x == 0 ? 1 : x - 1;
+            flu = fln;
+        } else if (x == 0) {
+            inlet_equilibrium<P>(p, u_in, g);
+#pragma unroll
+            for (int i = 0; i < 9; i++) put(fout[i * plane + k], g[i]);
+            return;
+        }
+    }
     const bool per_x = L.bc_x == LBM_PERIODIC, per_y = L.bc_y == LBM_PERIODIC;
 #pragma unroll
     for (int i = 0; i < 9; i++) {
-        int xs = x - cx(i), ys = y - cy(i);
+        int xs = xu - cx(i), ys = y - cy(i);
         // wrap along periodic axes; clamp elsewhere (the value is then bounced)
         if (xs < 0) xs = per_x ? xs + L.nx : 0;
         if (xs >= L.nx) xs = per_x ? xs - L.nx : L.nx - 1;
@@ -200,8 +281,9 @@ __device__ __noinline__ void update_node(const StepParams &p, const typename Raw
         if (ys >= L.ny) ys = per_y ? ys - L.ny : L.ny - 1;
         g[i] = cvt(fin[i * plane + ys * L.pitch + xs]);
     }
-    if (fl & 0x1FEu) bounce<P, LOCAL>(p, fin, x, y, fl, g);
+    if (flu & 0x1FEu) bounce<P, LOCAL>(p, fin, xu, y, flu, g);
     collide<P, FORCE>(p, g);
+    if (OPEN && open) extrapolate_open<P, FORCE>(p, x == 0, u_in, g);
 #pragma unroll
     for (int i = 0; i < 9; i++) {
         R v;
@@ -212,7 +294,7 @@ __device__ __noinline__ void update_node(const StepParams &p, const typename Raw
 
 // One tile: row y, nodes bx * SC_BLOCK_X * V .. + SC_BLOCK_X * V - 1 (the
 // whole block works on the same tile).
-template <int P, int V, bool FORCE, bool LOCAL>
+template <int P, int V, bool FORCE, bool LOCAL, bool OPEN>
 __device__ __forceinline__ void sc_tile(const StepParams &p, int bx, int y) {
     using R = typename Raw<P>::R;
     using C = typename Prec<P>::C;
@@ -328,75 +410,43 @@ __device__ __forceinline__ void sc_tile(const StepParams &p, int bx, int y) {
     while (slow) {
         const int j = __ffs(slow) - 1;
         slow &= slow - 1;
-        update_node<P, FORCE, LOCAL>(p, fin, fout, x0 + j, y);
+        update_node<P, FORCE, LOCAL, OPEN>(p, fin, fout, x0 + j, y);
     }
 }
 
 // Open channel (bc_x = LBM_OPEN), after the fused kernel of step t has
-// written the populations of t+1 into f: the columns x = 0 and x = nx - 1 of
-// row y take the non-equilibrium extrapolation of their inner neighbour n
-// (x = 1, x = nx - 2): f_b = f_n + feq(rho_b, u_b) - feq(rho_n, u_n), with
-// rho_n, u_n the neighbour's density and velocity (from its post-collision
-// populations: BGK keeps rho and rho u, Guo forcing adds F to rho u).
-// Inlet: u_b = (u_in(y), 0), the parabolic profile of peak umax, and rho_b =
-// rho_n; outlet: rho_b = rho0, u_b = u_n.  Next to a solid neighbour the
-// inlet takes feq(rho0, u_in) and the outlet keeps its own update (a resting
-// wall beyond the edge).
+// written the populations of t+1 into f: column x = 0 (inlet) or x = nx - 1
+// (outlet) of row y takes the non-equilibrium extrapolation of its inner
+// neighbour's post-collision populations (extrapolate_open); next to a solid
+// neighbour the inlet takes feq(rho0, u_in) and the outlet keeps its own
+// update (a resting wall beyond the edge).  open_row does both columns.
 template <int P, bool FORCE>
-__device__ __forceinline__ void open_row(const StepParams &p, typename Raw<P>::R *f, int y) {
+__device__ __forceinline__ void open_col(const StepParams &p, typename Raw<P>::R *f, int y,
+                                         bool inlet) {
     using C = typename Prec<P>::C;
     const Lattice &L = p.L;
     const int plane = (int)L.plane;
-    for (int side = 0; side < 2; side++) {
-        const bool inlet = side == 0;
-        const int x = inlet ? 0 : L.nx - 1;
-        const int k = y * L.pitch + x, kn = inlet ? k + 1 : k - 1;
-        if (p.flags[k] & 1u) continue;
-        C u_in = 0;
-        if (inlet) {
-            const double h = (double)L.ny, yy = (double)y + 0.5;
-            u_in = (C)(4.0 * p.umax * yy * (h - yy) / (h * h));
-        }
-        C g[9];
-        if (p.flags[kn] & 1u) {
-            if (!inlet) continue;
-            const C r = pick<C>(p.rho0, p.rho0_f);
+    const int x = inlet ? 0 : L.nx - 1;
+    const int k = y * L.pitch + x, kn = inlet ? k + 1 : k - 1;
+    if (p.flags[k] & 1u) return;
+    const C u_in = inlet ? inlet_ux<C>(p, y) : (C)0;
+    C g[9];
+    if (p.flags[kn] & 1u) {
+        if (!inlet) return;
+        inlet_equilibrium<P>(p, u_in, g);
+    } else {
 #pragma unroll
-            for (int i = 0; i < 9; i++) {
-                const C eu = (C)cx(i) * u_in;
-                const C poly = (C)3 * eu + (C)4.5 * eu * eu - (C)1.5 * u_in * u_in;
-                g[i] = Prec<P>::dev ? wgt<C>(i) * ((r - (C)1) + r * poly)
-                                    : r * wgt<C>(i) * ((C)1 + poly);
-            }
-        } else {
-            C s0 = 0, jx = 0, jy = 0;
-#pragma unroll
-            for (int i = 0; i < 9; i++) {
-                g[i] = cvt(f[i * plane + kn]);
-                s0 += g[i];
-                jx += (C)cx(i) * g[i];
-                jy += (C)cy(i) * g[i];
-            }
-            const C rn = Prec<P>::dev ? (C)1 + s0 : s0;
-            if (FORCE) {
-                jx -= (C)0.5 * pick<C>(p.body_x, p.body_xf);
-                jy -= (C)0.5 * pick<C>(p.body_y, p.body_yf);
-            }
-            const C uxn = jx / rn, uyn = jy / rn;
-            const C ub = inlet ? u_in : uxn, vb = inlet ? (C)0 : uyn;
-            const C rb = inlet ? rn : pick<C>(p.rho0, p.rho0_f);
-            const C uun = uxn * uxn + uyn * uyn, uub = ub * ub + vb * vb;
-#pragma unroll
-            for (int i = 0; i < 9; i++) {
-                const C en = (C)cx(i) * uxn + (C)cy(i) * uyn, eb = (C)cx(i) * ub + (C)cy(i) * vb;
-                const C pn = (C)3 * en + (C)4.5 * en * en - (C)1.5 * uun;
-                const C pb = (C)3 * eb + (C)4.5 * eb * eb - (C)1.5 * uub;
-                g[i] += wgt<C>(i) * ((rb - rn) + rb * pb - rn * pn);
-            }
-        }
-#pragma unroll
-        for (int i = 0; i < 9; i++) put(f[i * plane + k], g[i]);
+        for (int i = 0; i < 9; i++) g[i] = cvt(f[i * plane + kn]);
+        extrapolate_open<P, FORCE>(p, inlet, u_in, g);
     }
+#pragma unroll
+    for (int i = 0; i < 9; i++) put(f[i * plane + k], g[i]);
+}
+
+template <int P, bool FORCE>
+__device__ __forceinline__ void open_row(const StepParams &p, typename Raw<P>::R *f, int y) {
+    open_col<P, FORCE>(p, f, y, true);
+    open_col<P, FORCE>(p, f, y, false);
 }
 
 }  // namespace

@@ -1,7 +1,7 @@
 // The fused kernel over a batch of independent domains (cases): the tiles
-// {case, x block, row} of every active case in one launch, each tile with its
-// own case's parameters and step counter; and the open-channel columns of
-// every active case.  The device code is in k_stream_collide.cuh.
+// {case, x block, first row} of every active case in one launch, each tile
+// with its own case's parameters and step counter; open-channel columns are
+// computed by the per-node path.  The device code is in k_stream_collide.cuh.
 #include "k_stream_collide.cuh"
 
 namespace gbm {
@@ -9,16 +9,19 @@ namespace gbm {
 namespace {
 
 // Batch of independent domains: persistent blocks walk the list of active
-// tiles {case, x block, row} of all cases (case-major), each tile with its
-// own case's parameters and step counter.
+// tiles {case, x block, first row} of all cases (case-major), each tile
+// (tile_h rows of SC_BLOCK_X * V nodes) with its own case's parameters and
+// step counter.
 template <int P, int V, bool FORCE, bool LOCAL>
 __global__ void __launch_bounds__(SC_BLOCK_X, 6)
     k_stream_collide_batch(const StepParams *__restrict__ cases, const int4 *__restrict__ tiles,
-                           const int *__restrict__ ntiles) {
+                           const int *__restrict__ ntiles, int tile_h) {
     const int n = *ntiles;
     for (int k = blockIdx.x; k < n; k += gridDim.x) {
         const int4 tl = tiles[k];
-        sc_tile<P, V, FORCE, LOCAL>(cases[tl.x], tl.y, tl.z);
+        const StepParams &p = cases[tl.x];
+        const int y1 = min(tl.z + tile_h, p.L.ny);
+        for (int y = tl.z; y < y1; y++) sc_tile<P, V, FORCE, LOCAL, true>(p, tl.y, y);
     }
 }
 
@@ -28,26 +31,19 @@ __global__ void __launch_bounds__(SC_BLOCK_X, 6)
 template <int P, int V>
 constexpr int tiles_min_blocks() { return (P == LBM_FP32_DEV && V <= 2) ? 10 : 6; }
 
-template <int P, int V, bool FORCE, bool LOCAL>
+template <int P, int V, bool FORCE, bool LOCAL, bool ROWS>
 __global__ void __launch_bounds__(SC_BLOCK_X, (tiles_min_blocks<P, V>()))
     k_stream_collide_tiles(const StepParams *__restrict__ cases, const int4 *__restrict__ tiles,
-                           const int *__restrict__ ntiles) {
+                           const int *__restrict__ ntiles, int tile_h) {
     if ((int)blockIdx.x >= *ntiles) return;
     const int4 tl = tiles[blockIdx.x];
-    sc_tile<P, V, FORCE, LOCAL>(cases[tl.x], tl.y, tl.z);
-}
-
-// Open-channel columns of the active cases: one block per active case.
-template <int P, bool FORCE>
-__global__ void k_open_batch(const StepParams *__restrict__ cases, const int *__restrict__ active,
-                             const int *__restrict__ nactive) {
-    using R = typename Raw<P>::R;
-    if ((int)blockIdx.x >= *nactive) return;
-    const StepParams &p = cases[active[blockIdx.x]];
-    if (p.L.bc_x != LBM_OPEN) return;
-    const long long t = *p.t;
-    R *f = static_cast<R *>((t & 1) ? p.f0 : p.f1);
-    for (int y = threadIdx.x; y < p.L.ny; y += blockDim.x) open_row<P, FORCE>(p, f, y);
+    const StepParams &p = cases[tl.x];
+    if (!ROWS) {
+        sc_tile<P, V, FORCE, LOCAL, true>(p, tl.y, tl.z);
+        return;
+    }
+    const int y1 = min(tl.z + tile_h, p.L.ny);
+    for (int y = tl.z; y < y1; y++) sc_tile<P, V, FORCE, LOCAL, true>(p, tl.y, y);
 }
 
 template <int P, int V, bool FORCE, bool LOCAL>
@@ -64,10 +60,13 @@ cudaError_t launch_scb(const BatchLaunch &b, cudaStream_t st) {
     }
     if (b.persistent)
         k_stream_collide_batch<P, V, FORCE, LOCAL>
-            <<<per_sm * sms, SC_BLOCK_X, 0, st>>>(b.cases, b.tiles, b.ntiles);
+            <<<per_sm * sms, SC_BLOCK_X, 0, st>>>(b.cases, b.tiles, b.ntiles, b.tile_h);
+    else if (b.max_tiles > 0 && b.tile_h == 1)
+        k_stream_collide_tiles<P, V, FORCE, LOCAL, false>
+            <<<b.max_tiles, SC_BLOCK_X, 0, st>>>(b.cases, b.tiles, b.ntiles, 1);
     else if (b.max_tiles > 0)
-        k_stream_collide_tiles<P, V, FORCE, LOCAL>
-            <<<b.max_tiles, SC_BLOCK_X, 0, st>>>(b.cases, b.tiles, b.ntiles);
+        k_stream_collide_tiles<P, V, FORCE, LOCAL, true>
+            <<<b.max_tiles, SC_BLOCK_X, 0, st>>>(b.cases, b.tiles, b.ntiles, b.tile_h);
     return cudaGetLastError();
 }
 
@@ -88,13 +87,6 @@ cudaError_t launch_scb_p(const BatchLaunch &b, cudaStream_t st) {
     }
 }
 
-template <int P>
-cudaError_t launch_ob(const BatchLaunch &b, int ncase, cudaStream_t st) {
-    if (b.force) k_open_batch<P, true><<<ncase, 128, 0, st>>>(b.cases, b.active, b.nactive);
-    else k_open_batch<P, false><<<ncase, 128, 0, st>>>(b.cases, b.active, b.nactive);
-    return cudaGetLastError();
-}
-
 }  // namespace
 
 int tile_nodes(int precision, int variant) {
@@ -108,14 +100,6 @@ cudaError_t launch_stream_collide_batch(const BatchLaunch &b, cudaStream_t st) {
         case LBM_FP64: return launch_scb_p<LBM_FP64>(b, st);
         case LBM_FP32_DEV: return launch_scb_p<LBM_FP32_DEV>(b, st);
         default: return launch_scb_p<LBM_FP16_DEV>(b, st);
-    }
-}
-
-cudaError_t launch_open_batch(const BatchLaunch &b, int ncase, cudaStream_t st) {
-    switch (b.precision) {
-        case LBM_FP64: return launch_ob<LBM_FP64>(b, ncase, st);
-        case LBM_FP32_DEV: return launch_ob<LBM_FP32_DEV>(b, ncase, st);
-        default: return launch_ob<LBM_FP16_DEV>(b, ncase, st);
     }
 }
 

@@ -820,10 +820,10 @@ struct lbm_batch {
     std::vector<lbm_ctx *> cases;
     int precision = 0, rho_w_mode = 0;
     bool force = false;
-    bool open = false;  // some case is an open channel
     // launch policy
     int variant = 0;
-    bool persistent = true, graph = true;
+    int tile_h = 1;  // rows per tile of the fused kernel
+    bool persistent = false, graph = true;
     // convergence test
     int every = 100;
     double tol = 1e-7;
@@ -897,6 +897,7 @@ gbm::BatchLaunch blaunch(const lbm_batch *b) {
     l.local = b->rho_w_mode == LBM_RHOW_LOCAL;
     l.max_items = b->max_items;
     l.max_tiles = b->max_tiles;
+    l.tile_h = b->tile_h;
     l.persistent = b->persistent;
     return l;
 }
@@ -946,7 +947,7 @@ lbm_status bprepare(lbm_batch *b) {
     std::vector<StepParams> hp(b->cases.size());
     for (size_t k = 0; k < b->cases.size(); k++) {
         const lbm_ctx *c = b->cases[k];
-        tiles += (long long)((c->cfg.nx + w - 1) / w) * c->cfg.ny;
+        tiles += (long long)((c->cfg.nx + w - 1) / w) * ((c->cfg.ny + b->tile_h - 1) / b->tile_h);
         tiles_min += (long long)((c->cfg.nx + wmin - 1) / wmin) * c->cfg.ny;
         items += c->nsolid;
         hp[k] = params(c);
@@ -999,10 +1000,6 @@ lbm_status benqueue_step(lbm_batch *b, const gbm::BatchLaunch &l, bool timed) {
     if (timed) {
         BCK(b, cudaEventRecord(b->ev[b->ev_used + 1], b->stream));
         b->ev_used += 2;
-    }
-    if (b->open) {
-        BCK(b, gbm::launch_open_batch(l, (int)b->cases.size(), b->stream));
-        b->launches++;
     }
     BCK(b, gbm::launch_solids_batch(l, b->stream));
     b->launches += 2;
@@ -1097,7 +1094,6 @@ lbm_status lbm_batch_create(const lbm_config *configs, int32_t ncase, lbm_batch 
         c->batch = b;
         b->cases.push_back(c);
         if (g.body_force[0] != 0.0 || g.body_force[1] != 0.0) b->force = true;
-        if (g.bc_x == LBM_OPEN) b->open = true;
     }
     const size_t n = (size_t)ncase;
     cudaError_t e = cudaMalloc(&b->cases_d, n * sizeof(StepParams));
@@ -1197,7 +1193,7 @@ lbm_status lbm_batch_run(lbm_batch *b, int64_t steps, int32_t *nactive) {
                 BCK(b, e);
             }
             BCK(b, cudaGraphLaunch(b->gexec, b->stream));
-            b->launches += (b->open ? 3 : 2) * chunk + 1;
+            b->launches += 2 * chunk + 1;
         } else {
             st = bsteps(b, chunk);
             if (st != LBM_OK) return st;
@@ -1240,19 +1236,24 @@ lbm_status lbm_batch_state(lbm_batch *b, int32_t *state, int64_t *steps, double 
     return LBM_OK;
 }
 
-lbm_status lbm_batch_set_launch(lbm_batch *b, int32_t variant, int32_t persistent, int32_t graph) {
-    if (!b || variant < 0 || variant > 2) return LBM_EINVAL;
-    if (variant != b->variant || (persistent != 0) != b->persistent) b->dirty = true;
+lbm_status lbm_batch_set_launch(lbm_batch *b, int32_t variant, int32_t tile_rows,
+                                int32_t persistent, int32_t graph) {
+    if (!b || variant < 0 || variant > 2 || tile_rows < 1 || tile_rows > 64) return LBM_EINVAL;
+    if (variant != b->variant || tile_rows != b->tile_h || (persistent != 0) != b->persistent)
+        b->dirty = true;
     b->variant = variant;
+    b->tile_h = tile_rows;
     b->persistent = persistent != 0;
     b->graph = graph != 0;
     bdrop_graph(b);
     return LBM_OK;
 }
 
-lbm_status lbm_batch_get_launch(const lbm_batch *b, int32_t *variant, int32_t *persistent) {
+lbm_status lbm_batch_get_launch(const lbm_batch *b, int32_t *variant, int32_t *tile_rows,
+                                int32_t *persistent) {
     if (!b) return LBM_EINVAL;
     if (variant) *variant = b->variant;
+    if (tile_rows) *tile_rows = b->tile_h;
     if (persistent) *persistent = b->persistent ? 1 : 0;
     return LBM_OK;
 }
@@ -1288,36 +1289,39 @@ lbm_status lbm_batch_autotune(lbm_batch *b, int32_t steps, int32_t *best) {
     const bool was_timing = b->timing;
     const double keep_ms = b->timed_ms;
     const int64_t keep_n = b->timed_launches;
+    // {variant, rows per tile, persistent}
+    static const int kShapes[][3] = {{0, 1, 0}, {1, 1, 0}, {2, 1, 0}, {0, 2, 0}, {1, 2, 0},
+                                     {2, 2, 0}, {1, 4, 0}, {2, 4, 0}, {1, 1, 1}, {2, 1, 1}};
     double best_ms = 0.0;
-    int best_v = 0, best_p = 1;
-    bool first = true;
-    for (int v = 0; v <= 2; v++) {
-        for (int pers = 1; pers >= 0; pers--) {
-            if (v != b->variant || (pers != 0) != b->persistent) b->dirty = true;
-            b->variant = v;
-            b->persistent = pers != 0;
-            st = bprepare(b);
-            if (st != LBM_OK) return st;
-            b->timing = true;
-            st = bsteps(b, 1);  // the first launch of a kernel is not timed
-            if (st == LBM_OK) st = bharvest(b);
-            b->timed_ms = 0.0;
-            b->timed_launches = 0;
-            if (st == LBM_OK) st = bsteps(b, steps);
-            if (st == LBM_OK) st = bharvest(b);
-            if (st != LBM_OK) return st;
-            const double ms = b->timed_ms / (b->timed_launches ? b->timed_launches : 1);
-            if (first || ms < best_ms) {
-                best_ms = ms;
-                best_v = v;
-                best_p = pers;
-                first = false;
-            }
+    int pick = 0;
+    const int nshape = (int)(sizeof kShapes / sizeof kShapes[0]);
+    for (int k = 0; k < nshape; k++) {
+        const int *sh = kShapes[k];
+        if (sh[0] != b->variant || sh[1] != b->tile_h || (sh[2] != 0) != b->persistent)
+            b->dirty = true;
+        b->variant = sh[0];
+        b->tile_h = sh[1];
+        b->persistent = sh[2] != 0;
+        st = bprepare(b);
+        if (st != LBM_OK) return st;
+        b->timing = true;
+        st = bsteps(b, 1);  // the first launch of a kernel is not timed
+        if (st == LBM_OK) st = bharvest(b);
+        b->timed_ms = 0.0;
+        b->timed_launches = 0;
+        if (st == LBM_OK) st = bsteps(b, steps);
+        if (st == LBM_OK) st = bharvest(b);
+        if (st != LBM_OK) return st;
+        const double ms = b->timed_ms / (b->timed_launches ? b->timed_launches : 1);
+        if (k == 0 || ms < best_ms) {
+            best_ms = ms;
+            pick = k;
         }
     }
     b->dirty = true;
-    b->variant = best_v;
-    b->persistent = best_p != 0;
+    b->variant = kShapes[pick][0];
+    b->tile_h = kShapes[pick][1];
+    b->persistent = kShapes[pick][2] != 0;
     b->timing = was_timing;
     b->timed_ms = keep_ms;
     b->timed_launches = keep_n;
@@ -1326,8 +1330,9 @@ lbm_status lbm_batch_autotune(lbm_batch *b, int32_t steps, int32_t *best) {
     if (st == LBM_OK) st = bgather(b);
     if (st != LBM_OK) return st;
     if (best) {
-        best[0] = best_v;
-        best[1] = best_p;
+        best[0] = kShapes[pick][0];
+        best[1] = kShapes[pick][1];
+        best[2] = kShapes[pick][2];
     }
     return LBM_OK;
 }

@@ -281,7 +281,8 @@ struct BatchLaunch {
     int precision, variant;
     bool force, local;
     int max_items;            // capacity of items (all solids of all cases)
-    int max_tiles;            // capacity of tiles (all tiles of all cases)
+    int max_tiles;            // tiles of all cases at the current tile shape
+    int tile_h;               // rows per tile
     bool persistent;          // fused kernel: persistent blocks, else one block per tile
 };
 
@@ -303,7 +304,6 @@ cudaError_t launch_open_columns(const StepParams &p, cudaStream_t st);
 
 // k_stream_collide_batch.cu
 cudaError_t launch_stream_collide_batch(const BatchLaunch &b, cudaStream_t st);
-cudaError_t launch_open_batch(const BatchLaunch &b, int ncase, cudaStream_t st);
 int tile_nodes(int precision, int variant);  // nodes along x of one tile
 // k_solid_step.cu: per-solid work of a step in one cooperative launch (force
 // record of time t, motion, t += 1; with SOLIDS_REMASK also re-rasterisation

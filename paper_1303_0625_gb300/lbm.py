@@ -98,8 +98,9 @@ _SIGNATURES = {
     "lbm_batch_set_convergence": (_I32, [_P, _I32, ctypes.c_double, _I64]),
     "lbm_batch_run": (_I32, [_P, _I64, ctypes.POINTER(_I32)]),
     "lbm_batch_state": (_I32, [_P, _P, _P, _P]),
-    "lbm_batch_set_launch": (_I32, [_P, _I32, _I32, _I32]),
-    "lbm_batch_get_launch": (_I32, [_P, ctypes.POINTER(_I32), ctypes.POINTER(_I32)]),
+    "lbm_batch_set_launch": (_I32, [_P, _I32, _I32, _I32, _I32]),
+    "lbm_batch_get_launch": (_I32, [_P, ctypes.POINTER(_I32), ctypes.POINTER(_I32),
+                                    ctypes.POINTER(_I32)]),
     "lbm_batch_autotune": (_I32, [_P, _I32, _P]),
     "lbm_batch_set_timing": (_I32, [_P, _I32]),
     "lbm_batch_get_timing": (_I32, [_P, _D, ctypes.POINTER(_I64)]),
@@ -333,20 +334,27 @@ def lbm_batch_state(b, state, steps, drag):
     _bcheck(load().lbm_batch_state(b, _ptr(state), _ptr(steps), _ptr(drag)), b)
 
 
-def lbm_batch_set_launch(b, variant: int, persistent: bool, graph: bool = True):
-    _bcheck(load().lbm_batch_set_launch(b, int(variant), int(bool(persistent)), int(bool(graph))), b)
+def lbm_batch_set_launch(b, variant: int, tile_rows: int = 1, persistent: bool = False,
+                         graph: bool = True):
+    _bcheck(load().lbm_batch_set_launch(b, int(variant), int(tile_rows), int(bool(persistent)),
+                                        int(bool(graph))), b)
 
 
 def lbm_batch_get_launch(b):
-    v, p = _I32(), _I32()
-    _bcheck(load().lbm_batch_get_launch(b, ctypes.byref(v), ctypes.byref(p)), b)
-    return int(v.value), int(p.value)
+    """(variant, tile_rows, persistent)"""
+    v, h, p = _I32(), _I32(), _I32()
+    _bcheck(load().lbm_batch_get_launch(b, ctypes.byref(v), ctypes.byref(h), ctypes.byref(p)), b)
+    return int(v.value), int(h.value), int(p.value)
+
+
+LBM_BATCH_TUNE_SHAPES = 10
 
 
 def lbm_batch_autotune(b, steps: int = 4):
-    best = np.zeros(2, dtype=np.int32)
+    """Fastest (variant, tile_rows, persistent); see lbm.h."""
+    best = np.zeros(3, dtype=np.int32)
     _bcheck(load().lbm_batch_autotune(b, int(steps), _ptr(best)), b)
-    return int(best[0]), int(best[1])
+    return int(best[0]), int(best[1]), int(best[2])
 
 
 def lbm_batch_set_timing(b, enable: bool):
@@ -595,14 +603,15 @@ class Batch:
             self._views[k] = v
         return self._views[k]
 
-    def set_launch(self, variant: int, persistent: bool = True, graph: bool = True):
-        lbm_batch_set_launch(self._h, variant, persistent, graph)
+    def set_launch(self, variant: int, tile_rows: int = 1, persistent: bool = False,
+                   graph: bool = True):
+        lbm_batch_set_launch(self._h, variant, tile_rows, persistent, graph)
 
     def launch(self):
         return lbm_batch_get_launch(self._h)
 
     def autotune(self, steps: int = 4, cache: str | None = None):
-        """Fastest (variant, persistent) of the fused kernel for this batch.
+        """Fastest (variant, tile_rows, persistent) of the fused kernel.
         With ``cache`` (a JSON file), a result stored under the same key (GPU
         name, precision and the batch's size classes) is reused without
         timing, and a new result is stored."""
@@ -616,9 +625,9 @@ class Batch:
             except (OSError, ValueError):
                 table = {}
             if key in table:
-                v, p = table[key]
-                self.set_launch(int(v), bool(p))
-                return int(v), int(p)
+                v, h, p = table[key]
+                self.set_launch(int(v), int(h), bool(p))
+                return int(v), int(h), int(p)
         best = lbm_batch_autotune(self._h, steps)
         if cache:
             import json

@@ -5,8 +5,8 @@ unstable case, and the autotuner's cache.
 
 Tolerances are those of the single-domain parity tests: FP64 forces <= 1e-12
 relative (scale as in _pairs.force_rel) and populations <= 1e-12 absolute;
-FP32 forces <= 1e-5.  A batch case and the same case run alone execute the
-same arithmetic, so they are compared for equality.
+FP32 forces <= 1e-5.  A batch case and the same case run alone evaluate the
+same expressions, so they are compared at rounding level.
 """
 import json
 
@@ -30,13 +30,20 @@ def _batch(ws, precision="fp64", ring=256, **kw):
 
 
 def _assert_same_case(b, k, w, steps, precision):
-    """Case k of the batch equals the same workload run alone."""
+    """Case k of the batch agrees with the same workload run alone to
+    rounding: the batch computes the open columns in its per-node path (the
+    neighbour's update recomputed there) where the single domain reads the
+    neighbour's stored update, and it splits a disk's link sums over the
+    warps of a block.  Populations within 1e-12 (FP64) / 1e-6 (FP32,
+    |f| < 0.5), forces within 1e-13 / 1e-6 of the force scale."""
     alone = make_gpu(w, precision, ring=steps)
     alone.step(steps)
     v = b.case(k)
     assert v.t == steps
-    assert np.array_equal(v.get_f(), alone.get_f())
-    assert np.array_equal(v.forces(0, steps), alone.forces(0, steps))
+    tol = 1e-13 if precision == "fp64" else 1e-6
+    assert np.abs(v.get_f() - alone.get_f()).max() <= (1e-12 if precision == "fp64" else 1e-6)
+    radii = [s["r"] for s in w["solids"]]
+    assert force_rel(v.forces(0, steps), alone.forces(0, steps), radii) <= tol
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
@@ -79,21 +86,22 @@ def test_batch_fp32_forces_against_fp64_oracle():
         assert force_rel(got, ref, [s["r"] for s in w["solids"]]) <= 1e-5
 
 
-@pytest.mark.parametrize("variant", [0, 1, 2])
-@pytest.mark.parametrize("persistent", [True, False])
-def test_batch_launch_policies_agree(variant, persistent):
-    """Tile width, persistent or per-tile blocks, graph or direct launches:
+@pytest.mark.parametrize("variant,rows,persistent",
+                         [(0, 1, False), (1, 1, False), (2, 1, False), (1, 2, False),
+                          (2, 4, False), (1, 3, False), (0, 1, True), (1, 2, True), (2, 1, True)])
+def test_batch_launch_policies_agree(variant, rows, persistent):
+    """Tile width and height, persistent or per-tile blocks, graph or direct launches:
     the same arithmetic, compiled separately per width, so populations agree
     to FP32 rounding (a few ulp after 40 steps; |f| < 0.5)."""
     ws = _sweep(4, seed=43)
     ref = _batch(ws, "fp32")
-    ref.set_launch(0, True, graph=False)
+    ref.set_launch(0, 1, False, graph=False)
     ref.run(40)
     b = _batch(ws, "fp32")
-    b.set_launch(variant, persistent, graph=True)
+    b.set_launch(variant, rows, persistent, graph=True)
     b.set_convergence(every=20, tol=0.0, max_steps=10**6)
     b.run(40)
-    assert b.launch() == (variant, int(persistent))
+    assert b.launch() == (variant, rows, int(persistent))
     for k in range(len(ws)):
         assert np.abs(b.case(k).get_f() - ref.case(k).get_f()).max() <= 1e-6
 
@@ -139,7 +147,7 @@ def test_step_cap_and_all_retired():
 
 def test_unstable_case_is_isolated():
     """A case driven far past the stability limit is retired as unstable;
-    the other cases are unaffected (equal to their runs alone)."""
+    the other cases are unaffected (they agree with their runs alone)."""
     ws = _sweep(3, seed=59)
     bad = dict(ws[1], tau=0.5001, inflow_umax=0.9)
     ws2 = [ws[0], bad, ws[2]]
@@ -181,7 +189,7 @@ def test_autotune_and_json_cache(tmp_path):
     table = json.loads(cache.read_text())
     assert list(table.values()) == [list(best)]
     _, steps, _ = b.state()
-    assert (steps == 6 * 4).all()  # 6 launch policies x (1 + 3) real steps
+    assert (steps == L.LBM_BATCH_TUNE_SHAPES * 4).all()  # every shape x (1 + 3) real steps
     b2 = _batch(ws, "fp32", ring=4)
     assert b2.autotune(steps=3, cache=str(cache)) == best
     _, steps2, _ = b2.state()
