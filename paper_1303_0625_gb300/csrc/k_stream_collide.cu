@@ -7,9 +7,9 @@ namespace gbm {
 
 namespace {
 
-template <int P, int V, bool FORCE, bool LOCAL>
+template <int P, int V, bool FORCE, bool LOCAL, bool WALLS>
 __global__ void __launch_bounds__(SC_BLOCK_X) k_stream_collide(const StepParams p) {
-    sc_tile<P, V, FORCE, LOCAL, false>(p, blockIdx.x, blockIdx.y);
+    sc_tile<P, V, FORCE, LOCAL, false, WALLS>(p, blockIdx.x, blockIdx.y);
 }
 
 // Open-channel columns of every row, on the populations of t+1.
@@ -22,10 +22,16 @@ __global__ void k_open_columns(const StepParams p) {
     open_row<P, FORCE>(p, static_cast<R *>((t & 1) ? p.f0 : p.f1), y);
 }
 
+// Walled domains (y walls) with rho_w = rho0 in FP32/FP64 take the kernel
+// whose vector path also covers the wall rows.
 template <int P, int V, bool FORCE, bool LOCAL>
 cudaError_t launch_sc(const StepParams &p, cudaStream_t st) {
     dim3 grid((p.L.nx + SC_BLOCK_X * V - 1) / (SC_BLOCK_X * V), p.L.ny);
-    k_stream_collide<P, V, FORCE, LOCAL><<<grid, SC_BLOCK_X, 0, st>>>(p);
+    if (walls_on_vector_path<P, LOCAL>() && p.L.bc_y == LBM_WALL)
+        k_stream_collide<P, V, FORCE, LOCAL, walls_on_vector_path<P, LOCAL>()>
+            <<<grid, SC_BLOCK_X, 0, st>>>(p);
+    else
+        k_stream_collide<P, V, FORCE, LOCAL, false><<<grid, SC_BLOCK_X, 0, st>>>(p);
     return cudaGetLastError();
 }
 

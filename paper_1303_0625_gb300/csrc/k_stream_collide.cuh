@@ -294,8 +294,14 @@ __device__ __noinline__ void update_node(const StepParams &p, const typename Raw
 
 // One tile: row y, nodes bx * SC_BLOCK_X * V .. + SC_BLOCK_X * V - 1 (the
 // whole block works on the same tile).
-template <int P, int V, bool FORCE, bool LOCAL, bool OPEN>
+// WALLS: bounce-back from the y walls on the vector path (FP32 and FP64 with
+// rho_w = rho0 only; FP16 storage would round the bounced values).
+template <int P, bool LOCAL>
+__host__ __device__ constexpr bool walls_on_vector_path() { return !LOCAL && P != LBM_FP16_DEV; }
+
+template <int P, int V, bool FORCE, bool LOCAL, bool OPEN, bool WALLS = false>
 __device__ __forceinline__ void sc_tile(const StepParams &p, int bx, int y) {
+    static_assert(!WALLS || walls_on_vector_path<P, LOCAL>(), "wall rows need rho0 and R == C");
     using R = typename Raw<P>::R;
     using C = typename Prec<P>::C;
     const Lattice &L = p.L;
@@ -351,6 +357,38 @@ __device__ __forceinline__ void sc_tile(const StepParams &p, int bx, int y) {
         halo[6] = hl[1];
         halo[7] = hl[2];
     }
+    // Wall rows (WALLS): the populations that arrive from the wall (y = -1/2
+    // or ny - 1/2) are the node's own opposite populations plus the moving-wall
+    // term, 6 w_i rho0 (e_i . u_wall) (Sec. III.A, rho_w = rho0).  They are
+    // written where the pulls below read them, so the row stays on the vector
+    // path; nodes with any other bounced population still take the per-node path.
+    uint16_t wall_bits = 0;
+    if (WALLS && L.bc_y == LBM_WALL && (y == 0 || y == L.ny - 1)) {
+        const bool lo = y == 0;
+        wall_bits = lo ? 0x64 : 0x190;  // {2, 5, 6} at y = 0, {4, 7, 8} at y = ny - 1
+        const C uw = lo ? pick<C>(p.wall_ux0, (float)p.wall_ux0) : pick<C>(p.wall_ux1, (float)p.wall_ux1);
+        const C rho_w = pick<C>(p.rho0, p.rho0_f);
+#pragma unroll
+        for (int i = 1; i < 9; i++) {
+            if (!((wall_bits >> i) & 1u)) continue;
+            Pack<R, V> own;  // the node's own population opp(i), row y
+            own.u = __ldg(reinterpret_cast<const typename Word<sizeof(R) * V>::T *>(
+                fin + opp(i) * plane + r0 + xl));
+            const C term = (C)6 * wgt<C>(i) * rho_w * ((C)cx(i) * uw);
+#pragma unroll
+            for (int j = 0; j < V; j++) {
+                const R b = (R)(cvt(own.r[j]) + term);
+                if (cx(i) == 0) raw[i].r[j] = b;
+                else if (cx(i) == 1) {
+                    if (j == 0) halo[i] = b;
+                    else raw[i].r[j - 1] = b;
+                } else {
+                    if (j == V - 1) halo[i] = b;
+                    else raw[i].r[j + 1] = b;
+                }
+            }
+        }
+    }
 #define PULL(i, j) \
     cvt(cx(i) == 0 ? raw[i].r[j] \
                    : (cx(i) == 1 ? ((j) == 0 ? halo[i] : raw[i].r[(j) - 1]) \
@@ -376,7 +414,7 @@ __device__ __forceinline__ void sc_tile(const StepParams &p, int bx, int y) {
         uy[j] = FORCE ? (jy + (C)0.5 * pick<C>(p.body_y, p.body_yf)) * inv : jy * inv;
         const uint16_t f = fl.f[j];
         const int x = x0 + j;
-        if (!(f & 1u) && ((f & 0x1FEu) || x == 0 || x == L.nx - 1)) slow |= 1u << j;
+        if (!(f & 1u) && ((f & 0x1FEu & ~wall_bits) || x == 0 || x == L.nx - 1)) slow |= 1u << j;
         else if (!(f & 1u) && x < L.nx &&
                  (!(r > (C)0) || !(fabs(ux[j]) < (C)1e30) || !(fabs(uy[j]) < (C)1e30)))
             atomicOr(p.status, 1);

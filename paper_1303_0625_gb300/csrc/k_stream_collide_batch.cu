@@ -21,7 +21,7 @@ __global__ void __launch_bounds__(SC_BLOCK_X, 6)
         const int4 tl = tiles[k];
         const StepParams &p = cases[tl.x];
         const int y1 = min(tl.z + tile_h, p.L.ny);
-        for (int y = tl.z; y < y1; y++) sc_tile<P, V, FORCE, LOCAL, true>(p, tl.y, y);
+        for (int y = tl.z; y < y1; y++) sc_tile<P, V, FORCE, LOCAL, true, walls_on_vector_path<P, LOCAL>()>(p, tl.y, y);
     }
 }
 
@@ -39,11 +39,11 @@ __global__ void __launch_bounds__(SC_BLOCK_X, (tiles_min_blocks<P, V>()))
     const int4 tl = tiles[blockIdx.x];
     const StepParams &p = cases[tl.x];
     if (!ROWS) {
-        sc_tile<P, V, FORCE, LOCAL, true>(p, tl.y, tl.z);
+        sc_tile<P, V, FORCE, LOCAL, true, walls_on_vector_path<P, LOCAL>()>(p, tl.y, tl.z);
         return;
     }
     const int y1 = min(tl.z + tile_h, p.L.ny);
-    for (int y = tl.z; y < y1; y++) sc_tile<P, V, FORCE, LOCAL, true>(p, tl.y, y);
+    for (int y = tl.z; y < y1; y++) sc_tile<P, V, FORCE, LOCAL, true, walls_on_vector_path<P, LOCAL>()>(p, tl.y, y);
 }
 
 template <int P, int V, bool FORCE, bool LOCAL>
