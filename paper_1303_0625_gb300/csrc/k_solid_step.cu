@@ -858,10 +858,11 @@ cudaError_t launch_sw(const StepParams &p, int mode, cudaStream_t st) {
 // Force records of a batch of independent domains whose solids rest: one
 // block per (case, solid) item of the active list, phase F only.  The last
 // block to finish (a ticket, no waiting) advances the step counter of every
-// active case, after every block has read it.
+// active case and swaps its population buffers (batch convention: f0 holds
+// the current time), after every block has read them.
 template <int P, bool LOCAL>
 __global__ void __launch_bounds__(SW_BLOCK)
-    k_solids_batch(const StepParams *__restrict__ cases, const int2 *__restrict__ items,
+    k_solids_batch(StepParams *cases, const int2 *__restrict__ items,
                    const int *__restrict__ nitems, const int *__restrict__ active,
                    const int *__restrict__ nactive, unsigned int *ticket) {
     __shared__ bool last;
@@ -874,7 +875,7 @@ __global__ void __launch_bounds__(SW_BLOCK)
         const int2 it = items[k];
         const StepParams &p = cases[it.x];
         const long long t = *p.t;
-        const void *fcur = (t & 1) ? p.f1 : p.f0;
+        const void *fcur = p.f0;  // batch convention: f0 holds time t
         if (!solid_ok(p.S[it.y])) {
             if (threadIdx.x == 0) atomicOr(p.status, 2);
             continue;
@@ -902,7 +903,13 @@ __global__ void __launch_bounds__(SW_BLOCK)
     if (!last) return;
     __threadfence();
     const int na = *nactive;
-    for (int a = threadIdx.x; a < na; a += blockDim.x) *cases[active[a]].t += 1;
+    for (int a = threadIdx.x; a < na; a += blockDim.x) {
+        StepParams &p = cases[active[a]];
+        *p.t += 1;
+        void *f = p.f0;  // the populations of t+1 become the current ones
+        p.f0 = p.f1;
+        p.f1 = f;
+    }
     if (threadIdx.x == 0) *ticket = 0;
 }
 

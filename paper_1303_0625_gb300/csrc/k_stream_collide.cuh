@@ -99,7 +99,7 @@ __device__ __forceinline__ void bounce(const StepParams &p, const typename Raw<P
         C vx = 0, vy = 0;
         int xs, ys;
         if (L.bc_y == LBM_WALL && (sy < 0 || sy >= L.ny)) {
-            vx = pick<C>(sy < 0 ? p.wall_ux0 : p.wall_ux1, (float)(sy < 0 ? p.wall_ux0 : p.wall_ux1));
+            vx = sy < 0 ? pick<C>(p.wall_ux0, p.wall_ux0_f) : pick<C>(p.wall_ux1, p.wall_ux1_f);
         } else if (locate(L, sx, sy, xs, ys)) {
             const uint16_t o = p.owner[cell_of(L, xs, ys)];
             if (o != FLUID) {
@@ -172,11 +172,12 @@ __device__ __forceinline__ void collide(const StepParams &p, typename Prec<P>::C
 }
 
 // Inlet profile of an open channel at row y: u_in = 4 umax y' (ny - y') / ny^2,
-// y' = y + 1/2 (walls at y = -1/2 and ny - 1/2).
+// y' = y + 1/2 (walls at y = -1/2 and ny - 1/2); in the precision C of the
+// kernel (no FP64 arithmetic in the FP32 kernels).
 template <class C>
 __device__ __forceinline__ C inlet_ux(const StepParams &p, int y) {
-    const double h = (double)p.L.ny, yy = (double)y + 0.5;
-    return (C)(4.0 * p.umax * yy * (h - yy) / (h * h));
+    const C h = (C)p.L.ny, yy = (C)y + (C)0.5;
+    return (C)4 * pick<C>(p.umax, p.umax_f) * yy * (h - yy) / (h * h);
 }
 
 // feq(rho0, (u_in, 0)) into g (deviation form in the deviation modes).
@@ -307,7 +308,10 @@ __device__ __forceinline__ void sc_tile(const StepParams &p, int bx, int y) {
     const Lattice &L = p.L;
     const int lane = threadIdx.x & 31;
     const int x0 = (bx * SC_BLOCK_X + threadIdx.x) * V;
-    const long long t = *p.t;
+    // OPEN marks the batch kernels, whose case parameters keep the current
+    // populations in f0 and the next in f1 (swapped as the clock advances);
+    // a single domain selects by the parity of its step counter
+    const long long t = OPEN ? 0 : *p.t;
     const R *__restrict__ fin = static_cast<const R *>((t & 1) ? p.f1 : p.f0);
     R *__restrict__ fout = static_cast<R *>((t & 1) ? p.f0 : p.f1);
     const int plane = (int)L.plane;
@@ -366,7 +370,7 @@ __device__ __forceinline__ void sc_tile(const StepParams &p, int bx, int y) {
     if (WALLS && L.bc_y == LBM_WALL && (y == 0 || y == L.ny - 1)) {
         const bool lo = y == 0;
         wall_bits = lo ? 0x64 : 0x190;  // {2, 5, 6} at y = 0, {4, 7, 8} at y = ny - 1
-        const C uw = lo ? pick<C>(p.wall_ux0, (float)p.wall_ux0) : pick<C>(p.wall_ux1, (float)p.wall_ux1);
+        const C uw = lo ? pick<C>(p.wall_ux0, p.wall_ux0_f) : pick<C>(p.wall_ux1, p.wall_ux1_f);
         const C rho_w = pick<C>(p.rho0, p.rho0_f);
 #pragma unroll
         for (int i = 1; i < 9; i++) {

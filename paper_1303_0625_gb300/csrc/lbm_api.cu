@@ -125,6 +125,9 @@ StepParams params(const lbm_ctx *c) {
     p.body_xf = (float)g.body_force[0];
     p.body_yf = (float)g.body_force[1];
     p.rho0_f = (float)g.rho0;
+    p.wall_ux0_f = (float)g.wall_ux[0];
+    p.wall_ux1_f = (float)g.wall_ux[1];
+    p.umax_f = (float)g.inflow_umax;
     p.bar = c->bar_d;
     return p;
 }
@@ -831,6 +834,7 @@ struct lbm_batch {
     int since_test = 0;  // batch steps since the last test
     // device tables
     bool dirty = true;  // parameters or lists must be rebuilt before stepping
+    bool uploaded = false;  // cases_d holds parameters (with the f0 = current convention)
     StepParams *cases_d = nullptr;
     int4 *tiles_d = nullptr;
     int2 *items_d = nullptr;
@@ -941,6 +945,17 @@ void brelease(lbm_batch *b) {
 lbm_status bprepare(lbm_batch *b) {
     if (!b->dirty) return LBM_OK;
     bdrop_graph(b);
+    if (b->uploaded) {
+        // the cases' clocks moved on the device: the buffer holding the
+        // current populations follows the parity of each clock
+        const size_t n = b->cases.size();
+        BCK(b, gbm::launch_batch_converge(blaunch(b), bstate(b), gbm::BATCH_GATHER, b->stream));
+        b->launches++;
+        BCK(b, cudaMemcpyAsync(b->steps.data(), b->steps_d, n * sizeof(long long),
+                               cudaMemcpyDeviceToHost, b->stream));
+        BCK(b, cudaStreamSynchronize(b->stream));
+        for (size_t k = 0; k < n; k++) b->cases[k]->t = b->steps[k];
+    }
     const int w = gbm::tile_nodes(b->precision, b->variant);
     const int wmin = gbm::tile_nodes(b->precision, 2);
     long long tiles = 0, tiles_min = 0, items = 0;
@@ -952,6 +967,10 @@ lbm_status bprepare(lbm_batch *b) {
         items += c->nsolid;
         hp[k] = params(c);
         hp[k].sc_variant = b->variant;
+        if (c->t & 1) {  // batch convention: f0 holds the current populations
+            hp[k].f0 = c->f[1];
+            hp[k].f1 = c->f[0];
+        }
     }
     if (tiles_min >= (1ll << 31) || items >= (1ll << 31))
         return bfail(b, LBM_EINVAL, "batch too large: %lld tiles", tiles_min);
@@ -982,6 +1001,7 @@ lbm_status bprepare(lbm_batch *b) {
     BCK(b, cudaStreamSynchronize(b->stream));  // hp must outlive the copy
     b->since_test = 0;
     b->dirty = false;
+    b->uploaded = true;
     return LBM_OK;
 }
 

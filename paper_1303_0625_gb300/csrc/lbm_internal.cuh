@@ -81,6 +81,7 @@ struct StepParams {
     int rho_w_mode, refill, precision;
     int sc_variant;           // node width per thread of the advection-collision kernel
     float omega_f, body_xf, body_yf, rho0_f;  // FP32 copies for the FP32 kernels
+    float wall_ux0_f, wall_ux1_f, umax_f;
     unsigned int *bar;        // grid barrier of the per-solid kernel: {count, generation}
 };
 
@@ -270,7 +271,7 @@ __device__ __forceinline__ long long cell_of(const Lattice &L, int x, int y) {
 // Device tables of a batch of independent domains (k_stream_collide.cu and
 // k_solid_step.cu).
 struct BatchLaunch {
-    const StepParams *cases;  // [ncase], device
+    StepParams *cases;        // [ncase], device; f0 = populations of the case's time t
     int4 *tiles;              // active tiles {case, x block, row, 0}, device
     int *ntiles;              // device
     int2 *items;              // active (case, local solid) pairs, device
