@@ -52,6 +52,8 @@ def parse():
                     help="skip the e2e pass, the other precisions and the CPU baseline")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--batch-steps", type=int, default=1000)
+    ap.add_argument("--sed-steps", type=int, default=400)
+    ap.add_argument("--precision-horizon", type=int, default=500)
     ap.add_argument("--batch-cases", type=int, default=512)
     ap.add_argument("--batch-only", action="store_true",
                     help="measure only the cylinder-sweep batch and print its record")
@@ -292,6 +294,8 @@ def run_ours(a, ws, rank, local):
                            "ms_per_step": round(m["ms"] / k, 5)}
         line["modes"] = modes
         line["batch"] = run_batch(a, local, stream, peak)
+        line["sedimentation"] = run_sedimentation(a, local, stream, peak)
+        line["precision_study"] = run_precision_study(a, w, local, stream)
         line["cpu_baseline"] = run_cpu_baseline(a, w, a.cpu_seconds)
     elif rank == 0:
         line["e2e"] = None
@@ -357,6 +361,87 @@ def run_batch(a, local, stream, peak):
            "kernel_gbs": round(gbs, 1), "kernel_frac_of_hbm": round(gbs / peak, 4),
            "kernel_avg_ms": round(k_ms / max(k_n, 1), 5)}
     b.close()
+    return out
+
+
+def run_sedimentation(a, local, stream, peak):
+    """Freely moving particles: 200 disks of radius 10 (density ratio 1.5)
+    settling under gravity 1e-5 in a 2048 x 8192 box with walls, tau 0.7,
+    FP32 populations, FP64 Newton-Euler motion with lubrication below a gap
+    of 2.  MLUPS over a bounded number of steps from rest."""
+    import torch
+
+    import paper_1303_0625_gb300 as G
+    import workloads as W
+
+    w = W.sedimentation()
+    cells = w["nx"] * w["ny"]
+    lat = G.Lattice.from_workload(w, precision=G.LBM_FP32_DEV, device=local,
+                                  stream=stream.cuda_stream, force_ring=64)
+    variant = lat.autotune(4)
+    lat.step(a.warmup)
+    lat.sync()
+    steps = a.sed_steps
+    y0 = lat.solids()[:, 1].copy()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    n0 = lat.launch_count()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    lat.step(steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    lat.sync()
+    launches = lat.launch_count() - n0
+    lat.set_timing(True)
+    lat.step(50)
+    k_ms, k_n = lat.timing()
+    dy = lat.solids()[:, 1] - y0
+    lat.close()
+    bytes_launch = algorithmic_bytes("fp32", cells)
+    gbs = bytes_launch / (k_ms / k_n / 1e3) / 1e9
+    return {"workload": "sedimentation: 2048 x 8192 walled box, 200 free disks r 10, density "
+                        "ratio 1.5, g 1e-5, tau 0.7, fp32 populations, fp64 rigid-body motion",
+            "steps": steps, "ms_per_step": round(ms / steps, 5),
+            "mlups": round(cells * steps / (ms / 1e3) / 1e6, 1), "kernel_variant": variant,
+            "kernel_gbs": round(gbs, 1), "kernel_frac_of_hbm": round(gbs / peak, 4),
+            "gpu_launches": launches,
+            "mean_descent": round(float(-dy.mean()), 6)}
+
+
+def run_precision_study(a, w, local, stream):
+    """Force error of the deviation-storage modes against the FP64 mode on
+    the precision-study workload (the FP64 mode matches the FP64 oracle to
+    1e-12 in the parity tests).  Per horizon: the largest error over all
+    disks and both force forms, relative to the larger of the force's
+    magnitude and the one-sided pressure force 2 rho0 r / 3 (torque: times r).
+    The horizon stops below the step where this overlapping-disk workload
+    produces a non-finite density in every mode (about 550)."""
+    import numpy as np
+
+    import paper_1303_0625_gb300 as G
+
+    horizons = [1, 10, 100, a.precision_horizon]
+    n = horizons[-1]
+    radii = np.array([s["r"] for s in w["solids"]])
+    rec = {}
+    for prec in ("fp64", "fp32", "fp16"):
+        lat = G.Lattice.from_workload(w, precision=G.PRECISION_NAMES[prec], device=local,
+                                      stream=stream.cuda_stream, force_ring=n)
+        rec[prec] = lat.step_record(n)  # [n][nsolid][2][3]
+        lat.sync()
+        lat.close()
+    ref = rec["fp64"]
+    f0 = 2.0 * radii / 3.0
+    scale = np.empty_like(ref)
+    fmag = np.abs(ref).max(axis=0, keepdims=True)
+    scale[..., :2] = np.maximum(fmag[..., :2], f0[None, :, None, None])
+    scale[..., 2:] = np.maximum(fmag[..., 2:], (f0 * radii)[None, :, None, None])
+    out = {"reference": "fp64 mode on the GPU", "horizons": horizons}
+    for prec in ("fp32", "fp16"):
+        err = np.abs(rec[prec] - ref) / scale
+        out[prec] = [float("%.3g" % err[h - 1].max()) for h in horizons]
     return out
 
 
