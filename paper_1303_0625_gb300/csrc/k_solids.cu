@@ -117,6 +117,26 @@ __global__ void k_import_populations(const StepParams p, const double *in) {
     for (int i = 0; i < 9; i++) put64<P>(f, L.plane, i, k, in[i * n + o]);
 }
 
+// Equilibrium initial state from a network prediction pred [3][ny][nx]
+// (FP32): rho = 1 + U^2 p0, u = U (p1, p2) at every fluid node (Eq. 8).
+template <int P>
+__global__ void k_warm_start(const StepParams p, const float *pred, double U) {
+    const Lattice &L = p.L;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
+    if (x >= L.nx) return;
+    const long long k = cell_of(L, x, y), n = (long long)L.nx * L.ny, o = (long long)y * L.nx + x;
+    if (p.flags[k] & 1u) return;
+    const long long t = *p.t;
+    void *f = (t & 1) ? p.f1 : p.f0;
+    const double rho = 1.0 + U * U * (double)pred[o];
+    const double ux = U * (double)pred[n + o], uy = U * (double)pred[2 * n + o];
+    const double uu = ux * ux + uy * uy;
+    for (int i = 0; i < 9; i++) {
+        const double eu = cx(i) * ux + cy(i) * uy;
+        put64<P>(f, L.plane, i, k, rho * wgt<double>(i) * (1.0 + 3.0 * eu + 4.5 * eu * eu - 1.5 * uu));
+    }
+}
+
 __global__ void k_export_owner(const StepParams p, int32_t *out) {
     const Lattice &L = p.L;
     const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
@@ -211,6 +231,16 @@ cudaError_t launch_import_populations(const StepParams &p, const double *in, cud
         case LBM_FP64: k_import_populations<LBM_FP64><<<cell_grid(p.L), 128, 0, st>>>(p, in); break;
         case LBM_FP32_DEV: k_import_populations<LBM_FP32_DEV><<<cell_grid(p.L), 128, 0, st>>>(p, in); break;
         default: k_import_populations<LBM_FP16_DEV><<<cell_grid(p.L), 128, 0, st>>>(p, in);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_warm_start(const StepParams &p, const float *pred, double u_scale,
+                              cudaStream_t st) {
+    switch (p.precision) {
+        case LBM_FP64: k_warm_start<LBM_FP64><<<cell_grid(p.L), 128, 0, st>>>(p, pred, u_scale); break;
+        case LBM_FP32_DEV: k_warm_start<LBM_FP32_DEV><<<cell_grid(p.L), 128, 0, st>>>(p, pred, u_scale); break;
+        default: k_warm_start<LBM_FP16_DEV><<<cell_grid(p.L), 128, 0, st>>>(p, pred, u_scale);
     }
     return cudaGetLastError();
 }

@@ -11,6 +11,7 @@
 #include <mutex>
 
 #include "lbm_internal.cuh"
+#include "lbm_nn.h"
 
 using gbm::DSolid;
 using gbm::StepParams;
@@ -600,6 +601,14 @@ lbm_status lbm_set_populations(lbm_ctx *c, const double *f, int32_t on_device) {
     CK(c, gbm::launch_import_populations(p, static_cast<const double *>(c->scratch), c->stream));
     c->launches++;
     CK(c, cudaStreamSynchronize(c->stream));
+    return LBM_OK;
+}
+
+lbm_status lbm_warm_start(lbm_ctx *c, const float *pred, double u_scale) {
+    if (!c || !pred || !std::isfinite(u_scale)) return LBM_EINVAL;
+    CK(c, cudaSetDevice(c->cfg.device));
+    CK(c, gbm::launch_warm_start(params(c), pred, u_scale, c->stream));
+    c->launches++;
     return LBM_OK;
 }
 

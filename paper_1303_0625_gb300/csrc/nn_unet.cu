@@ -1,0 +1,1060 @@
+// The warm-start U-Net on the GPU: forward, backward and Adam, with every
+// 3x3 convolution an implicit GEMM on the tensor cores (BF16 operands, FP32
+// accumulation) and the remaining layers (pooling, upsampling with
+// concatenation, the 1x1 head, the loss) as small kernels of their own.
+//
+// Layout: activations NHWC in BF16 (channels innermost, every channel count
+// a multiple of 8, so that 8 channels are one 16-byte load); conv weights
+// [Cout][tap][Cin] (tap = 3 ky + kx) in BF16, with a transposed copy
+// [Cin][tap][Cout] for the backward pass over the data; FP32 master weights,
+// gradients and Adam moments in the same layout.
+//
+// Convolutions as GEMMs (P = B H W pixels, s(tap) = (ky - 1, kx - 1)):
+//   forward      out[p][co]  = sum_{tap,ci} x[p + s][ci] w[co][tap][ci]        M=P  N=Cout K=9 Cin
+//   data grad    dx[p][ci]   = sum_{tap,co} dz[p - s][co] w[co][tap][ci]       M=P  N=Cin  K=9 Cout
+//   weight grad  dw[co][tap][ci] = sum_p dz[p][co] x[p + s][ci]                M=Cout N=9 Cin K=P
+// (zero outside the image).  The weight gradient splits K over blocks and
+// adds FP32 partial sums atomically.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <random>
+#include <string>
+#include <vector>
+
+#include "lbm_nn.h"
+
+namespace nn {
+
+using bf16 = __nv_bfloat16;
+
+// ------------------------------------------------------------ GEMM core
+
+constexpr int BM = 64, BN = 64, BK = 32, LDS = BK + 8;  // smem rows padded by 16 bytes
+constexpr int GEMM_THREADS = 128;                       // 2 x 2 warps of 32 x 32
+
+struct alignas(16) Tiles {
+    bf16 a[BM][LDS];
+    bf16 b[BN][LDS];
+};
+
+__device__ __forceinline__ void mma_bf16(float (&c)[4], const uint32_t (&a)[4],
+                                         const uint32_t (&b)[2]) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+        "{%8,%9}, {%0,%1,%2,%3};\n"
+        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+__device__ __forceinline__ void ldsm_x4(uint32_t (&r)[4], const void *p) {
+    const uint32_t a = (uint32_t)__cvta_generic_to_shared(p);
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(a));
+}
+
+__device__ __forceinline__ void ldsm_x2(uint32_t (&r)[2], const void *p) {
+    const uint32_t a = (uint32_t)__cvta_generic_to_shared(p);
+    asm volatile("ldmatrix.sync.aligned.m8n8.x2.shared.b16 {%0,%1}, [%2];\n"
+                 : "=r"(r[0]), "=r"(r[1])
+                 : "r"(a));
+}
+
+// C[M][N] = sum_k A[m][k] B[n][k] over this block's K range; the operation
+// Op gathers the tiles (load_a, load_b) and consumes the result (store).
+template <class Op>
+__global__ void __launch_bounds__(GEMM_THREADS) k_gemm(const Op op) {
+    __shared__ Tiles t;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int wm = warp >> 1, wn = warp & 1;
+    const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
+    int kb = 0, ke = op.K;
+    if (gridDim.z > 1) {
+        kb = blockIdx.z * op.kchunk;
+        ke = min(op.K, kb + op.kchunk);
+    }
+    float c[2][4][4] = {};
+    for (int k0 = kb; k0 < ke; k0 += BK) {
+        op.load_a(t.a, m0, k0, ke, tid);
+        op.load_b(t.b, n0, k0, ke, tid);
+        __syncthreads();
+#pragma unroll
+        for (int ks = 0; ks < BK; ks += 16) {
+            uint32_t af[2][4], bfr[4][2];
+#pragma unroll
+            for (int mi = 0; mi < 2; mi++)
+                ldsm_x4(af[mi], &t.a[wm * 32 + mi * 16 + (lane & 15)][ks + (lane >> 4) * 8]);
+#pragma unroll
+            for (int ni = 0; ni < 4; ni++)
+                ldsm_x2(bfr[ni], &t.b[wn * 32 + ni * 8 + (lane & 7)][ks + ((lane >> 3) & 1) * 8]);
+#pragma unroll
+            for (int mi = 0; mi < 2; mi++)
+#pragma unroll
+                for (int ni = 0; ni < 4; ni++) mma_bf16(c[mi][ni], af[mi], bfr[ni]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int mi = 0; mi < 2; mi++)
+#pragma unroll
+        for (int ni = 0; ni < 4; ni++) {
+            const int r = m0 + wm * 32 + mi * 16 + (lane >> 2);
+            const int col = n0 + wn * 32 + ni * 8 + (lane & 3) * 2;
+            op.store(r, col, c[mi][ni][0], c[mi][ni][1]);
+            op.store(r + 8, col, c[mi][ni][2], c[mi][ni][3]);
+        }
+}
+
+// Geometry of an NHWC image batch.
+struct Img {
+    int B, H, W;
+    __device__ __forceinline__ bool shift(int p, int dy, int dx, int &q) const {
+        const int hw = H * W;
+        const int n = p / hw, r = p - n * hw, y = r / W, x = r - y * W;
+        const int ys = y + dy, xs = x + dx;
+        if (ys < 0 || ys >= H || xs < 0 || xs >= W) return false;
+        q = (n * H + ys) * W + xs;
+        return true;
+    }
+};
+
+// Forward convolution (sign = +1) or the gradient with respect to its input
+// (sign = -1, w the transposed weights): out[p][n] = act(bias + sum over taps
+// and source channels of src[p + sign s(tap)][c] w[n][tap][c]), times
+// (mask > 0) when a mask is given.
+struct ConvOp {
+    const bf16 *src;   // [P][Cs]
+    const bf16 *w;     // [N][taps][Cs]
+    const float *bias; // [N] or null
+    const bf16 *mask;  // [P][N] or null
+    bf16 *out;         // [P][N]
+    Img img;
+    int Cs, taps, sign, relu;
+    int M, N, K, kchunk;
+
+    __device__ __forceinline__ void load_a(bf16 (&a)[BM][LDS], int m0, int k0, int ke, int tid) const {
+#pragma unroll
+        for (int i = 0; i < 2; i++) {
+            const int q = tid + i * GEMM_THREADS, r = q >> 2, cc = q & 3;
+            const int p = m0 + r, k = k0 + cc * 8;
+            uint4 v = make_uint4(0, 0, 0, 0);
+            if (p < M && k < ke) {
+                const int tap = k / Cs, c = k - tap * Cs;
+                int qp = p;
+                bool ok = true;
+                if (taps == 9) ok = img.shift(p, sign * (tap / 3 - 1), sign * (tap % 3 - 1), qp);
+                if (ok) v = *reinterpret_cast<const uint4 *>(src + (size_t)qp * Cs + c);
+            }
+            *reinterpret_cast<uint4 *>(&a[r][cc * 8]) = v;
+        }
+    }
+    __device__ __forceinline__ void load_b(bf16 (&b)[BN][LDS], int n0, int k0, int ke, int tid) const {
+#pragma unroll
+        for (int i = 0; i < 2; i++) {
+            const int q = tid + i * GEMM_THREADS, r = q >> 2, cc = q & 3;
+            const int n = n0 + r, k = k0 + cc * 8;
+            uint4 v = make_uint4(0, 0, 0, 0);
+            if (n < N && k < ke) v = *reinterpret_cast<const uint4 *>(w + (size_t)n * K + k);
+            *reinterpret_cast<uint4 *>(&b[r][cc * 8]) = v;
+        }
+    }
+    __device__ __forceinline__ void store(int m, int n, float v0, float v1) const {
+        if (m >= M || n >= N) return;
+        if (bias) {
+            v0 += bias[n];
+            v1 += bias[n + 1];
+        }
+        if (relu) {
+            v0 = fmaxf(v0, 0.f);
+            v1 = fmaxf(v1, 0.f);
+        }
+        const size_t o = (size_t)m * N + n;
+        if (mask) {
+            const __nv_bfloat162 mk = *reinterpret_cast<const __nv_bfloat162 *>(mask + o);
+            if (!(__bfloat162float(mk.x) > 0.f)) v0 = 0.f;
+            if (!(__bfloat162float(mk.y) > 0.f)) v1 = 0.f;
+        }
+        *reinterpret_cast<__nv_bfloat162 *>(out + o) = __floats2bfloat162_rn(v0, v1);
+    }
+};
+
+// Weight gradient: dw[co][tap][c] += sum_p dz[p][co] x[p + s(tap)][c] over
+// this block's pixel range (K = pixels).
+struct WgradOp {
+    const bf16 *dz;  // [P][Co]
+    const bf16 *x;   // [P][Ci]
+    float *dw;       // [Co][taps][Ci]
+    Img img;
+    int Co, Ci, taps;
+    int M, N, K, kchunk;  // M = Co, N = taps Ci, K = P
+
+    __device__ __forceinline__ void load_a(bf16 (&a)[BM][LDS], int m0, int k0, int ke, int tid) const {
+        // 32 pixels x 64 output channels: chunk (pixel, 8 channels), transposed into a[co][pixel]
+#pragma unroll
+        for (int i = 0; i < 2; i++) {
+            const int q = tid + i * GEMM_THREADS, pl = q >> 3, cc = q & 7;
+            const int p = k0 + pl, co = m0 + cc * 8;
+            uint4 v = make_uint4(0, 0, 0, 0);
+            if (p < ke && co < M) v = *reinterpret_cast<const uint4 *>(dz + (size_t)p * Co + co);
+            const bf16 *e = reinterpret_cast<const bf16 *>(&v);
+#pragma unroll
+            for (int j = 0; j < 8; j++) a[cc * 8 + j][pl] = e[j];
+        }
+    }
+    __device__ __forceinline__ void load_b(bf16 (&b)[BN][LDS], int n0, int k0, int ke, int tid) const {
+#pragma unroll
+        for (int i = 0; i < 2; i++) {
+            const int q = tid + i * GEMM_THREADS, pl = q >> 3, cc = q & 7;
+            const int p = k0 + pl, n = n0 + cc * 8;
+            uint4 v = make_uint4(0, 0, 0, 0);
+            if (p < ke && n < N) {
+                const int tap = n / Ci, c = n - tap * Ci;
+                int qp = p;
+                bool ok = true;
+                if (taps == 9) ok = img.shift(p, tap / 3 - 1, tap % 3 - 1, qp);
+                if (ok) v = *reinterpret_cast<const uint4 *>(x + (size_t)qp * Ci + c);
+            }
+            const bf16 *e = reinterpret_cast<const bf16 *>(&v);
+#pragma unroll
+            for (int j = 0; j < 8; j++) b[cc * 8 + j][pl] = e[j];
+        }
+    }
+    __device__ __forceinline__ void store(int m, int n, float v0, float v1) const {
+        if (m >= M || n >= N) return;
+        atomicAdd(dw + (size_t)m * N + n, v0);
+        atomicAdd(dw + (size_t)m * N + n + 1, v1);
+    }
+};
+
+// ------------------------------------------------------ other layers
+
+constexpr int EW = 256;  // threads of the elementwise kernels
+
+inline unsigned blocks(long long n) { return (unsigned)((n + EW - 1) / EW); }
+
+// NCHW float input [B][8][H][W] -> NHWC BF16 [P][8]
+__global__ void k_pack_input(const float *in, bf16 *x, int B, int HW) {
+    const long long i = (long long)blockIdx.x * EW + threadIdx.x;
+    if (i >= (long long)B * HW * 8) return;
+    const int c = (int)(i & 7);
+    const long long p = i >> 3, n = p / HW, r = p - n * HW;
+    x[i] = __float2bfloat16(in[(n * 8 + c) * HW + r]);
+}
+
+// 2x2 average pooling of NHWC [B][H][W][C] into [B][H/2][W/2][C]
+__global__ void k_pool(const bf16 *in, bf16 *out, int B, int H, int W, int C) {
+    const long long i = (long long)blockIdx.x * EW + threadIdx.x;
+    const int Ho = H / 2, Wo = W / 2;
+    if (i >= (long long)B * Ho * Wo * C) return;
+    const int c = (int)(i % C);
+    const long long p = i / C;
+    const int x = (int)(p % Wo), y = (int)((p / Wo) % Ho);
+    const long long n = p / ((long long)Wo * Ho);
+    const long long b0 = ((n * H + 2 * y) * W + 2 * x) * C + c;
+    const float s = __bfloat162float(in[b0]) + __bfloat162float(in[b0 + C]) +
+                    __bfloat162float(in[b0 + (long long)W * C]) +
+                    __bfloat162float(in[b0 + (long long)W * C + C]);
+    out[i] = __float2bfloat16(0.25f * s);
+}
+
+// de[p][c] = (e[p][c] > 0) * dpool[p/2][c] / 4 + dskip[p][c] (dskip: a
+// channel slice of stride Cs at offset off, already masked)
+__global__ void k_pool_back(const bf16 *dpool, const bf16 *e, const bf16 *dskip, int Cs, int off,
+                            bf16 *de, int B, int H, int W, int C) {
+    const long long i = (long long)blockIdx.x * EW + threadIdx.x;
+    if (i >= (long long)B * H * W * C) return;
+    const int c = (int)(i % C);
+    const long long p = i / C;
+    const int x = (int)(p % W), y = (int)((p / W) % H);
+    const long long n = p / ((long long)W * H);
+    const long long q = (n * (H / 2) + y / 2) * (W / 2) + x / 2;
+    float v = __bfloat162float(e[i]) > 0.f ? 0.25f * __bfloat162float(dpool[q * C + c]) : 0.f;
+    if (dskip) v += __bfloat162float(dskip[p * Cs + off + c]);
+    de[i] = __float2bfloat16(v);
+}
+
+// cat[p] = [up(d)[p] (Cu channels), e[p] (Ce channels)]
+__global__ void k_upcat(const bf16 *d, const bf16 *e, bf16 *cat, int B, int H, int W, int Cu,
+                        int Ce) {
+    const int Cc = Cu + Ce;
+    const long long i = (long long)blockIdx.x * EW + threadIdx.x;
+    if (i >= (long long)B * H * W * Cc) return;
+    const int c = (int)(i % Cc);
+    const long long p = i / Cc;
+    if (c < Cu) {
+        const int x = (int)(p % W), y = (int)((p / W) % H);
+        const long long n = p / ((long long)W * H);
+        const long long q = (n * (H / 2) + y / 2) * (W / 2) + x / 2;
+        cat[i] = d[q * Cu + c];
+    } else {
+        cat[i] = e[p * Ce + (c - Cu)];
+    }
+}
+
+// dd[q][c] = sum over the 2x2 children p of q of dcat[p][c], c < Cu
+__global__ void k_up_back(const bf16 *dcat, int Cc, bf16 *dd, int B, int Hc, int Wc, int Cu) {
+    const long long i = (long long)blockIdx.x * EW + threadIdx.x;
+    if (i >= (long long)B * Hc * Wc * Cu) return;
+    const int c = (int)(i % Cu);
+    const long long q = i / Cu;
+    const int x = (int)(q % Wc), y = (int)((q / Wc) % Hc);
+    const long long n = q / ((long long)Wc * Hc);
+    const int H = 2 * Hc, W = 2 * Wc;
+    const long long p0 = (n * H + 2 * y) * W + 2 * x;
+    const float s = __bfloat162float(dcat[p0 * Cc + c]) + __bfloat162float(dcat[(p0 + 1) * Cc + c]) +
+                    __bfloat162float(dcat[(p0 + W) * Cc + c]) +
+                    __bfloat162float(dcat[(p0 + W + 1) * Cc + c]);
+    dd[i] = __float2bfloat16(s);
+}
+
+// 1x1 head: out[n][o][y][x] = b[o] + sum_c w[o][c] d[p][c] (FP32), NCHW output
+__global__ void k_head(const bf16 *d, const float *w, const float *b, float *out, int B, int HW,
+                       int C) {
+    const long long p = (long long)blockIdx.x * EW + threadIdx.x;
+    if (p >= (long long)B * HW) return;
+    float acc[3] = {b[0], b[1], b[2]};
+    for (int c = 0; c < C; c += 8) {
+        const uint4 v = *reinterpret_cast<const uint4 *>(d + p * C + c);
+        const bf16 *e = reinterpret_cast<const bf16 *>(&v);
+#pragma unroll
+        for (int j = 0; j < 8; j++) {
+            const float x = __bfloat162float(e[j]);
+#pragma unroll
+            for (int o = 0; o < 3; o++) acc[o] += w[o * C + c + j] * x;
+        }
+    }
+    const long long n = p / HW, r = p - n * HW;
+#pragma unroll
+    for (int o = 0; o < 3; o++) out[(n * 3 + o) * HW + r] = acc[o];
+}
+
+// fluid-node count (for the loss normalisation)
+__global__ void k_count(const float *fluid, long long n, float *cnt) {
+    __shared__ float s[EW];
+    float a = 0.f;
+    for (long long i = (long long)blockIdx.x * EW + threadIdx.x; i < n; i += (long long)gridDim.x * EW)
+        a += fluid[i];
+    s[threadIdx.x] = a;
+    __syncthreads();
+    for (int o = EW / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) s[threadIdx.x] += s[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) atomicAdd(cnt, s[0]);
+}
+
+// loss = sum (out - t)^2 m / (3 count); dout = 2 (out - t) m / (3 count)
+__global__ void k_loss(const float *out, const float *tgt, const float *fluid, const float *cnt,
+                       float *dout, double *loss, int B, int HW) {
+    __shared__ float s[EW];
+    const long long n3 = (long long)B * 3 * HW;
+    const float inv = 1.f / (3.f * fmaxf(*cnt, 1.f));
+    float a = 0.f;
+    for (long long i = (long long)blockIdx.x * EW + threadIdx.x; i < n3; i += (long long)gridDim.x * EW) {
+        const long long n = i / (3 * HW), r = i % HW;
+        const float m = fluid[n * HW + r];
+        const float d = (out[i] - tgt[i]) * m;
+        a += d * d;
+        dout[i] = 2.f * d * inv;
+    }
+    s[threadIdx.x] = a;
+    __syncthreads();
+    for (int o = EW / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) s[threadIdx.x] += s[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) atomicAdd(loss, (double)(s[0] * inv));
+}
+
+// head backward: dd[p][c] = (d[p][c] > 0) sum_o dout[o][p] w[o][c];
+// dw[o][c] += sum_p dout[o][p] d[p][c]; db[o] += sum_p dout[o][p]
+template <int C>
+__global__ void k_head_back(const float *dout, const bf16 *d, const float *w, bf16 *dd, float *dw,
+                            float *db, int B, int HW) {
+    __shared__ float red[4 * C];
+    for (int i = threadIdx.x; i < 4 * C; i += blockDim.x) red[i] = 0.f;
+    __syncthreads();
+    const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    float g[3] = {0.f, 0.f, 0.f};
+    float lw[3][C];
+    if (p < (long long)B * HW) {
+        const long long n = p / HW, r = p - n * HW;
+#pragma unroll
+        for (int o = 0; o < 3; o++) g[o] = dout[(n * 3 + o) * HW + r];
+#pragma unroll
+        for (int c = 0; c < C; c++) {
+            const float x = __bfloat162float(d[p * C + c]);
+            const float v = g[0] * w[c] + g[1] * w[C + c] + g[2] * w[2 * C + c];
+            dd[p * C + c] = __float2bfloat16(x > 0.f ? v : 0.f);
+#pragma unroll
+            for (int o = 0; o < 3; o++) lw[o][c] = g[o] * x;
+        }
+    } else {
+#pragma unroll
+        for (int o = 0; o < 3; o++)
+#pragma unroll
+            for (int c = 0; c < C; c++) lw[o][c] = 0.f;
+    }
+    // warp sums, then one shared atomic per warp and value
+#pragma unroll
+    for (int o = 0; o < 3; o++) {
+#pragma unroll
+        for (int c = 0; c < C; c++) {
+            float v = lw[o][c];
+            for (int s = 16; s > 0; s >>= 1) v += __shfl_down_sync(0xffffffffu, v, s);
+            if ((threadIdx.x & 31) == 0) atomicAdd(&red[o * C + c], v);
+        }
+        float v = g[o];
+        for (int s = 16; s > 0; s >>= 1) v += __shfl_down_sync(0xffffffffu, v, s);
+        if ((threadIdx.x & 31) == 0) atomicAdd(&red[3 * C + o], v);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < 3 * C; i += blockDim.x) atomicAdd(dw + i, red[i]);
+    if (threadIdx.x < 3) atomicAdd(db + threadIdx.x, red[3 * C + threadIdx.x]);
+}
+
+// db[c] += sum_p dz[p][c] (NHWC BF16), C <= 256
+__global__ void k_colsum(const bf16 *dz, long long P, int C, float *db) {
+    __shared__ float s[EW];
+    const int c = threadIdx.x % C, rows = EW / C;
+    const int r0 = threadIdx.x / C;
+    float a = 0.f;
+    if (r0 < rows)
+        for (long long p = (long long)blockIdx.x * rows + r0; p < P; p += (long long)gridDim.x * rows)
+            a += __bfloat162float(dz[p * C + c]);
+    s[threadIdx.x] = a;
+    __syncthreads();
+    if (threadIdx.x < C) {
+        float t = 0.f;
+        for (int r = 0; r < rows; r++) t += s[r * C + threadIdx.x];
+        atomicAdd(db + threadIdx.x, t);
+    }
+}
+
+// Adam on the flat FP32 master vector; refreshes the BF16 copies.
+__global__ void k_adam(float *w, const float *g, float *m, float *v, bf16 *wb, long long n, float lr,
+                       float c1, float c2) {
+    const long long i = (long long)blockIdx.x * EW + threadIdx.x;
+    if (i >= n) return;
+    const float gi = g[i];
+    const float mi = 0.9f * m[i] + 0.1f * gi, vi = 0.999f * v[i] + 0.001f * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    const float wi = w[i] - lr * (mi / c1) / (sqrtf(vi / c2) + 1e-8f);
+    w[i] = wi;
+    wb[i] = __float2bfloat16(wi);
+}
+
+__global__ void k_to_bf16(const float *w, bf16 *wb, long long n) {
+    const long long i = (long long)blockIdx.x * EW + threadIdx.x;
+    if (i < n) wb[i] = __float2bfloat16(w[i]);
+}
+
+// wt[ci][tap][co] = w[co][tap][ci]
+__global__ void k_transpose_w(const bf16 *w, bf16 *wt, int Co, int taps, int Ci) {
+    const long long i = (long long)blockIdx.x * EW + threadIdx.x;
+    if (i >= (long long)Co * taps * Ci) return;
+    const int ci = (int)(i % Ci), tap = (int)((i / Ci) % taps), co = (int)(i / ((long long)Ci * taps));
+    wt[((long long)ci * taps + tap) * Co + co] = w[i];
+}
+
+// network input of one case: mask (owner >= 0) and Re / 100, zero elsewhere
+__global__ void k_case_input(const int32_t *owner, float re100, float *in, int HW) {
+    const int i = blockIdx.x * EW + threadIdx.x;
+    if (i >= HW) return;
+    in[i] = owner[i] >= 0 ? 1.f : 0.f;
+    in[HW + i] = re100;
+    for (int c = 2; c < 8; c++) in[c * HW + i] = 0.f;
+}
+
+}  // namespace nn
+
+// ================================================================ network
+
+using nn::bf16;
+
+namespace {
+
+struct Conv {
+    int ci, co, k;           // k = 3 or 1
+    size_t w_off, b_off;     // into the flat parameter vector (internal layout)
+    bf16 *wt = nullptr;      // transposed BF16 weights [ci][tap][co]
+};
+
+struct Level {
+    int H, W, C;
+    bf16 *inp = nullptr;  // pooled input (l > 0)
+    bf16 *ea = nullptr, *e = nullptr;              // encoder: relu(conv a), level output
+    bf16 *cat = nullptr, *da = nullptr, *d = nullptr;  // decoder (l < L-1)
+    bf16 *g1 = nullptr, *g2 = nullptr, *gcat = nullptr, *gin = nullptr;  // gradients
+};
+
+}  // namespace
+
+struct lbm_unet {
+    lbm_unet_config cfg{};
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    std::vector<Conv> convs;  // parameter order
+    std::vector<Level> lv;
+    long long nparam = 0;
+    float *w = nullptr, *g = nullptr, *m = nullptr, *v = nullptr;
+    bf16 *wb = nullptr;      // BF16 copy of the whole vector (biases unused)
+    bf16 *x = nullptr;       // packed input [P0][8]
+    float *out = nullptr, *dout = nullptr;
+    float *io_in = nullptr, *io_out = nullptr, *io_tgt = nullptr, *io_fl = nullptr;  // staging
+    float *grad_abi = nullptr;
+    float *cnt = nullptr;
+    double *loss = nullptr;
+    long long adam_t = 0;
+    std::string err;
+    std::vector<void *> allocs;
+};
+
+namespace {
+
+thread_local std::string g_nn_error;
+
+lbm_status nfail(lbm_unet *n, lbm_status st, const char *fmt, ...) __attribute__((format(printf, 3, 4)));
+lbm_status nfail(lbm_unet *n, lbm_status st, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (n) n->err = buf;
+    else g_nn_error = buf;
+    return st;
+}
+
+#define NCK(n, call)                                                                        \
+    do {                                                                                    \
+        cudaError_t e_ = (call);                                                            \
+        if (e_ != cudaSuccess)                                                              \
+            return nfail((n), e_ == cudaErrorMemoryAllocation ? LBM_ENOMEM : LBM_ECUDA,     \
+                         "%s failed: %s", #call, cudaGetErrorString(e_));                  \
+    } while (0)
+
+template <class T>
+cudaError_t nalloc(lbm_unet *n, T **p, size_t count) {
+    cudaError_t e = cudaMalloc(reinterpret_cast<void **>(p), count * sizeof(T) + 16);
+    if (e == cudaSuccess) n->allocs.push_back(*p);
+    return e;
+}
+
+void nrelease(lbm_unet *n) {
+    if (!n) return;
+    for (void *p : n->allocs) cudaFree(p);
+    if (n->own_stream && n->stream) cudaStreamDestroy(n->stream);
+    delete n;
+}
+
+int conv_index(const lbm_unet *n, const char kind, int l, int ab) {
+    // order: enc0a enc0b ... enc{L-1}b, dec{L-2}a dec{L-2}b ... dec0b, head
+    const int L = n->cfg.levels;
+    if (kind == 'e') return 2 * l + ab;
+    if (kind == 'd') return 2 * L + 2 * (L - 2 - l) + ab;
+    return 2 * L + 2 * (L - 1);
+}
+
+cudaError_t conv_fwd(lbm_unet *n, const Conv &cv, const bf16 *src, bf16 *dst, int B, int H, int W,
+                     bool relu) {
+    nn::ConvOp op{};
+    op.src = src;
+    op.w = n->wb + cv.w_off;
+    op.bias = n->w + cv.b_off;
+    op.mask = nullptr;
+    op.out = dst;
+    op.img = {B, H, W};
+    op.Cs = cv.ci;
+    op.taps = cv.k * cv.k;
+    op.sign = 1;
+    op.relu = relu;
+    op.M = B * H * W;
+    op.N = cv.co;
+    op.K = op.taps * cv.ci;
+    op.kchunk = op.K;
+    const dim3 grid((op.M + nn::BM - 1) / nn::BM, (op.N + nn::BN - 1) / nn::BN);
+    nn::k_gemm<nn::ConvOp><<<grid, nn::GEMM_THREADS, 0, n->stream>>>(op);
+    return cudaGetLastError();
+}
+
+// gradient with respect to the conv's input (masked by mask > 0 when given)
+cudaError_t conv_dgrad(lbm_unet *n, const Conv &cv, const bf16 *dz, const bf16 *mask, bf16 *dx,
+                       int B, int H, int W) {
+    nn::ConvOp op{};
+    op.src = dz;
+    op.w = cv.wt;
+    op.bias = nullptr;
+    op.mask = mask;
+    op.out = dx;
+    op.img = {B, H, W};
+    op.Cs = cv.co;
+    op.taps = cv.k * cv.k;
+    op.sign = -1;
+    op.relu = 0;
+    op.M = B * H * W;
+    op.N = cv.ci;
+    op.K = op.taps * cv.co;
+    op.kchunk = op.K;
+    const dim3 grid((op.M + nn::BM - 1) / nn::BM, (op.N + nn::BN - 1) / nn::BN);
+    nn::k_gemm<nn::ConvOp><<<grid, nn::GEMM_THREADS, 0, n->stream>>>(op);
+    return cudaGetLastError();
+}
+
+cudaError_t conv_wgrad(lbm_unet *n, const Conv &cv, const bf16 *dz, const bf16 *x, int B, int H,
+                       int W) {
+    nn::WgradOp op{};
+    op.dz = dz;
+    op.x = x;
+    op.dw = n->g + cv.w_off;
+    op.img = {B, H, W};
+    op.Co = cv.co;
+    op.Ci = cv.ci;
+    op.taps = cv.k * cv.k;
+    op.M = cv.co;
+    op.N = op.taps * cv.ci;
+    op.K = B * H * W;
+    const int mt = (op.M + nn::BM - 1) / nn::BM, nt = (op.N + nn::BN - 1) / nn::BN;
+    int z = 1200 / (mt * nt);
+    const int kt = (op.K + nn::BK - 1) / nn::BK;
+    if (z < 1) z = 1;
+    if (z > kt) z = kt;
+    op.kchunk = ((kt + z - 1) / z) * nn::BK;
+    z = (op.K + op.kchunk - 1) / op.kchunk;
+    const dim3 grid(mt, nt, z);
+    nn::k_gemm<nn::WgradOp><<<grid, nn::GEMM_THREADS, 0, n->stream>>>(op);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const long long P = op.K;
+    int nb = (int)((P * cv.co + nn::EW - 1) / nn::EW);
+    if (nb > 1024) nb = 1024;
+    nn::k_colsum<<<nb, nn::EW, 0, n->stream>>>(dz, P, cv.co, n->g + cv.b_off);
+    return cudaGetLastError();
+}
+
+cudaError_t refresh_weights(lbm_unet *n) {
+    nn::k_to_bf16<<<nn::blocks(n->nparam), nn::EW, 0, n->stream>>>(n->w, n->wb, n->nparam);
+    cudaError_t e = cudaGetLastError();
+    for (const Conv &cv : n->convs) {
+        if (e != cudaSuccess) return e;
+        const long long cnt = (long long)cv.co * cv.k * cv.k * cv.ci;
+        nn::k_transpose_w<<<nn::blocks(cnt), nn::EW, 0, n->stream>>>(n->wb + cv.w_off, cv.wt, cv.co,
+                                                                   cv.k * cv.k, cv.ci);
+        e = cudaGetLastError();
+    }
+    return e;
+}
+
+lbm_status forward(lbm_unet *n, const float *in_dev, int B) {
+    const int L = n->cfg.levels, H = n->cfg.height, W = n->cfg.width;
+    NCK(n, (nn::k_pack_input<<<nn::blocks((long long)B * H * W * 8), nn::EW, 0, n->stream>>>(
+               in_dev, n->x, B, H * W),
+           cudaGetLastError()));
+    for (int l = 0; l < L; l++) {
+        Level &v = n->lv[l];
+        const bf16 *inp = n->x;
+        if (l > 0) {
+            const Level &u = n->lv[l - 1];
+            NCK(n, (nn::k_pool<<<nn::blocks((long long)B * v.H * v.W * u.C), nn::EW, 0, n->stream>>>(
+                       u.e, v.inp, B, u.H, u.W, u.C),
+                   cudaGetLastError()));
+            inp = v.inp;
+        }
+        NCK(n, conv_fwd(n, n->convs[conv_index(n, 'e', l, 0)], inp, v.ea, B, v.H, v.W, true));
+        NCK(n, conv_fwd(n, n->convs[conv_index(n, 'e', l, 1)], v.ea, v.e, B, v.H, v.W, true));
+    }
+    const bf16 *d = n->lv[L - 1].e;
+    for (int l = L - 2; l >= 0; l--) {
+        Level &v = n->lv[l];
+        const int Cu = n->lv[l + 1].C;
+        NCK(n, (nn::k_upcat<<<nn::blocks((long long)B * v.H * v.W * (Cu + v.C)), nn::EW, 0,
+                              n->stream>>>(d, v.e, v.cat, B, v.H, v.W, Cu, v.C),
+               cudaGetLastError()));
+        NCK(n, conv_fwd(n, n->convs[conv_index(n, 'd', l, 0)], v.cat, v.da, B, v.H, v.W, true));
+        NCK(n, conv_fwd(n, n->convs[conv_index(n, 'd', l, 1)], v.da, v.d, B, v.H, v.W, true));
+        d = v.d;
+    }
+    const Conv &hd = n->convs[conv_index(n, 'h', 0, 0)];
+    NCK(n, (nn::k_head<<<nn::blocks((long long)B * H * W), nn::EW, 0, n->stream>>>(
+               d, n->w + hd.w_off, n->w + hd.b_off, n->out, B, H * W, n->lv[0].C),
+           cudaGetLastError()));
+    return LBM_OK;
+}
+
+lbm_status backward(lbm_unet *n, const float *tgt_dev, const float *fl_dev, int B) {
+    const int L = n->cfg.levels, H = n->cfg.height, W = n->cfg.width;
+    const long long HW = (long long)H * W;
+    NCK(n, cudaMemsetAsync(n->g, 0, n->nparam * sizeof(float), n->stream));
+    NCK(n, cudaMemsetAsync(n->cnt, 0, sizeof(float), n->stream));
+    NCK(n, cudaMemsetAsync(n->loss, 0, sizeof(double), n->stream));
+    NCK(n, (nn::k_count<<<256, nn::EW, 0, n->stream>>>(fl_dev, B * HW, n->cnt), cudaGetLastError()));
+    NCK(n, (nn::k_loss<<<1024, nn::EW, 0, n->stream>>>(n->out, tgt_dev, fl_dev, n->cnt, n->dout,
+                                                       n->loss, B, (int)HW),
+           cudaGetLastError()));
+    // head: gradient of d0 (masked by d0 > 0) into lv[0].g1
+    Level &v0 = n->lv[0];
+    const bf16 *d0 = L > 1 ? v0.d : v0.e;
+    const Conv &hd = n->convs[conv_index(n, 'h', 0, 0)];
+    const unsigned hb = nn::blocks(B * HW);
+    if (v0.C == 32)
+        nn::k_head_back<32><<<hb, nn::EW, 0, n->stream>>>(n->dout, d0, n->w + hd.w_off, v0.g1,
+                                                          n->g + hd.w_off, n->g + hd.b_off, B, (int)HW);
+    else if (v0.C == 16)
+        nn::k_head_back<16><<<hb, nn::EW, 0, n->stream>>>(n->dout, d0, n->w + hd.w_off, v0.g1,
+                                                          n->g + hd.w_off, n->g + hd.b_off, B, (int)HW);
+    else
+        nn::k_head_back<8><<<hb, nn::EW, 0, n->stream>>>(n->dout, d0, n->w + hd.w_off, v0.g1,
+                                                         n->g + hd.w_off, n->g + hd.b_off, B, (int)HW);
+    NCK(n, cudaGetLastError());
+    // decoder: g1 of level l holds d(d_l) (masked)
+    for (int l = 0; l < L - 1; l++) {
+        Level &v = n->lv[l];
+        const Conv &cb = n->convs[conv_index(n, 'd', l, 1)], &ca = n->convs[conv_index(n, 'd', l, 0)];
+        NCK(n, conv_wgrad(n, cb, v.g1, v.da, B, v.H, v.W));
+        NCK(n, conv_dgrad(n, cb, v.g1, v.da, v.g2, B, v.H, v.W));
+        NCK(n, conv_wgrad(n, ca, v.g2, v.cat, B, v.H, v.W));
+        NCK(n, conv_dgrad(n, ca, v.g2, v.cat, v.gcat, B, v.H, v.W));
+        Level &u = n->lv[l + 1];
+        NCK(n, (nn::k_up_back<<<nn::blocks((long long)B * u.H * u.W * u.C), nn::EW, 0, n->stream>>>(
+                   v.gcat, u.C + v.C, u.g1, B, u.H, u.W, u.C),
+               cudaGetLastError()));
+    }
+    // encoder: g1 of level l holds d(e_l) (masked)
+    for (int l = L - 1; l >= 0; l--) {
+        Level &v = n->lv[l];
+        const Conv &cb = n->convs[conv_index(n, 'e', l, 1)], &ca = n->convs[conv_index(n, 'e', l, 0)];
+        const bf16 *inp = l > 0 ? v.inp : n->x;
+        NCK(n, conv_wgrad(n, cb, v.g1, v.ea, B, v.H, v.W));
+        NCK(n, conv_dgrad(n, cb, v.g1, v.ea, v.g2, B, v.H, v.W));
+        NCK(n, conv_wgrad(n, ca, v.g2, inp, B, v.H, v.W));
+        if (l == 0) break;
+        NCK(n, conv_dgrad(n, ca, v.g2, nullptr, v.gin, B, v.H, v.W));
+        Level &u = n->lv[l - 1];
+        NCK(n, (nn::k_pool_back<<<nn::blocks((long long)B * u.H * u.W * u.C), nn::EW, 0, n->stream>>>(
+                   v.gin, u.e, u.gcat, v.C + u.C, v.C, u.g1, B, u.H, u.W, u.C),
+               cudaGetLastError()));
+    }
+    return LBM_OK;
+}
+
+// host permutation between the ABI layout [co][ci][k][k] and the internal
+// [co][tap][ci]
+void abi_to_internal(const lbm_unet *n, const float *a, std::vector<float> &w) {
+    w.assign(n->nparam, 0.f);
+    size_t o = 0;
+    for (const Conv &cv : n->convs) {
+        const int t = cv.k * cv.k;
+        for (int co = 0; co < cv.co; co++)
+            for (int ci = 0; ci < cv.ci; ci++)
+                for (int tap = 0; tap < t; tap++)
+                    w[cv.w_off + ((size_t)co * t + tap) * cv.ci + ci] = a[o + ((size_t)co * cv.ci + ci) * t + tap];
+        o += (size_t)cv.co * cv.ci * t;
+        for (int co = 0; co < cv.co; co++) w[cv.b_off + co] = a[o + co];
+        o += cv.co;
+    }
+}
+
+void internal_to_abi(const lbm_unet *n, const float *w, float *a) {
+    size_t o = 0;
+    for (const Conv &cv : n->convs) {
+        const int t = cv.k * cv.k;
+        for (int co = 0; co < cv.co; co++)
+            for (int ci = 0; ci < cv.ci; ci++)
+                for (int tap = 0; tap < t; tap++)
+                    a[o + ((size_t)co * cv.ci + ci) * t + tap] = w[cv.w_off + ((size_t)co * t + tap) * cv.ci + ci];
+        o += (size_t)cv.co * cv.ci * t;
+        for (int co = 0; co < cv.co; co++) a[o + co] = w[cv.b_off + co];
+        o += cv.co;
+    }
+}
+
+lbm_status stage_inputs(lbm_unet *n, const float *in, const float *tgt, const float *fl, int B,
+                        int on_device, const float **din, const float **dtgt, const float **dfl) {
+    const size_t HW = (size_t)n->cfg.height * n->cfg.width;
+    if (on_device) {
+        *din = in;
+        if (dtgt) *dtgt = tgt;
+        if (dfl) *dfl = fl;
+        return LBM_OK;
+    }
+    NCK(n, cudaMemcpyAsync(n->io_in, in, (size_t)B * 8 * HW * sizeof(float), cudaMemcpyHostToDevice,
+                           n->stream));
+    *din = n->io_in;
+    if (dtgt) {
+        NCK(n, cudaMemcpyAsync(n->io_tgt, tgt, (size_t)B * 3 * HW * sizeof(float),
+                               cudaMemcpyHostToDevice, n->stream));
+        *dtgt = n->io_tgt;
+    }
+    if (dfl) {
+        NCK(n, cudaMemcpyAsync(n->io_fl, fl, (size_t)B * HW * sizeof(float), cudaMemcpyHostToDevice,
+                               n->stream));
+        *dfl = n->io_fl;
+    }
+    return LBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+lbm_status lbm_unet_create(const lbm_unet_config *cfg, lbm_unet **out) {
+    if (!cfg || !out) return nfail(nullptr, LBM_EINVAL, "null argument");
+    *out = nullptr;
+    const lbm_unet_config &c = *cfg;
+    if (c.levels < 2 || c.levels > 4 || c.base < 8 || c.base % 8 || c.base > 64)
+        return nfail(nullptr, LBM_EINVAL, "levels must be 2..4 and base a multiple of 8 up to 64");
+    const int div = 1 << (c.levels - 1);
+    if (c.height < div || c.width < div || c.height % div || c.width % div)
+        return nfail(nullptr, LBM_EINVAL, "height and width must be multiples of %d", div);
+    if (c.max_batch < 1 || (long long)c.max_batch * c.height * c.width >= (1ll << 31))
+        return nfail(nullptr, LBM_EINVAL, "max_batch out of range");
+    if (c.base != 8 && c.base != 16 && c.base != 32)
+        return nfail(nullptr, LBM_EINVAL, "base must be 8, 16 or 32");
+    if (cudaSetDevice(c.device) != cudaSuccess)
+        return nfail(nullptr, LBM_ECUDA, "cannot select device %d", c.device);
+    lbm_unet *n = new (std::nothrow) lbm_unet;
+    if (!n) return nfail(nullptr, LBM_ENOMEM, "host allocation failed");
+    n->cfg = c;
+    if (c.stream) {
+        n->stream = static_cast<cudaStream_t>(c.stream);
+    } else {
+        if (cudaStreamCreateWithFlags(&n->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            nrelease(n);
+            return nfail(nullptr, LBM_ECUDA, "stream creation failed");
+        }
+        n->own_stream = true;
+    }
+    const int L = c.levels;
+    // parameter layout
+    std::vector<int> ch(L);
+    for (int l = 0; l < L; l++) ch[l] = c.base << l;
+    size_t off = 0;
+    auto add = [&](int ci, int co, int k) {
+        Conv cv;
+        cv.ci = ci;
+        cv.co = co;
+        cv.k = k;
+        cv.w_off = off;
+        off += (size_t)co * ci * k * k;
+        off = (off + 7) & ~size_t(7);  // keep every weight block 16-byte aligned in BF16
+        cv.b_off = off;
+        off += (co + 7) & ~7;
+        n->convs.push_back(cv);
+    };
+    int cin = 8;
+    for (int l = 0; l < L; l++) {
+        add(cin, ch[l], 3);
+        add(ch[l], ch[l], 3);
+        cin = ch[l];
+    }
+    for (int l = L - 2; l >= 0; l--) {
+        add(ch[l + 1] + ch[l], ch[l], 3);
+        add(ch[l], ch[l], 3);
+    }
+    add(ch[0], 3, 1);
+    n->nparam = (long long)off;
+    cudaError_t e = cudaSuccess;
+    const size_t B = c.max_batch;
+    e = nalloc(n, &n->w, off);
+    if (e == cudaSuccess) e = nalloc(n, &n->g, off);
+    if (e == cudaSuccess) e = nalloc(n, &n->m, off);
+    if (e == cudaSuccess) e = nalloc(n, &n->v, off);
+    if (e == cudaSuccess) e = nalloc(n, &n->wb, off);
+    for (Conv &cv : n->convs)
+        if (e == cudaSuccess) e = nalloc(n, &cv.wt, (size_t)cv.co * cv.ci * cv.k * cv.k);
+    const size_t HW = (size_t)c.height * c.width;
+    if (e == cudaSuccess) e = nalloc(n, &n->x, B * HW * 8);
+    if (e == cudaSuccess) e = nalloc(n, &n->out, B * HW * 3);
+    if (e == cudaSuccess) e = nalloc(n, &n->dout, B * HW * 3);
+    if (e == cudaSuccess) e = nalloc(n, &n->io_in, B * HW * 8);
+    if (e == cudaSuccess) e = nalloc(n, &n->io_out, B * HW * 3);
+    if (e == cudaSuccess) e = nalloc(n, &n->io_tgt, B * HW * 3);
+    if (e == cudaSuccess) e = nalloc(n, &n->io_fl, B * HW);
+    if (e == cudaSuccess) e = nalloc(n, &n->cnt, 1);
+    if (e == cudaSuccess) e = nalloc(n, &n->loss, 1);
+    n->lv.resize(L);
+    for (int l = 0; l < L && e == cudaSuccess; l++) {
+        Level &v = n->lv[l];
+        v.H = c.height >> l;
+        v.W = c.width >> l;
+        v.C = ch[l];
+        const size_t P = B * v.H * v.W;
+        const int cprev = l > 0 ? ch[l - 1] : 8;
+        const int cnext = l + 1 < L ? ch[l + 1] : 0;
+        if (l > 0) e = nalloc(n, &v.inp, P * cprev);
+        if (e == cudaSuccess) e = nalloc(n, &v.ea, P * v.C);
+        if (e == cudaSuccess) e = nalloc(n, &v.e, P * v.C);
+        if (e == cudaSuccess && l < L - 1) e = nalloc(n, &v.cat, P * (v.C + cnext));
+        if (e == cudaSuccess && l < L - 1) e = nalloc(n, &v.da, P * v.C);
+        if (e == cudaSuccess && l < L - 1) e = nalloc(n, &v.d, P * v.C);
+        if (e == cudaSuccess) e = nalloc(n, &v.g1, P * v.C);
+        if (e == cudaSuccess) e = nalloc(n, &v.g2, P * v.C);
+        if (e == cudaSuccess && l < L - 1) e = nalloc(n, &v.gcat, P * (v.C + cnext));
+        if (e == cudaSuccess && l > 0) e = nalloc(n, &v.gin, P * cprev);
+    }
+    if (e == cudaSuccess) e = cudaMemsetAsync(n->m, 0, off * sizeof(float), n->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(n->v, 0, off * sizeof(float), n->stream);
+    if (e != cudaSuccess) {
+        lbm_status st = e == cudaErrorMemoryAllocation ? LBM_ENOMEM : LBM_ECUDA;
+        nfail(nullptr, st, "lbm_unet_create: %s", cudaGetErrorString(e));
+        nrelease(n);
+        return st;
+    }
+    // He-normal weights (std sqrt(2 / fan_in)), zero biases, seeded
+    std::vector<float> w(off, 0.f);
+    std::mt19937_64 rng(c.seed);
+    std::normal_distribution<double> nd(0.0, 1.0);
+    for (const Conv &cv : n->convs) {
+        const double sd = std::sqrt(2.0 / (cv.ci * cv.k * cv.k));
+        for (size_t i = 0; i < (size_t)cv.co * cv.ci * cv.k * cv.k; i++) w[cv.w_off + i] = (float)(sd * nd(rng));
+    }
+    e = cudaMemcpyAsync(n->w, w.data(), off * sizeof(float), cudaMemcpyHostToDevice, n->stream);
+    if (e == cudaSuccess) e = refresh_weights(n);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(n->stream);
+    if (e != cudaSuccess) {
+        nfail(nullptr, LBM_ECUDA, "lbm_unet_create: %s", cudaGetErrorString(e));
+        nrelease(n);
+        return LBM_ECUDA;
+    }
+    *out = n;
+    return LBM_OK;
+}
+
+lbm_status lbm_unet_destroy(lbm_unet *n) {
+    if (!n) return LBM_OK;
+    cudaSetDevice(n->cfg.device);
+    cudaStreamSynchronize(n->stream);
+    nrelease(n);
+    return LBM_OK;
+}
+
+const char *lbm_unet_last_error(const lbm_unet *n) { return n ? n->err.c_str() : g_nn_error.c_str(); }
+
+int64_t lbm_unet_param_count(const lbm_unet *n) {
+    if (!n) return -1;
+    int64_t s = 0;
+    for (const Conv &cv : n->convs) s += (int64_t)cv.co * cv.ci * cv.k * cv.k + cv.co;
+    return s;
+}
+
+lbm_status lbm_unet_get_params(lbm_unet *n, float *a, int32_t on_device) {
+    if (!n || !a) return LBM_EINVAL;
+    NCK(n, cudaSetDevice(n->cfg.device));
+    std::vector<float> w(n->nparam), h(lbm_unet_param_count(n));
+    NCK(n, cudaMemcpyAsync(w.data(), n->w, w.size() * sizeof(float), cudaMemcpyDeviceToHost, n->stream));
+    NCK(n, cudaStreamSynchronize(n->stream));
+    internal_to_abi(n, w.data(), h.data());
+    if (on_device) {
+        NCK(n, cudaMemcpyAsync(a, h.data(), h.size() * sizeof(float), cudaMemcpyHostToDevice, n->stream));
+        NCK(n, cudaStreamSynchronize(n->stream));
+    } else {
+        std::memcpy(a, h.data(), h.size() * sizeof(float));
+    }
+    return LBM_OK;
+}
+
+lbm_status lbm_unet_set_params(lbm_unet *n, const float *a, int32_t on_device) {
+    if (!n || !a) return LBM_EINVAL;
+    NCK(n, cudaSetDevice(n->cfg.device));
+    std::vector<float> h(lbm_unet_param_count(n)), w;
+    if (on_device) {
+        NCK(n, cudaMemcpyAsync(h.data(), a, h.size() * sizeof(float), cudaMemcpyDeviceToHost, n->stream));
+        NCK(n, cudaStreamSynchronize(n->stream));
+    } else {
+        std::memcpy(h.data(), a, h.size() * sizeof(float));
+    }
+    for (float x : h)
+        if (!std::isfinite(x)) return nfail(n, LBM_EINVAL, "non-finite parameter");
+    abi_to_internal(n, h.data(), w);
+    NCK(n, cudaMemcpyAsync(n->w, w.data(), w.size() * sizeof(float), cudaMemcpyHostToDevice, n->stream));
+    NCK(n, refresh_weights(n));
+    NCK(n, cudaMemsetAsync(n->m, 0, n->nparam * sizeof(float), n->stream));
+    NCK(n, cudaMemsetAsync(n->v, 0, n->nparam * sizeof(float), n->stream));
+    n->adam_t = 0;
+    NCK(n, cudaStreamSynchronize(n->stream));
+    return LBM_OK;
+}
+
+lbm_status lbm_unet_forward(lbm_unet *n, const float *in, float *out, int32_t B, int32_t on_device) {
+    if (!n || !in || !out || B < 1 || B > n->cfg.max_batch) return LBM_EINVAL;
+    NCK(n, cudaSetDevice(n->cfg.device));
+    const float *din = nullptr;
+    lbm_status st = stage_inputs(n, in, nullptr, nullptr, B, on_device, &din, nullptr, nullptr);
+    if (st == LBM_OK) st = forward(n, din, B);
+    if (st != LBM_OK) return st;
+    const size_t bytes = (size_t)B * 3 * n->cfg.height * n->cfg.width * sizeof(float);
+    NCK(n, cudaMemcpyAsync(out, n->out, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                           n->stream));
+    if (!on_device) NCK(n, cudaStreamSynchronize(n->stream));
+    return LBM_OK;
+}
+
+lbm_status lbm_unet_gradients(lbm_unet *n, const float *in, const float *tgt, const float *fl,
+                              int32_t B, float *grads, double *loss, int32_t on_device) {
+    if (!n || !in || !tgt || !fl || !grads || B < 1 || B > n->cfg.max_batch) return LBM_EINVAL;
+    NCK(n, cudaSetDevice(n->cfg.device));
+    const float *din, *dt, *df;
+    lbm_status st = stage_inputs(n, in, tgt, fl, B, on_device, &din, &dt, &df);
+    if (st == LBM_OK) st = forward(n, din, B);
+    if (st == LBM_OK) st = backward(n, dt, df, B);
+    if (st != LBM_OK) return st;
+    std::vector<float> g(n->nparam), h(lbm_unet_param_count(n));
+    double l = 0.0;
+    NCK(n, cudaMemcpyAsync(g.data(), n->g, g.size() * sizeof(float), cudaMemcpyDeviceToHost, n->stream));
+    NCK(n, cudaMemcpyAsync(&l, n->loss, sizeof(double), cudaMemcpyDeviceToHost, n->stream));
+    NCK(n, cudaStreamSynchronize(n->stream));
+    internal_to_abi(n, g.data(), h.data());
+    if (on_device) {
+        NCK(n, cudaMemcpyAsync(grads, h.data(), h.size() * sizeof(float), cudaMemcpyHostToDevice, n->stream));
+        NCK(n, cudaStreamSynchronize(n->stream));
+    } else {
+        std::memcpy(grads, h.data(), h.size() * sizeof(float));
+    }
+    if (loss) *loss = l;
+    return LBM_OK;
+}
+
+lbm_status lbm_unet_train_step(lbm_unet *n, const float *in, const float *tgt, const float *fl,
+                               int32_t B, float lr, double *loss, int32_t on_device) {
+    if (!n || !in || !tgt || !fl || B < 1 || B > n->cfg.max_batch || !(lr > 0.f)) return LBM_EINVAL;
+    NCK(n, cudaSetDevice(n->cfg.device));
+    const float *din, *dt, *df;
+    lbm_status st = stage_inputs(n, in, tgt, fl, B, on_device, &din, &dt, &df);
+    if (st == LBM_OK) st = forward(n, din, B);
+    if (st == LBM_OK) st = backward(n, dt, df, B);
+    if (st != LBM_OK) return st;
+    n->adam_t++;
+    const float c1 = (float)(1.0 - std::pow(0.9, (double)n->adam_t));
+    const float c2 = (float)(1.0 - std::pow(0.999, (double)n->adam_t));
+    NCK(n, (nn::k_adam<<<nn::blocks(n->nparam), nn::EW, 0, n->stream>>>(n->w, n->g, n->m, n->v, n->wb,
+                                                                       n->nparam, lr, c1, c2),
+           cudaGetLastError()));
+    for (const Conv &cv : n->convs) {
+        const long long cnt = (long long)cv.co * cv.k * cv.k * cv.ci;
+        NCK(n, (nn::k_transpose_w<<<nn::blocks(cnt), nn::EW, 0, n->stream>>>(n->wb + cv.w_off, cv.wt, cv.co,
+                                                                          cv.k * cv.k, cv.ci),
+               cudaGetLastError()));
+    }
+    if (loss) {
+        NCK(n, cudaMemcpyAsync(loss, n->loss, sizeof(double), cudaMemcpyDeviceToHost, n->stream));
+        NCK(n, cudaStreamSynchronize(n->stream));
+    }
+    return LBM_OK;
+}
+
+lbm_status lbm_unet_input(lbm_unet *n, const int32_t *owner, double re, float *in) {
+    if (!n || !owner || !in || !std::isfinite(re)) return LBM_EINVAL;
+    NCK(n, cudaSetDevice(n->cfg.device));
+    const int HW = n->cfg.height * n->cfg.width;
+    NCK(n, (nn::k_case_input<<<nn::blocks(HW), nn::EW, 0, n->stream>>>(owner, (float)(re / 100.0), in, HW),
+           cudaGetLastError()));
+    return LBM_OK;
+}
+
+}  // extern "C"

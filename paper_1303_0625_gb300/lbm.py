@@ -49,6 +49,12 @@ class lbm_config(ctypes.Structure):
     ]
 
 
+class lbm_unet_config(ctypes.Structure):
+    _fields_ = [("levels", ctypes.c_int32), ("base", ctypes.c_int32), ("height", ctypes.c_int32),
+                ("width", ctypes.c_int32), ("max_batch", ctypes.c_int32), ("device", ctypes.c_int32),
+                ("seed", ctypes.c_uint64), ("stream", ctypes.c_void_p)]
+
+
 class lbm_disk(ctypes.Structure):
     _fields_ = [
         ("cx", ctypes.c_double), ("cy", ctypes.c_double), ("r", ctypes.c_double),
@@ -106,15 +112,29 @@ _SIGNATURES = {
     "lbm_batch_get_timing": (_I32, [_P, _D, ctypes.POINTER(_I64)]),
     "lbm_batch_launch_count": (_I64, [_P]),
     "lbm_batch_last_error": (ctypes.c_char_p, [_P]),
+    "lbm_unet_create": (_I32, [ctypes.POINTER(lbm_unet_config), ctypes.POINTER(_P)]),
+    "lbm_unet_destroy": (_I32, [_P]),
+    "lbm_unet_last_error": (ctypes.c_char_p, [_P]),
+    "lbm_unet_param_count": (_I64, [_P]),
+    "lbm_unet_get_params": (_I32, [_P, _P, _I32]),
+    "lbm_unet_set_params": (_I32, [_P, _P, _I32]),
+    "lbm_unet_forward": (_I32, [_P, _P, _P, _I32, _I32]),
+    "lbm_unet_gradients": (_I32, [_P, _P, _P, _P, _I32, _P, _D, _I32]),
+    "lbm_unet_train_step": (_I32, [_P, _P, _P, _P, _I32, ctypes.c_float, _D, _I32]),
+    "lbm_unet_input": (_I32, [_P, _P, ctypes.c_double, _P]),
+    "lbm_warm_start": (_I32, [_P, _P, ctypes.c_double]),
 }
 
 
 def header_symbols() -> list[str]:
-    """Names of the functions declared in include/lbm.h."""
-    with open(os.path.join(_build.INCLUDE, "lbm.h")) as fh:
-        text = fh.read()
-    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    return re.findall(r"\b(lbm_[a-z_0-9]+)\s*\(", text)
+    """Names of the functions declared in include/lbm.h and include/lbm_nn.h."""
+    out = []
+    for name in ("lbm.h", "lbm_nn.h"):
+        with open(os.path.join(_build.INCLUDE, name)) as fh:
+            text = fh.read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        out += re.findall(r"\b(lbm_[a-z_0-9]+)\s*\(", text)
+    return out
 
 
 def library_path() -> str:
@@ -375,6 +395,122 @@ def lbm_batch_launch_count(b) -> int:
 def lbm_batch_last_error(b=None) -> str:
     r = load().lbm_batch_last_error(b)
     return r.decode() if r else ""
+
+
+# ------------------------------------------------------ warm-start net
+
+def _ncheck(st: int, net=None):
+    if st != LBM_OK:
+        lib = load()
+        r = lib.lbm_unet_last_error(net)
+        raise LBMError(st, (r.decode() if r else "") or lib.lbm_status_string(st).decode())
+
+
+def lbm_unet_create(cfg: lbm_unet_config):
+    h = _P()
+    _ncheck(load().lbm_unet_create(ctypes.byref(cfg), ctypes.byref(h)))
+    return h
+
+
+def lbm_unet_destroy(net):
+    _ncheck(load().lbm_unet_destroy(net), net)
+
+
+def lbm_unet_param_count(net) -> int:
+    return int(load().lbm_unet_param_count(net))
+
+
+def lbm_unet_get_params(net, out, on_device: bool = False):
+    _ncheck(load().lbm_unet_get_params(net, _ptr(out), int(on_device)), net)
+
+
+def lbm_unet_set_params(net, params, on_device: bool = False):
+    _ncheck(load().lbm_unet_set_params(net, _ptr(params), int(on_device)), net)
+
+
+def lbm_unet_forward(net, x, out, batch: int, on_device: bool = False):
+    _ncheck(load().lbm_unet_forward(net, _ptr(x), _ptr(out), int(batch), int(on_device)), net)
+
+
+def lbm_unet_gradients(net, x, target, fluid, batch: int, grads, on_device: bool = False) -> float:
+    loss = ctypes.c_double()
+    _ncheck(load().lbm_unet_gradients(net, _ptr(x), _ptr(target), _ptr(fluid), int(batch),
+                                      _ptr(grads), ctypes.byref(loss), int(on_device)), net)
+    return float(loss.value)
+
+
+def lbm_unet_train_step(net, x, target, fluid, batch: int, lr: float, on_device: bool = False) -> float:
+    loss = ctypes.c_double()
+    _ncheck(load().lbm_unet_train_step(net, _ptr(x), _ptr(target), _ptr(fluid), int(batch),
+                                       float(lr), ctypes.byref(loss), int(on_device)), net)
+    return float(loss.value)
+
+
+def lbm_unet_input(net, owner_dev, reynolds: float, in_dev):
+    _ncheck(load().lbm_unet_input(net, _ptr(owner_dev), float(reynolds), _ptr(in_dev)), net)
+
+
+def lbm_warm_start(ctx, prediction_dev, u_scale: float):
+    _check(load().lbm_warm_start(ctx, _ptr(prediction_dev), float(u_scale)), ctx)
+
+
+class UNet:
+    """Owns an lbm_unet (see include/lbm_nn.h)."""
+
+    def __init__(self, height, width, *, levels=4, base=32, max_batch=8, seed=0, device=0,
+                 stream=None):
+        self.cfg = lbm_unet_config(levels=levels, base=base, height=height, width=width,
+                                   max_batch=max_batch, device=device, seed=seed, stream=stream)
+        self.levels, self.base, self.H, self.W = levels, base, height, width
+        self.max_batch = max_batch
+        self._h = lbm_unet_create(self.cfg)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lbm_unet_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def handle(self):
+        return self._h
+
+    @property
+    def nparam(self) -> int:
+        return lbm_unet_param_count(self._h)
+
+    def params(self) -> np.ndarray:
+        out = np.empty(self.nparam, dtype=np.float32)
+        lbm_unet_get_params(self._h, out)
+        return out
+
+    def set_params(self, p):
+        lbm_unet_set_params(self._h, np.ascontiguousarray(p, dtype=np.float32))
+
+    def forward(self, x: np.ndarray) -> np.ndarray:
+        x = np.ascontiguousarray(x, dtype=np.float32)
+        out = np.empty((x.shape[0], 3, self.H, self.W), dtype=np.float32)
+        lbm_unet_forward(self._h, x, out, x.shape[0])
+        return out
+
+    def gradients(self, x, target, fluid):
+        x = np.ascontiguousarray(x, dtype=np.float32)
+        g = np.empty(self.nparam, dtype=np.float32)
+        loss = lbm_unet_gradients(self._h, x, np.ascontiguousarray(target, dtype=np.float32),
+                                  np.ascontiguousarray(fluid, dtype=np.float32), x.shape[0], g)
+        return loss, g
+
+    def train_step(self, x, target, fluid, lr, on_device=False) -> float:
+        if not on_device:
+            x = np.ascontiguousarray(x, dtype=np.float32)
+            target = np.ascontiguousarray(target, dtype=np.float32)
+            fluid = np.ascontiguousarray(fluid, dtype=np.float32)
+        return lbm_unet_train_step(self._h, x, target, fluid, x.shape[0], lr, on_device)
 
 
 # ----------------------------------------------------------- convenience

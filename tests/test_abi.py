@@ -46,6 +46,25 @@ def test_struct_layout_matches_header(tmp_path):
     assert vals[2:] == offs
 
 
+def test_unet_config_layout_matches_header(tmp_path):
+    import os
+    import subprocess
+    src = tmp_path / "layout_nn.c"
+    fields = [f for f, _ in L.lbm_unet_config._fields_]
+    body = ['#include <stdio.h>', '#include <stddef.h>', '#include "lbm_nn.h"', "int main(void){",
+            'printf("%zu\\n", sizeof(lbm_unet_config));']
+    body += [f'printf("%zu\\n", offsetof(lbm_unet_config, {f}));' for f in fields]
+    body += ["return 0;}"]
+    src.write_text("\n".join(body))
+    exe = tmp_path / "layout_nn"
+    subprocess.run(["gcc", "-I", os.path.join(os.path.dirname(L._build.PKG), "include"),
+                    str(src), "-o", str(exe)], check=True)
+    vals = list(map(int, subprocess.run([str(exe)], capture_output=True, text=True,
+                                        check=True).stdout.split()))
+    assert vals == [ctypes.sizeof(L.lbm_unet_config)] + \
+        [getattr(L.lbm_unet_config, f).offset for f in fields]
+
+
 @pytest.mark.parametrize("field,value", [("tau", 0.5), ("tau", 0.2), ("nx", 3), ("precision", 7),
                                          ("refill", 0), ("force_ring", 0), ("reserved", 1),
                                          ("bc_y", 2)])
