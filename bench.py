@@ -55,6 +55,11 @@ def parse():
     ap.add_argument("--sed-steps", type=int, default=400)
     ap.add_argument("--precision-horizon", type=int, default=500)
     ap.add_argument("--batch-cases", type=int, default=512)
+    ap.add_argument("--warm-start", action="store_true",
+                    help="train the warm-start network and measure time to converged drag")
+    ap.add_argument("--ws-train", type=int, default=1024)
+    ap.add_argument("--ws-test", type=int, default=256)
+    ap.add_argument("--ws-epochs", type=int, default=20)
     ap.add_argument("--batch-only", action="store_true",
                     help="measure only the cylinder-sweep batch and print its record")
     ap.add_argument("--batch-warmup", type=int, default=100)
@@ -445,6 +450,56 @@ def run_precision_study(a, w, local, stream):
     return out
 
 
+def run_warm_start(a, local):
+    """Learned warm start on 256 x 128 channels with 1-4 fixed disks and Re
+    in 1..100: train the U-Net on steady fields the batch engine computes for
+    a training set, then on held-out cases measure the steps and the wall
+    time (inference included) until every case's drag is within 1e-4 of its
+    converged cold-start value, warm against cold, same batch engine and GPU.
+    Cases without a steady state within the step cap are left out and
+    counted."""
+    import numpy as np
+    import torch
+
+    import paper_1303_0625_gb300 as G
+    import workloads as W
+    from paper_1303_0625_gb300 import warmstart as WS
+
+    torch.cuda.set_device(local)
+    t0 = time.time()
+    train_cases = W.warm_start_channels(a.ws_train, seed_offset=5)
+    runs = WS.steady(train_cases, device=local)
+    data = WS.dataset(train_cases, runs)
+    t_data = time.time() - t0
+    net = G.UNet(128, 256, levels=4, base=32, max_batch=16, seed=3, device=local)
+    t1 = time.time()
+    losses = WS.train(net, data, epochs=a.ws_epochs, batch=16, lr=1e-3, lr_end=1e-5)
+    t_train = time.time() - t1
+    test_all = W.warm_start_channels(a.ws_test, seed_offset=6)
+    ref = WS.steady(test_all, device=local, fields=False)
+    keep = np.flatnonzero(ref["state"] == G.LBM_CASE_CONVERGED)
+    test = [test_all[k] for k in keep]
+    d_star = ref["drag"][keep]
+    cold = WS.time_to_drag(test, d_star, device=local)
+    warm = WS.time_to_drag(test, d_star, net=net, device=local)
+    steps_c, steps_w = cold["steps"].astype(float), warm["steps"].astype(float)
+    return {"metric": "time-to-drag at 1e-4 rel err, warm vs cold start",
+            "workload": "256x128 channels, 1-4 fixed disks r 6-16, Re 1..100, tau from Re "
+                        "(>= 0.53), velocity inlet / pressure outlet, fp32 batch engine",
+            "train_cases": len(train_cases), "train_steady": int(len(data["index"])),
+            "data_seconds": round(t_data, 1), "train_seconds": round(t_train, 1),
+            "epochs": a.ws_epochs, "final_loss": float("%.4g" % losses[-1]),
+            "test_cases": len(test_all), "test_steady": len(test),
+            "excluded_unsteady": int(len(test_all) - len(test)),
+            "cold": {"wall_s": round(cold["wall"], 3), "batch_steps": int(cold["batch_steps"]),
+                     "median_case_steps": float(np.median(steps_c))},
+            "warm": {"wall_s": round(warm["wall"], 3), "batch_steps": int(warm["batch_steps"]),
+                     "median_case_steps": float(np.median(steps_w)),
+                     "fallbacks": int(warm["fallback"].sum())},
+            "wall_speedup": round(cold["wall"] / warm["wall"], 3),
+            "median_step_speedup": round(float(np.median(steps_c / np.maximum(steps_w, 1))), 3)}
+
+
 def run_e2e(a, w, local, stream):
     """Same metric through the C ABI with host buffers: initial populations
     from pinned host memory, force records read back every 50 steps."""
@@ -547,6 +602,9 @@ def main():
     ws, rank, local = dist_setup()
     if a.impl == "reference":
         run_reference(a, ws, rank)
+    elif a.warm_start:
+        if rank == 0:
+            print(json.dumps(run_warm_start(a, local)), flush=True)
     elif a.batch_only:
         import torch
         torch.cuda.set_device(local)

@@ -18,7 +18,8 @@
  *           with ReLU per level, 2x2 average pooling between levels; decoder:
  *           2x nearest upsampling, concatenation [upsampled, skip], two 3x3
  *           convs with ReLU; head: 1x1 conv to 3 channels, no ReLU;
- *   outputs [B][3][H][W] float: (rho - 1) / U^2, u_x / U, u_y / U;
+ *   outputs [B][3][H][W] float: the scaled density deviation and velocity
+ *           (lbm_warm_start names the scales);
  *   params  per conv, in the order enc0a, enc0b, ..., enc{L-1}b, dec{L-2}a,
  *           dec{L-2}b, ..., dec0b, head: weights [Cout][Cin][k][k] then
  *           biases [Cout], float.
@@ -87,9 +88,10 @@ lbm_status lbm_unet_input(lbm_unet *net, const int32_t *owner_device, double rey
                           float *in_device);
 
 /* Initial state of ctx from a network output [3][H][W] (device floats):
- * at every fluid node f = f^eq(1 + U^2 p0, U p1, U p2), U = u_scale
+ * at every fluid node f = f^eq(1 + rho_scale p0, u_scale p1, u_scale p2)
  * (Eq. 8).  The domain must be H x W; solid nodes keep their state. */
-lbm_status lbm_warm_start(lbm_ctx *ctx, const float *prediction_device, double u_scale);
+lbm_status lbm_warm_start(lbm_ctx *ctx, const float *prediction_device, double u_scale,
+                          double rho_scale);
 
 #ifdef __cplusplus
 }

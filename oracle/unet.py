@@ -18,7 +18,7 @@ steady fields the method generates).  Readings, all stated here once:
   head         1x1 conv (no ReLU) to 3 output channels
   inputs       channel 0: solid mask (1 solid, 0 fluid); channel 1: Re / 100;
                channels 2..7: zero (the kernels take 8 input channels)
-  outputs      (rho - 1) / U^2, u_x / U, u_y / U with U the inlet peak speed
+  outputs      three channels: the scaled density deviation and velocity
   loss         mean over fluid nodes and the 3 channels of (out - target)^2
   optimizer    Adam with bias correction (beta1 0.9, beta2 0.999, eps 1e-8)
 

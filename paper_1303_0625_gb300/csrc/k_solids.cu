@@ -118,9 +118,9 @@ __global__ void k_import_populations(const StepParams p, const double *in) {
 }
 
 // Equilibrium initial state from a network prediction pred [3][ny][nx]
-// (FP32): rho = 1 + U^2 p0, u = U (p1, p2) at every fluid node (Eq. 8).
+// (FP32): rho = 1 + R p0, u = U (p1, p2) at every fluid node (Eq. 8).
 template <int P>
-__global__ void k_warm_start(const StepParams p, const float *pred, double U) {
+__global__ void k_warm_start(const StepParams p, const float *pred, double U, double R) {
     const Lattice &L = p.L;
     const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
     if (x >= L.nx) return;
@@ -128,7 +128,7 @@ __global__ void k_warm_start(const StepParams p, const float *pred, double U) {
     if (p.flags[k] & 1u) return;
     const long long t = *p.t;
     void *f = (t & 1) ? p.f1 : p.f0;
-    const double rho = 1.0 + U * U * (double)pred[o];
+    const double rho = 1.0 + R * (double)pred[o];
     const double ux = U * (double)pred[n + o], uy = U * (double)pred[2 * n + o];
     const double uu = ux * ux + uy * uy;
     for (int i = 0; i < 9; i++) {
@@ -236,11 +236,12 @@ cudaError_t launch_import_populations(const StepParams &p, const double *in, cud
 }
 
 cudaError_t launch_warm_start(const StepParams &p, const float *pred, double u_scale,
-                              cudaStream_t st) {
+                              double rho_scale, cudaStream_t st) {
+    const dim3 g = cell_grid(p.L);
     switch (p.precision) {
-        case LBM_FP64: k_warm_start<LBM_FP64><<<cell_grid(p.L), 128, 0, st>>>(p, pred, u_scale); break;
-        case LBM_FP32_DEV: k_warm_start<LBM_FP32_DEV><<<cell_grid(p.L), 128, 0, st>>>(p, pred, u_scale); break;
-        default: k_warm_start<LBM_FP16_DEV><<<cell_grid(p.L), 128, 0, st>>>(p, pred, u_scale);
+        case LBM_FP64: k_warm_start<LBM_FP64><<<g, 128, 0, st>>>(p, pred, u_scale, rho_scale); break;
+        case LBM_FP32_DEV: k_warm_start<LBM_FP32_DEV><<<g, 128, 0, st>>>(p, pred, u_scale, rho_scale); break;
+        default: k_warm_start<LBM_FP16_DEV><<<g, 128, 0, st>>>(p, pred, u_scale, rho_scale);
     }
     return cudaGetLastError();
 }

@@ -604,10 +604,10 @@ lbm_status lbm_set_populations(lbm_ctx *c, const double *f, int32_t on_device) {
     return LBM_OK;
 }
 
-lbm_status lbm_warm_start(lbm_ctx *c, const float *pred, double u_scale) {
-    if (!c || !pred || !std::isfinite(u_scale)) return LBM_EINVAL;
+lbm_status lbm_warm_start(lbm_ctx *c, const float *pred, double u_scale, double rho_scale) {
+    if (!c || !pred || !std::isfinite(u_scale) || !std::isfinite(rho_scale)) return LBM_EINVAL;
     CK(c, cudaSetDevice(c->cfg.device));
-    CK(c, gbm::launch_warm_start(params(c), pred, u_scale, c->stream));
+    CK(c, gbm::launch_warm_start(params(c), pred, u_scale, rho_scale, c->stream));
     c->launches++;
     return LBM_OK;
 }

@@ -122,7 +122,7 @@ _SIGNATURES = {
     "lbm_unet_gradients": (_I32, [_P, _P, _P, _P, _I32, _P, _D, _I32]),
     "lbm_unet_train_step": (_I32, [_P, _P, _P, _P, _I32, ctypes.c_float, _D, _I32]),
     "lbm_unet_input": (_I32, [_P, _P, ctypes.c_double, _P]),
-    "lbm_warm_start": (_I32, [_P, _P, ctypes.c_double]),
+    "lbm_warm_start": (_I32, [_P, _P, ctypes.c_double, ctypes.c_double]),
 }
 
 
@@ -450,8 +450,8 @@ def lbm_unet_input(net, owner_dev, reynolds: float, in_dev):
     _ncheck(load().lbm_unet_input(net, _ptr(owner_dev), float(reynolds), _ptr(in_dev)), net)
 
 
-def lbm_warm_start(ctx, prediction_dev, u_scale: float):
-    _check(load().lbm_warm_start(ctx, _ptr(prediction_dev), float(u_scale)), ctx)
+def lbm_warm_start(ctx, prediction_dev, u_scale: float, rho_scale: float):
+    _check(load().lbm_warm_start(ctx, _ptr(prediction_dev), float(u_scale), float(rho_scale)), ctx)
 
 
 class UNet:

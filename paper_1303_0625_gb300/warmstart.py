@@ -1,0 +1,199 @@
+"""Learned warm start of steady channel flows past fixed disks.
+
+Host-side orchestration only: every step runs in the library's kernels (the
+batch engine for the lattice-Boltzmann runs, the U-Net kernels for training
+and inference, ``lbm_warm_start`` for the initial state).  PyTorch supplies
+device buffers.
+
+  steady(cases)          run a batch of cases to a steady state (drag change
+                         below tol per `every` steps) and collect the fields
+  dataset(cases, runs)   network inputs (solid mask, Re / 100), targets
+                         (scaled rho - 1 and u) and fluid masks
+  train(net, data, ...)  mini-batch Adam on the masked MSE
+  time_to_drag(...)      steps and wall time until every case's drag is within
+                         rel of its converged value, from the plain (cold)
+                         initial state or from the network's prediction (warm),
+                         with the drift check and the fallback to a cold start
+
+Scales (per case, U = peak inlet speed): u = U p_u, rho - 1 = (100 U^2 / Re) p_rho,
+so that both targets are of order one from Re = 1 to 100.
+"""
+from __future__ import annotations
+
+import time
+
+import numpy as np
+
+from . import lbm as L
+
+
+def rho_scale(case) -> float:
+    return 100.0 * case["u_scale"] ** 2 / case["re"]
+
+
+def _batch(cases, precision, device, stream, ring=4):
+    return L.Batch.from_workloads(cases, precision=precision, force_ring=ring, device=device,
+                                  stream=stream)
+
+
+def steady(cases, *, precision=L.LBM_FP32_DEV, tol=1e-7, every=100, cap=300_000, chunk=1000,
+           device=0, stream=None, fields=True):
+    """Run every case to a steady state; returns dict with state, steps,
+    drag and (with fields) rho, ux, uy [N][ny][nx] (NaN at solids)."""
+    b = _batch(cases, precision, device, stream)
+    b.set_convergence(every=every, tol=tol, max_steps=cap)
+    t0 = time.perf_counter()
+    while b.run(chunk) > 0:
+        pass
+    wall = time.perf_counter() - t0
+    st, steps, drag = b.state()
+    out = dict(state=st, steps=steps, drag=drag, wall=wall)
+    if fields:
+        ny, nx = cases[0]["ny"], cases[0]["nx"]
+        rho = np.empty((len(cases), ny, nx))
+        ux = np.empty_like(rho)
+        uy = np.empty_like(rho)
+        for k in range(len(cases)):
+            rho[k], ux[k], uy[k] = b.case(k).fields()
+        out.update(rho=rho, ux=ux, uy=uy)
+    b.close()
+    return out
+
+
+def dataset(cases, runs):
+    """Inputs [N][8][H][W], targets [N][3][H][W], fluid [N][H][W] (float32) of
+    the cases that reached a steady state."""
+    keep = np.flatnonzero(runs["state"] == L.LBM_CASE_CONVERGED)
+    n = len(keep)
+    ny, nx = cases[0]["ny"], cases[0]["nx"]
+    x = np.zeros((n, 8, ny, nx), dtype=np.float32)
+    y = np.zeros((n, 3, ny, nx), dtype=np.float32)
+    f = np.zeros((n, ny, nx), dtype=np.float32)
+    for j, k in enumerate(keep):
+        solid = np.isnan(runs["rho"][k])
+        U = cases[k]["u_scale"]
+        x[j, 0] = solid
+        x[j, 1] = cases[k]["re"] / 100.0
+        f[j] = ~solid
+        y[j, 0] = np.where(solid, 0.0, (runs["rho"][k] - 1.0) / rho_scale(cases[k]))
+        y[j, 1] = np.where(solid, 0.0, runs["ux"][k] / U)
+        y[j, 2] = np.where(solid, 0.0, runs["uy"][k] / U)
+    return dict(x=x, y=y, fluid=f, index=keep)
+
+
+def train(net, data, *, epochs=20, batch=16, lr=1e-3, lr_end=1e-4, seed=0, log=None):
+    """Mini-batch Adam over the dataset (held on the device); the learning
+    rate decays geometrically from lr to lr_end.  Returns the epoch losses."""
+    import torch
+
+    dev = torch.device("cuda", net.cfg.device)
+    X = torch.from_numpy(data["x"]).to(dev)
+    Y = torch.from_numpy(data["y"]).to(dev)
+    F = torch.from_numpy(data["fluid"]).to(dev)
+    n = X.shape[0]
+    rng = np.random.default_rng(seed)
+    losses = []
+    steps = max(1, epochs * (n // batch))
+    k = 0
+    for ep in range(epochs):
+        order = rng.permutation(n)
+        tot, cnt = 0.0, 0
+        for s in range(0, n - batch + 1, batch):
+            idx = torch.from_numpy(order[s:s + batch]).to(dev)
+            xb, yb, fb = X[idx].contiguous(), Y[idx].contiguous(), F[idx].contiguous()
+            rate = lr * (lr_end / lr) ** (k / steps)
+            tot += L.lbm_unet_train_step(net.handle, xb, yb, fb, batch, rate, on_device=True)
+            cnt += 1
+            k += 1
+        losses.append(tot / max(cnt, 1))
+        if log:
+            log(f"epoch {ep} loss {losses[-1]:.4e}")
+    return losses
+
+
+def predict(net, data_x, batch=16):
+    """Network outputs for inputs [N][8][H][W] (host), as a device tensor."""
+    import torch
+
+    dev = torch.device("cuda", net.cfg.device)
+    X = torch.from_numpy(data_x).to(dev)
+    out = torch.empty((X.shape[0], 3, X.shape[2], X.shape[3]), dtype=torch.float32, device=dev)
+    for s in range(0, X.shape[0], batch):
+        e = min(X.shape[0], s + batch)
+        L.lbm_unet_forward(net.handle, X[s:e].contiguous(), out[s:e], e - s, on_device=True)
+    return out
+
+
+def _mass(ctx):
+    """Total fluid mass of a case, or NaN once its state is unusable."""
+    try:
+        return float(np.nansum(ctx.fields()[0]))
+    except L.LBMError:
+        return float("nan")
+
+
+def time_to_drag(cases, d_star, *, net=None, rel=1e-4, precision=L.LBM_FP32_DEV, every=100,
+                 cap=300_000, drift_steps=200, drift_mass=1e-2, device=0, stream=None):
+    """Steps and wall time until every case's Eq. 5 drag is within rel of
+    d_star (the converged drag of the plain run), starting cold (net None)
+    or warm from the network's prediction.  Warm cases are checked after
+    drift_steps: an unstable state, a non-finite drag or a total-mass change
+    above drift_mass (relative) restarts that case cold.  The wall time
+    covers input assembly, inference and every step."""
+    import torch
+
+    dev = torch.device("cuda", device)
+    b = _batch(cases, precision, device, stream)
+    b.set_convergence(every=every, tol=0.0, max_steps=cap)  # retire only at the cap
+    n = len(cases)
+    ny, nx = cases[0]["ny"], cases[0]["nx"]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    fallback = np.zeros(n, dtype=bool)
+    mass0 = None
+    if net is not None:
+        owner = torch.empty((ny, nx), dtype=torch.int32, device=dev)
+        xin = torch.empty((n, 8, ny, nx), dtype=torch.float32, device=dev)
+        for k in range(n):
+            L.lbm_get_owner(b.case(k).handle, owner, on_device=True)
+            L.lbm_unet_input(net.handle, owner, cases[k]["re"], xin[k])
+        out = torch.empty((n, 3, ny, nx), dtype=torch.float32, device=dev)
+        for s in range(0, n, net.max_batch):
+            e = min(n, s + net.max_batch)
+            L.lbm_unet_forward(net.handle, xin[s:e], out[s:e], e - s, on_device=True)
+        torch.cuda.synchronize()
+        for k in range(n):
+            L.lbm_warm_start(b.case(k).handle, out[k], cases[k]["u_scale"], rho_scale(cases[k]))
+        mass0 = np.array([_mass(b.case(k)) for k in range(n)])
+    done = np.full(n, -1, dtype=np.int64)
+    drift = None
+    steps = 0
+    while steps < cap:
+        b.run(every)
+        steps += every
+        st, stp, drag = b.state()
+        if net is not None and steps == drift_steps:
+            drift = np.zeros(n)
+            for k in range(n):
+                m = _mass(b.case(k))
+                drift[k] = abs(m - mass0[k]) / abs(mass0[k]) if np.isfinite(m) else np.inf
+                if st[k] == L.LBM_CASE_UNSTABLE or not np.isfinite(drag[k]) or \
+                        not drift[k] <= drift_mass:
+                    fallback[k] = True
+            if fallback.any():  # those cases start again, cold, in a batch of their own
+                sub = [cases[k] for k in np.flatnonzero(fallback)]
+                r = time_to_drag(sub, d_star[fallback], rel=rel, precision=precision, every=every,
+                                 cap=cap, device=device, stream=stream)
+                done[fallback] = r["steps"] + steps
+        ok = np.abs(drag - d_star) <= rel * np.abs(d_star)
+        newly = ok & (done < 0) & ~fallback
+        done[newly] = steps
+        leave = (~ok) & (done >= 0) & ~fallback  # left the band again: not done yet
+        done[leave] = -1
+        if (done >= 0).all():
+            break
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    b.close()
+    return dict(steps=done, wall=wall, fallback=fallback, batch_steps=steps,
+                drift=drift if net is not None and steps >= drift_steps else None)

@@ -122,9 +122,10 @@ def test_warm_start_sets_the_predicted_equilibrium():
     pred = rng.normal(0.0, 0.3, (3, H, W)).astype(np.float32)
     U_ = 0.05
     dev = torch.from_numpy(pred).cuda()
-    L.lbm_warm_start(lat.handle, dev, U_)
+    R = 3e-3
+    L.lbm_warm_start(lat.handle, dev, U_, R)
     rho, ux, uy = lat.fields()
     fl = lat.owner() < 0
-    assert np.allclose(rho[fl], 1.0 + U_ * U_ * pred[0][fl], atol=2e-6)
+    assert np.allclose(rho[fl], 1.0 + R * pred[0][fl], atol=2e-6)
     assert np.allclose(ux[fl], U_ * pred[1][fl], atol=2e-6)
     assert np.allclose(uy[fl], U_ * pred[2][fl], atol=2e-6)

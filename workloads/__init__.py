@@ -171,6 +171,48 @@ def cylinder_sweep(ncase=512, *, seed_offset=3, nx_range=(128, 1024), ny_range=(
     return out
 
 
+def warm_start_channels(ncase, *, seed_offset=5, nx=256, ny=128, umax=0.05, tau_min=0.53,
+                        umax_cap=0.12, re_range=(1.0, 100.0), rmin=6.0, rmax=16.0):
+    """Channels of the learned warm start: nx x ny, bounce-back walls in y,
+    Poiseuille velocity inlet and pressure outlet, 1-4 fixed disks of radius
+    uniform in [rmin, rmax] at seeded non-overlapping positions (gap >= 4),
+    each at least its diameter from the walls and twice its diameter from
+    the inlet and outlet.  Re uniform in re_range on the largest diameter d
+    and the mean inlet speed U_mean = umax / 1.5; tau = 1/2 + 3 U_mean d / Re;
+    below tau_min, tau = tau_min and U_mean = Re (tau - 1/2) / (3 d), the case
+    drawn again when its peak 1.5 U_mean would exceed umax_cap.  Returns a
+    list of case descriptions (with ``re`` and ``u_scale`` = peak speed)."""
+    rng = np.random.default_rng(BASE_SEED + seed_offset)
+    out = []
+    while len(out) < ncase:
+        k = int(rng.integers(1, 5))
+        disks = []
+        for _ in range(200):
+            if len(disks) == k:
+                break
+            r = float(rng.uniform(rmin, rmax))
+            cx = float(rng.uniform(4 * r, nx - 4 * r))
+            cy = float(rng.uniform(3 * r, ny - 3 * r))
+            if all((cx - d["cx"]) ** 2 + (cy - d["cy"]) ** 2 > (r + d["r"] + 4) ** 2 for d in disks):
+                disks.append(_disk(cx, cy, r))
+        if not disks:
+            continue
+        re = float(rng.uniform(*re_range))
+        d = 2.0 * max(x["r"] for x in disks)
+        umean = umax / 1.5
+        tau = 0.5 + 3.0 * umean * d / re
+        if tau < tau_min:
+            tau = tau_min
+            umean = re * (tau - 0.5) / (3.0 * d)
+            if 1.5 * umean > umax_cap:
+                continue
+        out.append(dict(nx=nx, ny=ny, tau=tau, rho0=1.0, bc_x=OPEN, bc_y=WALL, u0=(0.0, 0.0),
+                        wall_ux=(0.0, 0.0), body_force=(0.0, 0.0), inflow_umax=1.5 * umean,
+                        u_scale=1.5 * umean, re=re, rho_w_mode=RHOW_CONST, refill=1,
+                        solids=disks))
+    return out
+
+
 def crop_disks(cfg, nx, ny):
     """Copy of a periodic workload restricted to the disks whose whole extent
     (plus a 2-node gap) lies inside [0, nx) x [0, ny)."""
