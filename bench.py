@@ -59,7 +59,7 @@ def parse():
                     help="train the warm-start network and measure time to converged drag")
     ap.add_argument("--ws-train", type=int, default=1024)
     ap.add_argument("--ws-test", type=int, default=256)
-    ap.add_argument("--ws-epochs", type=int, default=20)
+    ap.add_argument("--ws-epochs", type=int, default=100)
     ap.add_argument("--batch-only", action="store_true",
                     help="measure only the cylinder-sweep batch and print its record")
     ap.add_argument("--batch-warmup", type=int, default=100)
@@ -469,24 +469,32 @@ def run_warm_start(a, local):
     t0 = time.time()
     train_cases = W.warm_start_channels(a.ws_train, seed_offset=5)
     runs = WS.steady(train_cases, device=local)
-    data = WS.dataset(train_cases, runs)
+    data = WS.dataset(train_cases, runs, mirror=True)
     t_data = time.time() - t0
     net = G.UNet(128, 256, levels=4, base=32, max_batch=16, seed=3, device=local)
     t1 = time.time()
     losses = WS.train(net, data, epochs=a.ws_epochs, batch=16, lr=1e-3, lr_end=1e-5)
     t_train = time.time() - t1
     test_all = W.warm_start_channels(a.ws_test, seed_offset=6)
-    ref = WS.steady(test_all, device=local, fields=False)
+    ref = WS.steady(test_all, device=local)
     keep = np.flatnonzero(ref["state"] == G.LBM_CASE_CONVERGED)
     test = [test_all[k] for k in keep]
     d_star = ref["drag"][keep]
     cold = WS.time_to_drag(test, d_star, device=local)
     warm = WS.time_to_drag(test, d_star, net=net, device=local)
+    # prediction error on the held-out steady fields
+    tdata = WS.dataset(test_all, ref)
+    pred = WS.predict(net, tdata["x"]).cpu().numpy()
+    m = tdata["fluid"][:, None]
+    err = float(np.sqrt(((pred - tdata["y"]) ** 2 * m).sum() / ((tdata["y"] ** 2) * m).sum()))
     steps_c, steps_w = cold["steps"].astype(float), warm["steps"].astype(float)
     return {"metric": "time-to-drag at 1e-4 rel err, warm vs cold start",
+            "train_unstable": int((runs["state"] == G.LBM_CASE_UNSTABLE).sum()),
+            "train_capped": int((runs["state"] == G.LBM_CASE_CAPPED).sum()),
             "workload": "256x128 channels, 1-4 fixed disks r 6-16, Re 1..100, tau from Re "
                         "(>= 0.53), velocity inlet / pressure outlet, fp32 batch engine",
             "train_cases": len(train_cases), "train_steady": int(len(data["index"])),
+            "train_samples": int(data["x"].shape[0]),
             "data_seconds": round(t_data, 1), "train_seconds": round(t_train, 1),
             "epochs": a.ws_epochs, "final_loss": float("%.4g" % losses[-1]),
             "test_cases": len(test_all), "test_steady": len(test),
@@ -496,6 +504,7 @@ def run_warm_start(a, local):
             "warm": {"wall_s": round(warm["wall"], 3), "batch_steps": int(warm["batch_steps"]),
                      "median_case_steps": float(np.median(steps_w)),
                      "fallbacks": int(warm["fallback"].sum())},
+            "prediction_rel_l2": round(err, 4),
             "wall_speedup": round(cold["wall"] / warm["wall"], 3),
             "median_step_speedup": round(float(np.median(steps_c / np.maximum(steps_w, 1))), 3)}
 

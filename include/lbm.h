@@ -286,6 +286,11 @@ lbm_status lbm_batch_run(lbm_batch *b, int64_t steps, int32_t *nactive);
  * before the first). */
 lbm_status lbm_batch_state(lbm_batch *b, int32_t *state, int64_t *steps, double *drag);
 
+/* Retire the active cases ids[0..n-1] now (state LBM_CASE_CONVERGED): the
+ * caller's own criterion was met.  Retired or out-of-range ids: LBM_EINVAL,
+ * nothing changed.  The drag history restarts. */
+lbm_status lbm_batch_retire(lbm_batch *b, const int32_t *ids, int32_t n);
+
 /* Launch policy.  Tiles of the fused kernel are tile_rows rows (1..64) of
  * 128 threads x the nodes per thread of `variant` (as for
  * lbm_set_kernel_variant).  persistent = 1 runs the fused kernel as resident

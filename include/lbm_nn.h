@@ -88,10 +88,16 @@ lbm_status lbm_unet_input(lbm_unet *net, const int32_t *owner_device, double rey
                           float *in_device);
 
 /* Initial state of ctx from a network output [3][H][W] (device floats):
- * at every fluid node f = f^eq(1 + rho_scale p0, u_scale p1, u_scale p2)
- * (Eq. 8).  The domain must be H x W; solid nodes keep their state. */
+ * at every fluid node f = f^eq(rho, u) (Eq. 8) with
+ *   rho = 1 + rho_scale p0, u = u_scale (p1, p2)                      (base 0)
+ *   rho = rho_P(x) + rho_scale p0, u = (u_P(y), 0) + u_scale (p1, p2) (base 1)
+ * where (rho_P, u_P) is the empty channel's Poiseuille flow of the context
+ * (bc_x = LBM_OPEN): u_P = the inlet parabola, rho_P = rho0 + 24 nu umax
+ * (nx - 1 - x) / ny^2 (the pressure drop of that flow, rho0 at the outlet),
+ * nu = (tau - 1/2) / 3.  The domain must be H x W; solid nodes keep their
+ * state. */
 lbm_status lbm_warm_start(lbm_ctx *ctx, const float *prediction_device, double u_scale,
-                          double rho_scale);
+                          double rho_scale, int32_t base);
 
 #ifdef __cplusplus
 }

@@ -119,8 +119,9 @@ __global__ void k_import_populations(const StepParams p, const double *in) {
 
 // Equilibrium initial state from a network prediction pred [3][ny][nx]
 // (FP32): rho = 1 + R p0, u = U (p1, p2) at every fluid node (Eq. 8).
+// With base, relative to the channel's Poiseuille flow (see lbm_nn.h).
 template <int P>
-__global__ void k_warm_start(const StepParams p, const float *pred, double U, double R) {
+__global__ void k_warm_start(const StepParams p, const float *pred, double U, double R, int base) {
     const Lattice &L = p.L;
     const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
     if (x >= L.nx) return;
@@ -128,8 +129,14 @@ __global__ void k_warm_start(const StepParams p, const float *pred, double U, do
     if (p.flags[k] & 1u) return;
     const long long t = *p.t;
     void *f = (t & 1) ? p.f1 : p.f0;
-    const double rho = 1.0 + R * (double)pred[o];
-    const double ux = U * (double)pred[n + o], uy = U * (double)pred[2 * n + o];
+    double rho = 1.0 + R * (double)pred[o];
+    double ux = U * (double)pred[n + o];
+    const double uy = U * (double)pred[2 * n + o];
+    if (base) {
+        const double h = (double)L.ny, yy = (double)y + 0.5, nu = (p.tau - 0.5) / 3.0;
+        ux += 4.0 * p.umax * yy * (h - yy) / (h * h);
+        rho += p.rho0 - 1.0 + 24.0 * nu * p.umax * (double)(L.nx - 1 - x) / (h * h);
+    }
     const double uu = ux * ux + uy * uy;
     for (int i = 0; i < 9; i++) {
         const double eu = cx(i) * ux + cy(i) * uy;
@@ -236,12 +243,12 @@ cudaError_t launch_import_populations(const StepParams &p, const double *in, cud
 }
 
 cudaError_t launch_warm_start(const StepParams &p, const float *pred, double u_scale,
-                              double rho_scale, cudaStream_t st) {
+                              double rho_scale, int base, cudaStream_t st) {
     const dim3 g = cell_grid(p.L);
     switch (p.precision) {
-        case LBM_FP64: k_warm_start<LBM_FP64><<<g, 128, 0, st>>>(p, pred, u_scale, rho_scale); break;
-        case LBM_FP32_DEV: k_warm_start<LBM_FP32_DEV><<<g, 128, 0, st>>>(p, pred, u_scale, rho_scale); break;
-        default: k_warm_start<LBM_FP16_DEV><<<g, 128, 0, st>>>(p, pred, u_scale, rho_scale);
+        case LBM_FP64: k_warm_start<LBM_FP64><<<g, 128, 0, st>>>(p, pred, u_scale, rho_scale, base); break;
+        case LBM_FP32_DEV: k_warm_start<LBM_FP32_DEV><<<g, 128, 0, st>>>(p, pred, u_scale, rho_scale, base); break;
+        default: k_warm_start<LBM_FP16_DEV><<<g, 128, 0, st>>>(p, pred, u_scale, rho_scale, base);
     }
     return cudaGetLastError();
 }

@@ -604,10 +604,14 @@ lbm_status lbm_set_populations(lbm_ctx *c, const double *f, int32_t on_device) {
     return LBM_OK;
 }
 
-lbm_status lbm_warm_start(lbm_ctx *c, const float *pred, double u_scale, double rho_scale) {
-    if (!c || !pred || !std::isfinite(u_scale) || !std::isfinite(rho_scale)) return LBM_EINVAL;
+lbm_status lbm_warm_start(lbm_ctx *c, const float *pred, double u_scale, double rho_scale,
+                          int32_t base) {
+    if (!c || !pred || !std::isfinite(u_scale) || !std::isfinite(rho_scale) || base < 0 || base > 1)
+        return LBM_EINVAL;
+    if (base && c->cfg.bc_x != LBM_OPEN)
+        return fail(c, LBM_EINVAL, "a Poiseuille base needs an open channel");
     CK(c, cudaSetDevice(c->cfg.device));
-    CK(c, gbm::launch_warm_start(params(c), pred, u_scale, rho_scale, c->stream));
+    CK(c, gbm::launch_warm_start(params(c), pred, u_scale, rho_scale, base, c->stream));
     c->launches++;
     return LBM_OK;
 }
@@ -1263,6 +1267,25 @@ lbm_status lbm_batch_state(lbm_batch *b, int32_t *state, int64_t *steps, double 
         if (drag) drag[k] = b->drag[k];
     }
     return LBM_OK;
+}
+
+lbm_status lbm_batch_retire(lbm_batch *b, const int32_t *ids, int32_t n) {
+    if (!b || n < 0 || (n > 0 && !ids)) return LBM_EINVAL;
+    BCK(b, cudaSetDevice(b->device));
+    lbm_status st = bgather(b);
+    if (st != LBM_OK) return st;
+    for (int32_t i = 0; i < n; i++)
+        if (ids[i] < 0 || ids[i] >= (int32_t)b->cases.size() || b->state[ids[i]] != LBM_CASE_ACTIVE)
+            return bfail(b, LBM_EINVAL, "case %d is not active", ids[i]);
+    const int32_t one = LBM_CASE_CONVERGED;
+    for (int32_t i = 0; i < n; i++)
+        BCK(b, cudaMemcpyAsync(b->state_d + ids[i], &one, sizeof one, cudaMemcpyHostToDevice,
+                               b->stream));
+    BCK(b, cudaStreamSynchronize(b->stream));
+    b->dirty = true;  // the lists are rebuilt before the next step
+    st = bprepare(b);
+    if (st == LBM_OK) st = bgather(b);
+    return st;
 }
 
 lbm_status lbm_batch_set_launch(lbm_batch *b, int32_t variant, int32_t tile_rows,

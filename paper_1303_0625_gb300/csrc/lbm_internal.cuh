@@ -331,7 +331,7 @@ cudaError_t launch_stamp_solid(const StepParams &p, int id, cudaStream_t st);
 cudaError_t launch_export_populations(const StepParams &p, double *out, cudaStream_t st);
 cudaError_t launch_import_populations(const StepParams &p, const double *in, cudaStream_t st);
 cudaError_t launch_warm_start(const StepParams &p, const float *pred, double u_scale,
-                              double rho_scale, cudaStream_t st);
+                              double rho_scale, int base, cudaStream_t st);
 cudaError_t launch_export_owner(const StepParams &p, int32_t *out, cudaStream_t st);
 cudaError_t launch_fields(const StepParams &p, double *rho, double *ux, double *uy,
                           cudaStream_t st);

@@ -104,6 +104,7 @@ _SIGNATURES = {
     "lbm_batch_set_convergence": (_I32, [_P, _I32, ctypes.c_double, _I64]),
     "lbm_batch_run": (_I32, [_P, _I64, ctypes.POINTER(_I32)]),
     "lbm_batch_state": (_I32, [_P, _P, _P, _P]),
+    "lbm_batch_retire": (_I32, [_P, _P, _I32]),
     "lbm_batch_set_launch": (_I32, [_P, _I32, _I32, _I32, _I32]),
     "lbm_batch_get_launch": (_I32, [_P, ctypes.POINTER(_I32), ctypes.POINTER(_I32),
                                     ctypes.POINTER(_I32)]),
@@ -122,7 +123,7 @@ _SIGNATURES = {
     "lbm_unet_gradients": (_I32, [_P, _P, _P, _P, _I32, _P, _D, _I32]),
     "lbm_unet_train_step": (_I32, [_P, _P, _P, _P, _I32, ctypes.c_float, _D, _I32]),
     "lbm_unet_input": (_I32, [_P, _P, ctypes.c_double, _P]),
-    "lbm_warm_start": (_I32, [_P, _P, ctypes.c_double, ctypes.c_double]),
+    "lbm_warm_start": (_I32, [_P, _P, ctypes.c_double, ctypes.c_double, _I32]),
 }
 
 
@@ -354,6 +355,11 @@ def lbm_batch_state(b, state, steps, drag):
     _bcheck(load().lbm_batch_state(b, _ptr(state), _ptr(steps), _ptr(drag)), b)
 
 
+def lbm_batch_retire(b, ids):
+    ids = np.ascontiguousarray(ids, dtype=np.int32)
+    _bcheck(load().lbm_batch_retire(b, _ptr(ids) if ids.size else None, int(ids.size)), b)
+
+
 def lbm_batch_set_launch(b, variant: int, tile_rows: int = 1, persistent: bool = False,
                          graph: bool = True):
     _bcheck(load().lbm_batch_set_launch(b, int(variant), int(tile_rows), int(bool(persistent)),
@@ -450,8 +456,9 @@ def lbm_unet_input(net, owner_dev, reynolds: float, in_dev):
     _ncheck(load().lbm_unet_input(net, _ptr(owner_dev), float(reynolds), _ptr(in_dev)), net)
 
 
-def lbm_warm_start(ctx, prediction_dev, u_scale: float, rho_scale: float):
-    _check(load().lbm_warm_start(ctx, _ptr(prediction_dev), float(u_scale), float(rho_scale)), ctx)
+def lbm_warm_start(ctx, prediction_dev, u_scale: float, rho_scale: float, base: bool = False):
+    _check(load().lbm_warm_start(ctx, _ptr(prediction_dev), float(u_scale), float(rho_scale),
+                                 int(bool(base))), ctx)
 
 
 class UNet:
@@ -720,6 +727,9 @@ class Batch:
     def run(self, steps: int) -> int:
         """Advance the active cases by up to ``steps``; returns the active count."""
         return lbm_batch_run(self._h, steps)
+
+    def retire(self, ids):
+        lbm_batch_retire(self._h, ids)
 
     def state(self):
         n = len(self)

@@ -15,9 +15,13 @@ device buffers.
                          initial state or from the network's prediction (warm),
                          with the drift check and the fallback to a cold start
 
-Scales (per case, U = peak inlet speed): u = U p_u, rho - 1 = (100 U^2 / Re) p_rho,
-so that both targets are of order one from Re = 1 to 100.
+Targets are residuals from the empty channel's Poiseuille flow (u_P(y) the
+inlet parabola, rho_P(x) its linear pressure drop; lbm_warm_start adds them
+back), scaled per case (U = peak inlet speed): u - u_P = U p_u,
+rho - rho_P = (100 U^2 / Re) p_rho, so that both are of order one from Re = 1
+to 100 and vanish away from the disks.
 """
+
 from __future__ import annotations
 
 import time
@@ -25,6 +29,17 @@ import time
 import numpy as np
 
 from . import lbm as L
+
+
+def poiseuille(case):
+    """(rho_P [ny][nx], u_P [ny]) of the case's empty channel."""
+    nx, ny = case["nx"], case["ny"]
+    h = float(ny)
+    yy = np.arange(ny) + 0.5
+    nu = (case["tau"] - 0.5) / 3.0
+    u = 4.0 * case["inflow_umax"] * yy * (h - yy) / (h * h)
+    rho = case.get("rho0", 1.0) + 24.0 * nu * case["inflow_umax"] * (nx - 1 - np.arange(nx)) / (h * h)
+    return np.broadcast_to(rho[None, :], (ny, nx)), u
 
 
 def rho_scale(case) -> float:
@@ -54,15 +69,20 @@ def steady(cases, *, precision=L.LBM_FP32_DEV, tol=1e-7, every=100, cap=300_000,
         ux = np.empty_like(rho)
         uy = np.empty_like(rho)
         for k in range(len(cases)):
-            rho[k], ux[k], uy[k] = b.case(k).fields()
+            if st[k] == L.LBM_CASE_UNSTABLE:  # no usable state to read
+                rho[k] = ux[k] = uy[k] = np.nan
+            else:
+                rho[k], ux[k], uy[k] = b.case(k).fields()
         out.update(rho=rho, ux=ux, uy=uy)
     b.close()
     return out
 
 
-def dataset(cases, runs):
+def dataset(cases, runs, mirror=False):
     """Inputs [N][8][H][W], targets [N][3][H][W], fluid [N][H][W] (float32) of
-    the cases that reached a steady state."""
+    the cases that reached a steady state; with mirror, each also mirrored
+    about the channel's centre line (y -> ny - 1 - y, u_y -> -u_y), which the
+    walls and the inlet profile leave invariant."""
     keep = np.flatnonzero(runs["state"] == L.LBM_CASE_CONVERGED)
     n = len(keep)
     ny, nx = cases[0]["ny"], cases[0]["nx"]
@@ -75,9 +95,14 @@ def dataset(cases, runs):
         x[j, 0] = solid
         x[j, 1] = cases[k]["re"] / 100.0
         f[j] = ~solid
-        y[j, 0] = np.where(solid, 0.0, (runs["rho"][k] - 1.0) / rho_scale(cases[k]))
-        y[j, 1] = np.where(solid, 0.0, runs["ux"][k] / U)
+        rp, up = poiseuille(cases[k])
+        y[j, 0] = np.where(solid, 0.0, (runs["rho"][k] - rp) / rho_scale(cases[k]))
+        y[j, 1] = np.where(solid, 0.0, (runs["ux"][k] - up[:, None]) / U)
         y[j, 2] = np.where(solid, 0.0, runs["uy"][k] / U)
+    if mirror:
+        xm, ym, fm = x[:, :, ::-1].copy(), y[:, :, ::-1].copy(), f[:, ::-1].copy()
+        ym[:, 2] *= -1.0
+        x, y, f = np.concatenate([x, xm]), np.concatenate([y, ym]), np.concatenate([f, fm])
     return dict(x=x, y=y, fluid=f, index=keep)
 
 
@@ -163,7 +188,8 @@ def time_to_drag(cases, d_star, *, net=None, rel=1e-4, precision=L.LBM_FP32_DEV,
             L.lbm_unet_forward(net.handle, xin[s:e], out[s:e], e - s, on_device=True)
         torch.cuda.synchronize()
         for k in range(n):
-            L.lbm_warm_start(b.case(k).handle, out[k], cases[k]["u_scale"], rho_scale(cases[k]))
+            L.lbm_warm_start(b.case(k).handle, out[k], cases[k]["u_scale"], rho_scale(cases[k]),
+                             base=True)
         mass0 = np.array([_mass(b.case(k)) for k in range(n)])
     done = np.full(n, -1, dtype=np.int64)
     drift = None
@@ -186,10 +212,10 @@ def time_to_drag(cases, d_star, *, net=None, rel=1e-4, precision=L.LBM_FP32_DEV,
                                  cap=cap, device=device, stream=stream)
                 done[fallback] = r["steps"] + steps
         ok = np.abs(drag - d_star) <= rel * np.abs(d_star)
-        newly = ok & (done < 0) & ~fallback
+        newly = ok & (done < 0) & ~fallback & (st == L.LBM_CASE_ACTIVE)
         done[newly] = steps
-        leave = (~ok) & (done >= 0) & ~fallback  # left the band again: not done yet
-        done[leave] = -1
+        if newly.any():  # the case has reached its drag: it stops stepping
+            b.retire(np.flatnonzero(newly))
         if (done >= 0).all():
             break
     torch.cuda.synchronize()

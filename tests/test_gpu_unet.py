@@ -82,8 +82,12 @@ def test_params_round_trip_in_oracle_layout():
     assert net.nparam == v.size and np.array_equal(net.params(), v)
 
 
-@pytest.mark.parametrize("levels,base,H,W,B", [(2, 8, 16, 32, 2), (3, 16, 32, 64, 2)])
-def test_forward_and_gradients_small(levels, base, H, W, B):
+@pytest.mark.parametrize("levels,base,H,W,B,gtol", [(2, 8, 16, 32, 2, 2e-2), (3, 16, 32, 64, 2, 2e-2),
+                                                     (4, 32, 32, 64, 2, 3e-2)])
+def test_forward_and_gradients_small(levels, base, H, W, B, gtol):
+    """Gradients of the deepest layers pass through the most BF16 roundings
+    (each <= 2^-9 relative): the 4-level chain has 14 of them between the
+    loss and enc3a, a worst-case accumulation of 2.8%, hence 3e-2 there."""
     net, p, x, t, fl = _case(levels, base, H, W, B, levels)
     y_ref, cache = U.forward(p, x, levels, keep=True)
     y = net.forward(x)
@@ -94,7 +98,7 @@ def test_forward_and_gradients_small(levels, base, H, W, B):
     assert abs(loss - loss_ref) <= 2e-2 * loss_ref
     gv = _unflat(g, levels, base)
     for k in g_ref:
-        assert _rel(gv[k], g_ref[k]) <= 2e-2, (k, _rel(gv[k], g_ref[k]))
+        assert _rel(gv[k], g_ref[k]) <= gtol, (k, _rel(gv[k], g_ref[k]))
 
 
 def test_full_network_forward_128x256():
@@ -129,3 +133,11 @@ def test_warm_start_sets_the_predicted_equilibrium():
     assert np.allclose(rho[fl], 1.0 + R * pred[0][fl], atol=2e-6)
     assert np.allclose(ux[fl], U_ * pred[1][fl], atol=2e-6)
     assert np.allclose(uy[fl], U_ * pred[2][fl], atol=2e-6)
+    # relative to the channel's Poiseuille flow
+    from paper_1303_0625_gb300 import warmstart as WS
+    case = dict(nx=W, ny=H, tau=0.7, inflow_umax=0.05, rho0=1.0)
+    rp, up = WS.poiseuille(case)
+    L.lbm_warm_start(lat.handle, dev, U_, R, base=True)
+    rho, ux, uy = lat.fields()
+    assert np.allclose(rho[fl], (rp + R * pred[0])[fl], atol=2e-6)
+    assert np.allclose(ux[fl], (up[:, None] + U_ * pred[1])[fl], atol=2e-6)
