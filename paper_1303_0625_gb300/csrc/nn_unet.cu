@@ -1,7 +1,10 @@
 // The warm-start U-Net on the GPU: forward, backward and Adam, with every
 // 3x3 convolution an implicit GEMM on the tensor cores (BF16 operands, FP32
-// accumulation) and the remaining layers (pooling, upsampling with
-// concatenation, the 1x1 head, the loss) as small kernels of their own.
+// accumulation): the forward and data-gradient convolutions with tcgen05
+// (accumulator in tensor memory), the weight gradient (whose operands are
+// transposed gathers) with mma.sync.  The remaining layers (pooling,
+// upsampling with concatenation, the 1x1 head, the loss, Adam) are small
+// kernels of their own.
 //
 // Layout: activations NHWC in BF16 (channels innermost, every channel count
 // a multiple of 8, so that 8 channels are one 16-byte load); conv weights
@@ -137,30 +140,65 @@ struct ConvOp {
     int Cs, taps, sign, relu;
     int M, N, K, kchunk;
 
+    // 8 consecutive K elements of row p of A (source channels of one tap)
+    __device__ __forceinline__ uint4 gather_a(int p, int k, int ke) const {
+        uint4 v = make_uint4(0, 0, 0, 0);
+        if (p < M && k < ke) {
+            const int tap = k / Cs, c = k - tap * Cs;
+            int qp = p;
+            bool ok = true;
+            if (taps == 9) ok = img.shift(p, sign * (tap / 3 - 1), sign * (tap % 3 - 1), qp);
+            if (ok) v = *reinterpret_cast<const uint4 *>(src + (size_t)qp * Cs + c);
+        }
+        return v;
+    }
+    // 8 consecutive K elements of row n of B (the weights of one output)
+    __device__ __forceinline__ uint4 gather_b(int n, int k, int ke) const {
+        uint4 v = make_uint4(0, 0, 0, 0);
+        if (n < N && k < ke) v = *reinterpret_cast<const uint4 *>(w + (size_t)n * K + k);
+        return v;
+    }
     __device__ __forceinline__ void load_a(bf16 (&a)[BM][LDS], int m0, int k0, int ke, int tid) const {
 #pragma unroll
         for (int i = 0; i < 2; i++) {
             const int q = tid + i * GEMM_THREADS, r = q >> 2, cc = q & 3;
-            const int p = m0 + r, k = k0 + cc * 8;
-            uint4 v = make_uint4(0, 0, 0, 0);
-            if (p < M && k < ke) {
-                const int tap = k / Cs, c = k - tap * Cs;
-                int qp = p;
-                bool ok = true;
-                if (taps == 9) ok = img.shift(p, sign * (tap / 3 - 1), sign * (tap % 3 - 1), qp);
-                if (ok) v = *reinterpret_cast<const uint4 *>(src + (size_t)qp * Cs + c);
-            }
-            *reinterpret_cast<uint4 *>(&a[r][cc * 8]) = v;
+            *reinterpret_cast<uint4 *>(&a[r][cc * 8]) = gather_a(m0 + r, k0 + cc * 8, ke);
         }
     }
     __device__ __forceinline__ void load_b(bf16 (&b)[BN][LDS], int n0, int k0, int ke, int tid) const {
 #pragma unroll
         for (int i = 0; i < 2; i++) {
             const int q = tid + i * GEMM_THREADS, r = q >> 2, cc = q & 3;
-            const int n = n0 + r, k = k0 + cc * 8;
-            uint4 v = make_uint4(0, 0, 0, 0);
-            if (n < N && k < ke) v = *reinterpret_cast<const uint4 *>(w + (size_t)n * K + k);
-            *reinterpret_cast<uint4 *>(&b[r][cc * 8]) = v;
+            *reinterpret_cast<uint4 *>(&b[r][cc * 8]) = gather_b(n0 + r, k0 + cc * 8, ke);
+        }
+    }
+    // epilogue of 16 consecutive outputs (n multiple of 8, N a multiple of 8)
+    __device__ __forceinline__ void store16(int m, int n, const float *v) const {
+        if (m >= M) return;
+#pragma unroll
+        for (int h = 0; h < 2; h++) {
+            const int nh = n + 8 * h;
+            if (nh >= N) return;
+            float o[8];
+#pragma unroll
+            for (int j = 0; j < 8; j++) {
+                o[j] = v[8 * h + j];
+                if (bias) o[j] += bias[nh + j];
+                if (relu) o[j] = fmaxf(o[j], 0.f);
+            }
+            const size_t off = (size_t)m * N + nh;
+            if (mask) {
+                const uint4 mk = *reinterpret_cast<const uint4 *>(mask + off);
+                const bf16 *me = reinterpret_cast<const bf16 *>(&mk);
+#pragma unroll
+                for (int j = 0; j < 8; j++)
+                    if (!(__bfloat162float(me[j]) > 0.f)) o[j] = 0.f;
+            }
+            uint4 pk;
+            __nv_bfloat162 *pp = reinterpret_cast<__nv_bfloat162 *>(&pk);
+#pragma unroll
+            for (int j = 0; j < 4; j++) pp[j] = __floats2bfloat162_rn(o[2 * j], o[2 * j + 1]);
+            *reinterpret_cast<uint4 *>(out + off) = pk;
         }
     }
     __device__ __forceinline__ void store(int m, int n, float v0, float v1) const {
@@ -230,6 +268,150 @@ struct WgradOp {
         atomicAdd(dw + (size_t)m * N + n + 1, v1);
     }
 };
+
+// ------------------------------------------------ tcgen05 convolution
+//
+// The forward and data-gradient convolutions (ConvOp) on the 5th-generation
+// tensor cores: a CTA of 128 threads owns a 128 x BN output tile whose FP32
+// accumulator lives in tensor memory (BN columns allocated per CTA).  Per
+// K block of 64, all threads gather the A (128 pixels x 64) and B (BN
+// outputs x 64) operands into shared memory in the K-major no-swizzle
+// layout of 8 x 16-byte core matrices (core matrix (row group g, K group j)
+// at g * 1024 + j * 128 bytes), then one thread issues four
+// tcgen05.mma.kind::f16 (M = 128, N = BN, K = 16; BF16 in, FP32 accumulate)
+// and commits them to the stage's mbarrier.  Two stages: the gathers of
+// block k+1 overlap the MMAs of block k.  Every mbarrier wait is bounded;
+// a wait that runs out sets *err and the tile's results are not stored.
+constexpr int TC_M = 128, TC_K = 64, TC_THREADS = 128;
+constexpr int TC_SPIN = 1 << 24;
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// shared-memory matrix descriptor: K-major, no swizzle, 128 B between K
+// groups (leading), 1024 B between 8-row groups (stride)
+__device__ __forceinline__ uint64_t tc_desc(uint32_t addr) {
+    uint64_t d = (uint64_t)((addr >> 4) & 0x3FFF);
+    d |= (uint64_t)(128 >> 4) << 16;
+    d |= (uint64_t)(1024 >> 4) << 32;
+    d |= (uint64_t)1 << 46;
+    return d;
+}
+
+__device__ __forceinline__ bool tc_wait(uint32_t mbar, uint32_t parity) {
+    uint32_t done = 0;
+    for (int it = 0; it < TC_SPIN && !done; it++)
+        asm volatile(
+            "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+            "selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(mbar), "r"(parity)
+            : "memory");
+    return done != 0;
+}
+
+template <int BN>
+__global__ void __launch_bounds__(TC_THREADS) k_conv_tc(const ConvOp op, int *err) {
+    extern __shared__ __align__(1024) unsigned char smem[];
+    __shared__ uint32_t tmem_base;
+    __shared__ __align__(8) uint64_t mbar[2];
+    constexpr int SA = TC_M * TC_K * 2, SB = BN * TC_K * 2, STAGE = SA + SB;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int m0 = blockIdx.x * TC_M, n0 = blockIdx.y * BN;
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(
+                         smem_u32(&tmem_base)),
+                     "r"(BN));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
+    }
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&mbar[0])));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&mbar[1])));
+        asm volatile("fence.mbarrier_init.release.cluster;\n");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;\n");
+    const uint32_t tmem = tmem_base;
+    // kind::f16: D FP32, A and B BF16, both K-major, N = BN, M = 128
+    const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
+                           ((uint32_t)(TC_M >> 4) << 24);
+    const int nk = (op.K + TC_K - 1) / TC_K;
+    uint32_t issued[2] = {0, 0}, waited[2] = {0, 0};
+    bool ok = true;
+    for (int kt = 0; kt < nk; kt++) {
+        const int s = kt & 1;
+        if (issued[s] > waited[s]) {  // the MMAs that read this stage last time
+            ok &= tc_wait(smem_u32(&mbar[s]), waited[s] & 1);
+            waited[s]++;
+        }
+        unsigned char *sa = smem + s * STAGE, *sb = sa + SA;
+        const int k0 = kt * TC_K;
+#pragma unroll
+        for (int i = 0; i < (TC_M * 8) / TC_THREADS; i++) {
+            const int q = tid + i * TC_THREADS, r = q >> 3, kg = q & 7;
+            *reinterpret_cast<uint4 *>(sa + (r >> 3) * 1024 + kg * 128 + (r & 7) * 16) =
+                op.gather_a(m0 + r, k0 + kg * 8, op.K);
+        }
+#pragma unroll
+        for (int i = 0; i < (BN * 8) / TC_THREADS; i++) {
+            const int q = tid + i * TC_THREADS, r = q >> 3, kg = q & 7;
+            *reinterpret_cast<uint4 *>(sb + (r >> 3) * 1024 + kg * 128 + (r & 7) * 16) =
+                op.gather_b(n0 + r, k0 + kg * 8, op.K);
+        }
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+        __syncthreads();
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;\n");
+#pragma unroll
+            for (int ks = 0; ks < TC_K / 16; ks++) {
+                const uint64_t ad = tc_desc(smem_u32(sa) + ks * 256);
+                const uint64_t bd = tc_desc(smem_u32(sb) + ks * 256);
+                const uint32_t acc = (kt > 0 || ks > 0) ? 1u : 0u;
+                asm volatile(
+                    "{\n.reg .pred p;\nsetp.ne.u32 p, %4, 0;\n"
+                    "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+                    "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+            }
+            asm volatile(
+                "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                    smem_u32(&mbar[s])));
+        }
+        issued[s]++;
+    }
+    for (int s = 0; s < 2; s++)
+        while (issued[s] > waited[s]) {
+            ok &= tc_wait(smem_u32(&mbar[s]), waited[s] & 1);
+            waited[s]++;
+        }
+    asm volatile("tcgen05.fence::after_thread_sync;\n");
+    if (!ok) atomicOr(err, 1);
+    const int row = m0 + warp * 32 + lane;
+#pragma unroll
+    for (int c0 = 0; c0 < BN; c0 += 16) {
+        uint32_t v[16];
+        const uint32_t addr = tmem + ((uint32_t)(warp * 32) << 16) + c0;
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
+            "%14,%15}, [%16];\n"
+            : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+              "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
+              "=r"(v[14]), "=r"(v[15])
+            : "r"(addr));
+        asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+        if (ok && n0 + c0 < op.N) {
+            float f[16];
+#pragma unroll
+            for (int j = 0; j < 16; j++) f[j] = __uint_as_float(v[j]);
+            op.store16(row, n0 + c0, f);
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(BN));
+}
 
 // ------------------------------------------------------ other layers
 
@@ -511,6 +693,7 @@ struct lbm_unet {
     float *grad_abi = nullptr;
     float *cnt = nullptr;
     double *loss = nullptr;
+    int *err_d = nullptr;    // bit 0: a bounded wait of a tensor-core kernel ran out
     long long adam_t = 0;
     std::string err;
     std::vector<void *> allocs;
@@ -540,6 +723,18 @@ lbm_status nfail(lbm_unet *n, lbm_status st, const char *fmt, ...) {
                          "%s failed: %s", #call, cudaGetErrorString(e_));                  \
     } while (0)
 
+// after a synchronisation: a tensor-core kernel that gave up waiting
+lbm_status check_err(lbm_unet *n) {
+    int e = 0;
+    NCK(n, cudaMemcpyAsync(&e, n->err_d, sizeof(int), cudaMemcpyDeviceToHost, n->stream));
+    NCK(n, cudaStreamSynchronize(n->stream));
+    if (e) {
+        cudaMemsetAsync(n->err_d, 0, sizeof(int), n->stream);
+        return nfail(n, LBM_ETIMEOUT, "a bounded wait of the tensor-core convolution ran out");
+    }
+    return LBM_OK;
+}
+
 template <class T>
 cudaError_t nalloc(lbm_unet *n, T **p, size_t count) {
     cudaError_t e = cudaMalloc(reinterpret_cast<void **>(p), count * sizeof(T) + 16);
@@ -562,6 +757,25 @@ int conv_index(const lbm_unet *n, const char kind, int l, int ab) {
     return 2 * L + 2 * (L - 1);
 }
 
+template <int BN>
+cudaError_t launch_tc(lbm_unet *n, const nn::ConvOp &op) {
+    constexpr int smem = 2 * (nn::TC_M * nn::TC_K * 2 + BN * nn::TC_K * 2);
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(nn::k_conv_tc<BN>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    const dim3 grid((op.M + nn::TC_M - 1) / nn::TC_M, (op.N + BN - 1) / BN);
+    nn::k_conv_tc<BN><<<grid, nn::TC_THREADS, smem, n->stream>>>(op, n->err_d);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_conv_tc(lbm_unet *n, const nn::ConvOp &op) {
+    return op.N <= 64 ? launch_tc<64>(n, op) : launch_tc<128>(n, op);
+}
+
 cudaError_t conv_fwd(lbm_unet *n, const Conv &cv, const bf16 *src, bf16 *dst, int B, int H, int W,
                      bool relu) {
     nn::ConvOp op{};
@@ -579,9 +793,7 @@ cudaError_t conv_fwd(lbm_unet *n, const Conv &cv, const bf16 *src, bf16 *dst, in
     op.N = cv.co;
     op.K = op.taps * cv.ci;
     op.kchunk = op.K;
-    const dim3 grid((op.M + nn::BM - 1) / nn::BM, (op.N + nn::BN - 1) / nn::BN);
-    nn::k_gemm<nn::ConvOp><<<grid, nn::GEMM_THREADS, 0, n->stream>>>(op);
-    return cudaGetLastError();
+    return launch_conv_tc(n, op);
 }
 
 // gradient with respect to the conv's input (masked by mask > 0 when given)
@@ -602,9 +814,7 @@ cudaError_t conv_dgrad(lbm_unet *n, const Conv &cv, const bf16 *dz, const bf16 *
     op.N = cv.ci;
     op.K = op.taps * cv.co;
     op.kchunk = op.K;
-    const dim3 grid((op.M + nn::BM - 1) / nn::BM, (op.N + nn::BN - 1) / nn::BN);
-    nn::k_gemm<nn::ConvOp><<<grid, nn::GEMM_THREADS, 0, n->stream>>>(op);
-    return cudaGetLastError();
+    return launch_conv_tc(n, op);
 }
 
 cudaError_t conv_wgrad(lbm_unet *n, const Conv &cv, const bf16 *dz, const bf16 *x, int B, int H,
@@ -878,6 +1088,8 @@ lbm_status lbm_unet_create(const lbm_unet_config *cfg, lbm_unet **out) {
     if (e == cudaSuccess) e = nalloc(n, &n->io_fl, B * HW);
     if (e == cudaSuccess) e = nalloc(n, &n->cnt, 1);
     if (e == cudaSuccess) e = nalloc(n, &n->loss, 1);
+    if (e == cudaSuccess) e = nalloc(n, &n->err_d, 1);
+    if (e == cudaSuccess) e = cudaMemsetAsync(n->err_d, 0, sizeof(int), n->stream);
     n->lv.resize(L);
     for (int l = 0; l < L && e == cudaSuccess; l++) {
         Level &v = n->lv[l];
@@ -991,7 +1203,7 @@ lbm_status lbm_unet_forward(lbm_unet *n, const float *in, float *out, int32_t B,
     const size_t bytes = (size_t)B * 3 * n->cfg.height * n->cfg.width * sizeof(float);
     NCK(n, cudaMemcpyAsync(out, n->out, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
                            n->stream));
-    if (!on_device) NCK(n, cudaStreamSynchronize(n->stream));
+    if (!on_device) return check_err(n);
     return LBM_OK;
 }
 
@@ -1009,6 +1221,8 @@ lbm_status lbm_unet_gradients(lbm_unet *n, const float *in, const float *tgt, co
     NCK(n, cudaMemcpyAsync(g.data(), n->g, g.size() * sizeof(float), cudaMemcpyDeviceToHost, n->stream));
     NCK(n, cudaMemcpyAsync(&l, n->loss, sizeof(double), cudaMemcpyDeviceToHost, n->stream));
     NCK(n, cudaStreamSynchronize(n->stream));
+    st = check_err(n);
+    if (st != LBM_OK) return st;
     internal_to_abi(n, g.data(), h.data());
     if (on_device) {
         NCK(n, cudaMemcpyAsync(grads, h.data(), h.size() * sizeof(float), cudaMemcpyHostToDevice, n->stream));
@@ -1043,7 +1257,7 @@ lbm_status lbm_unet_train_step(lbm_unet *n, const float *in, const float *tgt, c
     }
     if (loss) {
         NCK(n, cudaMemcpyAsync(loss, n->loss, sizeof(double), cudaMemcpyDeviceToHost, n->stream));
-        NCK(n, cudaStreamSynchronize(n->stream));
+        return check_err(n);
     }
     return LBM_OK;
 }
