@@ -60,6 +60,8 @@ def parse():
     ap.add_argument("--ws-train", type=int, default=1024)
     ap.add_argument("--ws-test", type=int, default=256)
     ap.add_argument("--ws-epochs", type=int, default=100)
+    ap.add_argument("--unet", action="store_true",
+                    help="time the warm-start network's forward pass and training step")
     ap.add_argument("--batch-only", action="store_true",
                     help="measure only the cylinder-sweep batch and print its record")
     ap.add_argument("--batch-warmup", type=int, default=100)
@@ -450,6 +452,61 @@ def run_precision_study(a, w, local, stream):
     return out
 
 
+def run_unet(a, local, H=128, W=256, B=16, levels=4, base=32):
+    """Forward pass and training step of the warm-start U-Net (BF16 tensor
+    cores, FP32 accumulation) on a batch of B synthetic 128 x 256 inputs:
+    time per call (CUDA events) and algorithmic TFLOP/s of the convolutions
+    (forward 2 H W Cout Cin k^2 per sample and layer; a training step counts
+    three times the forward)."""
+    import numpy as np
+    import torch
+
+    import paper_1303_0625_gb300 as G
+    from paper_1303_0625_gb300 import lbm as L
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    flops = 0.0
+    cin = 8
+    ch = [base << l for l in range(levels)]
+    for l, c in enumerate(ch):
+        hw = (H >> l) * (W >> l)
+        flops += 2 * hw * 9 * (cin * c + c * c)
+        cin = c
+    for l in range(levels - 2, -1, -1):
+        hw = (H >> l) * (W >> l)
+        flops += 2 * hw * 9 * ((ch[l + 1] + ch[l]) * ch[l] + ch[l] * ch[l])
+    flops += 2 * H * W * ch[0] * 3
+    rng = np.random.default_rng(0)
+    x = torch.zeros((B, 8, H, W), device=dev)
+    x[:, 0] = torch.from_numpy((rng.random((B, H, W)) < 0.1).astype(np.float32)).to(dev)
+    x[:, 1] = 0.5
+    y = torch.from_numpy(rng.normal(0, 0.3, (B, 3, H, W)).astype(np.float32)).to(dev)
+    fl = 1.0 - x[:, 0].contiguous()
+    out = torch.empty((B, 3, H, W), device=dev)
+    net = G.UNet(H, W, levels=levels, base=base, max_batch=B, seed=0, device=local)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    res = {}
+    for name, fn, mult in (("forward", lambda: L.lbm_unet_forward(net.handle, x, out, B, True), 1),
+                           ("train_step", lambda: L.lbm_unet_train_step(net.handle, x, y, fl, B, 1e-4,
+                                                                        True), 3)):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        e0.record()
+        n = 10
+        for _ in range(n):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / n
+        res[name] = {"ms": round(ms, 3), "tflops": round(mult * flops * B / (ms / 1e3) / 1e12, 1)}
+    net.close()
+    return {"metric": "U-Net forward / training step throughput", "batch": B, "H": H, "W": W,
+            "levels": levels, "base": base, "gflop_per_sample_forward": round(flops / 1e9, 2),
+            **res}
+
+
 def run_warm_start(a, local):
     """Learned warm start on 256 x 128 channels with 1-4 fixed disks and Re
     in 1..100: train the U-Net on steady fields the batch engine computes for
@@ -611,6 +668,9 @@ def main():
     ws, rank, local = dist_setup()
     if a.impl == "reference":
         run_reference(a, ws, rank)
+    elif a.unet:
+        if rank == 0:
+            print(json.dumps(run_unet(a, local)), flush=True)
     elif a.warm_start:
         if rank == 0:
             print(json.dumps(run_warm_start(a, local)), flush=True)
