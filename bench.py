@@ -484,7 +484,9 @@ def run_unet(a, local, H=128, W=256, B=16, levels=4, base=32):
     y = torch.from_numpy(rng.normal(0, 0.3, (B, 3, H, W)).astype(np.float32)).to(dev)
     fl = 1.0 - x[:, 0].contiguous()
     out = torch.empty((B, 3, H, W), device=dev)
-    net = G.UNet(H, W, levels=levels, base=base, max_batch=B, seed=0, device=local)
+    stream = torch.cuda.Stream(device=dev)
+    net = G.UNet(H, W, levels=levels, base=base, max_batch=B, seed=0, device=local,
+                 stream=stream.cuda_stream)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     res = {}
     for name, fn, mult in (("forward", lambda: L.lbm_unet_forward(net.handle, x, out, B, True), 1),
@@ -493,11 +495,11 @@ def run_unet(a, local, H=128, W=256, B=16, levels=4, base=32):
         for _ in range(3):
             fn()
         torch.cuda.synchronize()
-        e0.record()
+        e0.record(stream)
         n = 10
         for _ in range(n):
             fn()
-        e1.record()
+        e1.record(stream)
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1) / n
         res[name] = {"ms": round(ms, 3), "tflops": round(mult * flops * B / (ms / 1e3) / 1e12, 1)}

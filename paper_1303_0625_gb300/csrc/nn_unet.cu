@@ -152,6 +152,17 @@ struct ConvOp {
         }
         return v;
     }
+    // address of the 8 K elements of row p of A, or null where they are zero
+    __device__ __forceinline__ const bf16 *addr_a(int p, int k, int ke) const {
+        if (p >= M || k >= ke) return nullptr;
+        const int tap = k / Cs, c = k - tap * Cs;
+        int qp = p;
+        if (taps == 9 && !img.shift(p, sign * (tap / 3 - 1), sign * (tap % 3 - 1), qp)) return nullptr;
+        return src + (size_t)qp * Cs + c;
+    }
+    __device__ __forceinline__ const bf16 *addr_b(int n, int k, int ke) const {
+        return (n < N && k < ke) ? w + (size_t)n * K + k : nullptr;
+    }
     // 8 consecutive K elements of row n of B (the weights of one output)
     __device__ __forceinline__ uint4 gather_b(int n, int k, int ke) const {
         uint4 v = make_uint4(0, 0, 0, 0);
@@ -273,16 +284,17 @@ struct WgradOp {
 //
 // The forward and data-gradient convolutions (ConvOp) on the 5th-generation
 // tensor cores: a CTA of 128 threads owns a 128 x BN output tile whose FP32
-// accumulator lives in tensor memory (BN columns allocated per CTA).  Per
-// K block of 64, all threads gather the A (128 pixels x 64) and B (BN
-// outputs x 64) operands into shared memory in the K-major no-swizzle
-// layout of 8 x 16-byte core matrices (core matrix (row group g, K group j)
-// at g * 1024 + j * 128 bytes), then one thread issues four
+// accumulator lives in tensor memory (BN columns allocated per CTA).  Each K
+// block of 64 is gathered into shared memory with cp.async (16 bytes per
+// copy, zero-filled outside the image) in the K-major no-swizzle layout of
+// 8 x 16-byte core matrices (core matrix (row group g, K group j) at
+// g * 1024 + j * 128 bytes); one thread then issues four
 // tcgen05.mma.kind::f16 (M = 128, N = BN, K = 16; BF16 in, FP32 accumulate)
-// and commits them to the stage's mbarrier.  Two stages: the gathers of
-// block k+1 overlap the MMAs of block k.  Every mbarrier wait is bounded;
-// a wait that runs out sets *err and the tile's results are not stored.
-constexpr int TC_M = 128, TC_K = 64, TC_THREADS = 128;
+// and commits them to the stage's mbarrier.  TC_STAGES stages: the copies of
+// the next blocks are in flight while the tensor cores work.  Every mbarrier
+// wait is bounded; a wait that runs out sets *err and the tile's results are
+// not stored.
+constexpr int TC_M = 128, TC_K = 64, TC_THREADS = 128, TC_STAGES = 3;
 constexpr int TC_SPIN = 1 << 24;
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
@@ -311,14 +323,38 @@ __device__ __forceinline__ bool tc_wait(uint32_t mbar, uint32_t parity) {
     return done != 0;
 }
 
+// 16-byte global -> shared copy; a null source fills zeros
+__device__ __forceinline__ void cp16(uint32_t dst, const void *src, const void *dummy) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(dst),
+                 "l"(src ? src : dummy), "r"(src ? 16 : 0)
+                 : "memory");
+}
+
+template <int BN>
+__device__ __forceinline__ void tc_stage(const ConvOp &op, uint32_t sa, int m0, int n0, int k0,
+                                         int tid) {
+    const uint32_t sb = sa + TC_M * TC_K * 2;
+#pragma unroll
+    for (int i = 0; i < (TC_M * 8) / TC_THREADS; i++) {
+        const int q = tid + i * TC_THREADS, r = q >> 3, kg = q & 7;
+        cp16(sa + (r >> 3) * 1024 + kg * 128 + (r & 7) * 16, op.addr_a(m0 + r, k0 + kg * 8, op.K), op.src);
+    }
+#pragma unroll
+    for (int i = 0; i < (BN * 8) / TC_THREADS; i++) {
+        const int q = tid + i * TC_THREADS, r = q >> 3, kg = q & 7;
+        cp16(sb + (r >> 3) * 1024 + kg * 128 + (r & 7) * 16, op.addr_b(n0 + r, k0 + kg * 8, op.K), op.w);
+    }
+}
+
 template <int BN>
 __global__ void __launch_bounds__(TC_THREADS) k_conv_tc(const ConvOp op, int *err) {
     extern __shared__ __align__(1024) unsigned char smem[];
     __shared__ uint32_t tmem_base;
-    __shared__ __align__(8) uint64_t mbar[2];
-    constexpr int SA = TC_M * TC_K * 2, SB = BN * TC_K * 2, STAGE = SA + SB;
+    __shared__ __align__(8) uint64_t mbar[TC_STAGES];
+    constexpr int STAGE = TC_M * TC_K * 2 + BN * TC_K * 2;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int m0 = blockIdx.x * TC_M, n0 = blockIdx.y * BN;
+    const uint32_t base = smem_u32(smem);
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(
                          smem_u32(&tmem_base)),
@@ -326,8 +362,8 @@ __global__ void __launch_bounds__(TC_THREADS) k_conv_tc(const ConvOp op, int *er
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
     }
     if (tid == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&mbar[0])));
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&mbar[1])));
+        for (int s = 0; s < TC_STAGES; s++)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&mbar[s])));
         asm volatile("fence.mbarrier_init.release.cluster;\n");
     }
     asm volatile("tcgen05.fence::before_thread_sync;\n");
@@ -338,36 +374,25 @@ __global__ void __launch_bounds__(TC_THREADS) k_conv_tc(const ConvOp op, int *er
     const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
                            ((uint32_t)(TC_M >> 4) << 24);
     const int nk = (op.K + TC_K - 1) / TC_K;
-    uint32_t issued[2] = {0, 0}, waited[2] = {0, 0};
+    uint32_t issued[TC_STAGES] = {}, waited[TC_STAGES] = {};
     bool ok = true;
+    // prologue: the first TC_STAGES - 1 blocks in flight
+#pragma unroll
+    for (int st = 0; st < TC_STAGES - 1; st++) {
+        if (st < nk) tc_stage<BN>(op, base + st * STAGE, m0, n0, st * TC_K, tid);
+        asm volatile("cp.async.commit_group;\n" ::: "memory");
+    }
     for (int kt = 0; kt < nk; kt++) {
-        const int s = kt & 1;
-        if (issued[s] > waited[s]) {  // the MMAs that read this stage last time
-            ok &= tc_wait(smem_u32(&mbar[s]), waited[s] & 1);
-            waited[s]++;
-        }
-        unsigned char *sa = smem + s * STAGE, *sb = sa + SA;
-        const int k0 = kt * TC_K;
-#pragma unroll
-        for (int i = 0; i < (TC_M * 8) / TC_THREADS; i++) {
-            const int q = tid + i * TC_THREADS, r = q >> 3, kg = q & 7;
-            *reinterpret_cast<uint4 *>(sa + (r >> 3) * 1024 + kg * 128 + (r & 7) * 16) =
-                op.gather_a(m0 + r, k0 + kg * 8, op.K);
-        }
-#pragma unroll
-        for (int i = 0; i < (BN * 8) / TC_THREADS; i++) {
-            const int q = tid + i * TC_THREADS, r = q >> 3, kg = q & 7;
-            *reinterpret_cast<uint4 *>(sb + (r >> 3) * 1024 + kg * 128 + (r & 7) * 16) =
-                op.gather_b(n0 + r, k0 + kg * 8, op.K);
-        }
+        const int s = kt % TC_STAGES;
+        asm volatile("cp.async.wait_group %0;\n" ::"n"(TC_STAGES - 2) : "memory");
         asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
         __syncthreads();
         if (tid == 0) {
             asm volatile("tcgen05.fence::after_thread_sync;\n");
+            const uint32_t sa = base + s * STAGE, sb = sa + TC_M * TC_K * 2;
 #pragma unroll
             for (int ks = 0; ks < TC_K / 16; ks++) {
-                const uint64_t ad = tc_desc(smem_u32(sa) + ks * 256);
-                const uint64_t bd = tc_desc(smem_u32(sb) + ks * 256);
+                const uint64_t ad = tc_desc(sa + ks * 256), bd = tc_desc(sb + ks * 256);
                 const uint32_t acc = (kt > 0 || ks > 0) ? 1u : 0u;
                 asm volatile(
                     "{\n.reg .pred p;\nsetp.ne.u32 p, %4, 0;\n"
@@ -379,12 +404,24 @@ __global__ void __launch_bounds__(TC_THREADS) k_conv_tc(const ConvOp op, int *er
                     smem_u32(&mbar[s])));
         }
         issued[s]++;
+        // refill the stage the previous block used, once its MMAs are done
+        const int nxt = kt + TC_STAGES - 1;
+        if (nxt < nk) {
+            const int s2 = nxt % TC_STAGES;
+            if (issued[s2] > waited[s2]) {
+                ok &= tc_wait(smem_u32(&mbar[s2]), waited[s2] & 1);
+                waited[s2]++;
+            }
+            tc_stage<BN>(op, base + s2 * STAGE, m0, n0, nxt * TC_K, tid);
+        }
+        asm volatile("cp.async.commit_group;\n" ::: "memory");
     }
-    for (int s = 0; s < 2; s++)
+    for (int s = 0; s < TC_STAGES; s++)
         while (issued[s] > waited[s]) {
             ok &= tc_wait(smem_u32(&mbar[s]), waited[s] & 1);
             waited[s]++;
         }
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
     asm volatile("tcgen05.fence::after_thread_sync;\n");
     if (!ok) atomicOr(err, 1);
     const int row = m0 + warp * 32 + lane;
@@ -428,70 +465,110 @@ __global__ void k_pack_input(const float *in, bf16 *x, int B, int HW) {
     x[i] = __float2bfloat16(in[(n * 8 + c) * HW + r]);
 }
 
+// The NHWC layers below work on groups of 8 channels (one 16-byte word);
+// every channel count is a multiple of 8.
+__device__ __forceinline__ void unpack8(const uint4 &v, float (&f)[8]) {
+    const __nv_bfloat162 *h = reinterpret_cast<const __nv_bfloat162 *>(&v);
+#pragma unroll
+    for (int j = 0; j < 4; j++) {
+        const float2 t = __bfloat1622float2(h[j]);
+        f[2 * j] = t.x;
+        f[2 * j + 1] = t.y;
+    }
+}
+__device__ __forceinline__ uint4 pack8(const float (&f)[8]) {
+    uint4 v;
+    __nv_bfloat162 *h = reinterpret_cast<__nv_bfloat162 *>(&v);
+#pragma unroll
+    for (int j = 0; j < 4; j++) h[j] = __floats2bfloat162_rn(f[2 * j], f[2 * j + 1]);
+    return v;
+}
+
 // 2x2 average pooling of NHWC [B][H][W][C] into [B][H/2][W/2][C]
 __global__ void k_pool(const bf16 *in, bf16 *out, int B, int H, int W, int C) {
+    const int G = C / 8, Ho = H / 2, Wo = W / 2;
     const long long i = (long long)blockIdx.x * EW + threadIdx.x;
-    const int Ho = H / 2, Wo = W / 2;
-    if (i >= (long long)B * Ho * Wo * C) return;
-    const int c = (int)(i % C);
-    const long long p = i / C;
+    if (i >= (long long)B * Ho * Wo * G) return;
+    const int g = (int)(i % G);
+    const long long p = i / G;
     const int x = (int)(p % Wo), y = (int)((p / Wo) % Ho);
     const long long n = p / ((long long)Wo * Ho);
-    const long long b0 = ((n * H + 2 * y) * W + 2 * x) * C + c;
-    const float s = __bfloat162float(in[b0]) + __bfloat162float(in[b0 + C]) +
-                    __bfloat162float(in[b0 + (long long)W * C]) +
-                    __bfloat162float(in[b0 + (long long)W * C + C]);
-    out[i] = __float2bfloat16(0.25f * s);
+    const long long b0 = ((n * H + 2 * y) * W + 2 * x) * C + 8 * g;
+    float a[8], t[8];
+    unpack8(*reinterpret_cast<const uint4 *>(in + b0), a);
+    const long long offs[3] = {C, (long long)W * C, (long long)W * C + C};
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+        unpack8(*reinterpret_cast<const uint4 *>(in + b0 + offs[k]), t);
+#pragma unroll
+        for (int j = 0; j < 8; j++) a[j] += t[j];
+    }
+#pragma unroll
+    for (int j = 0; j < 8; j++) a[j] *= 0.25f;
+    *reinterpret_cast<uint4 *>(out + p * C + 8 * g) = pack8(a);
 }
 
 // de[p][c] = (e[p][c] > 0) * dpool[p/2][c] / 4 + dskip[p][c] (dskip: a
 // channel slice of stride Cs at offset off, already masked)
 __global__ void k_pool_back(const bf16 *dpool, const bf16 *e, const bf16 *dskip, int Cs, int off,
                             bf16 *de, int B, int H, int W, int C) {
+    const int G = C / 8;
     const long long i = (long long)blockIdx.x * EW + threadIdx.x;
-    if (i >= (long long)B * H * W * C) return;
-    const int c = (int)(i % C);
-    const long long p = i / C;
+    if (i >= (long long)B * H * W * G) return;
+    const int g = (int)(i % G);
+    const long long p = i / G;
     const int x = (int)(p % W), y = (int)((p / W) % H);
     const long long n = p / ((long long)W * H);
     const long long q = (n * (H / 2) + y / 2) * (W / 2) + x / 2;
-    float v = __bfloat162float(e[i]) > 0.f ? 0.25f * __bfloat162float(dpool[q * C + c]) : 0.f;
-    if (dskip) v += __bfloat162float(dskip[p * Cs + off + c]);
-    de[i] = __float2bfloat16(v);
+    float dp[8], ev[8], ds[8] = {0, 0, 0, 0, 0, 0, 0, 0}, o[8];
+    unpack8(*reinterpret_cast<const uint4 *>(dpool + q * C + 8 * g), dp);
+    unpack8(*reinterpret_cast<const uint4 *>(e + p * C + 8 * g), ev);
+    if (dskip) unpack8(*reinterpret_cast<const uint4 *>(dskip + p * Cs + off + 8 * g), ds);
+#pragma unroll
+    for (int j = 0; j < 8; j++) o[j] = (ev[j] > 0.f ? 0.25f * dp[j] : 0.f) + ds[j];
+    *reinterpret_cast<uint4 *>(de + p * C + 8 * g) = pack8(o);
 }
 
 // cat[p] = [up(d)[p] (Cu channels), e[p] (Ce channels)]
 __global__ void k_upcat(const bf16 *d, const bf16 *e, bf16 *cat, int B, int H, int W, int Cu,
                         int Ce) {
-    const int Cc = Cu + Ce;
+    const int Gc = (Cu + Ce) / 8, Gu = Cu / 8;
     const long long i = (long long)blockIdx.x * EW + threadIdx.x;
-    if (i >= (long long)B * H * W * Cc) return;
-    const int c = (int)(i % Cc);
-    const long long p = i / Cc;
-    if (c < Cu) {
+    if (i >= (long long)B * H * W * Gc) return;
+    const int g = (int)(i % Gc);
+    const long long p = i / Gc;
+    uint4 v;
+    if (g < Gu) {
         const int x = (int)(p % W), y = (int)((p / W) % H);
         const long long n = p / ((long long)W * H);
         const long long q = (n * (H / 2) + y / 2) * (W / 2) + x / 2;
-        cat[i] = d[q * Cu + c];
+        v = *reinterpret_cast<const uint4 *>(d + q * Cu + 8 * g);
     } else {
-        cat[i] = e[p * Ce + (c - Cu)];
+        v = *reinterpret_cast<const uint4 *>(e + p * Ce + 8 * (g - Gu));
     }
+    *reinterpret_cast<uint4 *>(cat + p * (Cu + Ce) + 8 * g) = v;
 }
 
 // dd[q][c] = sum over the 2x2 children p of q of dcat[p][c], c < Cu
 __global__ void k_up_back(const bf16 *dcat, int Cc, bf16 *dd, int B, int Hc, int Wc, int Cu) {
+    const int G = Cu / 8;
     const long long i = (long long)blockIdx.x * EW + threadIdx.x;
-    if (i >= (long long)B * Hc * Wc * Cu) return;
-    const int c = (int)(i % Cu);
-    const long long q = i / Cu;
+    if (i >= (long long)B * Hc * Wc * G) return;
+    const int g = (int)(i % G);
+    const long long q = i / G;
     const int x = (int)(q % Wc), y = (int)((q / Wc) % Hc);
     const long long n = q / ((long long)Wc * Hc);
     const int H = 2 * Hc, W = 2 * Wc;
     const long long p0 = (n * H + 2 * y) * W + 2 * x;
-    const float s = __bfloat162float(dcat[p0 * Cc + c]) + __bfloat162float(dcat[(p0 + 1) * Cc + c]) +
-                    __bfloat162float(dcat[(p0 + W) * Cc + c]) +
-                    __bfloat162float(dcat[(p0 + W + 1) * Cc + c]);
-    dd[i] = __float2bfloat16(s);
+    const long long ps[4] = {p0, p0 + 1, p0 + W, p0 + W + 1};
+    float a[8] = {0, 0, 0, 0, 0, 0, 0, 0}, t[8];
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+        unpack8(*reinterpret_cast<const uint4 *>(dcat + ps[k] * Cc + 8 * g), t);
+#pragma unroll
+        for (int j = 0; j < 8; j++) a[j] += t[j];
+    }
+    *reinterpret_cast<uint4 *>(dd + q * Cu + 8 * g) = pack8(a);
 }
 
 // 1x1 head: out[n][o][y][x] = b[o] + sum_c w[o][c] d[p][c] (FP32), NCHW output
@@ -759,7 +836,7 @@ int conv_index(const lbm_unet *n, const char kind, int l, int ab) {
 
 template <int BN>
 cudaError_t launch_tc(lbm_unet *n, const nn::ConvOp &op) {
-    constexpr int smem = 2 * (nn::TC_M * nn::TC_K * 2 + BN * nn::TC_K * 2);
+    constexpr int smem = nn::TC_STAGES * (nn::TC_M * nn::TC_K * 2 + BN * nn::TC_K * 2);
     static bool attr = false;
     if (!attr) {
         cudaError_t e = cudaFuncSetAttribute(nn::k_conv_tc<BN>,
@@ -871,7 +948,7 @@ lbm_status forward(lbm_unet *n, const float *in_dev, int B) {
         const bf16 *inp = n->x;
         if (l > 0) {
             const Level &u = n->lv[l - 1];
-            NCK(n, (nn::k_pool<<<nn::blocks((long long)B * v.H * v.W * u.C), nn::EW, 0, n->stream>>>(
+            NCK(n, (nn::k_pool<<<nn::blocks((long long)B * v.H * v.W * u.C / 8), nn::EW, 0, n->stream>>>(
                        u.e, v.inp, B, u.H, u.W, u.C),
                    cudaGetLastError()));
             inp = v.inp;
@@ -883,7 +960,7 @@ lbm_status forward(lbm_unet *n, const float *in_dev, int B) {
     for (int l = L - 2; l >= 0; l--) {
         Level &v = n->lv[l];
         const int Cu = n->lv[l + 1].C;
-        NCK(n, (nn::k_upcat<<<nn::blocks((long long)B * v.H * v.W * (Cu + v.C)), nn::EW, 0,
+        NCK(n, (nn::k_upcat<<<nn::blocks((long long)B * v.H * v.W * (Cu + v.C) / 8), nn::EW, 0,
                               n->stream>>>(d, v.e, v.cat, B, v.H, v.W, Cu, v.C),
                cudaGetLastError()));
         NCK(n, conv_fwd(n, n->convs[conv_index(n, 'd', l, 0)], v.cat, v.da, B, v.H, v.W, true));
@@ -931,7 +1008,7 @@ lbm_status backward(lbm_unet *n, const float *tgt_dev, const float *fl_dev, int 
         NCK(n, conv_wgrad(n, ca, v.g2, v.cat, B, v.H, v.W));
         NCK(n, conv_dgrad(n, ca, v.g2, v.cat, v.gcat, B, v.H, v.W));
         Level &u = n->lv[l + 1];
-        NCK(n, (nn::k_up_back<<<nn::blocks((long long)B * u.H * u.W * u.C), nn::EW, 0, n->stream>>>(
+        NCK(n, (nn::k_up_back<<<nn::blocks((long long)B * u.H * u.W * u.C / 8), nn::EW, 0, n->stream>>>(
                    v.gcat, u.C + v.C, u.g1, B, u.H, u.W, u.C),
                cudaGetLastError()));
     }
@@ -946,7 +1023,7 @@ lbm_status backward(lbm_unet *n, const float *tgt_dev, const float *fl_dev, int 
         if (l == 0) break;
         NCK(n, conv_dgrad(n, ca, v.g2, nullptr, v.gin, B, v.H, v.W));
         Level &u = n->lv[l - 1];
-        NCK(n, (nn::k_pool_back<<<nn::blocks((long long)B * u.H * u.W * u.C), nn::EW, 0, n->stream>>>(
+        NCK(n, (nn::k_pool_back<<<nn::blocks((long long)B * u.H * u.W * u.C / 8), nn::EW, 0, n->stream>>>(
                    v.gin, u.e, u.gcat, v.C + u.C, v.C, u.g1, B, u.H, u.W, u.C),
                cudaGetLastError()));
     }
