@@ -60,6 +60,8 @@ def parse():
     ap.add_argument("--ws-train", type=int, default=1024)
     ap.add_argument("--ws-test", type=int, default=256)
     ap.add_argument("--ws-epochs", type=int, default=100)
+    ap.add_argument("--batch-converge", type=int, default=0, metavar="STEPS",
+                    help="run the 512-channel sweep until every case retires or STEPS steps")
     ap.add_argument("--unet", action="store_true",
                     help="time the warm-start network's forward pass and training step")
     ap.add_argument("--batch-only", action="store_true",
@@ -452,6 +454,50 @@ def run_precision_study(a, w, local, stream):
     return out
 
 
+def run_batch_converge(a, local):
+    """The 512-channel sweep run the way it is meant to be used: 100-step
+    graph blocks with the convergence test (drag change below 1e-7 per 100
+    steps), converged cases retiring, until every case has retired or the
+    step budget is spent.  Reports the wall time, the retired counts and the
+    aggregate MLUPS over the steps the cases actually took."""
+    import numpy as np
+    import torch
+
+    import paper_1303_0625_gb300 as G
+    import workloads as W
+
+    torch.cuda.set_device(local)
+    ws = W.cylinder_sweep(a.batch_cases)
+    cells = np.array([w["nx"] * w["ny"] for w in ws], dtype=np.int64)
+    b = G.Batch.from_workloads(ws, precision=G.LBM_FP32_DEV, force_ring=4, device=local)
+    shape = b.autotune(4)
+    b.set_convergence(every=100, tol=1e-7, max_steps=2_000_000)
+    _, s0, _ = b.state()
+    t0 = time.perf_counter()
+    done, marks = 0, []
+    while done < a.batch_converge:
+        n = min(10_000, a.batch_converge - done)
+        active = b.run(n)
+        done += n
+        marks.append([done, int(active), round(time.perf_counter() - t0, 2)])
+        if active == 0:
+            break
+    wall = time.perf_counter() - t0
+    st, s1, _ = b.state()
+    upd = float((cells * (s1 - s0)).sum())
+    b.close()
+    conv = st == G.LBM_CASE_CONVERGED
+    return {"metric": "cylinder sweep run to convergence (drag change < 1e-7 per 100 steps)",
+            "cases": len(ws), "launch_shape": list(shape), "budget_steps": a.batch_converge,
+            "batch_steps": done, "wall_s": round(wall, 2),
+            "converged": int(conv.sum()), "active": int((st == G.LBM_CASE_ACTIVE).sum()),
+            "unstable": int((st == G.LBM_CASE_UNSTABLE).sum()),
+            "steps_to_converge_pct_0_50_90_100": [int(np.percentile(s1[conv], q)) for q in (0, 50, 90, 100)]
+            if conv.any() else None,
+            "aggregate_mlups": round(upd / wall / 1e6, 1),
+            "active_after_steps": marks}
+
+
 def run_unet(a, local, H=128, W=256, B=16, levels=4, base=32):
     """Forward pass and training step of the warm-start U-Net (BF16 tensor
     cores, FP32 accumulation) on a batch of B synthetic 128 x 256 inputs:
@@ -670,6 +716,9 @@ def main():
     ws, rank, local = dist_setup()
     if a.impl == "reference":
         run_reference(a, ws, rank)
+    elif a.batch_converge:
+        if rank == 0:
+            print(json.dumps(run_batch_converge(a, local)), flush=True)
     elif a.unet:
         if rank == 0:
             print(json.dumps(run_unet(a, local)), flush=True)
