@@ -1,8 +1,8 @@
 // The warm-start U-Net on the GPU: forward, backward and Adam, with every
 // 3x3 convolution an implicit GEMM on the tensor cores (BF16 operands, FP32
-// accumulation): the forward and data-gradient convolutions with tcgen05
-// (accumulator in tensor memory), the weight gradient (whose operands are
-// transposed gathers) with mma.sync.  The remaining layers (pooling,
+// accumulation) with tcgen05 and the accumulator in tensor memory: forward
+// and data gradient with K-major operands, the weight gradient with MN-major
+// ones read straight from the NHWC tensors.  The remaining layers (pooling,
 // upsampling with concatenation, the 1x1 head, the loss, Adam) are small
 // kernels of their own.
 //
@@ -450,6 +450,161 @@ __global__ void __launch_bounds__(TC_THREADS) k_conv_tc(const ConvOp op, int *er
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(BN));
 }
 
+// Weight gradient on tcgen05: dw[co][tap][ci] += sum_p x[p + s(tap)][ci] dz[p][co],
+// i.e. D[m][n] with m = (tap, ci) (M = taps Cin), n = co, K = pixels.  Both
+// operands are MN-major in shared memory (8 consecutive channels of one
+// pixel form a 16-byte core-matrix row), so they are copied straight from the
+// NHWC tensors: core matrix (MN group g, K group j) at j * LBO + g * 128
+// bytes, LBO = (rows / 8) * 128.  The pixel range of a block is one split of
+// K (gridDim.z); results are added to dw with FP32 atomics.
+struct WgradTc {
+    const bf16 *dz;  // [P][Co]
+    const bf16 *x;   // [P][Ci]
+    float *dw;       // [Co][taps][Ci]
+    Img img;
+    int Co, Ci, taps, M, N, K, kchunk;  // M = taps Ci, N = Co, K = P
+};
+
+template <int BN>
+__device__ __forceinline__ void wg_stage(const WgradTc &op, uint32_t sa, int m0, int n0, int k0,
+                                         int ke, int tid) {
+    const uint32_t sb = sa + TC_M * TC_K * 2;
+#pragma unroll
+    for (int i = 0; i < (TC_M / 8 * TC_K) / TC_THREADS; i++) {
+        const int q = tid + i * TC_THREADS, g = q & 15, pl = q >> 4;  // 16 channel groups x 64 pixels
+        const int m = m0 + 8 * g, p = k0 + pl;
+        const bf16 *src = nullptr;
+        if (m < op.M && p < ke) {
+            const int tap = m / op.Ci, c = m - tap * op.Ci;
+            int qp = p;
+            if (op.taps == 1 || op.img.shift(p, tap / 3 - 1, tap % 3 - 1, qp))
+                src = op.x + (size_t)qp * op.Ci + c;
+        }
+        cp16(sa + (pl >> 3) * 2048 + g * 128 + (pl & 7) * 16, src, op.x);
+    }
+#pragma unroll
+    for (int i = 0; i < (BN / 8 * TC_K) / TC_THREADS; i++) {
+        const int q = tid + i * TC_THREADS, g = q % (BN / 8), pl = q / (BN / 8);
+        const int n = n0 + 8 * g, p = k0 + pl;
+        const bf16 *src = (n < op.N && p < ke) ? op.dz + (size_t)p * op.Co + n : nullptr;
+        cp16(sb + (pl >> 3) * (BN / 8 * 128) + g * 128 + (pl & 7) * 16, src, op.dz);
+    }
+}
+
+template <int BN>
+__global__ void __launch_bounds__(TC_THREADS) k_wgrad_tc(const WgradTc op, int *err) {
+    extern __shared__ __align__(1024) unsigned char smem[];
+    __shared__ uint32_t tmem_base;
+    __shared__ __align__(8) uint64_t mbar[TC_STAGES];
+    constexpr int STAGE = TC_M * TC_K * 2 + BN * TC_K * 2;
+    constexpr int TMEM_COLS = BN < 32 ? 32 : BN;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int m0 = blockIdx.x * TC_M, n0 = blockIdx.y * BN;
+    const int kb = blockIdx.z * op.kchunk, ke = min(op.K, kb + op.kchunk);
+    const uint32_t base = smem_u32(smem);
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(
+                         smem_u32(&tmem_base)),
+                     "r"(TMEM_COLS));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
+    }
+    if (tid == 0) {
+        for (int s = 0; s < TC_STAGES; s++)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&mbar[s])));
+        asm volatile("fence.mbarrier_init.release.cluster;\n");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;\n");
+    const uint32_t tmem = tmem_base;
+    // kind::f16: D FP32, A and B BF16, both MN-major, N = BN, M = 128
+    const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | (1u << 15) | (1u << 16) |
+                           ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(TC_M >> 4) << 24);
+    const int nk = (ke - kb + TC_K - 1) / TC_K;
+    uint32_t issued[TC_STAGES] = {}, waited[TC_STAGES] = {};
+    bool ok = true;
+#pragma unroll
+    for (int st = 0; st < TC_STAGES - 1; st++) {
+        if (st < nk) wg_stage<BN>(op, base + st * STAGE, m0, n0, kb + st * TC_K, ke, tid);
+        asm volatile("cp.async.commit_group;\n" ::: "memory");
+    }
+    for (int kt = 0; kt < nk; kt++) {
+        const int s = kt % TC_STAGES;
+        asm volatile("cp.async.wait_group %0;\n" ::"n"(TC_STAGES - 2) : "memory");
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+        __syncthreads();
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;\n");
+            const uint32_t sa = base + s * STAGE, sb = sa + TC_M * TC_K * 2;
+#pragma unroll
+            for (int ks = 0; ks < TC_K / 16; ks++) {
+                // two K groups per MMA; leading offset = K-group stride, stride offset = 128
+                uint64_t ad = (uint64_t)(((sa + ks * 4096) >> 4) & 0x3FFF);
+                ad |= (uint64_t)(2048 >> 4) << 16;
+                ad |= (uint64_t)(128 >> 4) << 32;
+                ad |= (uint64_t)1 << 46;
+                uint64_t bd = (uint64_t)(((sb + ks * 2 * (BN / 8 * 128)) >> 4) & 0x3FFF);
+                bd |= (uint64_t)((BN / 8 * 128) >> 4) << 16;
+                bd |= (uint64_t)(128 >> 4) << 32;
+                bd |= (uint64_t)1 << 46;
+                const uint32_t acc = (kt > 0 || ks > 0) ? 1u : 0u;
+                asm volatile(
+                    "{\n.reg .pred p;\nsetp.ne.u32 p, %4, 0;\n"
+                    "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+                    "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+            }
+            asm volatile(
+                "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                    smem_u32(&mbar[s])));
+        }
+        issued[s]++;
+        const int nxt = kt + TC_STAGES - 1;
+        if (nxt < nk) {
+            const int s2 = nxt % TC_STAGES;
+            if (issued[s2] > waited[s2]) {
+                ok &= tc_wait(smem_u32(&mbar[s2]), waited[s2] & 1);
+                waited[s2]++;
+            }
+            wg_stage<BN>(op, base + s2 * STAGE, m0, n0, kb + nxt * TC_K, ke, tid);
+        }
+        asm volatile("cp.async.commit_group;\n" ::: "memory");
+    }
+    for (int s = 0; s < TC_STAGES; s++)
+        while (issued[s] > waited[s]) {
+            ok &= tc_wait(smem_u32(&mbar[s]), waited[s] & 1);
+            waited[s]++;
+        }
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+    asm volatile("tcgen05.fence::after_thread_sync;\n");
+    if (!ok) atomicOr(err, 1);
+    const int m = m0 + warp * 32 + lane;
+#pragma unroll
+    for (int c0 = 0; c0 < BN; c0 += 16) {
+        uint32_t v[16];
+        const uint32_t addr = tmem + ((uint32_t)(warp * 32) << 16) + c0;
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
+            "%14,%15}, [%16];\n"
+            : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+              "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
+              "=r"(v[14]), "=r"(v[15])
+            : "r"(addr));
+        asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+        if (ok && m < op.M && nk > 0) {
+#pragma unroll
+            for (int j = 0; j < 16; j++) {
+                const int n = n0 + c0 + j;
+                if (n < op.N) atomicAdd(op.dw + (size_t)n * op.M + m, __uint_as_float(v[j]));
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem),
+                     "r"(TMEM_COLS));
+}
+
 // ------------------------------------------------------ other layers
 
 constexpr int EW = 256;  // threads of the elementwise kernels
@@ -894,8 +1049,52 @@ cudaError_t conv_dgrad(lbm_unet *n, const Conv &cv, const bf16 *dz, const bf16 *
     return launch_conv_tc(n, op);
 }
 
+template <int BN>
+cudaError_t launch_wg(lbm_unet *n, const nn::WgradTc &op, int z) {
+    constexpr int smem = nn::TC_STAGES * (nn::TC_M * nn::TC_K * 2 + BN * nn::TC_K * 2);
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(nn::k_wgrad_tc<BN>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    const dim3 grid((op.M + nn::TC_M - 1) / nn::TC_M, (op.N + BN - 1) / BN, z);
+    nn::k_wgrad_tc<BN><<<grid, nn::TC_THREADS, smem, n->stream>>>(op, n->err_d);
+    return cudaGetLastError();
+}
+
 cudaError_t conv_wgrad(lbm_unet *n, const Conv &cv, const bf16 *dz, const bf16 *x, int B, int H,
                        int W) {
+    if (cv.k == 3) {
+        nn::WgradTc op{};
+        op.dz = dz;
+        op.x = x;
+        op.dw = n->g + cv.w_off;
+        op.img = {B, H, W};
+        op.Co = cv.co;
+        op.Ci = cv.ci;
+        op.taps = 9;
+        op.M = 9 * cv.ci;
+        op.N = cv.co;
+        op.K = B * H * W;
+        const int bn = cv.co <= 32 ? 32 : (cv.co <= 64 ? 64 : 128);
+        const int mt = (op.M + nn::TC_M - 1) / nn::TC_M, nt = (op.N + bn - 1) / bn;
+        const int kt = (op.K + nn::TC_K - 1) / nn::TC_K;
+        int z = 2 * 152 * 2 / (mt * nt);
+        if (z < 1) z = 1;
+        if (z > kt) z = kt;
+        op.kchunk = ((kt + z - 1) / z) * nn::TC_K;
+        z = (op.K + op.kchunk - 1) / op.kchunk;
+        cudaError_t e = bn == 32 ? launch_wg<32>(n, op, z)
+                                 : (bn == 64 ? launch_wg<64>(n, op, z) : launch_wg<128>(n, op, z));
+        if (e != cudaSuccess) return e;
+        const long long P = op.K;
+        int nb = (int)((P * cv.co + nn::EW - 1) / nn::EW);
+        if (nb > 1024) nb = 1024;
+        nn::k_colsum<<<nb, nn::EW, 0, n->stream>>>(dz, P, cv.co, n->g + cv.b_off);
+        return cudaGetLastError();
+    }
     nn::WgradOp op{};
     op.dz = dz;
     op.x = x;
