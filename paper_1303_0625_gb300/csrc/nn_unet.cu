@@ -294,7 +294,8 @@ struct WgradOp {
 // the next blocks are in flight while the tensor cores work.  Every mbarrier
 // wait is bounded; a wait that runs out sets *err and the tile's results are
 // not stored.
-constexpr int TC_M = 128, TC_K = 64, TC_THREADS = 128, TC_STAGES = 3;
+constexpr int TC_M = 128, TC_K = 64, TC_THREADS = 256, TC_STAGES = 3;
+constexpr int TC_TABLE_MAX = 8192;  // bytes of the A operand's K table (K up to 8192)
 constexpr int TC_SPIN = 1 << 24;
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
@@ -330,19 +331,112 @@ __device__ __forceinline__ void cp16(uint32_t dst, const void *src, const void *
                  : "memory");
 }
 
-template <int BN>
-__device__ __forceinline__ void tc_stage(const ConvOp &op, uint32_t sa, int m0, int n0, int k0,
-                                         int tid) {
-    const uint32_t sb = sa + TC_M * TC_K * 2;
+// The MMA pipeline of the tcgen05 kernels: TC_STAGES shared-memory stages
+// filled with cp.async by every thread (stage(i, addr) copies K block i; it is
+// called for i = 0, 1, 2, ... in order), one thread issuing a block's four
+// K = 16 MMAs (mma(addr, accumulate)) and committing them to the stage's
+// mbarrier, which is waited for (bounded) before the stage is refilled.  The
+// block of iteration j completes phase j / TC_STAGES of barrier j % TC_STAGES,
+// and every barrier has at most one phase outstanding when it is waited for.
+// Returns false when a wait gave up.
+template <int STAGE, class StageFn, class MmaFn>
+__device__ __forceinline__ bool tc_pipeline(int nk, uint32_t base, uint64_t *mbar, int tid,
+                                            StageFn &&stage, MmaFn &&mma) {
+    bool ok = true;
 #pragma unroll
-    for (int i = 0; i < (TC_M * 8) / TC_THREADS; i++) {
-        const int q = tid + i * TC_THREADS, r = q >> 3, kg = q & 7;
-        cp16(sa + (r >> 3) * 1024 + kg * 128 + (r & 7) * 16, op.addr_a(m0 + r, k0 + kg * 8, op.K), op.src);
+    for (int st = 0; st < TC_STAGES - 1; st++) {
+        if (st < nk) stage(st, base + st * STAGE);
+        asm volatile("cp.async.commit_group;\n" ::: "memory");
     }
+    for (int kt = 0; kt < nk; kt++) {
+        const int s = kt % TC_STAGES;
+        asm volatile("cp.async.wait_group %0;\n" ::"n"(TC_STAGES - 2) : "memory");
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+        __syncthreads();
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;\n");
+            mma(base + s * STAGE, kt > 0);
+            asm volatile(
+                "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                    smem_u32(&mbar[s])));
+        }
+        // refill the stage of block kt - 1 once its MMAs are done
+        const int nxt = kt + TC_STAGES - 1;
+        if (nxt < nk) {
+            if (kt > 0) ok &= tc_wait(smem_u32(&mbar[(kt - 1) % TC_STAGES]), ((kt - 1) / TC_STAGES) & 1);
+            stage(nxt, base + (nxt % TC_STAGES) * STAGE);
+        }
+        asm volatile("cp.async.commit_group;\n" ::: "memory");
+    }
+    // blocks max(nk - TC_STAGES, 0) .. nk - 1 have not been waited for
+    for (int j = nk > TC_STAGES ? nk - TC_STAGES : 0; j < nk; j++)
+        ok &= tc_wait(smem_u32(&mbar[j % TC_STAGES]), (j / TC_STAGES) & 1);
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+    asm volatile("tcgen05.fence::after_thread_sync;\n");
+    return ok;
+}
+
+__device__ __forceinline__ void tc_alloc(uint32_t *slot, uint64_t *mbar, int ncols, int warp, int tid) {
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(
+                         smem_u32(slot)),
+                     "r"(ncols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
+    }
+    if (tid == 0) {
+        for (int s = 0; s < TC_STAGES; s++)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&mbar[s])));
+        asm volatile("fence.mbarrier_init.release.cluster;\n");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;\n");
+}
+
+__device__ __forceinline__ void tc_free(uint32_t tmem, int ncols, int warp) {
+    asm volatile("tcgen05.fence::before_thread_sync;\n");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(ncols));
+}
+
+// 16 consecutive FP32 accumulator columns of this warp's 32 TMEM lanes
+__device__ __forceinline__ void tc_ld16(uint32_t addr, float (&f)[16]) {
+    uint32_t v[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
+        "%14,%15}, [%16];\n"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+          "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
+          "=r"(v[14]), "=r"(v[15])
+        : "r"(addr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
 #pragma unroll
-    for (int i = 0; i < (BN * 8) / TC_THREADS; i++) {
-        const int q = tid + i * TC_THREADS, r = q >> 3, kg = q & 7;
-        cp16(sb + (r >> 3) * 1024 + kg * 128 + (r & 7) * 16, op.addr_b(n0 + r, k0 + kg * 8, op.K), op.w);
+    for (int j = 0; j < 16; j++) f[j] = __uint_as_float(v[j]);
+}
+
+__device__ __forceinline__ void tc_mma(uint32_t tmem, uint64_t ad, uint64_t bd, uint32_t idesc,
+                                       uint32_t acc) {
+    asm volatile(
+        "{\n.reg .pred p;\nsetp.ne.u32 p, %4, 0;\n"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+        "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+}
+
+// Shared-memory table of the K axis of a convolution's A operand, one entry
+// per 8 consecutive K elements: the element offset of the 8 source channels
+// from the row's own pixel, and the index 3 dy + dx + 4 of the displacement
+// (31 beyond K, which no row's bounds mask has).
+__device__ __forceinline__ void conv_table(const ConvOp &op, int2 *tab, int nent, int tid) {
+    for (int e = tid; e < nent; e += TC_THREADS) {
+        int2 v = make_int2(0, 31);
+        if (8 * e < op.K) {
+            const int k = 8 * e, tap = k / op.Cs, c = k - tap * op.Cs;
+            const int dy = op.taps == 9 ? op.sign * (tap / 3 - 1) : 0;
+            const int dx = op.taps == 9 ? op.sign * (tap % 3 - 1) : 0;
+            v = make_int2((dy * op.img.W + dx) * op.Cs + c, 3 * dy + dx + 4);
+        }
+        tab[e] = v;
     }
 }
 
@@ -355,99 +449,65 @@ __global__ void __launch_bounds__(TC_THREADS) k_conv_tc(const ConvOp op, int *er
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int m0 = blockIdx.x * TC_M, n0 = blockIdx.y * BN;
     const uint32_t base = smem_u32(smem);
-    if (warp == 0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(
-                         smem_u32(&tmem_base)),
-                     "r"(BN));
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
+    const int nk = (op.K + TC_K - 1) / TC_K, nkk = op.K >> 3;
+    int2 *tab = reinterpret_cast<int2 *>(smem + TC_STAGES * STAGE);
+    conv_table(op, tab, nk * (TC_K / 8), tid);
+    // this thread's A row (a pixel) and the 3x3 neighbours of it inside the image
+    const int r = tid & (TC_M - 1), p = m0 + r;
+    uint32_t inb = 0;
+    const bf16 *arow = op.src;
+    if (p < op.M) {
+        const int hw = op.img.H * op.img.W, q = p % hw, y = q / op.img.W, x = q - y * op.img.W;
+#pragma unroll
+        for (int b = 0; b < 9; b++) {
+            const int ys = y + b / 3 - 1, xs = x + b % 3 - 1;
+            if (ys >= 0 && ys < op.img.H && xs >= 0 && xs < op.img.W) inb |= 1u << b;
+        }
+        arow = op.src + (size_t)p * op.Cs;
     }
-    if (tid == 0) {
-        for (int s = 0; s < TC_STAGES; s++)
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&mbar[s])));
-        asm volatile("fence.mbarrier_init.release.cluster;\n");
-    }
-    asm volatile("tcgen05.fence::before_thread_sync;\n");
-    __syncthreads();
-    asm volatile("tcgen05.fence::after_thread_sync;\n");
+    // this thread's B row (an output channel)
+    const int rb = tid % BN, nb = n0 + rb;
+    const bf16 *brow = op.w + (size_t)(nb < op.N ? nb : 0) * op.K;
+    tc_alloc(&tmem_base, mbar, BN, warp, tid);  // its barrier also publishes the table
     const uint32_t tmem = tmem_base;
     // kind::f16: D FP32, A and B BF16, both K-major, N = BN, M = 128
     const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
                            ((uint32_t)(TC_M >> 4) << 24);
-    const int nk = (op.K + TC_K - 1) / TC_K;
-    uint32_t issued[TC_STAGES] = {}, waited[TC_STAGES] = {};
-    bool ok = true;
-    // prologue: the first TC_STAGES - 1 blocks in flight
+    auto stage = [&](int kt, uint32_t sa) {
+        const uint32_t sb = sa + TC_M * TC_K * 2;
+        const int kk0 = kt * (TC_K / 8);
 #pragma unroll
-    for (int st = 0; st < TC_STAGES - 1; st++) {
-        if (st < nk) tc_stage<BN>(op, base + st * STAGE, m0, n0, st * TC_K, tid);
-        asm volatile("cp.async.commit_group;\n" ::: "memory");
-    }
-    for (int kt = 0; kt < nk; kt++) {
-        const int s = kt % TC_STAGES;
-        asm volatile("cp.async.wait_group %0;\n" ::"n"(TC_STAGES - 2) : "memory");
-        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-        __syncthreads();
-        if (tid == 0) {
-            asm volatile("tcgen05.fence::after_thread_sync;\n");
-            const uint32_t sa = base + s * STAGE, sb = sa + TC_M * TC_K * 2;
+        for (int i = 0; i < TC_M * 8 / TC_THREADS; i++) {
+            const int kg = tid / TC_M + (TC_THREADS / TC_M) * i;
+            const int2 e = tab[kk0 + kg];
+            cp16(sa + (r >> 3) * 1024 + kg * 128 + (r & 7) * 16,
+                 ((inb >> e.y) & 1u) ? arow + e.x : nullptr, op.src);
+        }
 #pragma unroll
-            for (int ks = 0; ks < TC_K / 16; ks++) {
-                const uint64_t ad = tc_desc(sa + ks * 256), bd = tc_desc(sb + ks * 256);
-                const uint32_t acc = (kt > 0 || ks > 0) ? 1u : 0u;
-                asm volatile(
-                    "{\n.reg .pred p;\nsetp.ne.u32 p, %4, 0;\n"
-                    "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
-                    "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
-            }
-            asm volatile(
-                "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
-                    smem_u32(&mbar[s])));
+        for (int i = 0; i < BN * 8 / TC_THREADS; i++) {
+            const int kg = tid / BN + (TC_THREADS / BN) * i, kk = kk0 + kg;
+            cp16(sb + (rb >> 3) * 1024 + kg * 128 + (rb & 7) * 16,
+                 (nb < op.N && kk < nkk) ? brow + 8 * kk : nullptr, op.w);
         }
-        issued[s]++;
-        // refill the stage the previous block used, once its MMAs are done
-        const int nxt = kt + TC_STAGES - 1;
-        if (nxt < nk) {
-            const int s2 = nxt % TC_STAGES;
-            if (issued[s2] > waited[s2]) {
-                ok &= tc_wait(smem_u32(&mbar[s2]), waited[s2] & 1);
-                waited[s2]++;
-            }
-            tc_stage<BN>(op, base + s2 * STAGE, m0, n0, nxt * TC_K, tid);
-        }
-        asm volatile("cp.async.commit_group;\n" ::: "memory");
-    }
-    for (int s = 0; s < TC_STAGES; s++)
-        while (issued[s] > waited[s]) {
-            ok &= tc_wait(smem_u32(&mbar[s]), waited[s] & 1);
-            waited[s]++;
-        }
-    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
-    asm volatile("tcgen05.fence::after_thread_sync;\n");
+    };
+    auto mma = [&](uint32_t sa, bool accumulate) {
+        const uint32_t sb = sa + TC_M * TC_K * 2;
+#pragma unroll
+        for (int ks = 0; ks < TC_K / 16; ks++)
+            tc_mma(tmem, tc_desc(sa + ks * 256), tc_desc(sb + ks * 256), idesc,
+                   (accumulate || ks > 0) ? 1u : 0u);
+    };
+    const bool ok = tc_pipeline<STAGE>(nk, base, mbar, tid, stage, mma);
     if (!ok) atomicOr(err, 1);
-    const int row = m0 + warp * 32 + lane;
+    // epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31, columns of half w / 4
+    const int row = m0 + (warp & 3) * 32 + lane, cb = (warp >> 2) * (BN / 2);
 #pragma unroll
-    for (int c0 = 0; c0 < BN; c0 += 16) {
-        uint32_t v[16];
-        const uint32_t addr = tmem + ((uint32_t)(warp * 32) << 16) + c0;
-        asm volatile(
-            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
-            "%14,%15}, [%16];\n"
-            : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
-              "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
-              "=r"(v[14]), "=r"(v[15])
-            : "r"(addr));
-        asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
-        if (ok && n0 + c0 < op.N) {
-            float f[16];
-#pragma unroll
-            for (int j = 0; j < 16; j++) f[j] = __uint_as_float(v[j]);
-            op.store16(row, n0 + c0, f);
-        }
+    for (int c0 = 0; c0 < BN / 2; c0 += 16) {
+        float f[16];
+        tc_ld16(tmem + ((uint32_t)((warp & 3) * 32) << 16) + cb + c0, f);
+        if (ok && n0 + cb + c0 < op.N) op.store16(row, n0 + cb + c0, f);
     }
-    asm volatile("tcgen05.fence::before_thread_sync;\n");
-    __syncthreads();
-    if (warp == 0)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(BN));
+    tc_free(tmem, BN, warp);
 }
 
 // Weight gradient on tcgen05: dw[co][tap][ci] += sum_p x[p + s(tap)][ci] dz[p][co],
@@ -466,143 +526,98 @@ struct WgradTc {
 };
 
 template <int BN>
-__device__ __forceinline__ void wg_stage(const WgradTc &op, uint32_t sa, int m0, int n0, int k0,
-                                         int ke, int tid) {
-    const uint32_t sb = sa + TC_M * TC_K * 2;
-#pragma unroll
-    for (int i = 0; i < (TC_M / 8 * TC_K) / TC_THREADS; i++) {
-        const int q = tid + i * TC_THREADS, g = q & 15, pl = q >> 4;  // 16 channel groups x 64 pixels
-        const int m = m0 + 8 * g, p = k0 + pl;
-        const bf16 *src = nullptr;
-        if (m < op.M && p < ke) {
-            const int tap = m / op.Ci, c = m - tap * op.Ci;
-            int qp = p;
-            if (op.taps == 1 || op.img.shift(p, tap / 3 - 1, tap % 3 - 1, qp))
-                src = op.x + (size_t)qp * op.Ci + c;
-        }
-        cp16(sa + (pl >> 3) * 2048 + g * 128 + (pl & 7) * 16, src, op.x);
-    }
-#pragma unroll
-    for (int i = 0; i < (BN / 8 * TC_K) / TC_THREADS; i++) {
-        const int q = tid + i * TC_THREADS, g = q % (BN / 8), pl = q / (BN / 8);
-        const int n = n0 + 8 * g, p = k0 + pl;
-        const bf16 *src = (n < op.N && p < ke) ? op.dz + (size_t)p * op.Co + n : nullptr;
-        cp16(sb + (pl >> 3) * (BN / 8 * 128) + g * 128 + (pl & 7) * 16, src, op.dz);
-    }
-}
-
-template <int BN>
 __global__ void __launch_bounds__(TC_THREADS) k_wgrad_tc(const WgradTc op, int *err) {
     extern __shared__ __align__(1024) unsigned char smem[];
     __shared__ uint32_t tmem_base;
     __shared__ __align__(8) uint64_t mbar[TC_STAGES];
     constexpr int STAGE = TC_M * TC_K * 2 + BN * TC_K * 2;
-    constexpr int TMEM_COLS = BN < 32 ? 32 : BN;
+    constexpr int AG = TC_M * TC_K / 8 / TC_THREADS, BG = BN * TC_K / 8 / TC_THREADS;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int m0 = blockIdx.x * TC_M, n0 = blockIdx.y * BN;
     const int kb = blockIdx.z * op.kchunk, ke = min(op.K, kb + op.kchunk);
+    const int nk = ke > kb ? (ke - kb + TC_K - 1) / TC_K : 0;
     const uint32_t base = smem_u32(smem);
-    if (warp == 0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(
-                         smem_u32(&tmem_base)),
-                     "r"(TMEM_COLS));
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
+    // this thread copies pixel column pl of every K block, channel groups
+    // g = tid / TC_K + (TC_THREADS / TC_K) i; the (tap, channel) of each A group
+    // is fixed: its offset from the pixel and displacement (dy, dx)
+    const int pl = tid & (TC_K - 1), g0 = tid / TC_K;
+    int aoff[AG], ady[AG], adx[AG];
+#pragma unroll
+    for (int i = 0; i < AG; i++) {
+        const int m = m0 + 8 * (g0 + (TC_THREADS / TC_K) * i);
+        aoff[i] = 0;
+        ady[i] = 1 << 20;  // never inside the image
+        adx[i] = 0;
+        if (m < op.M) {
+            const int tap = m / op.Ci, c = m - tap * op.Ci;
+            ady[i] = op.taps == 9 ? tap / 3 - 1 : 0;
+            adx[i] = op.taps == 9 ? tap % 3 - 1 : 0;
+            aoff[i] = (ady[i] * op.img.W + adx[i]) * op.Ci + c;
+        }
     }
-    if (tid == 0) {
-        for (int s = 0; s < TC_STAGES; s++)
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&mbar[s])));
-        asm volatile("fence.mbarrier_init.release.cluster;\n");
-    }
-    asm volatile("tcgen05.fence::before_thread_sync;\n");
-    __syncthreads();
-    asm volatile("tcgen05.fence::after_thread_sync;\n");
+    // coordinates of this thread's pixel, advanced by TC_K per block
+    int p = kb + pl, xx = p % op.img.W, yy = (p / op.img.W) % op.img.H;
+    tc_alloc(&tmem_base, mbar, BN < 32 ? 32 : BN, warp, tid);
     const uint32_t tmem = tmem_base;
     // kind::f16: D FP32, A and B BF16, both MN-major, N = BN, M = 128
     const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | (1u << 15) | (1u << 16) |
                            ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(TC_M >> 4) << 24);
-    const int nk = (ke - kb + TC_K - 1) / TC_K;
-    uint32_t issued[TC_STAGES] = {}, waited[TC_STAGES] = {};
-    bool ok = true;
+    auto stage = [&](int, uint32_t sa) {
+        const uint32_t sb = sa + TC_M * TC_K * 2;
+        const bool pv = p < ke;
 #pragma unroll
-    for (int st = 0; st < TC_STAGES - 1; st++) {
-        if (st < nk) wg_stage<BN>(op, base + st * STAGE, m0, n0, kb + st * TC_K, ke, tid);
-        asm volatile("cp.async.commit_group;\n" ::: "memory");
-    }
-    for (int kt = 0; kt < nk; kt++) {
-        const int s = kt % TC_STAGES;
-        asm volatile("cp.async.wait_group %0;\n" ::"n"(TC_STAGES - 2) : "memory");
-        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-        __syncthreads();
-        if (tid == 0) {
-            asm volatile("tcgen05.fence::after_thread_sync;\n");
-            const uint32_t sa = base + s * STAGE, sb = sa + TC_M * TC_K * 2;
+        for (int i = 0; i < AG; i++) {
+            const int g = g0 + (TC_THREADS / TC_K) * i;
+            const bool in = pv && (unsigned)(yy + ady[i]) < (unsigned)op.img.H &&
+                            (unsigned)(xx + adx[i]) < (unsigned)op.img.W;
+            cp16(sa + (pl >> 3) * (TC_M / 8 * 128) + g * 128 + (pl & 7) * 16,
+                 in ? op.x + (size_t)p * op.Ci + aoff[i] : nullptr, op.x);
+        }
 #pragma unroll
-            for (int ks = 0; ks < TC_K / 16; ks++) {
-                // two K groups per MMA; leading offset = K-group stride, stride offset = 128
-                uint64_t ad = (uint64_t)(((sa + ks * 4096) >> 4) & 0x3FFF);
-                ad |= (uint64_t)(2048 >> 4) << 16;
-                ad |= (uint64_t)(128 >> 4) << 32;
-                ad |= (uint64_t)1 << 46;
-                uint64_t bd = (uint64_t)(((sb + ks * 2 * (BN / 8 * 128)) >> 4) & 0x3FFF);
-                bd |= (uint64_t)((BN / 8 * 128) >> 4) << 16;
-                bd |= (uint64_t)(128 >> 4) << 32;
-                bd |= (uint64_t)1 << 46;
-                const uint32_t acc = (kt > 0 || ks > 0) ? 1u : 0u;
-                asm volatile(
-                    "{\n.reg .pred p;\nsetp.ne.u32 p, %4, 0;\n"
-                    "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
-                    "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
-            }
-            asm volatile(
-                "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
-                    smem_u32(&mbar[s])));
+        for (int i = 0; i < BG; i++) {
+            const int g = g0 + (TC_THREADS / TC_K) * i, n = n0 + 8 * g;
+            cp16(sb + (pl >> 3) * (BN / 8 * 128) + g * 128 + (pl & 7) * 16,
+                 (pv && n < op.N) ? op.dz + (size_t)p * op.Co + n : nullptr, op.dz);
         }
-        issued[s]++;
-        const int nxt = kt + TC_STAGES - 1;
-        if (nxt < nk) {
-            const int s2 = nxt % TC_STAGES;
-            if (issued[s2] > waited[s2]) {
-                ok &= tc_wait(smem_u32(&mbar[s2]), waited[s2] & 1);
-                waited[s2]++;
-            }
-            wg_stage<BN>(op, base + s2 * STAGE, m0, n0, kb + nxt * TC_K, ke, tid);
+        p += TC_K;
+        xx += TC_K;
+        while (xx >= op.img.W) {
+            xx -= op.img.W;
+            if (++yy == op.img.H) yy = 0;
         }
-        asm volatile("cp.async.commit_group;\n" ::: "memory");
-    }
-    for (int s = 0; s < TC_STAGES; s++)
-        while (issued[s] > waited[s]) {
-            ok &= tc_wait(smem_u32(&mbar[s]), waited[s] & 1);
-            waited[s]++;
+    };
+    auto mma = [&](uint32_t sa, bool accumulate) {
+        const uint32_t sb = sa + TC_M * TC_K * 2;
+#pragma unroll
+        for (int ks = 0; ks < TC_K / 16; ks++) {
+            // two K groups per MMA; leading offset = K-group stride, stride offset = 128
+            uint64_t ad = (uint64_t)(((sa + ks * 2 * (TC_M / 8 * 128)) >> 4) & 0x3FFF);
+            ad |= (uint64_t)((TC_M / 8 * 128) >> 4) << 16;
+            ad |= (uint64_t)(128 >> 4) << 32;
+            ad |= (uint64_t)1 << 46;
+            uint64_t bd = (uint64_t)(((sb + ks * 2 * (BN / 8 * 128)) >> 4) & 0x3FFF);
+            bd |= (uint64_t)((BN / 8 * 128) >> 4) << 16;
+            bd |= (uint64_t)(128 >> 4) << 32;
+            bd |= (uint64_t)1 << 46;
+            tc_mma(tmem, ad, bd, idesc, (accumulate || ks > 0) ? 1u : 0u);
         }
-    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
-    asm volatile("tcgen05.fence::after_thread_sync;\n");
+    };
+    const bool ok = tc_pipeline<STAGE>(nk, base, mbar, tid, stage, mma);
     if (!ok) atomicOr(err, 1);
-    const int m = m0 + warp * 32 + lane;
+    const int m = m0 + (warp & 3) * 32 + lane, cb = (warp >> 2) * (BN / 2);
 #pragma unroll
-    for (int c0 = 0; c0 < BN; c0 += 16) {
-        uint32_t v[16];
-        const uint32_t addr = tmem + ((uint32_t)(warp * 32) << 16) + c0;
-        asm volatile(
-            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
-            "%14,%15}, [%16];\n"
-            : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
-              "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
-              "=r"(v[14]), "=r"(v[15])
-            : "r"(addr));
-        asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+    for (int c0 = 0; c0 < BN / 2; c0 += 16) {
+        float f[16];
+        tc_ld16(tmem + ((uint32_t)((warp & 3) * 32) << 16) + cb + c0, f);
         if (ok && m < op.M && nk > 0) {
 #pragma unroll
             for (int j = 0; j < 16; j++) {
-                const int n = n0 + c0 + j;
-                if (n < op.N) atomicAdd(op.dw + (size_t)n * op.M + m, __uint_as_float(v[j]));
+                const int n = n0 + cb + c0 + j;
+                if (n < op.N) atomicAdd(op.dw + (size_t)n * op.M + m, f[j]);
             }
         }
     }
-    asm volatile("tcgen05.fence::before_thread_sync;\n");
-    __syncthreads();
-    if (warp == 0)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem),
-                     "r"(TMEM_COLS));
+    tc_free(tmem, BN < 32 ? 32 : BN, warp);
 }
 
 // ------------------------------------------------------ other layers
@@ -926,6 +941,7 @@ struct lbm_unet {
     float *cnt = nullptr;
     double *loss = nullptr;
     int *err_d = nullptr;    // bit 0: a bounded wait of a tensor-core kernel ran out
+    int sms = 0;             // streaming multiprocessors of the device
     long long adam_t = 0;
     std::string err;
     std::vector<void *> allocs;
@@ -991,21 +1007,29 @@ int conv_index(const lbm_unet *n, const char kind, int l, int ab) {
 
 template <int BN>
 cudaError_t launch_tc(lbm_unet *n, const nn::ConvOp &op) {
-    constexpr int smem = nn::TC_STAGES * (nn::TC_M * nn::TC_K * 2 + BN * nn::TC_K * 2);
+    constexpr int stages = nn::TC_STAGES * (nn::TC_M * nn::TC_K * 2 + BN * nn::TC_K * 2);
+    const int table = ((op.K + nn::TC_K - 1) / nn::TC_K) * nn::TC_K;  // 8 bytes per 8 K elements
+    if (table > nn::TC_TABLE_MAX) return cudaErrorInvalidValue;
     static bool attr = false;
     if (!attr) {
         cudaError_t e = cudaFuncSetAttribute(nn::k_conv_tc<BN>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             stages + nn::TC_TABLE_MAX);
         if (e != cudaSuccess) return e;
         attr = true;
     }
     const dim3 grid((op.M + nn::TC_M - 1) / nn::TC_M, (op.N + BN - 1) / BN);
-    nn::k_conv_tc<BN><<<grid, nn::TC_THREADS, smem, n->stream>>>(op, n->err_d);
+    nn::k_conv_tc<BN><<<grid, nn::TC_THREADS, stages + table, n->stream>>>(op, n->err_d);
     return cudaGetLastError();
 }
 
+// N tile: the output channels rounded up to 32 or 64, else 128 unless that
+// leaves fewer than two tiles per SM
 cudaError_t launch_conv_tc(lbm_unet *n, const nn::ConvOp &op) {
-    return op.N <= 64 ? launch_tc<64>(n, op) : launch_tc<128>(n, op);
+    const int mt = (op.M + nn::TC_M - 1) / nn::TC_M;
+    if (op.N <= 32) return launch_tc<32>(n, op);
+    if (op.N <= 64 || (long long)mt * ((op.N + 127) / 128) < 2LL * n->sms) return launch_tc<64>(n, op);
+    return launch_tc<128>(n, op);
 }
 
 cudaError_t conv_fwd(lbm_unet *n, const Conv &cv, const bf16 *src, bf16 *dst, int B, int H, int W,
@@ -1081,7 +1105,7 @@ cudaError_t conv_wgrad(lbm_unet *n, const Conv &cv, const bf16 *dz, const bf16 *
         const int bn = cv.co <= 32 ? 32 : (cv.co <= 64 ? 64 : 128);
         const int mt = (op.M + nn::TC_M - 1) / nn::TC_M, nt = (op.N + bn - 1) / bn;
         const int kt = (op.K + nn::TC_K - 1) / nn::TC_K;
-        int z = 2 * 152 * 2 / (mt * nt);
+        int z = 4 * n->sms / (mt * nt);
         if (z < 1) z = 1;
         if (z > kt) z = kt;
         op.kchunk = ((kt + z - 1) / z) * nn::TC_K;
@@ -1307,6 +1331,9 @@ lbm_status lbm_unet_create(const lbm_unet_config *cfg, lbm_unet **out) {
     lbm_unet *n = new (std::nothrow) lbm_unet;
     if (!n) return nfail(nullptr, LBM_ENOMEM, "host allocation failed");
     n->cfg = c;
+    if (cudaDeviceGetAttribute(&n->sms, cudaDevAttrMultiProcessorCount, c.device) != cudaSuccess ||
+        n->sms < 1)
+        n->sms = 1;
     if (c.stream) {
         n->stream = static_cast<cudaStream_t>(c.stream);
     } else {
