@@ -452,8 +452,11 @@ __global__ void __launch_bounds__(TC_THREADS) k_conv_tc(const ConvOp op, int *er
     const int nk = (op.K + TC_K - 1) / TC_K, nkk = op.K >> 3;
     int2 *tab = reinterpret_cast<int2 *>(smem + TC_STAGES * STAGE);
     conv_table(op, tab, nk * (TC_K / 8), tid);
-    // this thread's A row (a pixel) and the 3x3 neighbours of it inside the image
-    const int r = tid & (TC_M - 1), p = m0 + r;
+    // Copies: lanes l and l + 16 of a warp take 8-channel chunks 2j and 2j + 1
+    // of one row, so a warp reads 16 rows x 32 contiguous bytes (whole
+    // sectors) and each 8-lane phase writes 8 rows of one core matrix.
+    // This thread's A row (a pixel) and its 3x3 neighbours inside the image:
+    const int r = 16 * warp + (lane & 15), p = m0 + r;
     uint32_t inb = 0;
     const bf16 *arow = op.src;
     if (p < op.M) {
@@ -465,8 +468,8 @@ __global__ void __launch_bounds__(TC_THREADS) k_conv_tc(const ConvOp op, int *er
         }
         arow = op.src + (size_t)p * op.Cs;
     }
-    // this thread's B row (an output channel)
-    const int rb = tid % BN, nb = n0 + rb;
+    // this thread's B row (an output channel) and first chunk pair
+    const int rb = 16 * (warp % (BN / 16)) + (lane & 15), nb = n0 + rb, kpb = warp / (BN / 16);
     const bf16 *brow = op.w + (size_t)(nb < op.N ? nb : 0) * op.K;
     tc_alloc(&tmem_base, mbar, BN, warp, tid);  // its barrier also publishes the table
     const uint32_t tmem = tmem_base;
@@ -478,14 +481,14 @@ __global__ void __launch_bounds__(TC_THREADS) k_conv_tc(const ConvOp op, int *er
         const int kk0 = kt * (TC_K / 8);
 #pragma unroll
         for (int i = 0; i < TC_M * 8 / TC_THREADS; i++) {
-            const int kg = tid / TC_M + (TC_THREADS / TC_M) * i;
+            const int kg = 2 * i + (lane >> 4);
             const int2 e = tab[kk0 + kg];
             cp16(sa + (r >> 3) * 1024 + kg * 128 + (r & 7) * 16,
                  ((inb >> e.y) & 1u) ? arow + e.x : nullptr, op.src);
         }
 #pragma unroll
         for (int i = 0; i < BN * 8 / TC_THREADS; i++) {
-            const int kg = tid / BN + (TC_THREADS / BN) * i, kk = kk0 + kg;
+            const int kg = 2 * (kpb + (TC_M / BN) * i) + (lane >> 4), kk = kk0 + kg;
             cp16(sb + (rb >> 3) * 1024 + kg * 128 + (rb & 7) * 16,
                  (nb < op.N && kk < nkk) ? brow + 8 * kk : nullptr, op.w);
         }
@@ -537,14 +540,16 @@ __global__ void __launch_bounds__(TC_THREADS) k_wgrad_tc(const WgradTc op, int *
     const int kb = blockIdx.z * op.kchunk, ke = min(op.K, kb + op.kchunk);
     const int nk = ke > kb ? (ke - kb + TC_K - 1) / TC_K : 0;
     const uint32_t base = smem_u32(smem);
-    // this thread copies pixel column pl of every K block, channel groups
-    // g = tid / TC_K + (TC_THREADS / TC_K) i; the (tap, channel) of each A group
-    // is fixed: its offset from the pixel and displacement (dy, dx)
-    const int pl = tid & (TC_K - 1), g0 = tid / TC_K;
+    // This thread copies pixel pl of every K block, channel groups
+    // g = 2 (w / 4 + 2 i) + l / 16 (warp w, lane l): lanes l and l + 16 take
+    // adjacent groups of one pixel (32 contiguous bytes), and each 8-lane
+    // phase writes 8 pixels of one core matrix.  The (tap, channel) of each A
+    // group is fixed: its offset from the pixel and displacement (dy, dx).
+    const int pl = 16 * (warp & 3) + (lane & 15), g0 = 2 * (warp >> 2) + (lane >> 4);
     int aoff[AG], ady[AG], adx[AG];
 #pragma unroll
     for (int i = 0; i < AG; i++) {
-        const int m = m0 + 8 * (g0 + (TC_THREADS / TC_K) * i);
+        const int m = m0 + 8 * (g0 + 4 * i);
         aoff[i] = 0;
         ady[i] = 1 << 20;  // never inside the image
         adx[i] = 0;
@@ -567,7 +572,7 @@ __global__ void __launch_bounds__(TC_THREADS) k_wgrad_tc(const WgradTc op, int *
         const bool pv = p < ke;
 #pragma unroll
         for (int i = 0; i < AG; i++) {
-            const int g = g0 + (TC_THREADS / TC_K) * i;
+            const int g = g0 + 4 * i;
             const bool in = pv && (unsigned)(yy + ady[i]) < (unsigned)op.img.H &&
                             (unsigned)(xx + adx[i]) < (unsigned)op.img.W;
             cp16(sa + (pl >> 3) * (TC_M / 8 * 128) + g * 128 + (pl & 7) * 16,
@@ -575,7 +580,7 @@ __global__ void __launch_bounds__(TC_THREADS) k_wgrad_tc(const WgradTc op, int *
         }
 #pragma unroll
         for (int i = 0; i < BG; i++) {
-            const int g = g0 + (TC_THREADS / TC_K) * i, n = n0 + 8 * g;
+            const int g = g0 + 4 * i, n = n0 + 8 * g;
             cp16(sb + (pl >> 3) * (BN / 8 * 128) + g * 128 + (pl & 7) * 16,
                  (pv && n < op.N) ? op.dz + (size_t)p * op.Co + n : nullptr, op.dz);
         }
