@@ -209,17 +209,20 @@ lbm_status lbm_get_timing(lbm_ctx *ctx, double *stream_collide_ms, int64_t *laun
 /* Kernel launches issued by the library since creation (all kernels). */
 int64_t lbm_launch_count(const lbm_ctx *ctx);
 
-/* Nodes per thread of the advection-collision kernel, as the width of one
- * population word: 0 = 16 bytes (default), 1 = 8 bytes, 2 = 4 bytes.  Every
- * variant evaluates the same expressions; the compiler may fuse multiply-adds
- * differently in each, so results agree to the storage precision's rounding
- * (not always bit for bit).  LBM_EINVAL for other values. */
+/* Launch variant of the advection-collision kernel.  Nodes per thread, as
+ * the width of one population word: 0 = 16 bytes (default), 1 = 8 bytes,
+ * 2 = 4 bytes; 3, 4, 5 = the same widths with the nodes next to solids and
+ * edges (the per-node path) computed by a second kernel after the first
+ * instead of inline.  Every variant evaluates the same expressions; the
+ * compiler may fuse multiply-adds differently in each, so results agree to
+ * the storage precision's rounding (not always bit for bit).  LBM_EINVAL for
+ * other values. */
 lbm_status lbm_set_kernel_variant(lbm_ctx *ctx, int32_t variant);
 int32_t lbm_kernel_variant(const lbm_ctx *ctx);
 
-/* Autotuner: run 1 + steps real steps with each variant of the
+/* Autotuner: run 1 + steps real steps with each of the 6 variants of the
  * advection-collision kernel, timed with CUDA events, and keep the fastest
- * (stored in *best when not NULL).  The simulation advances by 3 (1 + steps)
+ * (stored in *best when not NULL).  The simulation advances by 6 (1 + steps)
  * steps; results do not depend on the variant.  Waits for the stream. */
 lbm_status lbm_autotune(lbm_ctx *ctx, int32_t steps, int32_t *best);
 

@@ -7,9 +7,108 @@ namespace gbm {
 
 namespace {
 
-template <int P, int V, bool FORCE, bool LOCAL, bool WALLS>
+template <int P, int V, bool FORCE, bool LOCAL, bool WALLS, bool DEFER>
 __global__ void __launch_bounds__(SC_BLOCK_X) k_stream_collide(const StepParams p) {
-    sc_tile<P, V, FORCE, LOCAL, false, WALLS>(p, blockIdx.x, blockIdx.y);
+    sc_tile<P, V, FORCE, LOCAL, false, WALLS, DEFER>(p, blockIdx.x, blockIdx.y);
+}
+
+// With the per-node path deferred (variants 3-5), the nodes k_stream_collide
+// leaves to the per-node update (update_node) are computed from the same
+// populations after it, in two kernels:
+//   k_boundary_scan    one block per disk tests the nodes of the disk's box
+//                      against the ring r - 1 <= |x - R| <= r + 2, which holds
+//                      every fluid node with a link into the disk (fluid nodes
+//                      lie outside r, links are at most sqrt 2 long), gathers
+//                      the ring's fluid nodes with a bounced population in
+//                      shared memory and appends them to a device list (one
+//                      atomic per block and chunk);
+//   k_boundary_update  one thread per node of the list, then of the first and
+//                      last columns and, where the vector path does not take
+//                      them, of the wall rows.
+// The list's length is kept per step parity; the update kernel of step t
+// clears the slot of step t + 1.  A node next to two disks (or a disk and an
+// edge) is computed twice, with identical results.  Inline in the vector path
+// these nodes run with one or two active lanes per warp; which way is faster
+// depends on the workload (the autotuner measures both).
+constexpr int BN_BLOCK = 256, BN_CHUNK = 2048;
+
+template <int P, bool LOCAL>
+__global__ void __launch_bounds__(BN_BLOCK) k_boundary_scan(const StepParams p) {
+    __shared__ int list[BN_CHUNK];
+    __shared__ int count, gbase;
+    const Lattice &L = p.L;
+    const DSolid &b = p.S[blockIdx.x];
+    if (!solid_ok(b)) return;  // flagged by the per-solid kernel
+    const long long t = *p.t;
+    int *len = p.bnd + (t & 1);
+    int *out = p.bnd + 2;
+    const int xi = (int)floor(b.x), yi = (int)floor(b.y);
+    const float fx = (float)(b.x - xi), fy = (float)(b.y - yi);
+    const float ro = (float)b.r + 2.f, ri = (float)b.r - 1.f;
+    const float ro2 = ro * ro, ri2 = ri > 0.f ? ri * ri : 0.f;
+    const int h = boundary_half(b.r), bw = 2 * h + 1, n = bw * bw;
+    for (int c0 = 0; c0 < n; c0 += BN_CHUNK) {
+        if (threadIdx.x == 0) count = 0;
+        __syncthreads();
+        const int c1 = min(n, c0 + BN_CHUNK);
+        for (int q = c0 + (int)threadIdx.x; q < c1; q += BN_BLOCK) {
+            const int di = q % bw - h, dj = q / bw - h;
+            const float dx = (float)di - fx, dy = (float)dj - fy, d2 = dx * dx + dy * dy;
+            int x, y;
+            if (d2 >= ri2 && d2 <= ro2 && locate(L, xi + di, yi + dj, x, y)) {
+                const uint16_t fl = p.flags[cell_of(L, x, y)];
+                if (!(fl & 1u) && (fl & 0x1FEu)) list[atomicAdd(&count, 1)] = y * L.pitch + x;
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) gbase = count ? atomicAdd(len, count) : 0;
+        __syncthreads();
+        const int m = count, g0 = gbase;
+        for (int e = (int)threadIdx.x; e < m; e += BN_BLOCK) {
+            if (g0 + e < p.bnd_cap) out[g0 + e] = list[e];
+            else atomicOr(p.status, 16);
+        }
+        __syncthreads();  // list and count are reused by the next chunk
+    }
+}
+
+template <int P, bool FORCE, bool LOCAL>
+__host__ __device__ long long boundary_edge_nodes(const Lattice &L) {
+    long long n = L.nx > 1 ? 2LL * L.ny : (long long)L.ny;
+    if (!walls_on_vector_path<P, LOCAL>() && L.bc_y == LBM_WALL && L.nx > 2) n += 2LL * (L.nx - 2);
+    return n;
+}
+
+template <int P, bool FORCE, bool LOCAL>
+__global__ void __launch_bounds__(BN_BLOCK) k_boundary_update(const StepParams p) {
+    using R = typename Raw<P>::R;
+    const Lattice &L = p.L;
+    const long long t = *p.t;
+    const R *fin = static_cast<const R *>((t & 1) ? p.f1 : p.f0);
+    R *fout = static_cast<R *>((t & 1) ? p.f0 : p.f1);
+    const int nlist = (p.nsolid > 0 && p.bnd) ? min(p.bnd[t & 1], p.bnd_cap) : 0;
+    const int ncol = L.nx > 1 ? 2 * L.ny : L.ny;
+    const long long total = nlist + boundary_edge_nodes<P, FORCE, LOCAL>(L);
+    for (long long e = (long long)blockIdx.x * BN_BLOCK + threadIdx.x; e < total;
+         e += (long long)gridDim.x * BN_BLOCK) {
+        int x, y;
+        if (e < nlist) {
+            const int k = p.bnd[2 + e];
+            x = k % L.pitch;
+            y = k / L.pitch;
+        } else if (e < nlist + ncol) {
+            const int c = (int)(e - nlist);
+            y = L.nx > 1 ? c >> 1 : c;
+            x = (L.nx > 1 && (c & 1)) ? L.nx - 1 : 0;
+        } else {
+            const int c = (int)(e - nlist - ncol), w = L.nx - 2;
+            y = c < w ? 0 : L.ny - 1;
+            x = 1 + (c < w ? c : c - w);
+        }
+        if (!(p.flags[cell_of(L, x, y)] & 1u))
+            update_node<P, FORCE, LOCAL, false>(p, fin, fout, x, y);
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0 && p.bnd) p.bnd[(t + 1) & 1] = 0;
 }
 
 // Open-channel columns of every row, on the populations of t+1.
@@ -24,35 +123,61 @@ __global__ void k_open_columns(const StepParams p) {
 
 // Walled domains (y walls) with rho_w = rho0 in FP32/FP64 take the kernel
 // whose vector path also covers the wall rows.
-template <int P, int V, bool FORCE, bool LOCAL>
+template <int P, int V, bool FORCE, bool LOCAL, bool DEFER>
 cudaError_t launch_sc(const StepParams &p, cudaStream_t st) {
     dim3 grid((p.L.nx + SC_BLOCK_X * V - 1) / (SC_BLOCK_X * V), p.L.ny);
     if (walls_on_vector_path<P, LOCAL>() && p.L.bc_y == LBM_WALL)
-        k_stream_collide<P, V, FORCE, LOCAL, walls_on_vector_path<P, LOCAL>()>
+        k_stream_collide<P, V, FORCE, LOCAL, walls_on_vector_path<P, LOCAL>(), DEFER>
             <<<grid, SC_BLOCK_X, 0, st>>>(p);
     else
-        k_stream_collide<P, V, FORCE, LOCAL, false><<<grid, SC_BLOCK_X, 0, st>>>(p);
+        k_stream_collide<P, V, FORCE, LOCAL, false, DEFER><<<grid, SC_BLOCK_X, 0, st>>>(p);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess || !DEFER) return e;
+    if (p.nsolid > 0) {
+        k_boundary_scan<P, LOCAL><<<p.nsolid, BN_BLOCK, 0, st>>>(p);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) return e;
+    }
+    const long long most = (p.nsolid > 0 ? p.bnd_cap : 0) + boundary_edge_nodes<P, FORCE, LOCAL>(p.L);
+    long long blocks = (most + BN_BLOCK - 1) / BN_BLOCK;
+    if (blocks > 8LL * sms) blocks = 8LL * sms;
+    if (blocks < 1) blocks = 1;
+    k_boundary_update<P, FORCE, LOCAL><<<(unsigned)blocks, BN_BLOCK, 0, st>>>(p);
     return cudaGetLastError();
 }
 
-template <int P, int V>
+template <int P, int V, bool DEFER>
 cudaError_t launch_sc_v(const StepParams &p, cudaStream_t st) {
     const bool force = p.body_x != 0.0 || p.body_y != 0.0;
     const bool local = p.rho_w_mode == LBM_RHOW_LOCAL;
     if (force)
-        return local ? launch_sc<P, V, true, true>(p, st) : launch_sc<P, V, true, false>(p, st);
-    return local ? launch_sc<P, V, false, true>(p, st) : launch_sc<P, V, false, false>(p, st);
+        return local ? launch_sc<P, V, true, true, DEFER>(p, st)
+                     : launch_sc<P, V, true, false, DEFER>(p, st);
+    return local ? launch_sc<P, V, false, true, DEFER>(p, st)
+                 : launch_sc<P, V, false, false, DEFER>(p, st);
 }
 
 // Node widths per thread: variant 0 = one 16-byte word per population,
-// variant 1 = 8 bytes, variant 2 = 4 bytes.
+// variant 1 = 8 bytes, variant 2 = 4 bytes; variants 3-5 the same widths
+// with the per-node path deferred to k_boundary_scan / k_boundary_update.
 template <int P>
 cudaError_t launch_sc_p(const StepParams &p, cudaStream_t st) {
     constexpr int V16 = 16 / (int)sizeof(typename Raw<P>::R);
+    constexpr int V4 = V16 / 4 > 0 ? V16 / 4 : 1;
     switch (p.sc_variant) {
-        case 1: return launch_sc_v<P, V16 / 2>(p, st);
-        case 2: return launch_sc_v<P, (V16 / 4 > 0 ? V16 / 4 : 1)>(p, st);
-        default: return launch_sc_v<P, V16>(p, st);
+        case 1: return launch_sc_v<P, V16 / 2, false>(p, st);
+        case 2: return launch_sc_v<P, V4, false>(p, st);
+        case 3: return launch_sc_v<P, V16, true>(p, st);
+        case 4: return launch_sc_v<P, V16 / 2, true>(p, st);
+        case 5: return launch_sc_v<P, V4, true>(p, st);
+        default: return launch_sc_v<P, V16, false>(p, st);
     }
 }
 

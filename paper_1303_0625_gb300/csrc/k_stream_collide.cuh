@@ -63,6 +63,24 @@ __device__ __forceinline__ void put(unsigned short &d, float v) {
     d = __half_as_ushort(__float2half_rn(v));
 }
 
+// two adjacent values of a population plane at once (FP16: one half2)
+__device__ __forceinline__ void put2(float *d, float a, float b) {
+    d[0] = a;
+    d[1] = b;
+}
+__device__ __forceinline__ void put2(unsigned short *d, float a, float b) {
+    *reinterpret_cast<__half2 *>(d) = __floats2half2_rn(a, b);
+}
+
+// Paired FP32 arithmetic: one instruction for the same operation on two nodes.
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) {
+    return __fadd2_rn(a, make_float2(-b.x, -b.y));
+}
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 dup2(float a) { return make_float2(a, a); }
+
 __device__ __forceinline__ double shfl_up1(double v) { return __shfl_up_sync(0xffffffffu, v, 1); }
 __device__ __forceinline__ float shfl_up1(float v) { return __shfl_up_sync(0xffffffffu, v, 1); }
 __device__ __forceinline__ unsigned short shfl_up1(unsigned short v) {
@@ -300,7 +318,10 @@ __device__ __noinline__ void update_node(const StepParams &p, const typename Raw
 template <int P, bool LOCAL>
 __host__ __device__ constexpr bool walls_on_vector_path() { return !LOCAL && P != LBM_FP16_DEV; }
 
-template <int P, int V, bool FORCE, bool LOCAL, bool OPEN, bool WALLS = false>
+// DEFER: the per-node path is left to a later pass over the nodes next to
+// solids and edges (the single-domain kernel); otherwise each thread runs it
+// for its own nodes at the end of the tile.
+template <int P, int V, bool FORCE, bool LOCAL, bool OPEN, bool WALLS = false, bool DEFER = false>
 __device__ __forceinline__ void sc_tile(const StepParams &p, int bx, int y) {
     static_assert(!WALLS || walls_on_vector_path<P, LOCAL>(), "wall rows need rho0 and R == C");
     using R = typename Raw<P>::R;
@@ -397,9 +418,66 @@ __device__ __forceinline__ void sc_tile(const StepParams &p, int bx, int y) {
     cvt(cx(i) == 0 ? raw[i].r[j] \
                    : (cx(i) == 1 ? ((j) == 0 ? halo[i] : raw[i].r[(j) - 1]) \
                                  : ((j) == V - 1 ? halo[i] : raw[i].r[(j) + 1])))
+    uint32_t slow = 0;  // bit j: node j needs the per-node path
+    // node j needs the per-node path, or has a non-physical state (flagged)
+    auto classify = [&](int j, C r, C vx, C vy) {
+        const uint16_t f = fl.f[j];
+        const int x = x0 + j;
+        if (!(f & 1u) && ((f & 0x1FEu & ~wall_bits) || x == 0 || x == L.nx - 1)) slow |= 1u << j;
+        else if (!(f & 1u) && x < L.nx &&
+                 (!(r > (C)0) || !(fabs(vx) < (C)1e30) || !(fabs(vy) < (C)1e30)))
+            atomicOr(p.status, 1);
+    };
+    if constexpr (Prec<P>::dev && !FORCE && V % 2 == 0) {
+        // Deviation form, two nodes per instruction (FADD2 / FMUL2 / FFMA2).
+        // With E_i = s0 + rho (3 e_i.u + 4.5 (e_i.u)^2 - 1.5 u.u) the
+        // equilibrium deviation is w_i E_i, and BGK gives
+        // (1 - omega) g_i + omega w_i E_i.  Opposite populations share
+        // A = s0 - 1.5 rho u.u and the even part 4.5 rho (e.u)^2; the odd part
+        // 3 rho e.u changes sign.
+        const float om = p.omega_f;
+        const float2 omc = dup2(1.f - om);
+        Pack<R, V> o[9];
+#pragma unroll
+        for (int j = 0; j < V; j += 2) {
+            float2 g[9];
+#pragma unroll
+            for (int i = 0; i < 9; i++) g[i] = make_float2(PULL(i, j), PULL(i, j + 1));
+            const float2 s0 = add2(add2(add2(g[0], g[1]), add2(g[2], g[3])),
+                                   add2(add2(g[4], g[5]), add2(add2(g[6], g[7]), g[8])));
+            const float2 jx = sub2(add2(add2(g[1], g[5]), g[8]), add2(add2(g[3], g[6]), g[7]));
+            const float2 jy = sub2(add2(add2(g[2], g[5]), g[6]), add2(add2(g[4], g[7]), g[8]));
+            const float2 rho = add2(dup2(1.f), s0);
+            const float2 inv = make_float2(1.f / rho.x, 1.f / rho.y);
+            const float2 ux = mul2(jx, inv), uy = mul2(jy, inv);
+            classify(j, rho.x, ux.x, uy.x);
+            classify(j + 1, rho.y, ux.y, uy.y);
+            const float2 A = fma2(mul2(dup2(-1.5f), rho), fma2(ux, ux, mul2(uy, uy)), s0);
+            float2 out[9];
+            out[0] = fma2(dup2(om * wgt<float>(0)), A, mul2(omc, g[0]));
+            // (i, opp(i)) with e_i.u = eu: (1, 3) ux, (2, 4) uy, (5, 7) ux + uy, (6, 8) uy - ux
+            auto pair = [&](int i, int k, float2 eu) {
+                const float2 q = mul2(rho, eu);
+                const float2 sym = fma2(q, mul2(dup2(4.5f), eu), A);
+                const float2 ow = dup2(om * wgt<float>(i));
+                out[i] = fma2(ow, fma2(dup2(3.f), q, sym), mul2(omc, g[i]));
+                out[k] = fma2(ow, fma2(dup2(-3.f), q, sym), mul2(omc, g[k]));
+            };
+            pair(1, 3, ux);
+            pair(2, 4, uy);
+            pair(5, 7, add2(ux, uy));
+            pair(6, 8, sub2(uy, ux));
+            const bool s_a = fl.f[j] & 1u, s_b = fl.f[j + 1] & 1u;  // solid nodes store zeros
+#pragma unroll
+            for (int i = 0; i < 9; i++)
+                put2(&o[i].r[j], s_a ? 0.f : out[i].x, s_b ? 0.f : out[i].y);
+        }
+#pragma unroll
+        for (int i = 0; i < 9; i++)
+            *reinterpret_cast<typename Word<sizeof(R) * V>::T *>(fout + i * plane + r0 + x0) = o[i].u;
+    } else {
     // moments of every node from the pulled populations
     C s0[V], ux[V], uy[V], rho[V];
-    uint32_t slow = 0;  // bit j: node j needs the per-node path
 #pragma unroll
     for (int j = 0; j < V; j++) {
         C a = 0, jx = 0, jy = 0;
@@ -416,12 +494,7 @@ __device__ __forceinline__ void sc_tile(const StepParams &p, int bx, int y) {
         rho[j] = r;
         ux[j] = FORCE ? (jx + (C)0.5 * pick<C>(p.body_x, p.body_xf)) * inv : jx * inv;
         uy[j] = FORCE ? (jy + (C)0.5 * pick<C>(p.body_y, p.body_yf)) * inv : jy * inv;
-        const uint16_t f = fl.f[j];
-        const int x = x0 + j;
-        if (!(f & 1u) && ((f & 0x1FEu & ~wall_bits) || x == 0 || x == L.nx - 1)) slow |= 1u << j;
-        else if (!(f & 1u) && x < L.nx &&
-                 (!(r > (C)0) || !(fabs(ux[j]) < (C)1e30) || !(fabs(uy[j]) < (C)1e30)))
-            atomicOr(p.status, 1);
+        classify(j, r, ux[j], uy[j]);
     }
     // relax towards equilibrium, one population plane at a time
     const C om = pick<C>(p.omega, p.omega_f);
@@ -447,12 +520,15 @@ __device__ __forceinline__ void sc_tile(const StepParams &p, int bx, int y) {
         }
         *reinterpret_cast<typename Word<sizeof(R) * V>::T *>(fout + i * plane + r0 + x0) = o.u;
     }
+    }
 #undef PULL
     // nodes next to a solid or a wall and the first/last column
-    while (slow) {
-        const int j = __ffs(slow) - 1;
-        slow &= slow - 1;
-        update_node<P, FORCE, LOCAL, OPEN>(p, fin, fout, x0 + j, y);
+    if constexpr (!DEFER) {
+        while (slow) {
+            const int j = __ffs(slow) - 1;
+            slow &= slow - 1;
+            update_node<P, FORCE, LOCAL, OPEN>(p, fin, fout, x0 + j, y);
+        }
     }
 }
 

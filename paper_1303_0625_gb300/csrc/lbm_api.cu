@@ -29,6 +29,9 @@ struct lbm_ctx {
     int nsolid = 0;
     int *moving_d = nullptr;
     int moving_cap = 0;
+    int *bnd_d = nullptr;  // deferred per-node path: {length by step parity, list}
+    int bnd_cap = 0;
+    long long bnd_need = 0;  // sum over disks of their box sizes
     std::vector<int> moving;
     std::vector<uint8_t> is_moving;
     double *ring = nullptr;
@@ -50,6 +53,7 @@ struct lbm_ctx {
     double timed_ms = 0.0;
     int64_t timed_launches = 0;
     int64_t launches = 0;
+    int64_t graph_launches = 0;  // kernel launches in one replay of gexec
     // staging buffer for host transfers
     void *scratch = nullptr;
     size_t scratch_bytes = 0;
@@ -122,6 +126,8 @@ StepParams params(const lbm_ctx *c) {
     p.refill = g.refill;
     p.precision = g.precision;
     p.sc_variant = c->sc_variant;
+    p.bnd = c->bnd_d;
+    p.bnd_cap = c->bnd_cap;
     p.omega_f = (float)(1.0 / g.tau);
     p.body_xf = (float)g.body_force[0];
     p.body_yf = (float)g.body_force[1];
@@ -143,7 +149,7 @@ void release(lbm_ctx *c) {
     drop_graph(c);
     for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
     void *bufs[] = {c->f[0], c->f[1], c->owner, c->prev, c->flags, c->solids, c->moving_d,
-                    c->ring, c->t_d, c->status_d, c->bar_d, c->scratch};
+                    c->ring, c->t_d, c->status_d, c->bar_d, c->scratch, c->bnd_d};
     for (void *b : bufs)
         if (b) cudaFree(b);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
@@ -206,7 +212,7 @@ lbm_status enqueue_step(lbm_ctx *c, const StepParams &p, bool timed) {
     }
     if (p.nsolid > 0) CK(c, gbm::launch_solids(p, p.nmoving > 0 ? gbm::SOLIDS_REMASK : 0, c->stream));
     else CK(c, gbm::launch_tick(p, c->stream));
-    c->launches += 2;
+    c->launches += gbm::stream_collide_launches(p) + 1;
     return LBM_OK;
 }
 
@@ -234,6 +240,7 @@ lbm_status check_status(lbm_ctx *c) {
         cudaMemsetAsync(c->bar_d, 0, 2 * sizeof(unsigned int), c->stream);
         return fail(c, LBM_ETIMEOUT, "a grid-wide barrier of the per-solid kernel timed out");
     }
+    if (st & 16) return fail(c, LBM_ESTATE, "the list of nodes next to solids overflowed");
     return LBM_OK;
 }
 
@@ -411,6 +418,21 @@ lbm_status lbm_add_solid(lbm_ctx *c, const lbm_disk *d, int32_t *id_out) {
     c->is_moving.push_back(translates(s) ? 1 : 0);
     lbm_status st = upload_moving(c);
     if (st != LBM_OK) return st;
+    // room in the deferred per-node list for the new disk's box
+    const long long h = gbm::boundary_half(d->r);
+    c->bnd_need += (2 * h + 1) * (2 * h + 1);
+    if (c->bnd_need > c->bnd_cap) {
+        if (c->bnd_need > (1LL << 30)) return fail(c, LBM_EINVAL, "solids too large for the node list");
+        long long cap = c->bnd_cap ? c->bnd_cap : 4096;
+        while (cap < c->bnd_need) cap *= 2;
+        CK(c, cudaStreamSynchronize(c->stream));
+        if (c->bnd_d) CK(c, cudaFree(c->bnd_d));
+        c->bnd_d = nullptr;
+        c->bnd_cap = 0;
+        CK(c, cudaMalloc(&c->bnd_d, (size_t)(cap + 2) * sizeof(int)));
+        CK(c, cudaMemsetAsync(c->bnd_d, 0, 2 * sizeof(int), c->stream));
+        c->bnd_cap = (int)cap;
+    }
     StepParams p = params(c);
     CK(c, gbm::launch_stamp_solid(p, id, c->stream));
     c->launches += 2;
@@ -440,6 +462,7 @@ lbm_status lbm_step(lbm_ctx *c, int64_t n) {
                         return st;
                     }
                 }
+                c->graph_launches = c->launches - before;
                 c->launches = before;  // counted when the graph is launched
                 CK(c, cudaStreamEndCapture(c->stream, &graph));
                 cudaError_t e = cudaGraphInstantiate(&c->gexec, graph, 0);
@@ -447,7 +470,7 @@ lbm_status lbm_step(lbm_ctx *c, int64_t n) {
                 CK(c, e);
             }
             CK(c, cudaGraphLaunch(c->gexec, c->stream));
-            c->launches += (c->cfg.bc_x == LBM_OPEN ? 3 : 2) * (int64_t)c->graph_steps;
+            c->launches += c->graph_launches;
             done += c->graph_steps;
         }
     }
@@ -772,9 +795,11 @@ lbm_status lbm_get_timing(lbm_ctx *c, double *ms, int64_t *launches) {
 int64_t lbm_launch_count(const lbm_ctx *c) { return c ? c->launches : -1; }
 
 lbm_status lbm_set_kernel_variant(lbm_ctx *c, int32_t variant) {
-    if (!c || variant < 0 || variant > 2) return LBM_EINVAL;
+    if (!c || variant < 0 || variant >= gbm::KERNEL_VARIANTS) return LBM_EINVAL;
     drop_graph(c);
     c->sc_variant = variant;
+    // the deferred list's lengths are kept only while the deferred path runs
+    if (c->bnd_d) CK(c, cudaMemsetAsync(c->bnd_d, 0, 2 * sizeof(int), c->stream));
     return LBM_OK;
 }
 
@@ -790,9 +815,10 @@ lbm_status lbm_autotune(lbm_ctx *c, int32_t steps, int32_t *best) {
     if (st != LBM_OK) return st;
     double best_ms = 0.0;
     int best_v = 0;
-    for (int v = 0; v <= 2; v++) {
+    for (int v = 0; v < gbm::KERNEL_VARIANTS; v++) {
         c->sc_variant = v;
         drop_graph(c);
+        if (c->bnd_d) CK(c, cudaMemsetAsync(c->bnd_d, 0, 2 * sizeof(int), c->stream));
         c->timing = true;
         c->timed_ms = 0.0;
         c->timed_launches = 0;
@@ -810,6 +836,8 @@ lbm_status lbm_autotune(lbm_ctx *c, int32_t steps, int32_t *best) {
         }
     }
     c->sc_variant = best_v;
+    drop_graph(c);
+    if (c->bnd_d) CK(c, cudaMemsetAsync(c->bnd_d, 0, 2 * sizeof(int), c->stream));
     c->timing = was_timing;
     c->timed_ms = keep_ms;
     c->timed_launches = keep_n;

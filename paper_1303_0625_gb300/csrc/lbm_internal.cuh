@@ -83,7 +83,14 @@ struct StepParams {
     float omega_f, body_xf, body_yf, rho0_f;  // FP32 copies for the FP32 kernels
     float wall_ux0_f, wall_ux1_f, umax_f;
     unsigned int *bar;        // grid barrier of the per-solid kernel: {count, generation}
+    int *bnd;                 // deferred per-node path: {length at even t, at odd t, list...}
+    int bnd_cap;              // capacity of the list
 };
+
+// Half-width of the box around floor(R) that holds the ring r - 1 <= |x - R|
+// <= r + 2 of a disk (R within one node of floor(R)); the box has
+// (2 h + 1)^2 nodes, which bounds the disk's entries in the deferred list.
+__host__ __device__ inline int boundary_half(double r) { return (int)ceil(r) + 3; }
 
 template <class C> __device__ __forceinline__ C pick(double d, float f);
 template <> __device__ __forceinline__ double pick<double>(double d, float) { return d; }
@@ -299,6 +306,12 @@ struct BatchState {
 };
 
 // k_stream_collide.cu
+// the fused advection-collision kernel, and with variants 3-5 the pass over
+// the nodes it leaves to the per-node update
+constexpr int KERNEL_VARIANTS = 6;
+inline int stream_collide_launches(const StepParams &p) {
+    return p.sc_variant >= 3 ? (p.nsolid > 0 ? 3 : 2) : 1;
+}
 cudaError_t launch_stream_collide(const StepParams &p, cudaStream_t st);
 // open channel: columns 0 and nx-1 of the populations just written (t+1)
 cudaError_t launch_open_columns(const StepParams &p, cudaStream_t st);

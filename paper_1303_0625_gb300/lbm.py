@@ -669,6 +669,9 @@ class Lattice:
     def set_kernel_variant(self, variant: int):
         lbm_set_kernel_variant(self._h, variant)
 
+    def kernel_variant(self) -> int:
+        return lbm_kernel_variant(self._h)
+
     def autotune(self, steps: int = 4) -> int:
         return lbm_autotune(self._h, steps)
 

@@ -57,11 +57,13 @@ def seeded_f(w, seed, amp=0.01):
     return f
 
 
-def run_pair(w, steps, precision="fp64", perturb=None, graph=0):
+def run_pair(w, steps, precision="fp64", perturb=None, graph=0, variant=None):
     o = make_oracle(w)
     g = make_gpu(w, precision, ring=max(steps, 1))
     if graph:
         g.set_graph(graph)
+    if variant is not None:
+        g.set_kernel_variant(variant)
     if perturb is not None:
         f0 = seeded_f(w, perturb)
         o.set_f(f0)
