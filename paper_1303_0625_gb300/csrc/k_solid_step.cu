@@ -579,8 +579,10 @@ __device__ void phase_set(const StepParams &p, int s, int lane) {
         });
 }
 
-// prev := owner on the ring; the solid's state becomes t+1.
-__device__ void phase_sync(const StepParams &p, int s, int lane) {
+// prev := owner on the ring; the momentum of the solid's covered and fresh
+// nodes (its segment of ev_mom, summed in queue order) is booked into the
+// force record of t+1; the solid's state becomes t+1.
+__device__ void phase_sync(const StepParams &p, int s, int lane, long long t1) {
     DSolid &b = p.S[s];
     const DiskTest in0(b.x, b.y, b.r), in1(b.xn, b.yn, b.r);
     const Centre c0(b.x, b.y), c1(b.xn, b.yn);
@@ -604,6 +606,16 @@ __device__ void phase_sync(const StepParams &p, int s, int lane) {
         });
     __syncwarp();
     if (lane == 0) {
+        double acc[3] = {0.0, 0.0, 0.0};
+        for (int e = b.ev_off; e < b.ev_off + b.ev_n; e++) {
+            acc[0] += p.ev_mom[3 * e];
+            acc[1] += p.ev_mom[3 * e + 1];
+            acc[2] += p.ev_mom[3 * e + 2];
+        }
+        b.pend[0] = acc[0];
+        b.pend[1] = acc[1];
+        b.pend[2] = acc[2];
+        b.pend_t = t1;
         b.x = b.xn;
         b.y = b.yn;
         b.xw = b.xnw;
@@ -626,16 +638,12 @@ __device__ void phase_sync(const StepParams &p, int s, int lane) {
 
 // ------------------------------------------------------------ phase C
 
-constexpr int EVENTS = 256;  // covered/fresh nodes a warp can queue per solid and step
+constexpr int EVENTS = SOLID_EVENTS;
 
 // Ring of solid s: flags of nodes whose solidity changed (as they are found),
-// then the covered and fresh nodes (queued per warp in a fixed order and
-// handled one per lane).
-template <int P>
-__device__ void phase_changes(const StepParams &p, int s, int lane, long long t1, void *fnew,
-                              int *queue, int &qn) {
-    using C = typename Prec<P>::C;
-    using S = typename Prec<P>::S;
+// and the covered and fresh nodes, queued per warp in lane order and
+// published as the solid's segment of the step's event list.
+__device__ void phase_changes(const StepParams &p, int s, int lane, int *queue, int &qn) {
     DSolid &b = p.S[s];
     const Lattice &L = p.L;
     const DiskTest in0(b.x, b.y, b.r), in1(b.xn, b.yn, b.r);
@@ -693,12 +701,40 @@ __device__ void phase_changes(const StepParams &p, int s, int lane, long long t1
         });
     __syncwarp();
     const int n = min(qn, EVENTS);
+    // publish the events: one segment of the step's event list per solid
+    int off = 0;
+    if (lane == 0 && n) off = atomicAdd(p.ev_len, n);
+    off = __shfl_sync(FULL, off, 0);
+    const bool fits = off + n <= p.ev_cap;
+    for (int e = lane; e < n; e += 32) {
+        if (fits) p.ev[off + e] = make_int2(queue[e], s);
+    }
+    if (lane == 0) {
+        if (!fits) atomicOr(p.status, 8);
+        b.ev_off = off;
+        b.ev_n = fits ? n : 0;
+    }
+    __syncwarp();
+}
+
+// One covered or fresh node of the step's event list, with the whole warp:
+// the refill of a fresh node (Sec. IV.B), then the node's momentum (covered:
+// post-collision, into the solid; fresh: refilled, out of it) and its torque
+// about the solid's new centre, into the event's slot of ev_mom.  Events are
+// independent: a refill reads only nodes that were fluid before and after the
+// move.
+template <int P>
+__device__ void phase_event(const StepParams &p, int e, int lane, void *fnew) {
+    using C = typename Prec<P>::C;
+    using S = typename Prec<P>::S;
+    const Lattice &L = p.L;
     const S *fsn = static_cast<const S *>(fnew);
     const int pl = (int)L.plane;
+    const int2 ev = p.ev[e];
+    const int code = ev.x;
+    const DSolid &b = p.S[ev.y];
     double acc[3] = {0.0, 0.0, 0.0};
-    // one queued node at a time, with the whole warp
-    for (int e = 0; e < n; e++) {
-        const int code = queue[e];
+    {
         const int k = code >> 1;
         const int x = k % L.pitch, y = k / L.pitch;
         if (code & 1) {
@@ -780,10 +816,9 @@ __device__ void phase_changes(const StepParams &p, int s, int lane, long long t1
         }
     }
     if (lane == 0) {
-        b.pend[0] = acc[0];
-        b.pend[1] = acc[1];
-        b.pend[2] = acc[2];
-        b.pend_t = t1;
+        p.ev_mom[3 * e] = acc[0];
+        p.ev_mom[3 * e + 1] = acc[1];
+        p.ev_mom[3 * e + 2] = acc[2];
     }
     __syncwarp();
 }
@@ -820,12 +855,17 @@ __global__ void __launch_bounds__(SW_BLOCK) k_solids_step(const StepParams p, in
     grid_sync(p);
     for (int m = gw; m < p.nmoving; m += nw) {
         const int s = p.moving[m];
-        if (solid_ok(p.S[s])) phase_changes<P>(p, s, lane, t + 1, fnew, queue[wib], qn[wib]);
+        if (solid_ok(p.S[s])) phase_changes(p, s, lane, queue[wib], qn[wib]);
     }
     grid_sync(p);
+    // the step's covered and fresh nodes, dealt to every warp of the grid
+    const int nev = min(*(volatile int *)p.ev_len, p.ev_cap);
+    for (int e = gw; e < nev; e += nw) phase_event<P>(p, e, lane, fnew);
+    grid_sync(p);
+    if (blockIdx.x == 0 && threadIdx.x == 0) *p.ev_len = 0;  // every warp has read it
     for (int m = gw; m < p.nmoving; m += nw) {
         const int s = p.moving[m];
-        if (solid_ok(p.S[s])) phase_sync(p, s, lane);
+        if (solid_ok(p.S[s])) phase_sync(p, s, lane, t + 1);
     }
 }
 

@@ -29,6 +29,8 @@ struct lbm_ctx {
     int nsolid = 0;
     int *moving_d = nullptr;
     int moving_cap = 0;
+    void *ev_d = nullptr;  // covered/fresh events: {length, pad}, int2 list, 3 doubles each
+    int ev_cap = 0;
     int *bnd_d = nullptr;  // deferred per-node path: {length by step parity, list}
     int bnd_cap = 0;
     long long bnd_need = 0;  // sum over disks of their box sizes
@@ -128,6 +130,12 @@ StepParams params(const lbm_ctx *c) {
     p.sc_variant = c->sc_variant;
     p.bnd = c->bnd_d;
     p.bnd_cap = c->bnd_cap;
+    p.ev_len = static_cast<int *>(c->ev_d);
+    p.ev = c->ev_d ? reinterpret_cast<int2 *>(static_cast<char *>(c->ev_d) + 16) : nullptr;
+    p.ev_mom = c->ev_d ? reinterpret_cast<double *>(static_cast<char *>(c->ev_d) + 16 +
+                                                    (size_t)c->ev_cap * sizeof(int2))
+                       : nullptr;
+    p.ev_cap = c->ev_cap;
     p.omega_f = (float)(1.0 / g.tau);
     p.body_xf = (float)g.body_force[0];
     p.body_yf = (float)g.body_force[1];
@@ -149,7 +157,7 @@ void release(lbm_ctx *c) {
     drop_graph(c);
     for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
     void *bufs[] = {c->f[0], c->f[1], c->owner, c->prev, c->flags, c->solids, c->moving_d,
-                    c->ring, c->t_d, c->status_d, c->bar_d, c->scratch, c->bnd_d};
+                    c->ring, c->t_d, c->status_d, c->bar_d, c->scratch, c->bnd_d, c->ev_d};
     for (void *b : bufs)
         if (b) cudaFree(b);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
@@ -184,6 +192,20 @@ lbm_status upload_moving(lbm_ctx *c) {
     if (!c->moving.empty())
         CK(c, cudaMemcpyAsync(c->moving_d, c->moving.data(), c->moving.size() * sizeof(int),
                               cudaMemcpyHostToDevice, c->stream));
+    // event list of the per-solid kernel: SOLID_EVENTS per moving solid
+    const long long need = (long long)c->moving.size() * gbm::SOLID_EVENTS;
+    if (need > c->ev_cap) {
+        long long cap = c->ev_cap ? c->ev_cap : 64LL * gbm::SOLID_EVENTS;
+        while (cap < need) cap *= 2;
+        if (cap > (1LL << 28)) return fail(c, LBM_EINVAL, "too many moving solids");
+        CK(c, cudaStreamSynchronize(c->stream));
+        if (c->ev_d) CK(c, cudaFree(c->ev_d));
+        c->ev_d = nullptr;
+        c->ev_cap = 0;
+        CK(c, cudaMalloc(&c->ev_d, 16 + (size_t)cap * (sizeof(int2) + 3 * sizeof(double))));
+        CK(c, cudaMemsetAsync(c->ev_d, 0, 16, c->stream));
+        c->ev_cap = (int)cap;
+    }
     CK(c, cudaStreamSynchronize(c->stream));
     return LBM_OK;
 }

@@ -52,7 +52,11 @@ struct DSolid {
     float xwr, ywr;    // ... and the FP32 remainder, for FP32 lever arms
     int motion;
     int near;          // another disk may share a node with this one at t or t+1
+    int ev_off, ev_n;  // this step's segment of the covered/fresh event list
 };
+
+// covered/fresh nodes one solid can queue per step
+constexpr int SOLID_EVENTS = 256;
 
 struct Lattice {
     int nx, ny, pitch; // pitch = elements per row of every 2-D plane
@@ -83,6 +87,10 @@ struct StepParams {
     float omega_f, body_xf, body_yf, rho0_f;  // FP32 copies for the FP32 kernels
     float wall_ux0_f, wall_ux1_f, umax_f;
     unsigned int *bar;        // grid barrier of the per-solid kernel: {count, generation}
+    int2 *ev;                 // covered/fresh events of the step: {node code, solid}
+    double *ev_mom;           // [3] momentum and torque of each event
+    int *ev_len;              // events published this step (cleared after use)
+    int ev_cap;
     int *bnd;                 // deferred per-node path: {length at even t, at odd t, list...}
     int bnd_cap;              // capacity of the list
 };
