@@ -48,6 +48,9 @@ def parse():
     ap.add_argument("--nx", type=int, default=8192)
     ap.add_argument("--ny", type=int, default=4096)
     ap.add_argument("--ndisk", type=int, default=2000)
+    ap.add_argument("--variant", type=int, default=-1,
+                    help="launch variant of the advection-collision pass (0-5, see lbm.h); "
+                         "default: the autotuner's choice")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the e2e pass, the other precisions and the CPU baseline")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
@@ -193,9 +196,11 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def captured_traffic(precision, nx, ny):
-    """DRAM bytes per launch of the advection-collision kernel from the
-    committed ncu summary, if it was taken on the current kernel source."""
+def captured_traffic(precision, nx, ny, variant):
+    """DRAM bytes per step of the advection-collision pass (the fused kernel,
+    plus the slow-node kernels when the variant defers them) from the
+    committed ncu summary, if it was taken on the current kernel source with
+    the same inline or deferred slow-node path."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as fh:
@@ -203,6 +208,8 @@ def captured_traffic(precision, nx, ny):
     except (OSError, ValueError):
         return None
     if not rec or rec.get("kernel_sha256_16") != kernel_source_hash():
+        return None
+    if bool(rec.get("deferred", False)) != (variant >= 3):
         return None
     # captured on a smaller domain: traffic scales with the node count
     return rec["dram_bytes_per_launch"] * (nx * ny) / (rec["nx"] * rec["ny"])
@@ -231,7 +238,11 @@ def run_ours(a, ws, rank, local):
     def measure(precision, steps, warmup, sample_clocks):
         lat = G.Lattice.from_workload(w, precision=G.PRECISION_NAMES[precision], device=local,
                                       stream=stream.cuda_stream, force_ring=512)
-        variant = lat.autotune(4)  # picks the node width of the advection-collision kernel
+        if a.variant >= 0:
+            lat.set_kernel_variant(a.variant)
+            variant = a.variant
+        else:
+            variant = lat.autotune(4)  # node width and slow-node path of the fused pass
         lat.step(warmup)
         lat.sync()
         lat.set_timing(True)
@@ -265,10 +276,12 @@ def run_ours(a, ws, rank, local):
     bytes_launch = algorithmic_bytes(a.precision, cells)
     achieved = bytes_launch / (main["k1_avg_ms"] / 1e3) / 1e9
     peak = float(peaks.get("hbm_gbs", FALLBACK_HBM_GBS))
-    traffic = captured_traffic(a.precision, a.nx, a.ny)
+    traffic = captured_traffic(a.precision, a.nx, a.ny, main["variant"])
+    kernels = ("k_stream_collide + k_boundary_scan + k_boundary_update" if main["variant"] >= 3
+               else "k_stream_collide")
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "traffic": traffic,
-                "kernel": "k_stream_collide", "peak_source": f"{peak_kind} hbm_gbs",
+                "kernel": kernels, "peak_source": f"{peak_kind} hbm_gbs",
                 "algorithmic_bytes_per_launch": bytes_launch,
                 "bytes_per_node": 18 * STORAGE_BYTES[a.precision] + 2,
                 "avg_launch_ms": round(main["k1_avg_ms"], 5),
