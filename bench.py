@@ -67,6 +67,9 @@ def parse():
                     help="run the 512-channel sweep until every case retires or STEPS steps")
     ap.add_argument("--unet", action="store_true",
                     help="time the warm-start network's forward pass and training step")
+    ap.add_argument("--galilean", type=int, default=0, metavar="STEPS",
+                    help="free-disk sedimentation in frames moving at V (Sec. III.A), driven by "
+                         "Eq. 5 and by Eq. 4: trajectory deviations from V = 0 after STEPS steps")
     ap.add_argument("--batch-only", action="store_true",
                     help="measure only the cylinder-sweep batch and print its record")
     ap.add_argument("--batch-warmup", type=int, default=100)
@@ -724,6 +727,58 @@ def run_reference(a, ws, rank):
     print(json.dumps(line), flush=True)
 
 
+def run_galilean(a, local):
+    """Galilean test of Sec. III.A on the paper's geometry: a channel 120 wide
+    and 1200 long (periodic along its axis x, walls at y = -1/2 and 119.5),
+    tau 0.6, a free disk of diameter 30 released at 0.19 of the width.  Fluid,
+    walls and disk all start with the frame velocity V along the axis; the
+    trajectory relative to the channel, x - x0 - V t, should not depend on V.
+    Density ratio 1.5 and net gravity 7.4e-6 (terminal Reynolds number about
+    9): the paper's ratios 1.01 and 1.03 are unstable with half-way
+    bounce-back and explicit coupling.  FP64 storage and arithmetic."""
+    import numpy as np
+    import torch
+    import paper_1303_0625_gb300 as G
+    import workloads as W
+    torch.cuda.set_device(local)
+    width, length, r, tau, rs, gnet, every = 120, 1200, 15.0, 0.6, 1.5, 7.4e-6, 500
+    g = gnet / (1.0 - 1.0 / rs)
+    frames = (0.0, 0.001, 0.002, 0.01, 0.02)
+    traj = {}
+    t0 = time.perf_counter()
+    for cme in (0, 1):
+        for V in frames:
+            w = dict(nx=length, ny=width, tau=tau, rho0=1.0, bc_x=W.PERIODIC, bc_y=W.WALL,
+                     u0=(V, 0.0), wall_ux=(V, V), body_force=(0.0, 0.0), gravity=(-g, 0.0),
+                     rho_w_mode=0, refill=1, motion_cme=cme,
+                     solids=[dict(cx=0.6 * length, cy=0.19 * width - 0.5, r=r, vx=V, vy=0.0,
+                                  omega=0.0, rho_s=rs, motion=1)])
+            lat = G.Lattice.from_workload(w, precision=G.LBM_FP64, force_ring=8, device=local)
+            rows = []
+            for k in range(max(1, a.galilean // every)):
+                lat.step(every)
+                st = lat.solids()[0]
+                rows.append([st[0] - 0.6 * length - V * every * (k + 1), st[1], st[2] - V, st[3],
+                             st[4]])
+            lat.sync()
+            lat.close()
+            traj[(cme, V)] = np.array(rows)
+    out = {"metric": "trajectory relative to the channel vs frame velocity V (Sec. III.A)",
+           "geometry": f"{length}x{width} channel, disk r {r}, tau {tau}, rho_s/rho_f {rs}, "
+                       f"net gravity {gnet}", "steps": max(1, a.galilean // every) * every,
+           "seconds": round(time.perf_counter() - t0, 1)}
+    for cme, name in ((0, "eq5_gme"), (1, "eq4_cme")):
+        base = traj[(cme, 0.0)]
+        rec = {"final_V0": [round(float(v), 5) for v in base[-1]]}
+        for V in frames[1:]:
+            dev = np.abs(traj[(cme, V)] - base).max(axis=0)
+            rec[f"V={V}"] = {"max_dx": round(float(dev[0]), 4), "max_dy": round(float(dev[1]), 4),
+                             "max_dvx": float("%.3g" % dev[2]), "max_dvy": float("%.3g" % dev[3]),
+                             "max_domega": float("%.3g" % dev[4])}
+        out[name] = rec
+    return out
+
+
 def main():
     a = parse()
     ws, rank, local = dist_setup()
@@ -735,6 +790,9 @@ def main():
     elif a.unet:
         if rank == 0:
             print(json.dumps(run_unet(a, local)), flush=True)
+    elif a.galilean:
+        if rank == 0:
+            print(json.dumps(run_galilean(a, local)), flush=True)
     elif a.warm_start:
         if rank == 0:
             print(json.dumps(run_warm_start(a, local)), flush=True)

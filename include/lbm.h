@@ -80,7 +80,8 @@ typedef struct {
     int32_t refill;        /* LBM_REFILL_A1 (default) | A2 | A3 */
     int32_t force_ring;    /* number of most recent steps whose forces stay on device (>= 1) */
     int32_t device;        /* CUDA device ordinal */
-    int32_t reserved;      /* must be 0 */
+    int32_t motion_cme;    /* force driving LBM_FREE solids: 0 = Eq. 5 (Galilean invariant,
+                            * default), 1 = Eq. 4 (conventional; for comparison) */
     void *stream;          /* cudaStream_t to run on; NULL = a stream the context creates */
 } lbm_config;
 

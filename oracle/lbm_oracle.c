@@ -92,6 +92,7 @@ typedef struct {
     double lub_range;      /* gap below which the repulsive lubrication force acts */
     int32_t rho_w_mode;    /* 0: rho_w = rho0; 1: rho_w = density of the fluid node */
     int32_t refill;        /* 1: A1, 2: A2, 3: A3 */
+    int32_t motion_cme;    /* 1: free solids move under Eq. 4; 0: under Eq. 5 */
 } ora_config;
 
 typedef struct {
@@ -245,6 +246,7 @@ static double inlet_ux(const ora_config *c, int y)
 ora_sim *ora_create(const ora_config *c)
 {
     if (c->nx < 4 || c->ny < 4 || !(c->tau > 0.5)) return NULL;
+    if (c->motion_cme != 0 && c->motion_cme != 1) return NULL;
     ora_sim *S = (ora_sim *)calloc(1, sizeof(ora_sim));
     S->c = *c;
     S->cap = 16;
@@ -533,11 +535,12 @@ static void move_solids(ora_sim *S, const double *rec)
             b->y = b->ya + b->vy * dt;
             continue;
         }
-        /* Newton-Euler in FP64 driven by the Galilean-invariant force */
+        /* Newton-Euler in FP64 driven by the Galilean-invariant force (Eq. 5),
+         * or by the conventional one (Eq. 4) when the configuration asks */
         double M = b->rho_s * ORA_PI * b->r * b->r;
         double I = 0.5 * M * b->r * b->r;
         double buoy = 1.0 - c->rho0 / b->rho_s;
-        const double *r = rec + 6 * s + 3;
+        const double *r = rec + 6 * s + (c->motion_cme ? 0 : 3);
         double Fx = r[0] + buoy * M * c->gravity_x + fl[2 * s];
         double Fy = r[1] + buoy * M * c->gravity_y + fl[2 * s + 1];
         double vx1 = b->vx + Fx / M, vy1 = b->vy + Fy / M;

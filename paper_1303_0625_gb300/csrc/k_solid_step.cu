@@ -4,7 +4,8 @@
 //   F  forces:  every fluid-solid link of time t (Eq. 4 and Eq. 5, summed by
 //               Eq. 6 and Eq. 7) plus the momenta booked by the node-type
 //               changes into t, written to the force history; motion
-//               t -> t+1 (prescribed, or Newton-Euler on the Eq. 5 force)
+//               t -> t+1 (prescribed, or Newton-Euler on the Eq. 5 force;
+//               Eq. 4 when the context selects it for comparison)
 //   A  clear:   nodes of the old disk that the new disk leaves, owner s -> fluid
 //   B  set:     nodes of the new disk, owner := lowest id covering them
 //   C  changes: on the ring (old disk XOR new disk): node flags of every node
@@ -277,7 +278,8 @@ __device__ __forceinline__ void set_next_centre(const Lattice &L, DSolid &b) {
     b.ynf = (float)b.yn;
 }
 
-// Motion t -> t+1 of solid s; fg = Eq. 5 force and torque at t (lane 0).
+// Motion t -> t+1 of solid s; fg = force and torque at t (lane 0): Eq. 5,
+// or Eq. 4 when the context asks for the conventional form.
 // The lubrication sum runs over the lanes of the warp.
 __device__ void move_solid(const StepParams &p, int s, int lane, long long t, const double *fg) {
     DSolid &b = p.S[s];
@@ -453,8 +455,8 @@ __device__ void record_forces(const StepParams &p, int s, int lane, long long t,
         for (int q = 0; q < 3; q++) {
             const double pb = booked ? b.pend[q] : 0.0;
             rc[q] = acc[q] + pb;
-            fg[q] = acc[3 + q] + pb;
-            rg[q] = fg[q];
+            rg[q] = acc[3 + q] + pb;
+            fg[q] = p.motion_cme ? rc[q] : rg[q];  // the form that drives a free solid
         }
     }
     move_solid(p, s, lane, t, fg);

@@ -126,6 +126,7 @@ StepParams params(const lbm_ctx *c) {
     p.u0y = g.u0[1];
     p.rho_w_mode = g.rho_w_mode;
     p.refill = g.refill;
+    p.motion_cme = g.motion_cme;
     p.precision = g.precision;
     p.sc_variant = c->sc_variant;
     p.bnd = c->bnd_d;
@@ -305,7 +306,8 @@ lbm_status lbm_create(const lbm_config *cfg, lbm_ctx **out) {
     if (g.force_ring < 1) return fail(nullptr, LBM_EINVAL, "force_ring must be >= 1");
     if (9ll * g.ny * ((g.nx + 63) / 64 * 64) >= (1ll << 31))
         return fail(nullptr, LBM_EINVAL, "domain too large: 9 * ny * pitch must stay below 2^31");
-    if (g.reserved != 0) return fail(nullptr, LBM_EINVAL, "reserved must be 0");
+    if (g.motion_cme != 0 && g.motion_cme != 1)
+        return fail(nullptr, LBM_EINVAL, "motion_cme must be 0 or 1");
     if (g.bc_x == LBM_OPEN && g.bc_y != LBM_WALL)
         return fail(nullptr, LBM_EINVAL, "an open channel needs walls in y");
     if (cudaSetDevice(g.device) != cudaSuccess)

@@ -83,6 +83,7 @@ struct StepParams {
     double grav_x, grav_y, lub;
     double u0x, u0y;
     int rho_w_mode, refill, precision;
+    int motion_cme;           // free solids move under Eq. 4 (1) or Eq. 5 (0)
     int sc_variant;           // node width per thread of the advection-collision kernel
     float omega_f, body_xf, body_yf, rho0_f;  // FP32 copies for the FP32 kernels
     float wall_ux0_f, wall_ux1_f, umax_f;

@@ -44,7 +44,7 @@ class lbm_config(ctypes.Structure):
         ("gravity", ctypes.c_double * 2), ("lub_range", ctypes.c_double),
         ("precision", ctypes.c_int32), ("rho_w_mode", ctypes.c_int32),
         ("refill", ctypes.c_int32), ("force_ring", ctypes.c_int32),
-        ("device", ctypes.c_int32), ("reserved", ctypes.c_int32),
+        ("device", ctypes.c_int32), ("motion_cme", ctypes.c_int32),
         ("stream", ctypes.c_void_p),
     ]
 
@@ -525,7 +525,8 @@ class UNet:
 def make_config(nx, ny, tau, *, rho0=1.0, u0=(0.0, 0.0), bc_x=LBM_PERIODIC, bc_y=LBM_PERIODIC,
                 wall_ux=(0.0, 0.0), body_force=(0.0, 0.0), inflow_umax=0.0, gravity=(0.0, 0.0),
                 lub_range=0.0, precision=LBM_FP64, rho_w_mode=LBM_RHOW_CONST,
-                refill=LBM_REFILL_A1, force_ring=256, device=0, stream=None) -> lbm_config:
+                refill=LBM_REFILL_A1, force_ring=256, device=0, stream=None,
+                motion_cme=0) -> lbm_config:
     c = lbm_config_default()
     c.nx, c.ny, c.bc_x, c.bc_y = int(nx), int(ny), int(bc_x), int(bc_y)
     c.tau, c.rho0 = float(tau), float(rho0)
@@ -538,6 +539,7 @@ def make_config(nx, ny, tau, *, rho0=1.0, u0=(0.0, 0.0), bc_x=LBM_PERIODIC, bc_y
     c.precision = PRECISION_NAMES.get(precision, precision) if isinstance(precision, str) else int(precision)
     c.rho_w_mode, c.refill, c.force_ring = int(rho_w_mode), int(refill), int(force_ring)
     c.device = int(device)
+    c.motion_cme = int(motion_cme)
     c.stream = stream
     return c
 
@@ -559,7 +561,8 @@ class Lattice:
                     body_force=w.get("body_force", (0.0, 0.0)),
                     inflow_umax=w.get("inflow_umax", 0.0), gravity=w.get("gravity", (0.0, 0.0)),
                     lub_range=w.get("lub_range", 0.0), rho_w_mode=w.get("rho_w_mode", 0),
-                    refill=w.get("refill", 1), precision=precision)
+                    refill=w.get("refill", 1), precision=precision,
+                    motion_cme=w.get("motion_cme", 0))
         opts.update(kw)
         lat = cls(w["nx"], w["ny"], w["tau"], **opts)
         if add_solids:

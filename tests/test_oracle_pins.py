@@ -459,3 +459,29 @@ def test_lubrication_pair_symmetric():
     assert va[2] == pytest.approx((fa - push) / M, rel=1e-12, abs=1e-18)
     assert vb[2] == pytest.approx((fb + push) / M, rel=1e-12, abs=1e-18)
     assert va[2] == pytest.approx(-vb[2], rel=1e-12)
+
+
+# ------------------------------------------------- motion under Eq. 4 or 5
+
+@pytest.mark.parametrize("motion_cme", [0, 1])
+def test_free_motion_follows_the_selected_force_form(motion_cme):
+    """Newton's second law over one step: a free disk's velocity changes by
+    (F + (1 - rho0 / rho_s) M g) / M, with F the recorded Eq. 5 force by
+    default or the Eq. 4 force when that form is selected, M = rho_s pi r^2.
+    In a frame moving at V the two forms differ, so the test tells them apart."""
+    V, g, r, rs = 0.03, (-6e-4, 1e-4), 5.0, 1.5
+    o = O.Oracle(60, 40, 0.6, u0=(V, 0.0), bc_y=O.WALL, wall_ux=(V, V), gravity=g,
+                 motion_cme=motion_cme)
+    o.add_disk(30.3, 18.7, r, V, 0.0, 0.0, rs, O.FREE)
+    o.step(20)  # let the force develop
+    v0 = o.solid_state(0)[2:4]
+    rec = o.step(1)[0, 0]  # [Eq. 4, Eq. 5][Fx, Fy, T] at this step's time
+    v1 = o.solid_state(0)[2:4]
+    M = rs * math.pi * r * r
+    buoy = 1.0 - 1.0 / rs
+    F = rec[0 if motion_cme else 1]
+    other = rec[1 if motion_cme else 0]
+    expect = v0 + (F[:2] + buoy * M * np.array(g)) / M
+    assert np.allclose(v1, expect, rtol=0, atol=1e-15)
+    wrong = v0 + (other[:2] + buoy * M * np.array(g)) / M
+    assert np.abs(wrong - v1).max() > 1e-9
