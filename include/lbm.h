@@ -82,6 +82,9 @@ typedef struct {
     int32_t device;        /* CUDA device ordinal */
     int32_t motion_cme;    /* force driving LBM_FREE solids: 0 = Eq. 5 (Galilean invariant,
                             * default), 1 = Eq. 4 (conventional; for comparison) */
+    int32_t relative_changes; /* momentum of covered/fresh nodes in the Eq. 5 record:
+                               * 0 = m u as in the Eq. 4 record (default), 1 = m (u - v)
+                               * relative to the boundary velocity v at the node */
     void *stream;          /* cudaStream_t to run on; NULL = a stream the context creates */
 } lbm_config;
 

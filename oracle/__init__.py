@@ -59,7 +59,7 @@ class Config(ctypes.Structure):
         ("gravity_x", ctypes.c_double), ("gravity_y", ctypes.c_double),
         ("lub_range", ctypes.c_double),
         ("rho_w_mode", ctypes.c_int32), ("refill", ctypes.c_int32),
-        ("motion_cme", ctypes.c_int32),
+        ("motion_cme", ctypes.c_int32), ("relative_changes", ctypes.c_int32),
     ]
 
 
@@ -128,7 +128,7 @@ class Oracle:
     def __init__(self, nx, ny, tau, *, rho0=1.0, u0=(0.0, 0.0), bc_x=PERIODIC, bc_y=PERIODIC,
                  wall_ux=(0.0, 0.0), body_force=(0.0, 0.0), inflow_umax=0.0,
                  gravity=(0.0, 0.0), lub_range=0.0, rho_w_mode=RHOW_CONST, refill=REFILL_A1,
-                 motion_cme=0):
+                 motion_cme=0, relative_changes=0):
         lib = _load()
         c = Config()
         c.nx, c.ny, c.bc_x, c.bc_y = int(nx), int(ny), int(bc_x), int(bc_y)
@@ -141,6 +141,7 @@ class Oracle:
         c.lub_range = float(lub_range)
         c.rho_w_mode, c.refill = int(rho_w_mode), int(refill)
         c.motion_cme = int(motion_cme)
+        c.relative_changes = int(relative_changes)
         self._lib = lib
         self._h = lib.ora_create(ctypes.byref(c))
         if not self._h:

@@ -93,6 +93,8 @@ typedef struct {
     int32_t rho_w_mode;    /* 0: rho_w = rho0; 1: rho_w = density of the fluid node */
     int32_t refill;        /* 1: A1, 2: A2, 3: A3 */
     int32_t motion_cme;    /* 1: free solids move under Eq. 4; 0: under Eq. 5 */
+    int32_t relative_changes; /* 1: the Eq. 5 record books a covered or fresh node's
+                               * momentum relative to the boundary, m (u - v) */
 } ora_config;
 
 typedef struct {
@@ -116,6 +118,7 @@ typedef struct {
     int32_t *owner_prev;
     uint8_t *fresh;
     double *pending;  /* [nsolid][3] momentum booked for the next force record */
+    double *pending_rel; /* [nsolid][3] the same, relative to the boundary velocity */
     int raster_dirty; /* solids added since the owner map was last built */
 } ora_sim;
 
@@ -247,11 +250,13 @@ ora_sim *ora_create(const ora_config *c)
 {
     if (c->nx < 4 || c->ny < 4 || !(c->tau > 0.5)) return NULL;
     if (c->motion_cme != 0 && c->motion_cme != 1) return NULL;
+    if (c->relative_changes != 0 && c->relative_changes != 1) return NULL;
     ora_sim *S = (ora_sim *)calloc(1, sizeof(ora_sim));
     S->c = *c;
     S->cap = 16;
     S->s = (ora_solid *)calloc((size_t)S->cap, sizeof(ora_solid));
     S->pending = (double *)calloc((size_t)S->cap * 3, sizeof(double));
+    S->pending_rel = (double *)calloc((size_t)S->cap * 3, sizeof(double));
     S->f = (double *)calloc(9 * cells(S), sizeof(double));
     S->g = (double *)calloc(9 * cells(S), sizeof(double));
     S->owner = (int32_t *)malloc(cells(S) * sizeof(int32_t));
@@ -275,6 +280,7 @@ void ora_destroy(ora_sim *S)
     if (!S) return;
     free(S->s);
     free(S->pending);
+    free(S->pending_rel);
     free(S->f);
     free(S->g);
     free(S->owner);
@@ -290,6 +296,7 @@ int ora_add_disk(ora_sim *S, double cx, double cy, double r, double vx, double v
         S->cap *= 2;
         S->s = (ora_solid *)realloc(S->s, (size_t)S->cap * sizeof(ora_solid));
         S->pending = (double *)realloc(S->pending, (size_t)S->cap * 3 * sizeof(double));
+        S->pending_rel = (double *)realloc(S->pending_rel, (size_t)S->cap * 3 * sizeof(double));
     }
     int id = S->nsolid++;
     ora_solid *b = &S->s[id];
@@ -303,6 +310,7 @@ int ora_add_disk(ora_sim *S, double cx, double cy, double r, double vx, double v
     b->rho_s = rho_s;
     b->motion = motion;
     S->pending[3 * id] = S->pending[3 * id + 1] = S->pending[3 * id + 2] = 0.0;
+    S->pending_rel[3 * id] = S->pending_rel[3 * id + 1] = S->pending_rel[3 * id + 2] = 0.0;
     S->raster_dirty = 1; /* rasterised before the owner map is next used */
     return id;
 }
@@ -351,14 +359,16 @@ static void record_forces(ora_sim *S, double *rec)
             }
         }
     for (int s = 0; s < S->nsolid; s++) {
-        double *r = rec + 6 * s, *p = S->pending + 3 * s;
+        double *r = rec + 6 * s, *p = S->pending + 3 * s, *q = S->pending_rel + 3 * s;
+        const double *pg = S->c.relative_changes ? q : p; /* what the Eq. 5 record books */
         r[0] += p[0];
         r[1] += p[1];
         r[2] += p[2];
-        r[3] += p[0];
-        r[4] += p[1];
-        r[5] += p[2];
+        r[3] += pg[0];
+        r[4] += pg[1];
+        r[5] += pg[2];
         p[0] = p[1] = p[2] = 0.0;
+        q[0] = q[1] = q[2] = 0.0;
     }
 }
 
@@ -631,17 +641,23 @@ static void remask(ora_sim *S)
             size_t k = at(S, x, y);
             int was = S->owner_prev[k], now = S->owner[k];
             if (was < 0 && now >= 0) {
-                /* covered: the node's momentum goes to the solid */
-                double jx = 0.0, jy = 0.0, vx, vy, dx, dy;
+                /* covered: the node's momentum goes to the solid; relative to
+                 * the boundary it is m (u - v), m the node's mass */
+                double jx = 0.0, jy = 0.0, m = 0.0, vx, vy, dx, dy;
                 for (int j = 0; j < 9; j++) {
                     jx += EX[j] * S->f[j * N + k];
                     jy += EY[j] * S->f[j * N + k];
+                    m += S->f[j * N + k];
                 }
                 solid_point_velocity(S, now, (double)x, (double)y, &vx, &vy, &dx, &dy);
-                double *p = S->pending + 3 * now;
+                double *p = S->pending + 3 * now, *q = S->pending_rel + 3 * now;
                 p[0] += jx;
                 p[1] += jy;
                 p[2] += dx * jy - dy * jx;
+                const double rx = jx - m * vx, ry = jy - m * vy;
+                q[0] += rx;
+                q[1] += ry;
+                q[2] += dx * ry - dy * rx;
             }
             if (was >= 0 && now < 0) S->fresh[k] = 1;
         }
@@ -650,19 +666,24 @@ static void remask(ora_sim *S)
             size_t k = at(S, x, y);
             if (!S->fresh[k]) continue;
             int s = S->owner_prev[k];
-            double nf[9], jx = 0.0, jy = 0.0, vx, vy, dx, dy;
+            double nf[9], jx = 0.0, jy = 0.0, m = 0.0, vx, vy, dx, dy;
             refill_node(S, x, y, s, nf);
             for (int j = 0; j < 9; j++) {
                 S->f[j * N + k] = nf[j];
                 jx += EX[j] * nf[j];
                 jy += EY[j] * nf[j];
+                m += nf[j];
             }
-            /* newborn: the solid gives the node its momentum */
+            /* newborn: the solid gives the node its momentum (relative: m (u - v)) */
             solid_point_velocity(S, s, (double)x, (double)y, &vx, &vy, &dx, &dy);
-            double *p = S->pending + 3 * s;
+            double *p = S->pending + 3 * s, *q = S->pending_rel + 3 * s;
             p[0] -= jx;
             p[1] -= jy;
             p[2] -= dx * jy - dy * jx;
+            const double rx = jx - m * vx, ry = jy - m * vy;
+            q[0] -= rx;
+            q[1] -= ry;
+            q[2] -= dx * ry - dy * rx;
         }
 }
 

@@ -453,9 +453,8 @@ __device__ void record_forces(const StepParams &p, int s, int lane, long long t,
         double *rc = p.ring + (slot * 2 + 0) * p.nsolid * 3 + (long long)s * 3;
         double *rg = p.ring + (slot * 2 + 1) * p.nsolid * 3 + (long long)s * 3;
         for (int q = 0; q < 3; q++) {
-            const double pb = booked ? b.pend[q] : 0.0;
-            rc[q] = acc[q] + pb;
-            rg[q] = acc[3 + q] + pb;
+            rc[q] = acc[q] + (booked ? b.pend[q] : 0.0);
+            rg[q] = acc[3 + q] + (booked ? b.pend[3 + q] : 0.0);
             fg[q] = p.motion_cme ? rc[q] : rg[q];  // the form that drives a free solid
         }
     }
@@ -608,15 +607,10 @@ __device__ void phase_sync(const StepParams &p, int s, int lane, long long t1) {
         });
     __syncwarp();
     if (lane == 0) {
-        double acc[3] = {0.0, 0.0, 0.0};
-        for (int e = b.ev_off; e < b.ev_off + b.ev_n; e++) {
-            acc[0] += p.ev_mom[3 * e];
-            acc[1] += p.ev_mom[3 * e + 1];
-            acc[2] += p.ev_mom[3 * e + 2];
-        }
-        b.pend[0] = acc[0];
-        b.pend[1] = acc[1];
-        b.pend[2] = acc[2];
+        double acc[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+        for (int e = b.ev_off; e < b.ev_off + b.ev_n; e++)
+            for (int q = 0; q < 6; q++) acc[q] += p.ev_mom[6 * e + q];
+        for (int q = 0; q < 6; q++) b.pend[q] = acc[q];
         b.pend_t = t1;
         b.x = b.xn;
         b.y = b.yn;
@@ -735,7 +729,7 @@ __device__ void phase_event(const StepParams &p, int e, int lane, void *fnew) {
     const int2 ev = p.ev[e];
     const int code = ev.x;
     const DSolid &b = p.S[ev.y];
-    double acc[3] = {0.0, 0.0, 0.0};
+    double acc[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
     {
         const int k = code >> 1;
         const int x = k % L.pitch, y = k / L.pitch;
@@ -799,12 +793,13 @@ __device__ void phase_event(const StepParams &p, int e, int lane, void *fnew) {
             }
             __syncwarp();
         }
-        // momentum of the node (post-collision if covered, refilled if fresh)
-        double jm[2] = {0.0, 0.0};
+        // momentum and mass of the node (post-collision if covered, refilled if fresh)
+        double jm[3] = {0.0, 0.0, 0.0};
         if (lane < 9) {
             const double v = f64<P>(fnew, L.plane, lane, k);
             jm[0] = cx(lane) * v;
             jm[1] = cy(lane) * v;
+            jm[2] = v;
         }
         warp_sum(jm);
         if (lane == 0) {
@@ -815,13 +810,16 @@ __device__ void phase_event(const StepParams &p, int e, int lane, void *fnew) {
             acc[0] += sgn * jm[0];
             acc[1] += sgn * jm[1];
             acc[2] += sgn * (dx * jm[1] - dy * jm[0]);
+            // the Eq. 5 record's booking: the same, or relative to the boundary, m (u - v)
+            const double rx = p.relative_changes ? jm[0] - jm[2] * ux : jm[0];
+            const double ry = p.relative_changes ? jm[1] - jm[2] * uy : jm[1];
+            acc[3] += sgn * rx;
+            acc[4] += sgn * ry;
+            acc[5] += sgn * (dx * ry - dy * rx);
         }
     }
-    if (lane == 0) {
-        p.ev_mom[3 * e] = acc[0];
-        p.ev_mom[3 * e + 1] = acc[1];
-        p.ev_mom[3 * e + 2] = acc[2];
-    }
+    if (lane == 0)
+        for (int q = 0; q < 6; q++) p.ev_mom[6 * e + q] = acc[q];
     __syncwarp();
 }
 

@@ -127,6 +127,7 @@ StepParams params(const lbm_ctx *c) {
     p.rho_w_mode = g.rho_w_mode;
     p.refill = g.refill;
     p.motion_cme = g.motion_cme;
+    p.relative_changes = g.relative_changes;
     p.precision = g.precision;
     p.sc_variant = c->sc_variant;
     p.bnd = c->bnd_d;
@@ -203,7 +204,7 @@ lbm_status upload_moving(lbm_ctx *c) {
         if (c->ev_d) CK(c, cudaFree(c->ev_d));
         c->ev_d = nullptr;
         c->ev_cap = 0;
-        CK(c, cudaMalloc(&c->ev_d, 16 + (size_t)cap * (sizeof(int2) + 3 * sizeof(double))));
+        CK(c, cudaMalloc(&c->ev_d, 16 + (size_t)cap * (sizeof(int2) + 6 * sizeof(double))));
         CK(c, cudaMemsetAsync(c->ev_d, 0, 16, c->stream));
         c->ev_cap = (int)cap;
     }
@@ -308,6 +309,8 @@ lbm_status lbm_create(const lbm_config *cfg, lbm_ctx **out) {
         return fail(nullptr, LBM_EINVAL, "domain too large: 9 * ny * pitch must stay below 2^31");
     if (g.motion_cme != 0 && g.motion_cme != 1)
         return fail(nullptr, LBM_EINVAL, "motion_cme must be 0 or 1");
+    if (g.relative_changes != 0 && g.relative_changes != 1)
+        return fail(nullptr, LBM_EINVAL, "relative_changes must be 0 or 1");
     if (g.bc_x == LBM_OPEN && g.bc_y != LBM_WALL)
         return fail(nullptr, LBM_EINVAL, "an open channel needs walls in y");
     if (cudaSetDevice(g.device) != cudaSuccess)

@@ -43,7 +43,8 @@ struct DSolid {
     double vx, vy, om; // V(t), Omega(t)
     double vxn, vyn, omn;
     double r, rho_s;
-    double pend[3];    // momentum booked by the node-type changes into time pend_t
+    double pend[6];    // momentum booked by the node-type changes into time pend_t:
+                       // [Fx, Fy, T] for the Eq. 4 record, then for the Eq. 5 record
     long long pend_t;  // time whose force record carries pend
     long long ta;      // time when added
     float vxf, vyf, omf;  // FP32 copies of vx, vy, om for the FP32 kernels
@@ -84,12 +85,13 @@ struct StepParams {
     double u0x, u0y;
     int rho_w_mode, refill, precision;
     int motion_cme;           // free solids move under Eq. 4 (1) or Eq. 5 (0)
+    int relative_changes;     // Eq. 5 record books covered/fresh momenta as m (u - v)
     int sc_variant;           // node width per thread of the advection-collision kernel
     float omega_f, body_xf, body_yf, rho0_f;  // FP32 copies for the FP32 kernels
     float wall_ux0_f, wall_ux1_f, umax_f;
     unsigned int *bar;        // grid barrier of the per-solid kernel: {count, generation}
     int2 *ev;                 // covered/fresh events of the step: {node code, solid}
-    double *ev_mom;           // [3] momentum and torque of each event
+    double *ev_mom;           // [6] momentum and torque of each event: Eq. 4, Eq. 5 booking
     int *ev_len;              // events published this step (cleared after use)
     int ev_cap;
     int *bnd;                 // deferred per-node path: {length at even t, at odd t, list...}

@@ -45,6 +45,7 @@ class lbm_config(ctypes.Structure):
         ("precision", ctypes.c_int32), ("rho_w_mode", ctypes.c_int32),
         ("refill", ctypes.c_int32), ("force_ring", ctypes.c_int32),
         ("device", ctypes.c_int32), ("motion_cme", ctypes.c_int32),
+        ("relative_changes", ctypes.c_int32),
         ("stream", ctypes.c_void_p),
     ]
 
@@ -526,7 +527,7 @@ def make_config(nx, ny, tau, *, rho0=1.0, u0=(0.0, 0.0), bc_x=LBM_PERIODIC, bc_y
                 wall_ux=(0.0, 0.0), body_force=(0.0, 0.0), inflow_umax=0.0, gravity=(0.0, 0.0),
                 lub_range=0.0, precision=LBM_FP64, rho_w_mode=LBM_RHOW_CONST,
                 refill=LBM_REFILL_A1, force_ring=256, device=0, stream=None,
-                motion_cme=0) -> lbm_config:
+                motion_cme=0, relative_changes=0) -> lbm_config:
     c = lbm_config_default()
     c.nx, c.ny, c.bc_x, c.bc_y = int(nx), int(ny), int(bc_x), int(bc_y)
     c.tau, c.rho0 = float(tau), float(rho0)
@@ -540,6 +541,7 @@ def make_config(nx, ny, tau, *, rho0=1.0, u0=(0.0, 0.0), bc_x=LBM_PERIODIC, bc_y
     c.rho_w_mode, c.refill, c.force_ring = int(rho_w_mode), int(refill), int(force_ring)
     c.device = int(device)
     c.motion_cme = int(motion_cme)
+    c.relative_changes = int(relative_changes)
     c.stream = stream
     return c
 
@@ -562,7 +564,8 @@ class Lattice:
                     inflow_umax=w.get("inflow_umax", 0.0), gravity=w.get("gravity", (0.0, 0.0)),
                     lub_range=w.get("lub_range", 0.0), rho_w_mode=w.get("rho_w_mode", 0),
                     refill=w.get("refill", 1), precision=precision,
-                    motion_cme=w.get("motion_cme", 0))
+                    motion_cme=w.get("motion_cme", 0),
+                    relative_changes=w.get("relative_changes", 0))
         opts.update(kw)
         lat = cls(w["nx"], w["ny"], w["tau"], **opts)
         if add_solids:

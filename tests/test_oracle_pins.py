@@ -485,3 +485,35 @@ def test_free_motion_follows_the_selected_force_form(motion_cme):
     assert np.allclose(v1, expect, rtol=0, atol=1e-15)
     wrong = v0 + (other[:2] + buoy * M * np.array(g)) / M
     assert np.abs(wrong - v1).max() > 1e-9
+
+
+@pytest.mark.parametrize("v", [(0.04, 0.0), (0.03, -0.025)])
+def test_relative_changes_vanish_in_uniform_motion(v):
+    """Fluid and disk moving together at v: the equilibrium at (rho0, v) is an
+    exact solution (the moving-wall term maps feq_i to feq_opp, and the A1
+    refill reproduces a uniform field).  Booked relative to the boundary, the
+    covered and fresh nodes then carry no momentum, so every Eq. 5 record is
+    the link sum of Eq. 10, sum 2 rho0 w_i e_i over the links of that step
+    (torque about R with x_s = x_f + e_i / 2).  Booked in absolute momentum
+    they carry +-rho0 v per node and the records differ at every step with a
+    node-type change."""
+    rho0, r = 1.0, 6.3
+    rel = O.Oracle(48, 40, 0.8, rho0=rho0, u0=v, relative_changes=1)
+    ab = O.Oracle(48, 40, 0.8, rho0=rho0, u0=v)
+    for o in (rel, ab):
+        o.add_disk(20.4, 17.7, r, v[0], v[1], 0.0, 1.0, O.PRESCRIBED)
+    differ = 0
+    for step in range(80):
+        links = rel.links()
+        x, y = rel.solid_state(0)[:2]
+        got = rel.step(1)[0, 0, 1]
+        other = ab.step(1)[0, 0, 1]
+        expect = np.zeros(3)
+        for xf, yf, i, _ in links:
+            fx, fy = 2 * rho0 * W[i] * EX[i], 2 * rho0 * W[i] * EY[i]
+            dx = xf + 0.5 * EX[i] - x
+            dy = yf + 0.5 * EY[i] - y
+            expect += (fx, fy, dx * fy - dy * fx)
+        assert np.allclose(got, expect, rtol=0, atol=1e-12), step
+        differ += np.abs(other - got).max() > 1e-3
+    assert differ >= 5  # the disk crossed several nodes
