@@ -238,10 +238,13 @@ def run_ours(a, ws, rank, local):
     cells = w["nx"] * w["ny"]
     peaks, peak_kind = measured_peaks()
 
-    def measure(precision, steps, warmup, sample_clocks):
+    def measure(precision, steps, warmup, sample_clocks, collision=0):
         lat = G.Lattice.from_workload(w, precision=G.PRECISION_NAMES[precision], device=local,
-                                      stream=stream.cuda_stream, force_ring=512)
-        if a.variant >= 0:
+                                      stream=stream.cuda_stream, force_ring=512,
+                                      collision=collision)
+        if collision:
+            variant = -1  # MRT has one launch shape
+        elif a.variant >= 0:
             lat.set_kernel_variant(a.variant)
             variant = a.variant
         else:
@@ -317,6 +320,14 @@ def run_ours(a, ws, rank, local):
                            "kernel_gbs": round(b / (m["k1_avg_ms"] / 1e3) / 1e9, 1),
                            "kernel_frac_of_hbm": round(b / (m["k1_avg_ms"] / 1e3) / 1e9 / peak, 4),
                            "ms_per_step": round(m["ms"] / k, 5)}
+        # MRT (Sec. IV's rates) on the same workload, FP32 deviation storage
+        k = max(20, a.steps // 4)
+        m = measure("fp32", k, 3, False, collision=1)
+        b = algorithmic_bytes("fp32", cells)
+        modes["fp32_mrt"] = {"mlups": round(cells * k / (m["ms"] / 1e3) / 1e6, 1), "steps": k,
+                             "kernel_gbs": round(b / (m["k1_avg_ms"] / 1e3) / 1e9, 1),
+                             "kernel_frac_of_hbm": round(b / (m["k1_avg_ms"] / 1e3) / 1e9 / peak, 4),
+                             "ms_per_step": round(m["ms"] / k, 5)}
         line["modes"] = modes
         line["batch"] = run_batch(a, local, stream, peak)
         line["sedimentation"] = run_sedimentation(a, local, stream, peak)

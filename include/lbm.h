@@ -61,6 +61,11 @@ enum { LBM_RHOW_CONST = 0 /* rho0 */, LBM_RHOW_LOCAL = 1 /* density of the fluid
 enum { LBM_REFILL_A1 = 1, LBM_REFILL_A2 = 2, LBM_REFILL_A3 = 3 };
 /* solid motion */
 enum { LBM_PRESCRIBED = 0, LBM_FREE = 1 };
+/* collision model: BGK (single relaxation time, Eq. 2) or MRT with the rates of
+ * Sec. IV, S = diag(0, 1.64, 1.54, 0, 1.9, 0, 1.9, 1/tau, 1/tau) on the moments
+ * (rho, e, eps, j_x, q_x, j_y, q_y, p_xx, p_xy); MRT takes no body force and
+ * runs one launch shape (lbm_set_kernel_variant has no effect on it) */
+enum { LBM_BGK = 0, LBM_MRT = 1 };
 /* force form: Eq. 4 (conventional) or Eq. 5 (Galilean invariant) */
 enum { LBM_CME = 0, LBM_GME = 1 };
 
@@ -85,6 +90,7 @@ typedef struct {
     int32_t relative_changes; /* momentum of covered/fresh nodes in the Eq. 5 record:
                                * 0 = m u as in the Eq. 4 record (default), 1 = m (u - v)
                                * relative to the boundary velocity v at the node */
+    int32_t collision;     /* LBM_BGK (default) | LBM_MRT; batches take LBM_BGK only */
     void *stream;          /* cudaStream_t to run on; NULL = a stream the context creates */
 } lbm_config;
 

@@ -60,6 +60,7 @@ class Config(ctypes.Structure):
         ("lub_range", ctypes.c_double),
         ("rho_w_mode", ctypes.c_int32), ("refill", ctypes.c_int32),
         ("motion_cme", ctypes.c_int32), ("relative_changes", ctypes.c_int32),
+        ("collision", ctypes.c_int32),
     ]
 
 
@@ -90,6 +91,7 @@ def _load():
             "ora_feq": (None, [D, D, D, dp]),
             "ora_link_force": (None, [ctypes.c_int, D, D, D, D, dp]),
             "ora_pending": (None, [P, dp]),
+            "ora_mrt_node": (None, [dp, dp, dp]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -111,6 +113,19 @@ def feq(rho: float, ux: float, uy: float) -> np.ndarray:
     return out
 
 
+def mrt_node(f, s) -> np.ndarray:
+    """One MRT collision of a node's populations f (9,) with moment rates s
+    (9,) in the basis (rho, e, eps, j_x, q_x, j_y, q_y, p_xx, p_xy)."""
+    f = np.ascontiguousarray(f, dtype=np.float64)
+    s = np.ascontiguousarray(s, dtype=np.float64)
+    out = np.empty(9)
+    _load().ora_mrt_node(_dp(f), _dp(s), _dp(out))
+    return out
+
+
+MRT_RATES = (0.0, 1.64, 1.54, 0.0, 1.9, 0.0, 1.9)  # then 1/tau twice (Sec. IV)
+
+
 def link_force(i: int, fi: float, fbb: float, vx: float, vy: float) -> np.ndarray:
     """Per-link force on the solid: [Eq. 4 x, Eq. 4 y, Eq. 5 x, Eq. 5 y].
 
@@ -128,7 +143,7 @@ class Oracle:
     def __init__(self, nx, ny, tau, *, rho0=1.0, u0=(0.0, 0.0), bc_x=PERIODIC, bc_y=PERIODIC,
                  wall_ux=(0.0, 0.0), body_force=(0.0, 0.0), inflow_umax=0.0,
                  gravity=(0.0, 0.0), lub_range=0.0, rho_w_mode=RHOW_CONST, refill=REFILL_A1,
-                 motion_cme=0, relative_changes=0):
+                 motion_cme=0, relative_changes=0, collision=0):
         lib = _load()
         c = Config()
         c.nx, c.ny, c.bc_x, c.bc_y = int(nx), int(ny), int(bc_x), int(bc_y)
@@ -142,6 +157,7 @@ class Oracle:
         c.rho_w_mode, c.refill = int(rho_w_mode), int(refill)
         c.motion_cme = int(motion_cme)
         c.relative_changes = int(relative_changes)
+        c.collision = int(collision)
         self._lib = lib
         self._h = lib.ora_create(ctypes.byref(c))
         if not self._h:

@@ -95,6 +95,7 @@ typedef struct {
     int32_t motion_cme;    /* 1: free solids move under Eq. 4; 0: under Eq. 5 */
     int32_t relative_changes; /* 1: the Eq. 5 record books a covered or fresh node's
                                * momentum relative to the boundary, m (u - v) */
+    int32_t collision;     /* 0: BGK; 1: MRT with the rates of Sec. IV (no body force) */
 } ora_config;
 
 typedef struct {
@@ -251,6 +252,8 @@ ora_sim *ora_create(const ora_config *c)
     if (c->nx < 4 || c->ny < 4 || !(c->tau > 0.5)) return NULL;
     if (c->motion_cme != 0 && c->motion_cme != 1) return NULL;
     if (c->relative_changes != 0 && c->relative_changes != 1) return NULL;
+    if (c->collision != 0 && c->collision != 1) return NULL;
+    if (c->collision == 1 && (c->body_fx != 0.0 || c->body_fy != 0.0)) return NULL;
     ora_sim *S = (ora_sim *)calloc(1, sizeof(ora_sim));
     S->c = *c;
     S->cap = 16;
@@ -441,6 +444,89 @@ static void open_column(ora_sim *S, int b, int n, int y, int inlet)
         *F(S, S->f, i, b, y) = eq_b[i] + (*F(S, S->f, i, n, y) - eq_n[i]);
 }
 
+/* ---------------------------------------------------------------- MRT
+ * Multiple-relaxation-time collision (Sec. IV names it, with the rates
+ * S = diag(0, 1.64, 1.54, 0, 1.9, 0, 1.9, 1/tau, 1/tau)): moments m = M f in
+ * the basis (rho, e, eps, j_x, q_x, j_y, q_y, p_xx, p_xy) of the D2Q9 model of
+ * the paper's refs. [33, 45], each moment relaxed at its rate towards the
+ * moment of the equilibrium Eq. 8, m_eq = M f_eq, then f = M^-1 m.  Row k of M
+ * evaluates a polynomial in (e_x, e_y) at the nine velocities; M^-1 is
+ * obtained by Gauss-Jordan elimination. */
+static double MRT_M[9][9], MRT_MI[9][9];
+static int mrt_ready = 0;
+
+static void mrt_init(void)
+{
+    if (mrt_ready) return;
+    for (int i = 0; i < 9; i++) {
+        double ex = EX[i], ey = EY[i], e2 = ex * ex + ey * ey;
+        MRT_M[0][i] = 1.0;                                   /* rho */
+        MRT_M[1][i] = 3.0 * e2 - 4.0;                        /* e: energy */
+        MRT_M[2][i] = 4.5 * e2 * e2 - 10.5 * e2 + 4.0;       /* eps: energy squared */
+        MRT_M[3][i] = ex;                                    /* j_x */
+        MRT_M[4][i] = (3.0 * e2 - 5.0) * ex;                 /* q_x: energy flux */
+        MRT_M[5][i] = ey;                                    /* j_y */
+        MRT_M[6][i] = (3.0 * e2 - 5.0) * ey;                 /* q_y */
+        MRT_M[7][i] = ex * ex - ey * ey;                     /* p_xx: normal stress */
+        MRT_M[8][i] = ex * ey;                               /* p_xy: shear stress */
+    }
+    double a[9][18];
+    for (int r = 0; r < 9; r++)
+        for (int k = 0; k < 18; k++) a[r][k] = k < 9 ? MRT_M[r][k] : (k - 9 == r ? 1.0 : 0.0);
+    for (int col = 0; col < 9; col++) {
+        int piv = col;
+        for (int r = col + 1; r < 9; r++)
+            if (fabs(a[r][col]) > fabs(a[piv][col])) piv = r;
+        for (int k = 0; k < 18; k++) {
+            double tmp = a[col][k];
+            a[col][k] = a[piv][k];
+            a[piv][k] = tmp;
+        }
+        double d = a[col][col];
+        for (int k = 0; k < 18; k++) a[col][k] /= d;
+        for (int r = 0; r < 9; r++) {
+            if (r == col || a[r][col] == 0.0) continue;
+            double m = a[r][col];
+            for (int k = 0; k < 18; k++) a[r][k] -= m * a[col][k];
+        }
+    }
+    for (int r = 0; r < 9; r++)
+        for (int k = 0; k < 9; k++) MRT_MI[r][k] = a[r][9 + k];
+    mrt_ready = 1;
+}
+
+/* One MRT collision of the populations f of a node with rates s[9]. */
+void ora_mrt_node(const double *f, const double *s, double *out)
+{
+    mrt_init();
+    double rho = 0.0, jx = 0.0, jy = 0.0, eq[9], m[9], meq[9], ms[9];
+    for (int i = 0; i < 9; i++) {
+        rho += f[i];
+        jx += EX[i] * f[i];
+        jy += EY[i] * f[i];
+    }
+    ora_feq(rho, jx / rho, jy / rho, eq);
+    for (int k = 0; k < 9; k++) {
+        m[k] = meq[k] = 0.0;
+        for (int i = 0; i < 9; i++) {
+            m[k] += MRT_M[k][i] * f[i];
+            meq[k] += MRT_M[k][i] * eq[i];
+        }
+        ms[k] = m[k] - s[k] * (m[k] - meq[k]);
+    }
+    for (int i = 0; i < 9; i++) {
+        out[i] = 0.0;
+        for (int k = 0; k < 9; k++) out[i] += MRT_MI[i][k] * ms[k];
+    }
+}
+
+/* The rates of Sec. IV: conserved moments 0, e 1.64, eps 1.54, q 1.9, stress 1/tau. */
+static void mrt_rates(double tau, double *s)
+{
+    const double r[9] = {0.0, 1.64, 1.54, 0.0, 1.9, 0.0, 1.9, 1.0 / tau, 1.0 / tau};
+    for (int k = 0; k < 9; k++) s[k] = r[k];
+}
+
 static void collide(ora_sim *S)
 {
     const ora_config *c = &S->c;
@@ -457,6 +543,13 @@ static void collide(ora_sim *S)
                 rho += g[i];
                 jx += EX[i] * g[i];
                 jy += EY[i] * g[i];
+            }
+            if (c->collision == 1) {
+                double s[9], out[9];
+                mrt_rates(tau, s);
+                ora_mrt_node(g, s, out);
+                for (int i = 0; i < 9; i++) *F(S, S->f, i, x, y) = out[i];
+                continue;
             }
             /* Guo forcing: u includes half the body force */
             double ux = (jx + 0.5 * Fx) / rho, uy = (jy + 0.5 * Fy) / rho;

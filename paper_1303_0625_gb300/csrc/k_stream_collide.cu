@@ -7,9 +7,9 @@ namespace gbm {
 
 namespace {
 
-template <int P, int V, bool FORCE, bool LOCAL, bool WALLS, bool DEFER>
+template <int P, int V, bool FORCE, bool LOCAL, bool WALLS, bool DEFER, int COLL = 0>
 __global__ void __launch_bounds__(SC_BLOCK_X) k_stream_collide(const StepParams p) {
-    sc_tile<P, V, FORCE, LOCAL, false, WALLS, DEFER>(p, blockIdx.x, blockIdx.y);
+    sc_tile<P, V, FORCE, LOCAL, false, WALLS, DEFER, COLL>(p, blockIdx.x, blockIdx.y);
 }
 
 // With the per-node path deferred (variants 3-5), the nodes k_stream_collide
@@ -167,8 +167,23 @@ cudaError_t launch_sc_v(const StepParams &p, cudaStream_t st) {
 // Node widths per thread: variant 0 = one 16-byte word per population,
 // variant 1 = 8 bytes, variant 2 = 4 bytes; variants 3-5 the same widths
 // with the per-node path deferred to k_boundary_scan / k_boundary_update.
+// MRT: one launch shape, 8-byte words per population plane, slow nodes inline.
+template <int P, bool LOCAL>
+cudaError_t launch_mrt(const StepParams &p, cudaStream_t st) {
+    constexpr int V = 8 / (int)sizeof(typename Raw<P>::R) > 0 ? 8 / (int)sizeof(typename Raw<P>::R) : 1;
+    dim3 grid((p.L.nx + SC_BLOCK_X * V - 1) / (SC_BLOCK_X * V), p.L.ny);
+    if (walls_on_vector_path<P, LOCAL>() && p.L.bc_y == LBM_WALL)
+        k_stream_collide<P, V, false, LOCAL, walls_on_vector_path<P, LOCAL>(), false, 1>
+            <<<grid, SC_BLOCK_X, 0, st>>>(p);
+    else
+        k_stream_collide<P, V, false, LOCAL, false, false, 1><<<grid, SC_BLOCK_X, 0, st>>>(p);
+    return cudaGetLastError();
+}
+
 template <int P>
 cudaError_t launch_sc_p(const StepParams &p, cudaStream_t st) {
+    if (p.collision == LBM_MRT)
+        return p.rho_w_mode == LBM_RHOW_LOCAL ? launch_mrt<P, true>(p, st) : launch_mrt<P, false>(p, st);
     constexpr int V16 = 16 / (int)sizeof(typename Raw<P>::R);
     constexpr int V4 = V16 / 4 > 0 ? V16 / 4 : 1;
     switch (p.sc_variant) {

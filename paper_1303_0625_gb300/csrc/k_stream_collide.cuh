@@ -189,6 +189,55 @@ __device__ __forceinline__ void collide(const StepParams &p, typename Prec<P>::C
     }
 }
 
+// MRT collision of one node in place (Sec. IV names the model and its rates
+// S = diag(0, 1.64, 1.54, 0, 1.9, 0, 1.9, 1/tau, 1/tau)): the moments of the
+// basis (rho, e, eps, j_x, q_x, j_y, q_y, p_xx, p_xy) relax towards those of
+// the Eq. 8 equilibrium, -2 rho + 3 j^2 / rho, rho - 3 j^2 / rho, -j,
+// (j_x^2 - j_y^2) / rho and j_x j_y / rho (in the deviation modes minus the
+// moments of the weights, which are 1, -2, 1 and zeros), and the change goes
+// back to the populations through the transposed basis over the squared row
+// norms (36, 36, 12, 12, 4, 4).  No body force.  CHECK: flag a non-physical
+// state (the vector path checks its fluid nodes itself; solid nodes there
+// hold no state).
+template <int P, bool CHECK>
+__device__ __forceinline__ void collide_mrt(const StepParams &p, typename Prec<P>::C (&g)[9]) {
+    using C = typename Prec<P>::C;
+    const C ax = g[1] + g[2] + g[3] + g[4], dg = g[5] + g[6] + g[7] + g[8];
+    const C s0 = g[0] + ax + dg;
+    const C jx = g[1] - g[3] + g[5] - g[6] - g[7] + g[8];
+    const C jy = g[2] - g[4] + g[5] + g[6] - g[7] - g[8];
+    const C rho = Prec<P>::dev ? (C)1 + s0 : s0;
+    const C inv = (C)1 / rho;
+    if (CHECK && (!(rho > (C)0) || !(fabs(jx * inv) < (C)1e30) || !(fabs(jy * inv) < (C)1e30)))
+        atomicOr(p.status, 1);
+    const C jj = (jx * jx + jy * jy) * inv;
+    const C e = (C)-4 * g[0] - ax + (C)2 * dg;
+    const C eps = (C)4 * g[0] - (C)2 * ax + dg;
+    const C qx = (C)2 * (g[3] - g[1]) + g[5] - g[6] - g[7] + g[8];
+    const C qy = (C)2 * (g[4] - g[2]) + g[5] + g[6] - g[7] - g[8];
+    const C pxx = g[1] - g[2] + g[3] - g[4];
+    const C pxy = g[5] - g[6] + g[7] - g[8];
+    const C eeq = Prec<P>::dev ? (C)-2 * s0 + (C)3 * jj : (C)-2 * rho + (C)3 * jj;
+    const C epseq = Prec<P>::dev ? s0 - (C)3 * jj : rho - (C)3 * jj;
+    const C om = pick<C>(p.omega, p.omega_f);
+    const C de = (C)(1.64 / 36.0) * (e - eeq);
+    const C dp = (C)(1.54 / 36.0) * (eps - epseq);
+    const C dqx = (C)(1.9 / 12.0) * (qx + jx);
+    const C dqy = (C)(1.9 / 12.0) * (qy + jy);
+    const C dxx = (C)0.25 * om * (pxx - (jx * jx - jy * jy) * inv);
+    const C dxy = (C)0.25 * om * (pxy - jx * jy * inv);
+    const C a = -de - (C)2 * dp, b = (C)2 * de + dp;
+    g[0] -= (C)4 * (dp - de);
+    g[1] -= a - (C)2 * dqx + dxx;
+    g[2] -= a - (C)2 * dqy - dxx;
+    g[3] -= a + (C)2 * dqx + dxx;
+    g[4] -= a + (C)2 * dqy - dxx;
+    g[5] -= b + dqx + dqy + dxy;
+    g[6] -= b - dqx + dqy - dxy;
+    g[7] -= b - dqx - dqy + dxy;
+    g[8] -= b + dqx - dqy - dxy;
+}
+
 // Inlet profile of an open channel at row y: u_in = 4 umax y' (ny - y') / ny^2,
 // y' = y + 1/2 (walls at y = -1/2 and ny - 1/2); in the precision C of the
 // kernel (no FP64 arithmetic in the FP32 kernels).
@@ -256,7 +305,7 @@ __device__ __forceinline__ void extrapolate_open(const StepParams &p, bool inlet
 // the inlet is feq(rho0, u_in) and the outlet updates as a walled node.
 // Without OPEN they update as walled nodes and a later pass (open_col)
 // replaces them.
-template <int P, bool FORCE, bool LOCAL, bool OPEN>
+template <int P, bool FORCE, bool LOCAL, bool OPEN, int COLL = 0>
 __device__ __noinline__ void update_node(const StepParams &p, const typename Raw<P>::R *fin,
                                          typename Raw<P>::R *fout, int x, int y) {
     using C = typename Prec<P>::C;
@@ -301,7 +350,8 @@ __device__ __noinline__ void update_node(const StepParams &p, const typename Raw
         g[i] = cvt(fin[i * plane + ys * L.pitch + xs]);
     }
     if (flu & 0x1FEu) bounce<P, LOCAL>(p, fin, xu, y, flu, g);
-    collide<P, FORCE>(p, g);
+    if constexpr (COLL == 1) collide_mrt<P, true>(p, g);
+    else collide<P, FORCE>(p, g);
     if (OPEN && open) extrapolate_open<P, FORCE>(p, x == 0, u_in, g);
 #pragma unroll
     for (int i = 0; i < 9; i++) {
@@ -321,7 +371,9 @@ __host__ __device__ constexpr bool walls_on_vector_path() { return !LOCAL && P !
 // DEFER: the per-node path is left to a later pass over the nodes next to
 // solids and edges (the single-domain kernel); otherwise each thread runs it
 // for its own nodes at the end of the tile.
-template <int P, int V, bool FORCE, bool LOCAL, bool OPEN, bool WALLS = false, bool DEFER = false>
+// COLL: 0 = BGK, 1 = MRT (no body force, slow nodes inline).
+template <int P, int V, bool FORCE, bool LOCAL, bool OPEN, bool WALLS = false, bool DEFER = false,
+          int COLL = 0>
 __device__ __forceinline__ void sc_tile(const StepParams &p, int bx, int y) {
     static_assert(!WALLS || walls_on_vector_path<P, LOCAL>(), "wall rows need rho0 and R == C");
     using R = typename Raw<P>::R;
@@ -428,7 +480,31 @@ __device__ __forceinline__ void sc_tile(const StepParams &p, int bx, int y) {
                  (!(r > (C)0) || !(fabs(vx) < (C)1e30) || !(fabs(vy) < (C)1e30)))
             atomicOr(p.status, 1);
     };
-    if constexpr (Prec<P>::dev && !FORCE && V % 2 == 0) {
+    if constexpr (COLL == 1) {
+        // MRT, one node at a time
+        static_assert(!FORCE && !DEFER, "MRT runs without body force and with inline slow nodes");
+        Pack<R, V> o[9];
+#pragma unroll
+        for (int j = 0; j < V; j++) {
+            C g[9];
+            C a = 0, jx = 0, jy = 0;
+#pragma unroll
+            for (int i = 0; i < 9; i++) {
+                g[i] = PULL(i, j);
+                a += g[i];
+                jx += (C)cx(i) * g[i];
+                jy += (C)cy(i) * g[i];
+            }
+            const C r = Prec<P>::dev ? (C)1 + a : a;
+            classify(j, r, jx / r, jy / r);
+            collide_mrt<P, false>(p, g);
+#pragma unroll
+            for (int i = 0; i < 9; i++) put(o[i].r[j], (fl.f[j] & 1u) ? (C)0 : g[i]);
+        }
+#pragma unroll
+        for (int i = 0; i < 9; i++)
+            *reinterpret_cast<typename Word<sizeof(R) * V>::T *>(fout + i * plane + r0 + x0) = o[i].u;
+    } else if constexpr (Prec<P>::dev && !FORCE && V % 2 == 0) {
         // Deviation form, two nodes per instruction (FADD2 / FMUL2 / FFMA2).
         // With E_i = s0 + rho (3 e_i.u + 4.5 (e_i.u)^2 - 1.5 u.u) the
         // equilibrium deviation is w_i E_i, and BGK gives
@@ -527,7 +603,7 @@ __device__ __forceinline__ void sc_tile(const StepParams &p, int bx, int y) {
         while (slow) {
             const int j = __ffs(slow) - 1;
             slow &= slow - 1;
-            update_node<P, FORCE, LOCAL, OPEN>(p, fin, fout, x0 + j, y);
+            update_node<P, FORCE, LOCAL, OPEN, COLL>(p, fin, fout, x0 + j, y);
         }
     }
 }

@@ -128,6 +128,7 @@ StepParams params(const lbm_ctx *c) {
     p.refill = g.refill;
     p.motion_cme = g.motion_cme;
     p.relative_changes = g.relative_changes;
+    p.collision = g.collision;
     p.precision = g.precision;
     p.sc_variant = c->sc_variant;
     p.bnd = c->bnd_d;
@@ -311,6 +312,10 @@ lbm_status lbm_create(const lbm_config *cfg, lbm_ctx **out) {
         return fail(nullptr, LBM_EINVAL, "motion_cme must be 0 or 1");
     if (g.relative_changes != 0 && g.relative_changes != 1)
         return fail(nullptr, LBM_EINVAL, "relative_changes must be 0 or 1");
+    if (g.collision != LBM_BGK && g.collision != LBM_MRT)
+        return fail(nullptr, LBM_EINVAL, "collision must be LBM_BGK or LBM_MRT");
+    if (g.collision == LBM_MRT && (g.body_force[0] != 0.0 || g.body_force[1] != 0.0))
+        return fail(nullptr, LBM_EINVAL, "MRT takes no body force");
     if (g.bc_x == LBM_OPEN && g.bc_y != LBM_WALL)
         return fail(nullptr, LBM_EINVAL, "an open channel needs walls in y");
     if (cudaSetDevice(g.device) != cudaSuccess)
@@ -1146,6 +1151,9 @@ extern "C" {
 lbm_status lbm_batch_create(const lbm_config *configs, int32_t ncase, lbm_batch **out) {
     if (!configs || !out || ncase < 1) return bfail(nullptr, LBM_EINVAL, "bad batch arguments");
     *out = nullptr;
+    for (int k = 0; k < ncase; k++)
+        if (configs[k].collision != LBM_BGK)
+            return bfail(nullptr, LBM_EINVAL, "case %d: batches run BGK only", k);
     for (int k = 1; k < ncase; k++)
         if (configs[k].precision != configs[0].precision ||
             configs[k].rho_w_mode != configs[0].rho_w_mode ||

@@ -86,6 +86,7 @@ struct StepParams {
     int rho_w_mode, refill, precision;
     int motion_cme;           // free solids move under Eq. 4 (1) or Eq. 5 (0)
     int relative_changes;     // Eq. 5 record books covered/fresh momenta as m (u - v)
+    int collision;            // LBM_BGK or LBM_MRT
     int sc_variant;           // node width per thread of the advection-collision kernel
     float omega_f, body_xf, body_yf, rho0_f;  // FP32 copies for the FP32 kernels
     float wall_ux0_f, wall_ux1_f, umax_f;
@@ -321,6 +322,7 @@ struct BatchState {
 // the nodes it leaves to the per-node update
 constexpr int KERNEL_VARIANTS = 6;
 inline int stream_collide_launches(const StepParams &p) {
+    if (p.collision == LBM_MRT) return 1;  // MRT keeps the slow nodes inline
     return p.sc_variant >= 3 ? (p.nsolid > 0 ? 3 : 2) : 1;
 }
 cudaError_t launch_stream_collide(const StepParams &p, cudaStream_t st);

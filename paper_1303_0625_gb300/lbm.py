@@ -24,6 +24,7 @@ LBM_RHOW_CONST, LBM_RHOW_LOCAL = 0, 1
 LBM_REFILL_A1, LBM_REFILL_A2, LBM_REFILL_A3 = 1, 2, 3
 LBM_PRESCRIBED, LBM_FREE = 0, 1
 LBM_CME, LBM_GME = 0, 1
+LBM_BGK, LBM_MRT = 0, 1
 
 PRECISION_NAMES = {"fp64": LBM_FP64, "fp32": LBM_FP32_DEV, "fp16": LBM_FP16_DEV}
 
@@ -45,7 +46,7 @@ class lbm_config(ctypes.Structure):
         ("precision", ctypes.c_int32), ("rho_w_mode", ctypes.c_int32),
         ("refill", ctypes.c_int32), ("force_ring", ctypes.c_int32),
         ("device", ctypes.c_int32), ("motion_cme", ctypes.c_int32),
-        ("relative_changes", ctypes.c_int32),
+        ("relative_changes", ctypes.c_int32), ("collision", ctypes.c_int32),
         ("stream", ctypes.c_void_p),
     ]
 
@@ -527,7 +528,7 @@ def make_config(nx, ny, tau, *, rho0=1.0, u0=(0.0, 0.0), bc_x=LBM_PERIODIC, bc_y
                 wall_ux=(0.0, 0.0), body_force=(0.0, 0.0), inflow_umax=0.0, gravity=(0.0, 0.0),
                 lub_range=0.0, precision=LBM_FP64, rho_w_mode=LBM_RHOW_CONST,
                 refill=LBM_REFILL_A1, force_ring=256, device=0, stream=None,
-                motion_cme=0, relative_changes=0) -> lbm_config:
+                motion_cme=0, relative_changes=0, collision=0) -> lbm_config:
     c = lbm_config_default()
     c.nx, c.ny, c.bc_x, c.bc_y = int(nx), int(ny), int(bc_x), int(bc_y)
     c.tau, c.rho0 = float(tau), float(rho0)
@@ -542,6 +543,7 @@ def make_config(nx, ny, tau, *, rho0=1.0, u0=(0.0, 0.0), bc_x=LBM_PERIODIC, bc_y
     c.device = int(device)
     c.motion_cme = int(motion_cme)
     c.relative_changes = int(relative_changes)
+    c.collision = int(collision)
     c.stream = stream
     return c
 
@@ -565,7 +567,8 @@ class Lattice:
                     lub_range=w.get("lub_range", 0.0), rho_w_mode=w.get("rho_w_mode", 0),
                     refill=w.get("refill", 1), precision=precision,
                     motion_cme=w.get("motion_cme", 0),
-                    relative_changes=w.get("relative_changes", 0))
+                    relative_changes=w.get("relative_changes", 0),
+                    collision=w.get("collision", 0))
         opts.update(kw)
         lat = cls(w["nx"], w["ny"], w["tau"], **opts)
         if add_solids:

@@ -517,3 +517,78 @@ def test_relative_changes_vanish_in_uniform_motion(v):
         assert np.allclose(got, expect, rtol=0, atol=1e-12), step
         differ += np.abs(other - got).max() > 1e-3
     assert differ >= 5  # the disk crossed several nodes
+
+
+# ------------------------------------------------------------------- MRT
+
+def _moments(f):
+    """The nine moments of the MRT basis, each from its polynomial in (e_x, e_y)."""
+    e2 = EX ** 2 + EY ** 2
+    polys = [np.ones(9), 3 * e2 - 4, 4.5 * e2 ** 2 - 10.5 * e2 + 4, EX, (3 * e2 - 5) * EX, EY,
+             (3 * e2 - 5) * EY, EX ** 2 - EY ** 2, EX * EY]
+    return np.array([p @ f for p in polys])
+
+
+def _near_eq(seed):
+    rng = np.random.default_rng(seed)
+    f = O.feq(1.02, 0.05, -0.03) * (1.0 + 0.05 * rng.standard_normal(9))
+    return f
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_mrt_relaxes_each_moment_at_its_rate(seed):
+    """MRT: every moment m_k of the basis relaxes towards the moment of the
+    Eq. 8 equilibrium at its own rate, m_k' - m_k^eq = (1 - s_k)(m_k - m_k^eq);
+    the moments are evaluated here from their definitions, so a wrong row of
+    the oracle's matrix or a rate on the wrong moment fails."""
+    tau = 0.7
+    s = np.array(list(O.MRT_RATES) + [1 / tau, 1 / tau])
+    f = _near_eq(seed)
+    rho, jx, jy = f.sum(), EX @ f, EY @ f
+    meq = _moments(O.feq(rho, jx / rho, jy / rho))
+    m = _moments(f)
+    out = _moments(O.mrt_node(f, s))
+    assert np.allclose(out - meq, (1 - s) * (m - meq), rtol=0, atol=1e-14)
+    # conserved moments unchanged, distinct rates really used
+    assert np.allclose(out[[0, 3, 5]], m[[0, 3, 5]], atol=1e-15)
+    assert np.abs(m - meq)[[1, 2, 4, 6, 7, 8]].min() > 1e-6
+
+
+def test_mrt_with_one_rate_is_bgk_and_keeps_equilibrium():
+    """With every rate 1/tau MRT is the BGK update f - (f - f_eq)/tau; an
+    equilibrium is a fixed point for the paper's rates."""
+    tau = 0.85
+    f = _near_eq(7)
+    rho, jx, jy = f.sum(), EX @ f, EY @ f
+    bgk = f - (f - O.feq(rho, jx / rho, jy / rho)) / tau
+    assert np.allclose(O.mrt_node(f, np.full(9, 1 / tau)), bgk, rtol=0, atol=1e-15)
+    eq = O.feq(0.97, -0.04, 0.06)
+    s = np.array(list(O.MRT_RATES) + [1 / tau, 1 / tau])
+    assert np.allclose(O.mrt_node(eq, s), eq, rtol=0, atol=1e-15)
+
+
+@pytest.mark.parametrize("collision", [0, 1])
+def test_shear_wave_decays_at_the_bgk_viscosity(collision):
+    """A small shear wave u_x = A sin(2 pi y / L) in a periodic box decays as
+    exp(-nu k^2 t) with nu = (tau - 1/2) / 3 for BGK and, since the stress
+    moments relax at 1/tau, for MRT too (closed form of the linearised
+    Navier-Stokes equations)."""
+    n, tau, A, t1, t2 = 64, 0.8, 1e-4, 200, 1800
+    o = O.Oracle(4, n, tau, collision=collision)
+    y = np.arange(n)
+    f = np.empty((9, n, 4))
+    for j in range(n):
+        f[:, j, :] = O.feq(1.0, A * np.sin(2 * np.pi * y[j] / n), 0.0)[:, None]
+    o.set_f(f)
+
+    def amplitude():
+        return 2.0 / n * (o.fields()[1][:, 0] @ np.sin(2 * np.pi * y / n))
+
+    o.step(t1, record=False)  # past the start-up transient of the equilibrium start
+    a1 = amplitude()
+    o.step(t2 - t1, record=False)
+    rate = -np.log(amplitude() / a1) / (t2 - t1)
+    nu = (tau - 0.5) / 3
+    # the lattice's O(k^2) correction to the rate is about 1e-3 at 64 nodes per wave
+    # (5e-4 for BGK, 1.0e-3 for MRT, whose other rates enter at that order)
+    assert rate == pytest.approx(nu * (2 * np.pi / n) ** 2, rel=2e-3)
