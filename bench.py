@@ -48,6 +48,10 @@ def parse():
     ap.add_argument("--nx", type=int, default=8192)
     ap.add_argument("--ny", type=int, default=4096)
     ap.add_argument("--ndisk", type=int, default=2000)
+    ap.add_argument("--collision", choices=["bgk", "mrt"], default="bgk",
+                    help="collision model of the main measurement (MRT: the rates of Sec. IV; "
+                         "on the 8192 x 4096 workload MRT turns unstable near step 300, so "
+                         "use --steps 200)")
     ap.add_argument("--variant", type=int, default=-1,
                     help="launch variant of the advection-collision pass (0-5, see lbm.h); "
                          "default: the autotuner's choice")
@@ -276,15 +280,19 @@ def run_ours(a, ws, rank, local):
         return dict(ms=ms, k1_avg_ms=k1_ms / max(k1_n, 1), launches=launches, nfluid=nfluid,
                     clocks=clocks.summary() if sample_clocks else None, variant=variant)
 
-    main = measure(a.precision, a.steps, a.warmup, rank == 0)
+    main = measure(a.precision, a.steps, a.warmup, rank == 0,
+                   collision=1 if a.collision == "mrt" else 0)
     t_max = max_over_ranks(main["ms"], ws)
     value = cells * a.steps * ws / (t_max / 1e3) / 1e6
     bytes_launch = algorithmic_bytes(a.precision, cells)
     achieved = bytes_launch / (main["k1_avg_ms"] / 1e3) / 1e9
     peak = float(peaks.get("hbm_gbs", FALLBACK_HBM_GBS))
-    traffic = captured_traffic(a.precision, a.nx, a.ny, main["variant"])
+    traffic = (None if a.collision == "mrt"  # the record is the BGK pass's
+               else captured_traffic(a.precision, a.nx, a.ny, main["variant"]))
     kernels = ("k_stream_collide + k_boundary_scan + k_boundary_update" if main["variant"] >= 3
                else "k_stream_collide")
+    if a.collision == "mrt":
+        kernels = "k_stream_collide (MRT)"
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "traffic": traffic,
                 "kernel": kernels, "peak_source": f"{peak_kind} hbm_gbs",
@@ -302,6 +310,7 @@ def run_ours(a, ws, rank, local):
                        "storage": {"fp64": "f64", "fp32": "f32 (f - w_i)",
                                    "fp16": "f16 (f - w_i)"}[a.precision],
                        "force_reduction": "f64, both forms every step",
+                       "collision": a.collision,
                        "l2": "inputs larger than L2 (populations "
                              f"{2 * 9 * cells * STORAGE_BYTES[a.precision] / 1e9:.2f} GB)",
                        "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
