@@ -40,7 +40,9 @@ def build(force: bool = False) -> str:
         tmp = _SO + f".{os.getpid()}.tmp"
         cmd = ["gcc", "-std=c11", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
                "-shared", "-o", tmp, _SRC, "-lm"]
-        subprocess.run(cmd, check=True)
+        # OpenMP for the per-node loops where the compiler has it; else one thread
+        if subprocess.run(cmd[:1] + ["-fopenmp"] + cmd[1:], capture_output=True).returncode != 0:
+            subprocess.run(cmd, check=True)
         os.replace(tmp, _SO)
     return _SO
 
@@ -92,6 +94,7 @@ def _load():
             "ora_link_force": (None, [ctypes.c_int, D, D, D, D, dp]),
             "ora_pending": (None, [P, dp]),
             "ora_mrt_node": (None, [dp, dp, dp]),
+            "ora_set_threads": (ctypes.c_int, [ctypes.c_int]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -111,6 +114,12 @@ def feq(rho: float, ux: float, uy: float) -> np.ndarray:
     out = np.empty(9)
     _load().ora_feq(rho, ux, uy, _dp(out))
     return out
+
+
+def set_threads(n: int = 0) -> int:
+    """Threads of the oracle's per-node loops (n < 1: all cores); returns the
+    count in effect (1 when the oracle was built without OpenMP)."""
+    return int(_load().ora_set_threads(int(n)))
 
 
 def mrt_node(f, s) -> np.ndarray:

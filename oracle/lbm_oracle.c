@@ -12,7 +12,10 @@
  * header or table with it.
  *
  * Everything is double precision, written as loops in the order the paper
- * states the method.  Compile with floating-point contraction disabled
+ * states the method.  Built with OpenMP, the two per-node loops (advection
+ * with bounce-back, collision) are shared among threads; every node's result
+ * depends only on the previous state, so the output does not depend on the
+ * thread count.  Sums over links, node-type changes and solids stay serial.  Compile with floating-point contraction disabled
  * (-ffp-contract=off) so that the geometric inside tests are rounded exactly
  * as written.
  *
@@ -56,6 +59,9 @@
  *     the inlet is feq(rho0, u_in) and the outlet updates as a node whose
  *     outside neighbours are a resting wall.
  */
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 #include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
@@ -380,6 +386,7 @@ static void record_forces(ora_sim *S, double *rec)
 static void advect(ora_sim *S)
 {
     const ora_config *c = &S->c;
+#pragma omp parallel for schedule(static)
     for (int y = 0; y < c->ny; y++)
         for (int x = 0; x < c->nx; x++) {
             if (S->owner[at(S, x, y)] >= 0) {
@@ -531,6 +538,8 @@ static void collide(ora_sim *S)
 {
     const ora_config *c = &S->c;
     double tau = c->tau, Fx = c->body_fx, Fy = c->body_fy;
+    if (c->collision == 1) mrt_init(); /* before the threads share the tables */
+#pragma omp parallel for schedule(static)
     for (int y = 0; y < c->ny; y++)
         for (int x = 0; x < c->nx; x++) {
             if (S->owner[at(S, x, y)] >= 0) {
@@ -800,6 +809,18 @@ void ora_step(ora_sim *S, int64_t n, double *rec)
 }
 
 /* --------------------------------------------------------- accessors */
+
+/* Threads of the per-node loops (1 without OpenMP); n < 1 selects all cores. */
+int ora_set_threads(int n)
+{
+#ifdef _OPENMP
+    omp_set_num_threads(n >= 1 ? n : omp_get_num_procs());
+    return omp_get_max_threads();
+#else
+    (void)n;
+    return 1;
+#endif
+}
 
 int64_t ora_time(const ora_sim *S) { return S->t; }
 int ora_nsolid(const ora_sim *S) { return S->nsolid; }

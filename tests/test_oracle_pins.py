@@ -592,3 +592,23 @@ def test_shear_wave_decays_at_the_bgk_viscosity(collision):
     # the lattice's O(k^2) correction to the rate is about 1e-3 at 64 nodes per wave
     # (5e-4 for BGK, 1.0e-3 for MRT, whose other rates enter at that order)
     assert rate == pytest.approx(nu * (2 * np.pi / n) ** 2, rel=2e-3)
+
+
+@pytest.mark.parametrize("collision", [0, 1])
+def test_oracle_threads_do_not_change_results(collision):
+    """The per-node loops shared among threads give bit-identical populations,
+    forces and solid states (each node depends only on the previous state)."""
+    def run(threads):
+        O.set_threads(threads)
+        o = O.Oracle(64, 48, 0.7, bc_y=O.WALL, wall_ux=(0.0, 0.02), collision=collision)
+        o.add_disk(20.3, 22.1, 6.2, 0.04, 0.01, 0.0, 1.0, O.PRESCRIBED)
+        o.add_disk(45.0, 20.0, 5.0, 0.0, 0.0, 0.0, 1.5, O.FREE)
+        rec = o.step(60)
+        return o.get_f(), rec, o.solid_state(1)
+    try:
+        a = run(1)
+        b = run(4)
+    finally:
+        O.set_threads(0)
+    for u, v in zip(a, b):
+        assert np.array_equal(u, v)
