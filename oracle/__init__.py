@@ -62,7 +62,7 @@ class Config(ctypes.Structure):
         ("lub_range", ctypes.c_double),
         ("rho_w_mode", ctypes.c_int32), ("refill", ctypes.c_int32),
         ("motion_cme", ctypes.c_int32), ("relative_changes", ctypes.c_int32),
-        ("collision", ctypes.c_int32),
+        ("collision", ctypes.c_int32), ("boundary", ctypes.c_int32),
     ]
 
 
@@ -95,6 +95,8 @@ def _load():
             "ora_pending": (None, [P, dp]),
             "ora_mrt_node": (None, [dp, dp, dp]),
             "ora_set_threads": (ctypes.c_int, [ctypes.c_int]),
+            "ora_link_fraction": (ctypes.c_double, [P, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                                    ctypes.c_int]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -152,7 +154,7 @@ class Oracle:
     def __init__(self, nx, ny, tau, *, rho0=1.0, u0=(0.0, 0.0), bc_x=PERIODIC, bc_y=PERIODIC,
                  wall_ux=(0.0, 0.0), body_force=(0.0, 0.0), inflow_umax=0.0,
                  gravity=(0.0, 0.0), lub_range=0.0, rho_w_mode=RHOW_CONST, refill=REFILL_A1,
-                 motion_cme=0, relative_changes=0, collision=0):
+                 motion_cme=0, relative_changes=0, collision=0, boundary=0):
         lib = _load()
         c = Config()
         c.nx, c.ny, c.bc_x, c.bc_y = int(nx), int(ny), int(bc_x), int(bc_y)
@@ -167,6 +169,7 @@ class Oracle:
         c.motion_cme = int(motion_cme)
         c.relative_changes = int(relative_changes)
         c.collision = int(collision)
+        c.boundary = int(boundary)
         self._lib = lib
         self._h = lib.ora_create(ctypes.byref(c))
         if not self._h:
@@ -228,6 +231,10 @@ class Oracle:
         out = np.empty(5)
         self._lib.ora_solid_state(self._h, int(s), _dp(out))
         return out
+
+    def link_fraction(self, s: int, x: int, y: int, i: int) -> float:
+        """Fraction of the link from node (x, y) along e_i at which it meets disk s."""
+        return float(self._lib.ora_link_fraction(self._h, int(s), int(x), int(y), int(i)))
 
     def solid_radius(self, s: int) -> float:
         return float(self._radius[s])

@@ -102,6 +102,7 @@ typedef struct {
     int32_t relative_changes; /* 1: the Eq. 5 record books a covered or fresh node's
                                * momentum relative to the boundary, m (u - v) */
     int32_t collision;     /* 0: BGK; 1: MRT with the rates of Sec. IV (no body force) */
+    int32_t boundary;      /* disks: 0 half-way bounce-back; 1 interpolated (ref. [40]) */
 } ora_config;
 
 typedef struct {
@@ -218,6 +219,56 @@ static double bounced(int i, double fi, double rho_w, double vx, double vy)
     return fi - 6.0 * W[i] * rho_w * (EX[i] * vx + EY[i] * vy);
 }
 
+/* --------------------------------------------- interpolated boundary
+ * The boundary condition the paper's simulations use (Sec. IV, ref. [40]):
+ * the disk's surface cuts a link at its true position, at fraction q of the
+ * link from the fluid node, instead of half-way, and the returning population
+ * is interpolated linearly from the populations near the wall.  The channel
+ * walls stay half-way (they lie at y = -1/2 and ny - 1/2). */
+
+/* Fraction q in (0, 1] of the link from the fluid node (x, y) along e_i at
+ * which it meets the circle of solid s (the node lies outside, x + e_i
+ * inside): the smaller root of |p + q e_i - R|^2 = r^2, with p - R at the
+ * nearest periodic image. */
+static double link_fraction(const ora_sim *S, int s, int x, int y, int i)
+{
+    const ora_solid *b = &S->s[s];
+    double px = min_image((double)x - b->x, S->c.nx, S->c.bc_x == ORA_PERIODIC);
+    double py = min_image((double)y - b->y, S->c.ny, S->c.bc_y == ORA_PERIODIC);
+    double a = (double)(EX[i] * EX[i] + EY[i] * EY[i]);
+    double h = px * EX[i] + py * EY[i];
+    double cc = px * px + py * py - b->r * b->r; /* > 0: the node is outside */
+    double disc = h * h - a * cc;
+    double q = disc > 0.0 ? (-h - sqrt(disc)) / a : 0.5;
+    if (!(q > 0.0)) q = 0.0;
+    if (q > 1.0) q = 1.0;
+    return q;
+}
+
+/* Population i arriving at the fluid node (x, y) from solid s, whose surface
+ * cuts the link along e_opp(i) at fraction q, from the post-collision
+ * populations f:
+ *   q < 1/2:  2q f_opp(x) + (1 - 2q) f_opp(x + e_i) + M
+ *   q >= 1/2: (f_opp(x) + M) / (2q) + (2q - 1) / (2q) f_i(x)
+ * with the moving-wall term M = 6 w_i rho_w (e_i . v), v the solid's velocity
+ * at the cut x - q e_i.  q = 1/2 is the half-way rule; where x + e_i is not a
+ * fluid node of the domain the half-way value f_opp(x) + M is taken.  Returns
+ * the cut's velocity and its offset from the centre through v and d. */
+static double returning(const ora_sim *S, double *f, int x, int y, int i, int s, double rho_w,
+                        double *vx, double *vy, double *dx, double *dy)
+{
+    const int o = OPP[i];
+    const double q = link_fraction(S, s, x, y, o);
+    solid_point_velocity(S, s, (double)x - q * EX[i], (double)y - q * EY[i], vx, vy, dx, dy);
+    const double back = *F(S, f, o, x, y);
+    const double m = 6.0 * W[i] * rho_w * (EX[i] * *vx + EY[i] * *vy);
+    if (q >= 0.5) return (back + m) / (2.0 * q) + (2.0 * q - 1.0) / (2.0 * q) * *F(S, f, i, x, y);
+    int xn, yn;
+    if (!locate(S, x + EX[i], y + EY[i], &xn, &yn) || S->owner[at(S, xn, yn)] >= 0)
+        return back + m;
+    return 2.0 * q * back + (1.0 - 2.0 * q) * *F(S, f, o, xn, yn) + m;
+}
+
 /* -------------------------------------------------------- rasterisation */
 
 static int inside_disk(double px, double py, double X, double Y, double r)
@@ -260,6 +311,7 @@ ora_sim *ora_create(const ora_config *c)
     if (c->relative_changes != 0 && c->relative_changes != 1) return NULL;
     if (c->collision != 0 && c->collision != 1) return NULL;
     if (c->collision == 1 && (c->body_fx != 0.0 || c->body_fy != 0.0)) return NULL;
+    if (c->boundary != 0 && c->boundary != 1) return NULL;
     ora_sim *S = (ora_sim *)calloc(1, sizeof(ora_sim));
     S->c = *c;
     S->cap = 16;
@@ -350,12 +402,18 @@ static void record_forces(ora_sim *S, double *rec)
                 if (!locate(S, x + EX[i], y + EY[i], &xb, &yb)) continue;
                 int s = S->owner[at(S, xb, yb)];
                 if (s < 0) continue;
-                /* intersection point of the half-way link */
-                double xs = (double)x + 0.5 * EX[i], ys = (double)y + 0.5 * EY[i];
-                double vx, vy, dx, dy;
-                solid_point_velocity(S, s, xs, ys, &vx, &vy, &dx, &dy);
+                double vx, vy, dx, dy, fbb;
                 double fi = *F(S, S->f, i, x, y);
-                double fbb = bounced(i, fi, rho_w, vx, vy);
+                if (c->boundary) {
+                    /* the population that returns to x along e_opp(i), and the
+                     * velocity and lever arm at the cut */
+                    fbb = returning(S, S->f, x, y, OPP[i], s, rho_w, &vx, &vy, &dx, &dy);
+                } else {
+                    /* intersection point of the half-way link */
+                    double xs = (double)x + 0.5 * EX[i], ys = (double)y + 0.5 * EY[i];
+                    solid_point_velocity(S, s, xs, ys, &vx, &vy, &dx, &dy);
+                    fbb = bounced(i, fi, rho_w, vx, vy);
+                }
                 double lf[4];
                 ora_link_force(i, fi, fbb, vx, vy, lf);
                 double *r = rec + 6 * s;
@@ -411,7 +469,10 @@ static void advect(ora_sim *S)
                     int xs, ys;
                     locate(S, sx, sy, &xs, &ys);
                     int s = S->owner[at(S, xs, ys)];
-                    if (s >= 0) {
+                    if (s >= 0 && c->boundary) {
+                        double vx, vy, dx, dy;
+                        val = returning(S, S->f, x, y, i, s, rho_w, &vx, &vy, &dx, &dy);
+                    } else if (s >= 0) {
                         double vx, vy, dx, dy;
                         solid_point_velocity(S, s, (double)x - 0.5 * EX[i], (double)y - 0.5 * EY[i],
                                              &vx, &vy, &dx, &dy);
@@ -809,6 +870,12 @@ void ora_step(ora_sim *S, int64_t n, double *rec)
 }
 
 /* --------------------------------------------------------- accessors */
+
+/* Fraction of the link from (x, y) along e_i at which it meets solid s. */
+double ora_link_fraction(const ora_sim *S, int s, int x, int y, int i)
+{
+    return link_fraction(S, s, x, y, i);
+}
 
 /* Threads of the per-node loops (1 without OpenMP); n < 1 selects all cores. */
 int ora_set_threads(int n)

@@ -16,7 +16,7 @@ def make_oracle(w):
                  rho_w_mode=w.get("rho_w_mode", 0), refill=w.get("refill", 1),
                  motion_cme=w.get("motion_cme", 0),
                  relative_changes=w.get("relative_changes", 0),
-                 collision=w.get("collision", 0))
+                 collision=w.get("collision", 0), boundary=w.get("boundary", 0))
     for s in w["solids"]:
         o.add_disk(s["cx"], s["cy"], s["r"], s["vx"], s["vy"], s["omega"], s["rho_s"], s["motion"])
     return o

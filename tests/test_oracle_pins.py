@@ -612,3 +612,88 @@ def test_oracle_threads_do_not_change_results(collision):
         O.set_threads(0)
     for u, v in zip(a, b):
         assert np.array_equal(u, v)
+
+
+# ----------------------------------------------- interpolated boundary [40]
+
+def _boundary_links(o):
+    """(x_f, y_f, i, solid, q) of every fluid-solid link, q the cut fraction."""
+    return [(x, y, i, s, o.link_fraction(s, x, y, i)) for x, y, i, s in o.links()]
+
+
+def test_link_fraction_is_the_circle_crossing():
+    """The cut x_f + q e_i lies on the disk's circle, and the link is fluid
+    before it (the smaller root)."""
+    X, Y, r = 20.37, 18.61, 6.23
+    o = O.Oracle(48, 40, 0.7, boundary=1)
+    o.add_disk(X, Y, r, 0.0, 0.0, 0.0, 1.0, O.PRESCRIBED)
+    links = _boundary_links(o)
+    assert len(links) > 40
+    qs = []
+    for x, y, i, s, q in links:
+        assert 0.0 < q <= 1.0
+        px, py = x + q * EX[i] - X, y + q * EY[i] - Y
+        assert math.hypot(px, py) == pytest.approx(r, abs=1e-12)
+        mx, my = x + 0.5 * q * EX[i] - X, y + 0.5 * q * EY[i] - Y
+        assert math.hypot(mx, my) > r
+        qs.append(q)
+    assert min(qs) < 0.3 and max(qs) > 0.7  # both interpolation branches occur
+
+
+@pytest.mark.parametrize("v", [(0.04, 0.0), (0.03, -0.025)])
+def test_interpolated_boundary_keeps_uniform_motion(v):
+    """Fluid and disk moving together at v: with the cut at any q the returned
+    population is f_eq(rho0, v) of its direction exactly (the interpolation
+    weights sum to one and the moving-wall term is scaled with them), so the
+    fluid stays at equilibrium; and with relative booking every Eq. 5 record
+    is the sum of the links' Eq. 5 values at equilibrium (the per-link
+    evaluation of Sec. III.C: (e_i - v) f_eq_i - (e_opp - v) f_eq_opp), with
+    torque levers at the cuts."""
+    rho0 = 1.0
+    o = O.Oracle(48, 40, 0.8, rho0=rho0, u0=v, boundary=1, relative_changes=1)
+    o.add_disk(20.4, 17.7, 6.3, v[0], v[1], 0.0, 1.0, O.PRESCRIBED)
+    eq = O.feq(rho0, *v)
+    for step in range(60):
+        links = _boundary_links(o)
+        x0, y0 = o.solid_state(0)[:2]
+        got = o.step(1)[0, 0, 1]
+        expect = np.zeros(3)
+        for xf, yf, i, _, q in links:
+            fx = (EX[i] - v[0]) * eq[i] - (EX[OPP[i]] - v[0]) * eq[OPP[i]]
+            fy = (EY[i] - v[1]) * eq[i] - (EY[OPP[i]] - v[1]) * eq[OPP[i]]
+            dx, dy = xf + q * EX[i] - x0, yf + q * EY[i] - y0
+            expect += (fx, fy, dx * fy - dy * fx)
+        assert np.allclose(got, expect, rtol=0, atol=1e-12), step
+    f = o.get_f()
+    fluid = o.owner() < 0
+    assert np.abs(f[:, fluid] - eq[:, None]).max() < 1e-13
+
+
+def test_interpolated_boundary_is_exact_for_linear_fields():
+    """For q < 1/2 the returned population is the outgoing population's value
+    at x_f + (1 - 2q) e_i, the point from which it reaches x_f in one step
+    after reflecting at the cut: linear interpolation reproduces it exactly
+    for populations that vary linearly in space.  Collision is made
+    negligible (tau = 1e12) so that one step is one streaming."""
+    nx, ny = 48, 40
+    o = O.Oracle(nx, ny, 1e12, boundary=1)
+    o.add_disk(20.37, 18.61, 6.23, 0.0, 0.0, 0.0, 1.0, O.PRESCRIBED)
+    rng = np.random.default_rng(5)
+    a, b, c = 0.1 + rng.random(9), 1e-3 * rng.standard_normal(9), 1e-3 * rng.standard_normal(9)
+    yy, xx = np.mgrid[0:ny, 0:nx]
+    f0 = a[:, None, None] + b[:, None, None] * xx + c[:, None, None] * yy
+    o.set_f(f0)
+    links = _boundary_links(o)
+    owner = o.owner()
+    o.step(1, record=False)
+    f1 = o.get_f()
+    checked = 0
+    for xf, yf, k, s, q in links:  # k points into the disk; population opp(k) returns
+        i = OPP[k]
+        xn, yn = xf + EX[i], yf + EY[i]
+        if q >= 0.5 or owner[yn, xn] >= 0:
+            continue
+        px, py = xf + (1 - 2 * q) * EX[i], yf + (1 - 2 * q) * EY[i]
+        assert f1[i, yf, xf] == pytest.approx(a[k] + b[k] * px + c[k] * py, rel=1e-9), (xf, yf, k)
+        checked += 1
+    assert checked > 10
