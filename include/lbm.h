@@ -66,6 +66,19 @@ enum { LBM_PRESCRIBED = 0, LBM_FREE = 1 };
  * (rho, e, eps, j_x, q_x, j_y, q_y, p_xx, p_xy); MRT takes no body force and
  * runs one launch shape (lbm_set_kernel_variant has no effect on it) */
 enum { LBM_BGK = 0, LBM_MRT = 1 };
+/* boundary condition on the disks: half-way bounce-back with the moving-wall
+ * term (Sec. III.A), or the interpolated boundary of the paper's simulations
+ * (Sec. IV, ref. [40]): the surface cuts the link from a fluid node x at
+ * fraction q (from the circle), and the returned population is
+ *   q <  1/2: 2q f~_opp(x) + (1 - 2q) f~_opp(x + e_i) + M
+ *   q >= 1/2: (f~_opp(x) + M) / (2q) + (2q - 1) / (2q) f~_i(x)
+ * with M = 6 w_i rho_w (e_i . v) and v the disk's velocity at the cut (the
+ * half-way value where x + e_i is not a fluid node).  The Eq. 4/5 forces use
+ * the same returned population, and v and the torque lever at the cut.  The
+ * channel walls stay half-way.  With it, BGK runs the per-node path in the
+ * deferred pass (kernel variants 0-2 act as 3-5).  Batches take LBM_HALFWAY
+ * only. */
+enum { LBM_HALFWAY = 0, LBM_INTERPOLATED = 1 };
 /* force form: Eq. 4 (conventional) or Eq. 5 (Galilean invariant) */
 enum { LBM_CME = 0, LBM_GME = 1 };
 
@@ -91,6 +104,7 @@ typedef struct {
                                * 0 = m u as in the Eq. 4 record (default), 1 = m (u - v)
                                * relative to the boundary velocity v at the node */
     int32_t collision;     /* LBM_BGK (default) | LBM_MRT; batches take LBM_BGK only */
+    int32_t boundary;      /* disks: LBM_HALFWAY (default) | LBM_INTERPOLATED */
     void *stream;          /* cudaStream_t to run on; NULL = a stream the context creates */
 } lbm_config;
 

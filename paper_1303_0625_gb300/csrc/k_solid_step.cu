@@ -409,19 +409,50 @@ __device__ void forces_sum(const StepParams &p, int s, int lane, const void *f, 
 #pragma unroll
             for (int i = 1; i < 9; i++) {
                 if (!((m >> opp(i)) & 1u) || own[u][i] != (uint16_t)s) continue;
-                // x_s = x_f + e_i / 2 relative to R, from the unwrapped coordinate
-                C dx, dy;
-                if (Prec<P>::dev) {
-                    dx = (C)(iu - c.xi) + (C)(0.5f * cx(i)) - (C)c.fx;
-                    dy = (C)(j - c.yi) + (C)(0.5f * cy(i)) - (C)c.fy;
-                } else {
-                    dx = (C)(((double)iu + 0.5 * cx(i)) - X);
-                    dy = (C)(((double)j + 0.5 * cy(i)) - Y);
-                }
-                const C ux = vx - om * dy, uy = vy + om * dx;
+                C dx, dy, ux, uy, fbb;
                 C fi = (C)cvt_s(fv[u][i]);
                 if (Prec<P>::dev) fi += wgt<C>(i);
-                const C fbb = fi - (C)6 * wgt<C>(i) * rho_w * ((C)cx(i) * ux + (C)cy(i) * uy);
+                if (p.boundary == LBM_INTERPOLATED) {
+                    // the cut at fraction q of the link, and the population that
+                    // returns to x_f along e_opp by the fused kernel's
+                    // interpolation (full populations; M = 6 w rho_w (e_opp . v))
+                    int x, y;
+                    locate(L, iu, j, x, y);
+                    const double q = link_fraction(L, b, x, y, i);
+                    double vxd, vyd, ddx, ddy;
+                    point_velocity(L, b.x, b.y, b.vx, b.vy, b.om, (double)x + q * cx(i),
+                                   (double)y + q * cy(i), vxd, vyd, ddx, ddy);
+                    dx = (C)ddx;
+                    dy = (C)ddy;
+                    ux = (C)vxd;
+                    uy = (C)vyd;
+                    const C mw = -(C)6 * wgt<C>(i) * rho_w * ((C)cx(i) * ux + (C)cy(i) * uy);
+                    C fo = (C)cvt_s(fv[u][opp(i)]);
+                    if (Prec<P>::dev) fo += wgt<C>(i);
+                    if (q >= 0.5) {
+                        fbb = (fi + mw) / (C)(2.0 * q) + (C)((2.0 * q - 1.0) / (2.0 * q)) * fo;
+                    } else if (!((m >> i) & 1u)) {  // x_f - e_i is a fluid node
+                        int xn, yn;
+                        locate(L, x - cx(i), y - cy(i), xn, yn);
+                        C fn = (C)cvt_s(fs[i * plane + (int)cell_of(L, xn, yn)]);
+                        if (Prec<P>::dev) fn += wgt<C>(i);
+                        fbb = (C)(2.0 * q) * fi + (C)(1.0 - 2.0 * q) * fn + mw;
+                    } else {
+                        fbb = fi + mw;
+                    }
+                } else {
+                    // x_s = x_f + e_i / 2 relative to R, from the unwrapped coordinate
+                    if (Prec<P>::dev) {
+                        dx = (C)(iu - c.xi) + (C)(0.5f * cx(i)) - (C)c.fx;
+                        dy = (C)(j - c.yi) + (C)(0.5f * cy(i)) - (C)c.fy;
+                    } else {
+                        dx = (C)(((double)iu + 0.5 * cx(i)) - X);
+                        dy = (C)(((double)j + 0.5 * cy(i)) - Y);
+                    }
+                    ux = vx - om * dy;
+                    uy = vy + om * dx;
+                    fbb = fi - (C)6 * wgt<C>(i) * rho_w * ((C)cx(i) * ux + (C)cy(i) * uy);
+                }
                 const C cmx = (C)cx(i) * fi - (C)cx(opp(i)) * fbb;
                 const C cmy = (C)cy(i) * fi - (C)cy(opp(i)) * fbb;
                 const C gmx = ((C)cx(i) - ux) * fi - ((C)cx(opp(i)) - ux) * fbb;

@@ -7,9 +7,10 @@ namespace gbm {
 
 namespace {
 
-template <int P, int V, bool FORCE, bool LOCAL, bool WALLS, bool DEFER, int COLL = 0>
+template <int P, int V, bool FORCE, bool LOCAL, bool WALLS, bool DEFER, int COLL = 0,
+          bool BND = false>
 __global__ void __launch_bounds__(SC_BLOCK_X) k_stream_collide(const StepParams p) {
-    sc_tile<P, V, FORCE, LOCAL, false, WALLS, DEFER, COLL>(p, blockIdx.x, blockIdx.y);
+    sc_tile<P, V, FORCE, LOCAL, false, WALLS, DEFER, COLL, BND>(p, blockIdx.x, blockIdx.y);
 }
 
 // With the per-node path deferred (variants 3-5), the nodes k_stream_collide
@@ -79,7 +80,7 @@ __host__ __device__ long long boundary_edge_nodes(const Lattice &L) {
     return n;
 }
 
-template <int P, bool FORCE, bool LOCAL>
+template <int P, bool FORCE, bool LOCAL, bool BND>
 __global__ void __launch_bounds__(BN_BLOCK) k_boundary_update(const StepParams p) {
     using R = typename Raw<P>::R;
     const Lattice &L = p.L;
@@ -106,7 +107,7 @@ __global__ void __launch_bounds__(BN_BLOCK) k_boundary_update(const StepParams p
             x = 1 + (c < w ? c : c - w);
         }
         if (!(p.flags[cell_of(L, x, y)] & 1u))
-            update_node<P, FORCE, LOCAL, false>(p, fin, fout, x, y);
+            update_node<P, FORCE, LOCAL, false, 0, BND>(p, fin, fout, x, y);
     }
     if (blockIdx.x == 0 && threadIdx.x == 0 && p.bnd) p.bnd[(t + 1) & 1] = 0;
 }
@@ -149,7 +150,10 @@ cudaError_t launch_sc(const StepParams &p, cudaStream_t st) {
     long long blocks = (most + BN_BLOCK - 1) / BN_BLOCK;
     if (blocks > 8LL * sms) blocks = 8LL * sms;
     if (blocks < 1) blocks = 1;
-    k_boundary_update<P, FORCE, LOCAL><<<(unsigned)blocks, BN_BLOCK, 0, st>>>(p);
+    if (p.boundary == LBM_INTERPOLATED)
+        k_boundary_update<P, FORCE, LOCAL, true><<<(unsigned)blocks, BN_BLOCK, 0, st>>>(p);
+    else
+        k_boundary_update<P, FORCE, LOCAL, false><<<(unsigned)blocks, BN_BLOCK, 0, st>>>(p);
     return cudaGetLastError();
 }
 
@@ -168,16 +172,22 @@ cudaError_t launch_sc_v(const StepParams &p, cudaStream_t st) {
 // variant 1 = 8 bytes, variant 2 = 4 bytes; variants 3-5 the same widths
 // with the per-node path deferred to k_boundary_scan / k_boundary_update.
 // MRT: one launch shape, 8-byte words per population plane, slow nodes inline.
-template <int P, bool LOCAL>
-cudaError_t launch_mrt(const StepParams &p, cudaStream_t st) {
+template <int P, bool LOCAL, bool BND>
+cudaError_t launch_mrt_b(const StepParams &p, cudaStream_t st) {
     constexpr int V = 8 / (int)sizeof(typename Raw<P>::R) > 0 ? 8 / (int)sizeof(typename Raw<P>::R) : 1;
     dim3 grid((p.L.nx + SC_BLOCK_X * V - 1) / (SC_BLOCK_X * V), p.L.ny);
     if (walls_on_vector_path<P, LOCAL>() && p.L.bc_y == LBM_WALL)
-        k_stream_collide<P, V, false, LOCAL, walls_on_vector_path<P, LOCAL>(), false, 1>
+        k_stream_collide<P, V, false, LOCAL, walls_on_vector_path<P, LOCAL>(), false, 1, BND>
             <<<grid, SC_BLOCK_X, 0, st>>>(p);
     else
-        k_stream_collide<P, V, false, LOCAL, false, false, 1><<<grid, SC_BLOCK_X, 0, st>>>(p);
+        k_stream_collide<P, V, false, LOCAL, false, false, 1, BND><<<grid, SC_BLOCK_X, 0, st>>>(p);
     return cudaGetLastError();
+}
+
+template <int P, bool LOCAL>
+cudaError_t launch_mrt(const StepParams &p, cudaStream_t st) {
+    return p.boundary == LBM_INTERPOLATED ? launch_mrt_b<P, LOCAL, true>(p, st)
+                                          : launch_mrt_b<P, LOCAL, false>(p, st);
 }
 
 template <int P>
@@ -186,7 +196,8 @@ cudaError_t launch_sc_p(const StepParams &p, cudaStream_t st) {
         return p.rho_w_mode == LBM_RHOW_LOCAL ? launch_mrt<P, true>(p, st) : launch_mrt<P, false>(p, st);
     constexpr int V16 = 16 / (int)sizeof(typename Raw<P>::R);
     constexpr int V4 = V16 / 4 > 0 ? V16 / 4 : 1;
-    switch (p.sc_variant) {
+    // the interpolated boundary runs the per-node path in the deferred pass only
+    switch (p.boundary == LBM_INTERPOLATED && p.sc_variant < 3 ? p.sc_variant + 3 : p.sc_variant) {
         case 1: return launch_sc_v<P, V16 / 2, false>(p, st);
         case 2: return launch_sc_v<P, V4, false>(p, st);
         case 3: return launch_sc_v<P, V16, true>(p, st);

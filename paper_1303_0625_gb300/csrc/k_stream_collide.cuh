@@ -96,7 +96,9 @@ __device__ __forceinline__ unsigned short shfl_dn1(unsigned short v) {
 // whose source x - e_i is a wall or a solid, becomes f~_opp(x) + 6 w_i rho_w
 // (e_i . v) with v the wall's or solid's velocity at x - e_i / 2 (Sec. III.A;
 // the moving-wall term).
-template <int P, bool LOCAL>
+// BND: disks with the interpolated boundary (LBM_INTERPOLATED), compiled only
+// into the kernels that run the per-node path outside the vector path.
+template <int P, bool LOCAL, bool BND = false>
 __device__ __forceinline__ void bounce(const StepParams &p, const typename Raw<P>::R *fin, int x,
                                        int y, uint16_t fl, typename Prec<P>::C (&g)[9]) {
     using C = typename Prec<P>::C;
@@ -120,6 +122,34 @@ __device__ __forceinline__ void bounce(const StepParams &p, const typename Raw<P
             vx = sy < 0 ? pick<C>(p.wall_ux0, p.wall_ux0_f) : pick<C>(p.wall_ux1, p.wall_ux1_f);
         } else if (locate(L, sx, sy, xs, ys)) {
             const uint16_t o = p.owner[cell_of(L, xs, ys)];
+            if (BND && o != FLUID) {
+                // the cut at fraction q of the link towards the wall; linear
+                // interpolation of the returned population (deviation form
+                // as well: the weights sum to one):
+                //   q < 1/2:  2q f~_opp(x) + (1 - 2q) f~_opp(x + e_i) + M
+                //   q >= 1/2: (f~_opp(x) + M) / (2q) + (2q - 1) / (2q) f~_i(x)
+                // M = 6 w_i rho_w (e_i . v), v at the cut x - q e_i; half-way
+                // value where x + e_i is not a fluid node
+                const DSolid &b = p.S[o];
+                const double q = link_fraction(L, b, x, y, opp(i));
+                double ux, uy, ddx, ddy;
+                point_velocity(L, b.x, b.y, b.vx, b.vy, b.om, (double)x - q * cx(i),
+                               (double)y - q * cy(i), ux, uy, ddx, ddy);
+                const C m = (C)6 * wgt<C>(i) * rho_w * ((C)cx(i) * (C)ux + (C)cy(i) * (C)uy);
+                const C back = cvt(fin[opp(i) * plane + k]);
+                if (q >= 0.5) {
+                    g[i] = (back + m) / (C)(2.0 * q) +
+                           (C)((2.0 * q - 1.0) / (2.0 * q)) * cvt(fin[i * plane + k]);
+                } else if (!((fl >> opp(i)) & 1u)) {
+                    int xn, yn;
+                    locate(L, x + cx(i), y + cy(i), xn, yn);
+                    g[i] = (C)(2.0 * q) * back +
+                           (C)(1.0 - 2.0 * q) * cvt(fin[opp(i) * plane + yn * L.pitch + xn]) + m;
+                } else {
+                    g[i] = back + m;
+                }
+                continue;
+            }
             if (o != FLUID) {
                 const DSolid &b = p.S[o];
                 vx = pick<C>(b.vx, b.vxf);
@@ -305,7 +335,7 @@ __device__ __forceinline__ void extrapolate_open(const StepParams &p, bool inlet
 // the inlet is feq(rho0, u_in) and the outlet updates as a walled node.
 // Without OPEN they update as walled nodes and a later pass (open_col)
 // replaces them.
-template <int P, bool FORCE, bool LOCAL, bool OPEN, int COLL = 0>
+template <int P, bool FORCE, bool LOCAL, bool OPEN, int COLL = 0, bool BND = false>
 __device__ __noinline__ void update_node(const StepParams &p, const typename Raw<P>::R *fin,
                                          typename Raw<P>::R *fout, int x, int y) {
     using C = typename Prec<P>::C;
@@ -349,7 +379,7 @@ __device__ __noinline__ void update_node(const StepParams &p, const typename Raw
         if (ys >= L.ny) ys = per_y ? ys - L.ny : L.ny - 1;
         g[i] = cvt(fin[i * plane + ys * L.pitch + xs]);
     }
-    if (flu & 0x1FEu) bounce<P, LOCAL>(p, fin, xu, y, flu, g);
+    if (flu & 0x1FEu) bounce<P, LOCAL, BND>(p, fin, xu, y, flu, g);
     if constexpr (COLL == 1) collide_mrt<P, true>(p, g);
     else collide<P, FORCE>(p, g);
     if (OPEN && open) extrapolate_open<P, FORCE>(p, x == 0, u_in, g);
@@ -373,7 +403,7 @@ __host__ __device__ constexpr bool walls_on_vector_path() { return !LOCAL && P !
 // for its own nodes at the end of the tile.
 // COLL: 0 = BGK, 1 = MRT (no body force, slow nodes inline).
 template <int P, int V, bool FORCE, bool LOCAL, bool OPEN, bool WALLS = false, bool DEFER = false,
-          int COLL = 0>
+          int COLL = 0, bool BND = false>
 __device__ __forceinline__ void sc_tile(const StepParams &p, int bx, int y) {
     static_assert(!WALLS || walls_on_vector_path<P, LOCAL>(), "wall rows need rho0 and R == C");
     using R = typename Raw<P>::R;
@@ -603,7 +633,7 @@ __device__ __forceinline__ void sc_tile(const StepParams &p, int bx, int y) {
         while (slow) {
             const int j = __ffs(slow) - 1;
             slow &= slow - 1;
-            update_node<P, FORCE, LOCAL, OPEN, COLL>(p, fin, fout, x0 + j, y);
+            update_node<P, FORCE, LOCAL, OPEN, COLL, BND>(p, fin, fout, x0 + j, y);
         }
     }
 }

@@ -129,6 +129,7 @@ StepParams params(const lbm_ctx *c) {
     p.motion_cme = g.motion_cme;
     p.relative_changes = g.relative_changes;
     p.collision = g.collision;
+    p.boundary = g.boundary;
     p.precision = g.precision;
     p.sc_variant = c->sc_variant;
     p.bnd = c->bnd_d;
@@ -316,6 +317,8 @@ lbm_status lbm_create(const lbm_config *cfg, lbm_ctx **out) {
         return fail(nullptr, LBM_EINVAL, "collision must be LBM_BGK or LBM_MRT");
     if (g.collision == LBM_MRT && (g.body_force[0] != 0.0 || g.body_force[1] != 0.0))
         return fail(nullptr, LBM_EINVAL, "MRT takes no body force");
+    if (g.boundary != LBM_HALFWAY && g.boundary != LBM_INTERPOLATED)
+        return fail(nullptr, LBM_EINVAL, "boundary must be LBM_HALFWAY or LBM_INTERPOLATED");
     if (g.bc_x == LBM_OPEN && g.bc_y != LBM_WALL)
         return fail(nullptr, LBM_EINVAL, "an open channel needs walls in y");
     if (cudaSetDevice(g.device) != cudaSuccess)
@@ -1152,8 +1155,9 @@ lbm_status lbm_batch_create(const lbm_config *configs, int32_t ncase, lbm_batch 
     if (!configs || !out || ncase < 1) return bfail(nullptr, LBM_EINVAL, "bad batch arguments");
     *out = nullptr;
     for (int k = 0; k < ncase; k++)
-        if (configs[k].collision != LBM_BGK)
-            return bfail(nullptr, LBM_EINVAL, "case %d: batches run BGK only", k);
+        if (configs[k].collision != LBM_BGK || configs[k].boundary != LBM_HALFWAY)
+            return bfail(nullptr, LBM_EINVAL,
+                         "case %d: batches run BGK with the half-way boundary only", k);
     for (int k = 1; k < ncase; k++)
         if (configs[k].precision != configs[0].precision ||
             configs[k].rho_w_mode != configs[0].rho_w_mode ||

@@ -87,6 +87,7 @@ struct StepParams {
     int motion_cme;           // free solids move under Eq. 4 (1) or Eq. 5 (0)
     int relative_changes;     // Eq. 5 record books covered/fresh momenta as m (u - v)
     int collision;            // LBM_BGK or LBM_MRT
+    int boundary;             // disks: LBM_HALFWAY or LBM_INTERPOLATED
     int sc_variant;           // node width per thread of the advection-collision kernel
     float omega_f, body_xf, body_yf, rho0_f;  // FP32 copies for the FP32 kernels
     float wall_ux0_f, wall_ux1_f, umax_f;
@@ -281,6 +282,24 @@ __device__ __forceinline__ void point_velocity(const Lattice &L, const double X,
     uy = vy + om * dx;
 }
 
+// Interpolated boundary (the disks' boundary condition of the paper's
+// simulations, ref. [40]): fraction q in (0, 1] of the link from the fluid
+// node (x, y) along e_i at which it meets the circle of disk b, the smaller
+// root of |p + q e_i - R|^2 = r^2 with p - R at the nearest periodic image.
+__device__ __forceinline__ double link_fraction(const Lattice &L, const DSolid &b, int x, int y,
+                                                int i) {
+    const double px = min_image(__dsub_rn((double)x, b.x), L.nx, L.bc_x == LBM_PERIODIC);
+    const double py = min_image(__dsub_rn((double)y, b.y), L.ny, L.bc_y == LBM_PERIODIC);
+    const double ex = cx(i), ey = cy(i);
+    const double a = ex * ex + ey * ey, h = px * ex + py * ey;
+    const double cc = px * px + py * py - b.r * b.r;  // > 0: the node is outside
+    const double disc = h * h - a * cc;
+    double q = disc > 0.0 ? (-h - sqrt(disc)) / a : 0.5;
+    if (!(q > 0.0)) q = 0.0;
+    if (q > 1.0) q = 1.0;
+    return q;
+}
+
 __device__ __forceinline__ long long cell_of(const Lattice &L, int x, int y) {
     return (long long)y * L.pitch + x;
 }
@@ -323,7 +342,8 @@ struct BatchState {
 constexpr int KERNEL_VARIANTS = 6;
 inline int stream_collide_launches(const StepParams &p) {
     if (p.collision == LBM_MRT) return 1;  // MRT keeps the slow nodes inline
-    return p.sc_variant >= 3 ? (p.nsolid > 0 ? 3 : 2) : 1;
+    const bool deferred = p.sc_variant >= 3 || p.boundary == LBM_INTERPOLATED;
+    return deferred ? (p.nsolid > 0 ? 3 : 2) : 1;
 }
 cudaError_t launch_stream_collide(const StepParams &p, cudaStream_t st);
 // open channel: columns 0 and nx-1 of the populations just written (t+1)

@@ -25,6 +25,7 @@ LBM_REFILL_A1, LBM_REFILL_A2, LBM_REFILL_A3 = 1, 2, 3
 LBM_PRESCRIBED, LBM_FREE = 0, 1
 LBM_CME, LBM_GME = 0, 1
 LBM_BGK, LBM_MRT = 0, 1
+LBM_HALFWAY, LBM_INTERPOLATED = 0, 1
 
 PRECISION_NAMES = {"fp64": LBM_FP64, "fp32": LBM_FP32_DEV, "fp16": LBM_FP16_DEV}
 
@@ -47,6 +48,7 @@ class lbm_config(ctypes.Structure):
         ("refill", ctypes.c_int32), ("force_ring", ctypes.c_int32),
         ("device", ctypes.c_int32), ("motion_cme", ctypes.c_int32),
         ("relative_changes", ctypes.c_int32), ("collision", ctypes.c_int32),
+        ("boundary", ctypes.c_int32),
         ("stream", ctypes.c_void_p),
     ]
 
@@ -528,7 +530,7 @@ def make_config(nx, ny, tau, *, rho0=1.0, u0=(0.0, 0.0), bc_x=LBM_PERIODIC, bc_y
                 wall_ux=(0.0, 0.0), body_force=(0.0, 0.0), inflow_umax=0.0, gravity=(0.0, 0.0),
                 lub_range=0.0, precision=LBM_FP64, rho_w_mode=LBM_RHOW_CONST,
                 refill=LBM_REFILL_A1, force_ring=256, device=0, stream=None,
-                motion_cme=0, relative_changes=0, collision=0) -> lbm_config:
+                motion_cme=0, relative_changes=0, collision=0, boundary=0) -> lbm_config:
     c = lbm_config_default()
     c.nx, c.ny, c.bc_x, c.bc_y = int(nx), int(ny), int(bc_x), int(bc_y)
     c.tau, c.rho0 = float(tau), float(rho0)
@@ -544,6 +546,7 @@ def make_config(nx, ny, tau, *, rho0=1.0, u0=(0.0, 0.0), bc_x=LBM_PERIODIC, bc_y
     c.motion_cme = int(motion_cme)
     c.relative_changes = int(relative_changes)
     c.collision = int(collision)
+    c.boundary = int(boundary)
     c.stream = stream
     return c
 
@@ -568,7 +571,7 @@ class Lattice:
                     refill=w.get("refill", 1), precision=precision,
                     motion_cme=w.get("motion_cme", 0),
                     relative_changes=w.get("relative_changes", 0),
-                    collision=w.get("collision", 0))
+                    collision=w.get("collision", 0), boundary=w.get("boundary", 0))
         opts.update(kw)
         lat = cls(w["nx"], w["ny"], w["tau"], **opts)
         if add_solids:

@@ -66,7 +66,7 @@ def test_unet_config_layout_matches_header(tmp_path):
 
 
 @pytest.mark.parametrize("field,value", [("tau", 0.5), ("tau", 0.2), ("nx", 3), ("precision", 7),
-                                         ("refill", 0), ("force_ring", 0), ("motion_cme", 2), ("relative_changes", -1), ("collision", 2),
+                                         ("refill", 0), ("force_ring", 0), ("motion_cme", 2), ("relative_changes", -1), ("collision", 2), ("boundary", 2),
                                          ("bc_y", 2)])
 def test_create_rejects_invalid_config_without_touching_the_gpu(field, value):
     c = L.make_config(32, 32, 0.8)
