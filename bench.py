@@ -74,6 +74,11 @@ def parse():
     ap.add_argument("--galilean", type=int, default=0, metavar="STEPS",
                     help="free-disk sedimentation in frames moving at V (Sec. III.A), driven by "
                          "Eq. 5 and by Eq. 4: trajectory deviations from V = 0 after STEPS steps")
+    ap.add_argument("--galilean-boundary", choices=["halfway", "interpolated"], default="halfway",
+                    help="disk boundary of --galilean")
+    ap.add_argument("--galilean-density", type=float, default=1.5,
+                    help="solid/fluid density ratio of --galilean (the paper's 1.01 and 1.03 "
+                         "need the interpolated boundary)")
     ap.add_argument("--batch-only", action="store_true",
                     help="measure only the cylinder-sweep batch and print its record")
     ap.add_argument("--batch-warmup", type=int, default=100)
@@ -770,14 +775,17 @@ def run_galilean(a, local):
     Three series: Eq. 5 drives the disk, Eq. 4 drives it, and Eq. 5 with the
     covered/fresh momenta booked relative to the boundary velocity.
     Density ratio 1.5 and net gravity 7.4e-6 (terminal Reynolds number about
-    9): the paper's ratios 1.01 and 1.03 are unstable with half-way
-    bounce-back and explicit coupling.  FP64 storage and arithmetic."""
+    9) by default: the paper's ratios 1.01 and 1.03 are unstable with half-way
+    bounce-back and explicit coupling, and run with the interpolated boundary
+    (--galilean-boundary interpolated --galilean-density 1.03).  FP64."""
     import numpy as np
     import torch
     import paper_1303_0625_gb300 as G
     import workloads as W
     torch.cuda.set_device(local)
-    width, length, r, tau, rs, gnet, every = 120, 1200, 15.0, 0.6, 1.5, 7.4e-6, 500
+    width, length, r, tau, gnet, every = 120, 1200, 15.0, 0.6, 7.4e-6, 500
+    rs = a.galilean_density
+    boundary = 1 if a.galilean_boundary == "interpolated" else 0
     g = gnet / (1.0 - 1.0 / rs)
     frames = (0.0, 0.001, 0.002, 0.01, 0.02)
     traj = {}
@@ -788,6 +796,7 @@ def run_galilean(a, local):
             w = dict(nx=length, ny=width, tau=tau, rho0=1.0, bc_x=W.PERIODIC, bc_y=W.WALL,
                      u0=(V, 0.0), wall_ux=(V, V), body_force=(0.0, 0.0), gravity=(-g, 0.0),
                      rho_w_mode=0, refill=1, motion_cme=cme, relative_changes=relative,
+                     boundary=boundary,
                      solids=[dict(cx=0.6 * length, cy=0.19 * width - 0.5, r=r, vx=V, vy=0.0,
                                   omega=0.0, rho_s=rs, motion=1)])
             lat = G.Lattice.from_workload(w, precision=G.LBM_FP64, force_ring=8, device=local)
@@ -802,7 +811,8 @@ def run_galilean(a, local):
             traj[(cme, relative, V)] = np.array(rows)
     out = {"metric": "trajectory relative to the channel vs frame velocity V (Sec. III.A)",
            "geometry": f"{length}x{width} channel, disk r {r}, tau {tau}, rho_s/rho_f {rs}, "
-                       f"net gravity {gnet}", "steps": max(1, a.galilean // every) * every,
+                       f"net gravity {gnet}, {a.galilean_boundary} boundary",
+           "steps": max(1, a.galilean // every) * every,
            "seconds": round(time.perf_counter() - t0, 1)}
     for cme, relative, name in series:
         base = traj[(cme, relative, 0.0)]
