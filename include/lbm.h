@@ -145,8 +145,13 @@ lbm_status lbm_add_solid(lbm_ctx *ctx, const lbm_disk *disk, int32_t *id_out);
  * waits.  nsteps >= 0. */
 lbm_status lbm_step(lbm_ctx *ctx, int64_t nsteps);
 
-/* Wait for all enqueued work; LBM_EUNSTABLE if any step produced a
- * non-finite or non-positive density. */
+/* Wait for all enqueued work.  The status a step's kernels raised:
+ * LBM_EUNSTABLE for a non-finite or non-positive density or a non-finite
+ * solid state; LBM_ETIMEOUT when a grid barrier of the per-solid kernel gave
+ * up; LBM_ESTATE when a solid covered or uncovered more than 256 nodes in one
+ * step (its event queue) or the deferred list of nodes next to solids
+ * overflowed (the step's momentum booking or slow-node update is then
+ * incomplete). */
 lbm_status lbm_sync(lbm_ctx *ctx);
 
 /* Copy the force records of steps first_step .. first_step+count-1 into out,

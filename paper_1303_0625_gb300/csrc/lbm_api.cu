@@ -266,6 +266,10 @@ lbm_status check_status(lbm_ctx *c) {
         cudaMemsetAsync(c->bar_d, 0, 2 * sizeof(unsigned int), c->stream);
         return fail(c, LBM_ETIMEOUT, "a grid-wide barrier of the per-solid kernel timed out");
     }
+    if (st & 8)
+        return fail(c, LBM_ESTATE,
+                    "a solid covered or uncovered more nodes in one step than its event queue "
+                    "holds (%d)", gbm::SOLID_EVENTS);
     if (st & 16) return fail(c, LBM_ESTATE, "the list of nodes next to solids overflowed");
     return LBM_OK;
 }
