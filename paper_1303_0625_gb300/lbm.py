@@ -531,6 +531,11 @@ def make_config(nx, ny, tau, *, rho0=1.0, u0=(0.0, 0.0), bc_x=LBM_PERIODIC, bc_y
                 lub_range=0.0, precision=LBM_FP64, rho_w_mode=LBM_RHOW_CONST,
                 refill=LBM_REFILL_A1, force_ring=256, device=0, stream=None,
                 motion_cme=0, relative_changes=0, collision=0, boundary=0) -> lbm_config:
+    """An lbm_config (see include/lbm.h for every field).  Model options:
+    collision LBM_BGK | LBM_MRT; boundary LBM_HALFWAY | LBM_INTERPOLATED (the
+    disks' boundary condition); motion_cme 1 drives free solids by the Eq. 4
+    force instead of Eq. 5; relative_changes 1 books covered and fresh nodes
+    in the Eq. 5 record as m (u - v)."""
     c = lbm_config_default()
     c.nx, c.ny, c.bc_x, c.bc_y = int(nx), int(ny), int(bc_x), int(bc_y)
     c.tau, c.rho0 = float(tau), float(rho0)
