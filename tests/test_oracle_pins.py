@@ -723,3 +723,23 @@ def test_galilean_invariance_of_eq5_with_the_interpolated_boundary():
     dev4 = np.abs(run(1, 0, 0.002) - run(1, 0, 0.0)).max()
     assert dev5 < 1e-4
     assert dev5 < dev4 / 5
+
+
+def test_refill_order_of_force_fluctuations():
+    """Fig. 5(d): a sedimenting disk (density ratio 1.03, interpolated
+    boundary, Eq. 5 with relative booking) fluctuates least with the
+    second-order extrapolation A1, then A2, then the neighbour average A3;
+    fluctuation by Eq. 11 against the force smoothed over 20 points."""
+    W_, L_, r, rs, gnet, steps = 40, 200, 5.0, 1.03, 2e-4, 1500
+    g = gnet / (1 - 1 / rs)
+
+    def fluctuation(refill):
+        o = O.Oracle(L_, W_, 0.6, bc_y=O.WALL, gravity=(-g, 0.0), boundary=1,
+                     relative_changes=1, refill=refill)
+        o.add_disk(0.6 * L_, 0.19 * W_ - 0.5, r, 0.0, 0.0, 0.0, rs, O.FREE)
+        fx = o.step(steps)[steps // 5:, 0, 1, 0]
+        smooth = np.array([fx[max(0, k - 10):k + 10].mean() for k in range(len(fx))])
+        return np.sqrt(((fx - smooth) ** 2).sum() / (smooth ** 2).sum())
+
+    e1, e2, e3 = (fluctuation(a) for a in (1, 2, 3))
+    assert e1 < e2 < e3
