@@ -134,13 +134,24 @@ lbm_status lbm_create(const lbm_config *cfg, lbm_ctx **out);
 lbm_status lbm_destroy(lbm_ctx *ctx);
 
 /* Add a rigid disk at the current time and rasterise it into the owner map
- * (nodes it covers become solid; no momentum is booked for them).  Solid ids
+ * (nodes it covers become solid; no momentum is booked for them).  The solid
+ * is the moving boundary of Sec. III.A: a rigid body whose surface point S
+ * has the velocity v = V + Omega x (S - R) that enters the bounced population
+ * and Eq. 5; LBM_FREE disks are the freely moving cylinders of Sec. IV
+ * (translation and rotation under gravity and the hydrodynamic force of
+ * Eq. 6-7).  Solid ids
  * are 0, 1, ... in order of addition; where disks overlap the lowest id owns
  * the node.  Errors: LBM_EINVAL (r <= 0, r >= min(nx, ny) / 2 - 4, centre not
  * finite, rho_s <= 0 for a free disk, more than 65534 solids). */
 lbm_status lbm_add_solid(lbm_ctx *ctx, const lbm_disk *disk, int32_t *id_out);
 
 /* Enqueue nsteps steps on the context's stream; returns without waiting.
+ * One step t -> t+1 is the lattice Boltzmann equation Eq. 1 split into
+ * collision Eq. 2 (BGK towards Eq. 8) and advection Eq. 3, with the solids'
+ * links handled by bounce-back and the moving-wall term (Sec. III.A), the
+ * force record of time t by Eq. 4-7 before advection, the solids' motion,
+ * and the node-type changes of Sec. I (covered nodes' momentum to the solid,
+ * fresh nodes refilled by the extrapolation of Sec. IV.B).
  * Device errors from earlier work surface here or at the next call that
  * waits.  nsteps >= 0. */
 lbm_status lbm_step(lbm_ctx *ctx, int64_t nsteps);
@@ -166,8 +177,10 @@ lbm_status lbm_forces(lbm_ctx *ctx, int32_t form, int64_t first_step, int64_t co
                       int32_t on_device);
 
 /* Density and velocity of the current post-collision state, each [ny][nx]
- * FP64; solid nodes are NaN.  With a body force the velocity is
- * (sum_i e_i f_i - F/2) / rho.  on_device as for lbm_forces. */
+ * FP64: the moments of Sec. II, rho = sum_i f_i and rho u = sum_i e_i f_i
+ * (collision conserves both, so pre- and post-collision agree); solid nodes
+ * are NaN.  With a body force the velocity is (sum_i e_i f_i - F/2) / rho.
+ * on_device as for lbm_forces. */
 lbm_status lbm_fields(lbm_ctx *ctx, double *rho, double *ux, double *uy, int32_t on_device);
 
 /* Same result as lbm_fields(ctx, rho, ux, uy, 0), for callers that must not

@@ -215,6 +215,48 @@ def test_open_channel_velocity_inlet_pressure_outlet():
     assert a["prof"] / b["prof"] == pytest.approx(4.0, rel=0.1)
 
 
+def _open_end_shear(tau, ny, nx=24, umax=1e-3):
+    """Relative error of the post-collision shear moment of the open ends
+    against the BGK stress of the parabola, (inlet, outlet)."""
+    nu = (tau - 0.5) / 3
+    o = O.Oracle(nx, ny, tau, bc_x=O.OPEN, bc_y=O.WALL, inflow_umax=umax)
+    o.step(int(12 * ny * ny / nu), record=False)
+    f = o.get_f()
+    ux = o.fields()[1]
+    y = np.arange(ny) + 0.5
+    shape = 4 * y * (ny - y) / ny**2
+    amp = (ux[:, nx // 2] * shape).sum() / (shape * shape).sum()  # the bulk parabola
+    out = []
+    for b, a in ((0, umax), (nx - 1, amp)):
+        fb = f[:, :, b]
+        rho = fb.sum(0)
+        u, v = (EX[:, None] * fb).sum(0) / rho, (EY[:, None] * fb).sum(0) / rho
+        eq = np.stack([O.feq(rho[j], u[j], v[j]) for j in range(ny)], axis=1)
+        pi = (EX[:, None] * EY[:, None] * (fb - eq)).sum(0)
+        want = -(tau - 1) * rho / 3 * a * 4 * (ny - 2 * y) / ny**2
+        out.append(float(np.abs(pi - want).max() / np.abs(want).max()))
+    return out
+
+
+def test_open_channel_ends_carry_the_bgk_shear_stress():
+    """The non-equilibrium part of the open ends' extrapolation: at steady
+    state the inlet and outlet columns' post-collision shear moment
+    sum_i e_x e_y (f~_i - f_eq_i(rho, u)), with rho and u the column's own
+    moments, equals the BGK stress of the parabola, -(tau - 1) rho du/dy / 3
+    (collision scales the Chapman-Enskog stress -tau rho du/dy / 3 by
+    1 - 1/tau).  Inlet: the prescribed parabola; outlet: the bulk one.  An
+    end column without the non-equilibrium term has no shear moment (error
+    1); with the term's sign flipped, error 2.  The inlet's error is the
+    first-order inlet defect (halving from ny = 16 to 32)."""
+    exact = 0.5 + math.sqrt(3) / 4
+    i16, o16 = _open_end_shear(exact, 16)
+    i32, o32 = _open_end_shear(exact, 32)
+    assert i16 < 0.03 and i32 < 0.015 and o16 < 1e-3 and o32 < 1e-3
+    assert i16 / i32 == pytest.approx(2.0, rel=0.2)
+    i8, o8 = _open_end_shear(0.8, 16)
+    assert i8 < 0.01 and o8 < 0.01
+
+
 # ------------------------------------------------------- bookkeeping
 
 def _perturbed(o, seed, amp=0.01, u=(0.0, 0.0)):
