@@ -55,6 +55,9 @@ def parse():
     ap.add_argument("--variant", type=int, default=-1,
                     help="launch variant of the advection-collision pass (0-5, see lbm.h); "
                          "default: the autotuner's choice")
+    ap.add_argument("--overlap", type=int, default=-1, choices=[-1, 0, 1],
+                    help="force kernel beside (1) or before (0) the advection-collision kernel; "
+                         "default: the autotuner's choice")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the e2e pass, the other precisions and the CPU baseline")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
@@ -76,8 +79,14 @@ def parse():
                          "Eq. 5 and by Eq. 4: trajectory deviations from V = 0 after STEPS steps")
     ap.add_argument("--galilean-boundary", choices=["halfway", "interpolated"], default="halfway",
                     help="disk boundary of --galilean")
+    ap.add_argument("--galilean-frames", type=str, default="0,0.001,0.002,0.01,0.02",
+                    help="frame velocities V of --galilean, comma-separated, the first 0")
+    ap.add_argument("--galilean-gravity", type=float, default=0.0,
+                    help="gravity of --galilean in lattice units (net of buoyancy: g (1 - rho_f/rho_s)); "
+                         "0 keeps the net gravity 7.4e-6; the paper's 980 cm/s^2 at its scales "
+                         "(dx = 0.4/120 cm, nu = 0.01 cm^2/s, tau 0.6) is 4.03e-4")
     ap.add_argument("--galilean-density", type=float, default=1.5,
-                    help="solid/fluid density ratio of --galilean (the paper's 1.01 and 1.03 "
+                    help="solid/fluid density ratio of --galilean (the paper's 1.003 and 1.03 "
                          "need the interpolated boundary)")
     ap.add_argument("--batch-only", action="store_true",
                     help="measure only the cylinder-sweep batch and print its record")
@@ -247,17 +256,21 @@ def run_ours(a, ws, rank, local):
     cells = w["nx"] * w["ny"]
     peaks, peak_kind = measured_peaks()
 
-    def measure(precision, steps, warmup, sample_clocks, collision=0):
+    def measure(precision, steps, warmup, sample_clocks, collision=0, boundary=0):
         lat = G.Lattice.from_workload(w, precision=G.PRECISION_NAMES[precision], device=local,
                                       stream=stream.cuda_stream, force_ring=512,
-                                      collision=collision)
+                                      collision=collision, boundary=boundary)
         if collision:
             variant = -1  # MRT has one launch shape
         elif a.variant >= 0:
             lat.set_kernel_variant(a.variant)
             variant = a.variant
+            if a.overlap >= 0:
+                lat.set_force_overlap(a.overlap)
         else:
-            variant = lat.autotune(4)  # node width and slow-node path of the fused pass
+            # node width and slow-node path of the fused pass, and where the
+            # force kernel runs
+            variant = lat.autotune(4)
         lat.step(warmup)
         lat.sync()
         lat.set_timing(True)
@@ -281,9 +294,11 @@ def run_ours(a, ws, rank, local):
         k1_ms, k1_n = lat.timing()
         launches = lat.launch_count() - launches0
         nfluid = int((lat.owner() < 0).sum())
+        overlap = lat.force_overlap()
         lat.close()
         return dict(ms=ms, k1_avg_ms=k1_ms / max(k1_n, 1), launches=launches, nfluid=nfluid,
-                    clocks=clocks.summary() if sample_clocks else None, variant=variant)
+                    clocks=clocks.summary() if sample_clocks else None, variant=variant,
+                    overlap=overlap)
 
     main = measure(a.precision, a.steps, a.warmup, rank == 0,
                    collision=1 if a.collision == "mrt" else 0)
@@ -305,6 +320,13 @@ def run_ours(a, ws, rank, local):
                 "bytes_per_node": 18 * STORAGE_BYTES[a.precision] + 2,
                 "avg_launch_ms": round(main["k1_avg_ms"], 5),
                 "kernel_variant": main["variant"],
+                "force_kernel": "beside it (second stream)" if main["overlap"] else "before it",
+                "frac_counts": "all nodes of the domain",
+                # the method's own work: the fluid nodes only
+                "frac_fluid_nodes": round(main["nfluid"] * (18 * STORAGE_BYTES[a.precision] + 2)
+                                          / (main["k1_avg_ms"] / 1e3) / 1e9 / peak, 4),
+                # the whole step (forces, motion and re-rasterisation included)
+                "step_frac": round(bytes_launch / (t_max / a.steps / 1e3) / 1e9 / peak, 4),
                 "share_of_step": round(main["k1_avg_ms"] / (main["ms"] / a.steps), 4)}
     line = {"metric": METRIC, "value": round(value, 1), "unit": "MLUPS", "n_gpus": ws,
             "steps": a.steps, "warmup": a.warmup, "ms_per_step": round(t_max / a.steps, 5),
@@ -342,6 +364,17 @@ def run_ours(a, ws, rank, local):
                              "kernel_gbs": round(b / (m["k1_avg_ms"] / 1e3) / 1e9, 1),
                              "kernel_frac_of_hbm": round(b / (m["k1_avg_ms"] / 1e3) / 1e9 / peak, 4),
                              "ms_per_step": round(m["ms"] / k, 5)}
+        # the interpolated boundary of the paper's simulations (Sec. IV, ref. [40])
+        m = measure("fp32", k, 3, False, boundary=G.LBM_INTERPOLATED)
+        modes["fp32_interpolated"] = {
+            "mlups": round(cells * k / (m["ms"] / 1e3) / 1e6, 1), "steps": k,
+            "kernel_gbs": round(b / (m["k1_avg_ms"] / 1e3) / 1e9, 1),
+            "kernel_frac_of_hbm": round(b / (m["k1_avg_ms"] / 1e3) / 1e9 / peak, 4),
+            "ms_per_step": round(m["ms"] / k, 5)}
+        for name, rec in modes.items():  # the whole step against the roofline of its storage
+            prec = "fp32" if name.startswith("fp32") else name
+            rec["step_frac"] = round(algorithmic_bytes(prec, cells) / (rec["ms_per_step"] / 1e3)
+                                     / 1e9 / peak, 4)
         line["modes"] = modes
         line["batch"] = run_batch(a, local, stream, peak)
         line["sedimentation"] = run_sedimentation(a, local, stream, peak)
@@ -775,20 +808,25 @@ def run_galilean(a, local):
     Three series: Eq. 5 drives the disk, Eq. 4 drives it, and Eq. 5 with the
     covered/fresh momenta booked relative to the boundary velocity.
     Density ratio 1.5 and net gravity 7.4e-6 (terminal Reynolds number about
-    9) by default: the paper's ratios 1.01 and 1.03 are unstable with half-way
+    9) by default: the paper's ratios 1.003 and 1.03 are unstable with half-way
     bounce-back and explicit coupling, and run with the interpolated boundary
-    (--galilean-boundary interpolated --galilean-density 1.03).  FP64."""
+    (--galilean-boundary interpolated --galilean-density 1.03 --galilean-frames
+    0,0.01,0.02 --galilean-gravity 4.03e-4, the paper's gravity).  FP64.  A
+    run that turns unstable is reported as such."""
     import numpy as np
     import torch
     import paper_1303_0625_gb300 as G
     import workloads as W
     torch.cuda.set_device(local)
-    width, length, r, tau, gnet, every = 120, 1200, 15.0, 0.6, 7.4e-6, 500
+    width, length, r, tau, every = 120, 1200, 15.0, 0.6, 500
     rs = a.galilean_density
     boundary = 1 if a.galilean_boundary == "interpolated" else 0
-    g = gnet / (1.0 - 1.0 / rs)
-    frames = (0.0, 0.001, 0.002, 0.01, 0.02)
-    traj = {}
+    g = a.galilean_gravity if a.galilean_gravity > 0 else 7.4e-6 / (1.0 - 1.0 / rs)
+    gnet = g * (1.0 - 1.0 / rs)
+    frames = tuple(float(v) for v in a.galilean_frames.split(","))
+    assert frames[0] == 0.0, "the first frame velocity is the reference, 0"
+    nu = (tau - 0.5) / 3.0
+    traj, unstable = {}, {}
     t0 = time.perf_counter()
     series = ((0, 0, "eq5_gme"), (1, 0, "eq4_cme"), (0, 1, "eq5_gme_relative_changes"))
     for cme, relative, _ in series:
@@ -801,22 +839,32 @@ def run_galilean(a, local):
                                   omega=0.0, rho_s=rs, motion=1)])
             lat = G.Lattice.from_workload(w, precision=G.LBM_FP64, force_ring=8, device=local)
             rows = []
-            for k in range(max(1, a.galilean // every)):
-                lat.step(every)
-                st = lat.solids()[0]
-                rows.append([st[0] - 0.6 * length - V * every * (k + 1), st[1], st[2] - V, st[3],
-                             st[4]])
-            lat.sync()
+            try:
+                for k in range(max(1, a.galilean // every)):
+                    lat.step(every)
+                    st = lat.solids()[0]
+                    rows.append([st[0] - 0.6 * length - V * every * (k + 1), st[1], st[2] - V,
+                                 st[3], st[4]])
+                lat.sync()
+            except G.LBMError as e:  # the method's instability, reported by the status word
+                unstable[(cme, relative, V)] = f"{e} (within steps {len(rows) * every}.."\
+                                               f"{(len(rows) + 1) * every})"
             lat.close()
             traj[(cme, relative, V)] = np.array(rows)
     out = {"metric": "trajectory relative to the channel vs frame velocity V (Sec. III.A)",
            "geometry": f"{length}x{width} channel, disk r {r}, tau {tau}, rho_s/rho_f {rs}, "
-                       f"net gravity {gnet}, {a.galilean_boundary} boundary",
+                       f"net gravity {gnet:.4g}, {a.galilean_boundary} boundary",
            "steps": max(1, a.galilean // every) * every,
            "seconds": round(time.perf_counter() - t0, 1)}
     for cme, relative, name in series:
         base = traj[(cme, relative, 0.0)]
-        rec = {"final_V0": [round(float(v), 5) for v in base[-1]]}
+        bad = {f"V={V}": unstable[(cme, relative, V)] for V in frames
+               if (cme, relative, V) in unstable}
+        if bad:
+            out[name] = {"unstable": bad}
+            continue
+        rec = {"final_V0": [round(float(v), 5) for v in base[-1]],
+               "terminal_Re_V0": round(float(2.0 * r * abs(base[-1][2]) / nu), 3)}
         for V in frames[1:]:
             dev = np.abs(traj[(cme, relative, V)] - base).max(axis=0)
             rec[f"V={V}"] = {"max_dx": round(float(dev[0]), 4), "max_dy": round(float(dev[1]), 4),

@@ -162,7 +162,8 @@ lbm_status lbm_step(lbm_ctx *ctx, int64_t nsteps);
  * up; LBM_ESTATE when a solid covered or uncovered more than 256 nodes in one
  * step (its event queue) or the deferred list of nodes next to solids
  * overflowed (the step's momentum booking or slow-node update is then
- * incomplete). */
+ * incomplete).  These conditions persist: every later waiting call returns
+ * them until lbm_load restores a saved state. */
 lbm_status lbm_sync(lbm_ctx *ctx);
 
 /* Copy the force records of steps first_step .. first_step+count-1 into out,
@@ -209,6 +210,27 @@ lbm_status lbm_fields_static(lbm_ctx *ctx, double *rho, double *ux, double *uy);
 lbm_status lbm_get_populations(lbm_ctx *ctx, double *f, int32_t on_device);
 lbm_status lbm_set_populations(lbm_ctx *ctx, const double *f, int32_t on_device);
 
+/* Checkpoints.  A saved state holds everything the next steps depend on: the
+ * populations of the current time in the storage precision, the owner map,
+ * the node flags, the solid table (FP64 centres, velocities, closed-form
+ * motion origins), the force history, the momenta the last re-rasterisation
+ * booked into the next force record, and the step counter.  lbm_state_size
+ * gives the bytes lbm_save needs now (they change with the step's
+ * covered/fresh event count).  lbm_save waits for the stream, then copies the
+ * state into buf (host memory the caller owns); it returns the status of the
+ * steps taken (a state after LBM_EUNSTABLE or LBM_ETIMEOUT is not saved).
+ * lbm_load restores a state into a context created with the same
+ * configuration (stream and device aside) and holding the same solids (the
+ * same lbm_add_solid calls): the status word and the bounded waits' counters
+ * are cleared, and the steps that follow give the same results, bit for bit,
+ * as those that followed the save.  Errors: LBM_EINVAL for a buffer that is
+ * too small, not a saved state, or from another configuration or solid
+ * count (nothing is changed then); a batch's cases are not saved one by
+ * one.  This is a service of the library; the paper has none. */
+lbm_status lbm_state_size(lbm_ctx *ctx, int64_t *bytes);
+lbm_status lbm_save(lbm_ctx *ctx, void *buf, int64_t bytes);
+lbm_status lbm_load(lbm_ctx *ctx, const void *buf, int64_t bytes);
+
 /* Owner map [ny][nx]: -1 for fluid, else the id of the solid covering the
  * node.  on_device as for lbm_forces. */
 lbm_status lbm_get_owner(lbm_ctx *ctx, int32_t *owner, int32_t on_device);
@@ -237,6 +259,15 @@ int32_t lbm_nsolid(const lbm_ctx *ctx);
 const char *lbm_last_error(const lbm_ctx *ctx);
 const char *lbm_status_string(lbm_status st);
 
+/* Bounded device waits: a grid-wide barrier of the re-rasterisation kernel
+ * gives up after `polls` polls of about 64 ns (default 2^24, about one
+ * second); the launch then stops, and the next call that waits returns
+ * LBM_ETIMEOUT (the step's per-solid work is incomplete: restore a state
+ * saved by lbm_save before stepping on).  0 gives up at once, so that every
+ * step with moving solids times out: the time-out path can be exercised
+ * without a stalled device.  LBM_EINVAL for polls < 0. */
+lbm_status lbm_set_wait_limit(lbm_ctx *ctx, int64_t polls);
+
 /* Launch policy.  steps_per_graph > 1 captures that many steps into one CUDA
  * graph and replays it; 0 or 1 launches each kernel directly (default 0). */
 lbm_status lbm_set_graph(lbm_ctx *ctx, int32_t steps_per_graph);
@@ -262,10 +293,20 @@ int64_t lbm_launch_count(const lbm_ctx *ctx);
 lbm_status lbm_set_kernel_variant(lbm_ctx *ctx, int32_t variant);
 int32_t lbm_kernel_variant(const lbm_ctx *ctx);
 
+/* Where the force kernel of a step (force record of time t, motion) runs:
+ * 1 = on a second stream of the context, beside the advection-collision
+ * kernel, which reads the same state (default); 0 = before it, on the
+ * context's stream.  Results do not depend on it.  LBM_EINVAL for other
+ * values. */
+lbm_status lbm_set_force_overlap(lbm_ctx *ctx, int32_t on);
+int32_t lbm_force_overlap(const lbm_ctx *ctx);
+
 /* Autotuner: run 1 + steps real steps with each of the 6 variants of the
- * advection-collision kernel, timed with CUDA events, and keep the fastest
- * (stored in *best when not NULL).  The simulation advances by 6 (1 + steps)
- * steps; results do not depend on the variant.  Waits for the stream. */
+ * advection-collision kernel, with the force kernel beside it and before it,
+ * timing whole steps with CUDA events, and keep the fastest pair (the variant
+ * stored in *best when not NULL; lbm_force_overlap tells the other).  The
+ * simulation advances by 12 (1 + steps) steps; results do not depend on the
+ * choice.  Waits for the stream. */
 lbm_status lbm_autotune(lbm_ctx *ctx, int32_t steps, int32_t *best);
 
 /* ------------------------------------------------------------------ batches

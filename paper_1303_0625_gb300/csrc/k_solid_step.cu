@@ -1,34 +1,41 @@
-// Per-solid work of one step, in one cooperative launch after the
-// advection-collision kernel of step t:
+// Per-solid work of one step t -> t+1, in two launches.
 //
-//   F  forces:  every fluid-solid link of time t (Eq. 4 and Eq. 5, summed by
-//               Eq. 6 and Eq. 7) plus the momenta booked by the node-type
-//               changes into t, written to the force history; motion
-//               t -> t+1 (prescribed, or Newton-Euler on the Eq. 5 force;
-//               Eq. 4 when the context selects it for comparison)
-//   A  clear:   nodes of the old disk that the new disk leaves, owner s -> fluid
-//   B  set:     nodes of the new disk, owner := lowest id covering them
-//   C  changes: on the ring (old disk XOR new disk): node flags of every node
-//               whose solidity changed and of its 8 neighbours; covered nodes
-//               give their momentum to the solid; fresh (newborn) nodes are
-//               refilled by extrapolation (Sec. IV.B) and take theirs from it
-//   D  sync:    prev := owner on the ring; the solid's state becomes t+1
+// k_forces runs beside the advection-collision kernel of the step (both only
+// read the populations of time t, the owner map and the node flags), one warp
+// per solid: the momentum booked by the node-type changes of the previous
+// step (the solid's segment of the event list), the link sums of Eq. 4 and
+// Eq. 5 over every fluid-solid link of time t (Eq. 6 and Eq. 7) -> the force
+// record of t; the motion t -> t+1 (prescribed, or Newton-Euler on the Eq. 5
+// force; Eq. 4 when the context selects it for comparison); the largest
+// displacement of any solid since the last pair test.
 //
-// Phases A-D run only when some solid translates.  One warp owns one solid
-// in a phase (solids are looped over when there are more solids than warps);
-// phases are separated by a grid-wide barrier whose wait is bounded (status
-// bit 2 instead of a hang).  Work per solid follows its perimeter: the nodes
-// near the ends of the disk's chord in every row (FP32 bounds with a one-node
-// margin) are dealt out to the warp's lanes, each lane fetching several nodes
-// before it processes them; every decision is taken by the exact test.  A
-// disk that comes within a node of another one ("near") also re-claims its
-// whole interior in phase B, which keeps the lowest-id rule exact where disks
-// overlap.
+// k_remask follows both, in one cooperative launch:
+//   P  only when some solid may have come within reach of another one since
+//      the last test: the near list of every moving solid, the solids whose
+//      centres are closer than r_s + r_q + NEAR_REACH + NEAR_MARGIN at t or
+//      t+1
+//   R  on the ring (old disk XOR new disk) of every moving solid: the owner
+//      at t and at t+1 from the geometry of the solid and of its near list
+//      (lowest id where disks overlap), so that no map of the old owners is
+//      kept; the owner map and the node flags of every node whose owner
+//      changed; covered and fresh nodes queued per warp in lane order and
+//      published as the solid's segment of the step's event list
+//   E  every warp of the grid takes events from the list: a fresh node is
+//      refilled by extrapolation (Sec. IV.B) from nodes fluid at t and at
+//      t+1; each event's momentum and torque go to its own slot; the moving
+//      solids' state becomes t+1; the clock advances.
+// The phases are separated by a grid-wide barrier whose wait is bounded.  A
+// node on the rings of several solids is written by each of their warps with
+// the same owner; flag bits are set and cleared atomically.
 //
-// Precision: in the FP32/FP16 modes the per-link products and each lane's
-// running sum over its links (a few dozen at most) are FP32; the reduction
-// across the lanes of the solid, the booked momenta and the motion are FP64
-// in a fixed lane order and tree.  The FP64 mode is FP64 throughout.
+// Work per solid follows its perimeter: the nodes near the ends of the disk's
+// chord in every row (FP32 bounds with a one-node margin) are dealt out to
+// the warp's lanes, each lane fetching several nodes before it processes
+// them; every decision is taken by the exact test.
+//
+// Precision: per-link products are in the arithmetic precision of the
+// storage mode (FP32 in the deviation modes); every sum over links and
+// across lanes, the booked momenta and the motion are FP64, in a fixed order.
 #include "lbm_internal.cuh"
 
 namespace gbm {
@@ -38,14 +45,17 @@ namespace {
 constexpr int SW_BLOCK = 256;
 constexpr int WARPS = SW_BLOCK / 32;
 constexpr int U = 4;                        // nodes a lane fetches at once
-constexpr long long SPIN_LIMIT = 1ll << 24; // polls of about 64 ns: roughly one second
 constexpr double PI = 3.14159265358979323846;
 constexpr unsigned FULL = 0xffffffffu;
 
 // ------------------------------------------------------------- barrier
 
 // Grid-wide barrier for a cooperative launch.  Returns false (and raises
-// status bit 2) if the other blocks did not arrive within SPIN_LIMIT polls.
+// status bit 2) if the other blocks did not arrive within p.spin_limit polls;
+// the caller's block then returns, and so does every block at its next
+// barrier.  A limit of 0 gives up at once: the barrier never completes (the
+// time-out path's test).  The arrival count is left as it stands; the host
+// clears it when it reads bit 2.
 __device__ bool grid_sync(const StepParams &p) {
     __shared__ int ok;
     __syncthreads();
@@ -55,14 +65,14 @@ __device__ bool grid_sync(const StepParams &p) {
         __threadfence();
         const unsigned int arrived = atomicAdd(p.bar, 1u) + 1u;
         ok = 1;
-        if (arrived == gridDim.x) {
+        if (arrived == gridDim.x && p.spin_limit > 0) {
             atomicExch(p.bar, 0u);
             __threadfence();
             atomicAdd(p.bar + 1, 1u);
         } else {
             long long spins = 0;
             while (*gen == g) {
-                if (++spins > SPIN_LIMIT) {
+                if (++spins > p.spin_limit) {
                     atomicOr(p.status, 4);
                     ok = 0;
                     break;
@@ -257,7 +267,7 @@ __device__ __forceinline__ void warp_nodes(int j0, int j1, int lane, RF &&rng, F
     warp_nodes_n<U>(j0, j1, lane, rng, fetch, process);
 }
 
-// --------------------------------------------------------- phase F
+// ------------------------------------------------------------- forces
 
 __device__ __forceinline__ double net_weight(const StepParams &p, const DSolid &b) {
     const double M = b.rho_s * PI * b.r * b.r;
@@ -339,23 +349,17 @@ __device__ void move_solid(const StepParams &p, int s, int lane, long long t, co
     b.omn = b.om + fg[2] / I;
 }
 
-// Population f_i of cell k in the link-math precision C.
-template <int P>
-__device__ __forceinline__ typename Prec<P>::C pop(const void *f, int plane, int i, int k) {
-    using C = typename Prec<P>::C;
-    using S = typename Prec<P>::S;
-    C v = (C)ldc(static_cast<const S *>(f) + i * plane + k);
-    if (Prec<P>::dev) v += wgt<C>(i);
-    return v;
-}
-
-// Force record of time t for solid s (populations f of time t), then its
-// motion to t+1.  Per link (x_f fluid, x_f + e_i owned by s): f_i = f~_i(x_f),
-// the bounced f_bb = f_i - 6 w_i rho_w (e_i . v) with v the solid's velocity
-// at x_s = x_f + e_i / 2; Eq. 4 = e_i f_i - e_opp f_bb, Eq. 5 = (e_i - v) f_i
-// - (e_opp - v) f_bb, torque (x_s - R) x F (Eq. 7).  A candidate node's
-// flags, its 9 populations and its 8 neighbours' owners are loaded together.
-template <int P, bool LOCAL>
+// Link sums of solid s at time t (populations f of time t), acc = Eq. 4
+// force and torque, then Eq. 5, summed over the warp (warp wi of nw sharing
+// the disk's rows).  Per link (x_f fluid, x_f + e_i owned by s): f_i =
+// f~_i(x_f), the bounced f_bb = f_i - 6 w_i rho_w (e_i . v) with v the
+// solid's velocity at x_s = x_f + e_i / 2; Eq. 4 = e_i f_i - e_opp f_bb,
+// Eq. 5 = (e_i - v) f_i - (e_opp - v) f_bb, torque (x_s - R) x F (Eq. 7).
+// BND: the interpolated boundary, whose links return the interpolated
+// population and use the velocity and lever arm at the cut.  A candidate
+// node's flags, its 9 populations and its 8 neighbours' owners are loaded
+// together.
+template <int P, bool LOCAL, bool BND>
 __device__ void forces_sum(const StepParams &p, int s, int lane, const void *f, int wi, int nw,
                            double (&acc)[6]) {
     using C = typename Prec<P>::C;
@@ -372,7 +376,7 @@ __device__ void forces_sum(const StepParams &p, int s, int lane, const void *f, 
     const float r = (float)b.r;
     int j0, j1;
     rows_of(Y, Y, b.r, 3, j0, j1);
-    C lacc[6] = {0, 0, 0, 0, 0, 0};  // this lane's links
+    double lacc[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};  // this lane's links
     int ii[UF], jj[UF];
     uint16_t fl[UF];
     uint16_t own[UF][9];
@@ -412,7 +416,7 @@ __device__ void forces_sum(const StepParams &p, int s, int lane, const void *f, 
                 C dx, dy, ux, uy, fbb;
                 C fi = (C)cvt_s(fv[u][i]);
                 if (Prec<P>::dev) fi += wgt<C>(i);
-                if (p.boundary == LBM_INTERPOLATED) {
+                if (BND) {
                     // the cut at fraction q of the link, and the population that
                     // returns to x_f along e_opp by the fused kernel's
                     // interpolation (full populations; M = 6 w rho_w (e_opp . v))
@@ -457,62 +461,94 @@ __device__ void forces_sum(const StepParams &p, int s, int lane, const void *f, 
                 const C cmy = (C)cy(i) * fi - (C)cy(opp(i)) * fbb;
                 const C gmx = ((C)cx(i) - ux) * fi - ((C)cx(opp(i)) - ux) * fbb;
                 const C gmy = ((C)cy(i) - uy) * fi - ((C)cy(opp(i)) - uy) * fbb;
-                lacc[0] += cmx;
-                lacc[1] += cmy;
-                lacc[2] += dx * cmy - dy * cmx;
-                lacc[3] += gmx;
-                lacc[4] += gmy;
-                lacc[5] += dx * gmy - dy * gmx;
+                lacc[0] += (double)cmx;
+                lacc[1] += (double)cmy;
+                lacc[2] += (double)(dx * cmy - dy * cmx);
+                lacc[3] += (double)gmx;
+                lacc[4] += (double)gmy;
+                lacc[5] += (double)(dx * gmy - dy * gmx);
             }
         },
         wi, nw);
 #pragma unroll
-    for (int q = 0; q < 6; q++) acc[q] = (double)lacc[q];
+    for (int q = 0; q < 6; q++) acc[q] = lacc[q];
     warp_sum(acc);
 }
 
-// Force record of time t of solid s from its link sums acc (lane 0: Eq. 4
-// force and torque, then Eq. 5), plus the momentum booked into t; then its
-// motion to t+1.
+// Force record of time t of solid s from its link sums acc and the momentum
+// booked into t by the node-type changes of the previous step (lane 0: Eq. 4
+// force and torque, then Eq. 5); then its motion to t+1.
 __device__ void record_forces(const StepParams &p, int s, int lane, long long t,
-                              const double (&acc)[6]) {
-    const DSolid &b = p.S[s];
+                              const double (&acc)[6], const double (&booked)[6]) {
     double fg[3] = {0.0, 0.0, 0.0};
     if (lane == 0) {
-        const bool booked = b.pend_t == t;
         const long long slot = t % p.ring_len;
         double *rc = p.ring + (slot * 2 + 0) * p.nsolid * 3 + (long long)s * 3;
         double *rg = p.ring + (slot * 2 + 1) * p.nsolid * 3 + (long long)s * 3;
         for (int q = 0; q < 3; q++) {
-            rc[q] = acc[q] + (booked ? b.pend[q] : 0.0);
-            rg[q] = acc[3 + q] + (booked ? b.pend[3 + q] : 0.0);
+            rc[q] = acc[q] + booked[q];
+            rg[q] = acc[3 + q] + booked[3 + q];
             fg[q] = p.motion_cme ? rc[q] : rg[q];  // the form that drives a free solid
         }
     }
     move_solid(p, s, lane, t, fg);
 }
 
-template <int P, bool LOCAL>
-__device__ void phase_forces(const StepParams &p, int s, int lane, long long t, const void *f) {
-    double acc[6];
-    forces_sum<P, LOCAL>(p, s, lane, f, 0, 1, acc);
-    record_forces(p, s, lane, t, acc);
+// One warp per solid (see the top of the file).
+template <int P, bool LOCAL, bool BND>
+__global__ void __launch_bounds__(SW_BLOCK) k_forces(const StepParams p) {
+    __shared__ float disp[WARPS];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int gw = blockIdx.x * WARPS + wib, nw = gridDim.x * WARPS;
+    float dmax = 0.f;  // lane 0: the largest displacement of this warp's solids
+    const long long t = *p.t;
+    const void *fcur = (t & 1) ? p.f1 : p.f0;  // populations of time t
+    // the previous step's events are reached through the solids' segments;
+    // the list fills again in this step's re-rasterisation
+    if (gw == 0 && lane == 0 && p.ev_len) *p.ev_len = 0;
+    for (int s = gw; s < p.nsolid; s += nw) {
+        DSolid &b = p.S[s];
+        if (!solid_ok(b)) {
+            if (lane == 0) atomicOr(p.status, 2);
+            continue;
+        }
+        double acc[6];
+        forces_sum<P, LOCAL, BND>(p, s, lane, fcur, 0, 1, acc);
+        double booked[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+        if (lane == 0 && b.ev_t == t)
+            for (int e = b.ev_off; e < b.ev_off + b.ev_n; e++)
+                for (int q = 0; q < 6; q++) booked[q] += p.ev_mom[6 * e + q];
+        record_forces(p, s, lane, t, acc, booked);
+        if (lane == 0) {
+            // distance from the centre at the last pair test, at t and t+1
+            const double d0 = hypot(b.x - b.tx, b.y - b.ty), d1 = hypot(b.xn - b.tx, b.yn - b.ty);
+            dmax = fmaxf(dmax, __double2float_ru(fmax(d0, d1)));
+        }
+    }
+    if (lane == 0) disp[wib] = dmax;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float m = 0.f;
+        for (int w = 0; w < WARPS; w++) m = fmaxf(m, disp[w]);
+        if (m > 0.f) atomicMax(p.bar + 2, __float_as_uint(m));  // non-negative: bits order as values
+    }
 }
 
-// ------------------------------------------------------- phases A, B, D
+// ----------------------------------------------------- re-rasterisation
 
-// Pair test: can another disk share a node with disk s at t or t+1 (centres
-// closer than r_s + r_q + 1.5)?  The centres are staged in shared memory one
-// tile at a time; every warp of the block tests its own disk against them.
-// Called by whole blocks: base + warp index is the disk (may be >= nsolid).
+// Pair test: the near list of the moving solid moving[base + warp index]
+// (whole blocks call it; base + warp index may be >= nmoving).  The centres
+// at t and t+1 of every solid are staged in shared memory one tile at a time.
+// FP32 distances with a slack far above their rounding.
 constexpr int NEAR_TILE = 1024;
-__device__ void phase_near_block(const StepParams &p, int base, float4 *pos, float *rad) {
+__device__ void phase_pairs_block(const StepParams &p, int base, float4 *pos, float *rad) {
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    const int s = base + wib;
+    const int m = base + wib;
+    const bool mine = m < p.nmoving;
+    const int s = mine ? p.moving[m] : -1;
     const Lattice &L = p.L;
     const bool px = L.bc_x == LBM_PERIODIC, py = L.bc_y == LBM_PERIODIC;
     const float nxf = (float)L.nx, nyf = (float)L.ny;
-    const bool mine = s < p.nsolid;
     float rb = 0.f, bx = 0.f, by = 0.f, bxn = 0.f, byn = 0.f;
     if (mine) {
         const DSolid &b = p.S[s];
@@ -522,7 +558,8 @@ __device__ void phase_near_block(const StepParams &p, int base, float4 *pos, flo
         bxn = b.xnf;
         byn = b.ynf;
     }
-    int near = 0;
+    uint16_t *out = mine ? p.near_id + (long long)s * NEAR_CAP : nullptr;
+    int cnt = 0;
     for (int t0 = 0; t0 < p.nsolid; t0 += NEAR_TILE) {
         const int n = min(NEAR_TILE, p.nsolid - t0);
         __syncthreads();
@@ -533,144 +570,92 @@ __device__ void phase_near_block(const StepParams &p, int base, float4 *pos, flo
         }
         __syncthreads();
         if (!mine) continue;
-        for (int q = lane; q < n; q += 32) {
-            if (t0 + q == s) continue;
-            const float4 c = pos[q];
-            const float lim = rb + rad[q] + 1.5f;
-            float dx = bx - c.x, dy = by - c.y, ex = bxn - c.z, ey = byn - c.w;
-            if (px) {
-                dx -= nxf * rintf(dx / nxf);
-                ex -= nxf * rintf(ex / nxf);
+        for (int q0 = 0; q0 < n; q0 += 32) {
+            const int q = q0 + lane;
+            bool hit = false;
+            if (q < n && t0 + q != s) {
+                const float4 c = pos[q];
+                const float lim = rb + rad[q] + NEAR_REACH + NEAR_MARGIN + 0.05f;
+                float dx = bx - c.x, dy = by - c.y, ex = bxn - c.z, ey = byn - c.w;
+                if (px) {
+                    dx -= nxf * rintf(dx / nxf);
+                    ex -= nxf * rintf(ex / nxf);
+                }
+                if (py) {
+                    dy -= nyf * rintf(dy / nyf);
+                    ey -= nyf * rintf(ey / nyf);
+                }
+                hit = dx * dx + dy * dy < lim * lim || ex * ex + ey * ey < lim * lim;
             }
-            if (py) {
-                dy -= nyf * rintf(dy / nyf);
-                ey -= nyf * rintf(ey / nyf);
+            const unsigned h = __ballot_sync(FULL, hit);
+            if (hit) {
+                const int at = cnt + __popc(h & ((1u << lane) - 1u));
+                if (at < NEAR_CAP) out[at] = (uint16_t)(t0 + q);
             }
-            if (dx * dx + dy * dy < lim * lim || ex * ex + ey * ey < lim * lim) near = 1;
+            cnt += __popc(h);
         }
     }
-    near = __any_sync(FULL, near);
-    if (mine && lane == 0) p.S[s].near = near;
+    if (mine && lane == 0) p.S[s].near_n = cnt <= NEAR_CAP ? cnt : -1;
 }
 
-// Nodes of the old disk that the new disk leaves: owner s -> fluid.
-__device__ void phase_clear(const StepParams &p, int s, int lane) {
-    const DSolid &b = p.S[s];
-    const DiskTest in0(b.x, b.y, b.r), in1(b.xn, b.yn, b.r);
-    const Centre c0(b.x, b.y), c1(b.xn, b.yn);
-    const float rr = (float)b.r + 0.01f;
-    int j0, j1;
-    rows_of(b.y, b.yn, b.r, 1, j0, j1);
-    int kk[U];
-    uint16_t ow[U];
-    warp_nodes(
-        j0, j1, lane, [&](int j, Ranges &R) { return ring_ranges(c0, c1, rr, j, R); },
-        [&](int i, int j, int u) {
-            int x, y;
-            if (!in0(i, j) || in1(i, j) || !locate(p.L, i, j, x, y)) return false;
-            kk[u] = (int)cell_of(p.L, x, y);
-            ow[u] = p.owner[kk[u]];
-            return true;
-        },
-        [&](int u, bool ok) {
-            if (ok && ow[u] == (uint16_t)s) p.owner[kk[u]] = FLUID;
-        });
+// Is the domain node (x, y) inside the disk (X, Y, r)?  Decided at the
+// node's periodic image nearest to the centre, by the exact test, as the
+// rasterisation of the disk decides it.
+__device__ __forceinline__ bool inside_at(const Lattice &L, int x, int y, double X, double Y,
+                                          double r) {
+    int i = x, j = y;
+    if (L.bc_x == LBM_PERIODIC) i += L.nx * (int)floor((X - (double)x) / (double)L.nx + 0.5);
+    if (L.bc_y == LBM_PERIODIC) j += L.ny * (int)floor((Y - (double)y) / (double)L.ny + 0.5);
+    const float dx = (float)((double)i - X), dy = (float)((double)j - Y), rr = (float)r + 1.0f;
+    if (dx * dx + dy * dy > rr * rr) return false;
+    return inside_disk(i, j, X, Y, r);
 }
 
-// Nodes of the new disk: owner := lowest id.  A disk that no other disk
-// comes near owns its interior already; only the nodes it newly covers
-// change.  A near disk re-claims its whole new chord in every row.
-__device__ void phase_set(const StepParams &p, int s, int lane) {
-    const DSolid &b = p.S[s];
-    const DiskTest in0(b.x, b.y, b.r), in1(b.xn, b.yn, b.r);
-    const Centre c0(b.x, b.y), c1(b.xn, b.yn);
-    const float rr = (float)b.r + 0.01f;
-    const bool full = b.near != 0;
-    int j0, j1;
-    if (full) rows_of(b.yn, b.yn, b.r, 1, j0, j1);
-    else rows_of(b.y, b.yn, b.r, 1, j0, j1);
-    int kk[U];
-    uint16_t ow[U];
-    warp_nodes(
-        j0, j1, lane,
-        [&](int j, Ranges &R) {
-            if (!full) return ring_ranges(c0, c1, rr, j, R);
-            R.a1 = 1;
-            R.b1 = 0;
-            return c1.span(j, rr, R.a0, R.b0);
-        },
-        [&](int i, int j, int u) {
-            int x, y;
-            if (!in1(i, j) || (!full && in0(i, j)) || !locate(p.L, i, j, x, y)) return false;
-            kk[u] = (int)cell_of(p.L, x, y);
-            ow[u] = p.owner[kk[u]];
-            return true;
-        },
-        [&](int u, bool ok) {
-            if (ok && ow[u] > (uint16_t)s) atomic_min_u16(p.owner + kk[u], (uint16_t)s);
-        });
-}
-
-// prev := owner on the ring; the momentum of the solid's covered and fresh
-// nodes (its segment of ev_mom, summed in queue order) is booked into the
-// force record of t+1; the solid's state becomes t+1.
-__device__ void phase_sync(const StepParams &p, int s, int lane, long long t1) {
-    DSolid &b = p.S[s];
-    const DiskTest in0(b.x, b.y, b.r), in1(b.xn, b.yn, b.r);
-    const Centre c0(b.x, b.y), c1(b.xn, b.yn);
-    const float rr = (float)b.r + 0.01f;
-    int j0, j1;
-    rows_of(b.y, b.yn, b.r, 1, j0, j1);
-    int kk[U];
-    uint16_t ow[U], pv[U];
-    warp_nodes(
-        j0, j1, lane, [&](int j, Ranges &R) { return ring_ranges(c0, c1, rr, j, R); },
-        [&](int i, int j, int u) {
-            int x, y;
-            if (in0(i, j) == in1(i, j) || !locate(p.L, i, j, x, y)) return false;
-            kk[u] = (int)cell_of(p.L, x, y);
-            ow[u] = p.owner[kk[u]];
-            pv[u] = p.prev[kk[u]];
-            return true;
-        },
-        [&](int u, bool ok) {
-            if (ok && pv[u] != ow[u]) p.prev[kk[u]] = ow[u];
-        });
-    __syncwarp();
-    if (lane == 0) {
-        double acc[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
-        for (int e = b.ev_off; e < b.ev_off + b.ev_n; e++)
-            for (int q = 0; q < 6; q++) acc[q] += p.ev_mom[6 * e + q];
-        for (int q = 0; q < 6; q++) b.pend[q] = acc[q];
-        b.pend_t = t1;
-        b.x = b.xn;
-        b.y = b.yn;
-        b.xw = b.xnw;
-        b.yw = b.ynw;
-        const double fxw = floor(b.xw), fyw = floor(b.yw);
-        b.xwi = (int)fxw;
-        b.ywi = (int)fyw;
-        b.xwr = (float)(b.xw - fxw);
-        b.ywr = (float)(b.yw - fyw);
-        b.vx = b.vxn;
-        b.vy = b.vyn;
-        b.om = b.omn;
-        b.vxf = (float)b.vxn;
-        b.vyf = (float)b.vyn;
-        b.omf = (float)b.omn;
-        b.xf = b.xnf;
-        b.yf = b.ynf;
+// Lowest-id owners of the domain node (x, y) at t (was) and t+1 (now), given
+// those of solid s alone: the solids of s's near list (every solid when the
+// list overflowed) that hold the node.  Centres at t: x, y (phase R only).
+__device__ void near_owners(const StepParams &p, const DSolid &b, int s, int x, int y,
+                            uint16_t &was, uint16_t &now) {
+    const int nn = b.near_n;
+    if (nn == 0) return;
+    const uint16_t *nl = p.near_id + (long long)s * NEAR_CAP;
+    const int n = nn < 0 ? p.nsolid : nn;
+    for (int k = 0; k < n; k++) {
+        const int q = nn < 0 ? k : (int)nl[k];
+        if (q == s || (q >= (int)was && q >= (int)now)) continue;
+        const DSolid &B = p.S[q];
+        if (q < (int)was && inside_at(p.L, x, y, B.x, B.y, B.r)) was = (uint16_t)q;
+        if (q < (int)now && inside_at(p.L, x, y, B.xn, B.yn, B.r)) now = (uint16_t)q;
     }
 }
 
-// ------------------------------------------------------------ phase C
+// Was the domain node (x, y) inside a solid at t?  Only solid s (a solid
+// with an event this step) and its near list can have held it, for a node
+// within NEAR_REACH of s's surface.  Centres at t: xo, yo (phase E).
+__device__ bool solid_at_t(const StepParams &p, const DSolid &b, int s, int x, int y) {
+    if (inside_at(p.L, x, y, b.xo, b.yo, b.r)) return true;
+    const int nn = b.near_n;
+    if (nn == 0) return false;
+    const uint16_t *nl = p.near_id + (long long)s * NEAR_CAP;
+    const int n = nn < 0 ? p.nsolid : nn;
+    for (int k = 0; k < n; k++) {
+        const int q = nn < 0 ? k : (int)nl[k];
+        if (q == s) continue;
+        const DSolid &B = p.S[q];
+        if (inside_at(p.L, x, y, B.xo, B.yo, B.r)) return true;
+    }
+    return false;
+}
 
 constexpr int EVENTS = SOLID_EVENTS;
 
-// Ring of solid s: flags of nodes whose solidity changed (as they are found),
-// and the covered and fresh nodes, queued per warp in lane order and
-// published as the solid's segment of the step's event list.
-__device__ void phase_changes(const StepParams &p, int s, int lane, int *queue, int &qn) {
+// Ring of solid s (phase R): owner and flags of every node whose owner
+// changes, and the covered and fresh nodes of s, queued per warp in lane
+// order and published as the solid's segment of the step's event list (to be
+// booked into the force record of t+1).  No memory is read per node: the
+// owners come from the geometry.
+__device__ void phase_ring(const StepParams &p, int s, int lane, long long t, int *queue,
+                           int &qn) {
     DSolid &b = p.S[s];
     const Lattice &L = p.L;
     const DiskTest in0(b.x, b.y, b.r), in1(b.xn, b.yn, b.r);
@@ -680,37 +665,43 @@ __device__ void phase_changes(const StepParams &p, int s, int lane, int *queue, 
     rows_of(b.y, b.yn, b.r, 1, j0, j1);
     if (lane == 0) qn = 0;
     __syncwarp();
-    int kk[U];
-    uint16_t ow[U], pv[U];
-    warp_nodes(
+    constexpr int UR = 2;  // nothing is loaded per node: a short batch suffices
+    int kk[UR];
+    bool w0[UR];  // on the ring the node is inside s at t (true) or at t+1 (false)
+    warp_nodes_n<UR>(
         j0, j1, lane, [&](int j, Ranges &R) { return ring_ranges(c0, c1, rr, j, R); },
         [&](int i, int j, int u) {
+            const bool a = in0(i, j);
+            if (a == in1(i, j)) return false;
             int x, y;
-            if (in0(i, j) == in1(i, j) || !locate(L, i, j, x, y)) return false;
+            if (!locate(L, i, j, x, y)) return false;
             kk[u] = (int)cell_of(L, x, y);
-            ow[u] = p.owner[kk[u]];
-            pv[u] = p.prev[kk[u]];
+            w0[u] = a;
             return true;
         },
         [&](int u, bool ok) {
             bool covered = false, fresh = false;
             const int k = kk[u];
             if (ok) {
-                const uint16_t now = ow[u], was = pv[u];
-                const bool sn = now != FLUID, sw = was != FLUID;
-                if (sn != sw) {
-                    // bit 0 of the node, bit d of the neighbour x + e_d
-                    const int x = k % L.pitch, y = k / L.pitch;
-                    flag_bit(p.flags, k, 0, sn);
+                uint16_t was = w0[u] ? (uint16_t)s : FLUID, now = w0[u] ? FLUID : (uint16_t)s;
+                const int x = k % L.pitch, y = k / L.pitch;
+                near_owners(p, b, s, x, y, was, now);
+                if (was != now) {
+                    p.owner[k] = now;
+                    const bool sn = now != FLUID;
+                    if (sn != (was != FLUID)) {
+                        // bit 0 of the node, bit d of the neighbour x + e_d
+                        flag_bit(p.flags, k, 0, sn);
 #pragma unroll
-                    for (int d = 1; d < 9; d++) {
-                        int xn, yn;
-                        if (locate(L, x + cx(d), y + cy(d), xn, yn))
-                            flag_bit(p.flags, cell_of(L, xn, yn), d, sn);
+                        for (int d = 1; d < 9; d++) {
+                            int xn, yn;
+                            if (locate(L, x + cx(d), y + cy(d), xn, yn))
+                                flag_bit(p.flags, cell_of(L, xn, yn), d, sn);
+                        }
                     }
                 }
-                covered = !sw && now == (uint16_t)s;
-                fresh = was == (uint16_t)s && !sn;
+                covered = was == FLUID && now == (uint16_t)s;
+                fresh = was == (uint16_t)s && now == FLUID;
             }
             // queue the covered and fresh nodes in lane order
             __syncwarp();
@@ -740,16 +731,19 @@ __device__ void phase_changes(const StepParams &p, int s, int lane, int *queue, 
         if (!fits) atomicOr(p.status, 8);
         b.ev_off = off;
         b.ev_n = fits ? n : 0;
+        b.ev_t = t + 1;
+        b.xo = b.x;
+        b.yo = b.y;
     }
     __syncwarp();
 }
 
-// One covered or fresh node of the step's event list, with the whole warp:
-// the refill of a fresh node (Sec. IV.B), then the node's momentum (covered:
-// post-collision, into the solid; fresh: refilled, out of it) and its torque
-// about the solid's new centre, into the event's slot of ev_mom.  Events are
-// independent: a refill reads only nodes that were fluid before and after the
-// move.
+// One covered or fresh node of the step's event list, with the whole warp
+// (phase E): the refill of a fresh node (Sec. IV.B), then the node's momentum
+// (covered: post-collision, into the solid; fresh: refilled, out of it) and
+// its torque about the solid's new centre, into the event's slot of ev_mom.
+// Events are independent: a refill reads only nodes that are fluid at t and
+// at t+1, which no event writes.
 template <int P>
 __device__ void phase_event(const StepParams &p, int e, int lane, void *fnew) {
     using C = typename Prec<P>::C;
@@ -770,7 +764,8 @@ __device__ void phase_event(const StepParams &p, int e, int lane, void *fnew) {
             if (lane < 24) {
                 const int i = lane / 3 + 1, d = lane % 3 + 1;
                 const int kp = neighbour(L, x, y, d * cx(i), d * cy(i));
-                use = kp >= 0 && p.owner[kp] == FLUID && p.prev[kp] == FLUID;
+                use = kp >= 0 && p.owner[kp] == FLUID &&
+                      !solid_at_t(p, b, ev.y, kp % L.pitch, kp / L.pitch);
             }
             const unsigned um = __ballot_sync(FULL, use);
             unsigned d3 = 0, d2 = 0, d1 = 0;  // directions old-fluid up to distance 3, 2, 1
@@ -854,74 +849,112 @@ __device__ void phase_event(const StepParams &p, int e, int lane, void *fnew) {
     __syncwarp();
 }
 
-// ------------------------------------------------------------- kernel
-
-template <int P, bool LOCAL>
-__global__ void __launch_bounds__(SW_BLOCK) k_solids_step(const StepParams p, int mode) {
-    __shared__ int queue[WARPS][EVENTS];
-    __shared__ int qn[WARPS];
-    __shared__ float4 near_pos[NEAR_TILE];
-    __shared__ float near_rad[NEAR_TILE];
-    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    const int gw = blockIdx.x * WARPS + wib, nw = gridDim.x * WARPS;
-    const long long t = *p.t;
-    const void *fcur = (t & 1) ? p.f1 : p.f0;  // populations of time t
-    void *fnew = ((t + 1) & 1) ? p.f1 : p.f0;  // populations of time t+1
-    for (int s = gw; s < p.nsolid; s += nw) {
-        if (solid_ok(p.S[s])) phase_forces<P, LOCAL>(p, s, lane, t, fcur);
-        else if (lane == 0) atomicOr(p.status, 2);
-    }
-    grid_sync(p);  // every block has read t: time advances
-    if (blockIdx.x == 0 && threadIdx.x == 0) *p.t = t + 1;
-    if (!(mode & SOLIDS_REMASK)) return;
-    for (int base = blockIdx.x * WARPS; base < p.nsolid; base += nw)
-        phase_near_block(p, base, near_pos, near_rad);
-    for (int m = gw; m < p.nmoving; m += nw) {
-        const int s = p.moving[m];
-        if (solid_ok(p.S[s])) phase_clear(p, s, lane);
-    }
-    grid_sync(p);
-    for (int s = gw; s < p.nsolid; s += nw)
-        if (solid_ok(p.S[s])) phase_set(p, s, lane);
-    grid_sync(p);
-    for (int m = gw; m < p.nmoving; m += nw) {
-        const int s = p.moving[m];
-        if (solid_ok(p.S[s])) phase_changes(p, s, lane, queue[wib], qn[wib]);
-    }
-    grid_sync(p);
-    // the step's covered and fresh nodes, dealt to every warp of the grid
-    const int nev = min(*(volatile int *)p.ev_len, p.ev_cap);
-    for (int e = gw; e < nev; e += nw) phase_event<P>(p, e, lane, fnew);
-    grid_sync(p);
-    if (blockIdx.x == 0 && threadIdx.x == 0) *p.ev_len = 0;  // every warp has read it
-    for (int m = gw; m < p.nmoving; m += nw) {
-        const int s = p.moving[m];
-        if (solid_ok(p.S[s])) phase_sync(p, s, lane, t + 1);
-    }
+// The state of a moving solid becomes that of t+1 (xo, yo keep R(t) for the
+// events of the step).
+__device__ __forceinline__ void advance_solid(DSolid &b) {
+    b.x = b.xn;
+    b.y = b.yn;
+    b.xw = b.xnw;
+    b.yw = b.ynw;
+    const double fxw = floor(b.xw), fyw = floor(b.yw);
+    b.xwi = (int)fxw;
+    b.ywi = (int)fyw;
+    b.xwr = (float)(b.xw - fxw);
+    b.ywr = (float)(b.yw - fyw);
+    b.vx = b.vxn;
+    b.vy = b.vyn;
+    b.om = b.omn;
+    b.vxf = (float)b.vxn;
+    b.vyf = (float)b.vyn;
+    b.omf = (float)b.omn;
+    b.xf = b.xnf;
+    b.yf = b.ynf;
 }
 
-template <int P, bool LOCAL>
-cudaError_t launch_sw(const StepParams &p, int mode, cudaStream_t st) {
+template <int P>
+__global__ void __launch_bounds__(SW_BLOCK, 3) k_remask(const StepParams p) {
+    __shared__ int queue[WARPS][EVENTS];
+    __shared__ int qn[WARPS];
+    __shared__ float4 tile_pos[NEAR_TILE];
+    __shared__ float tile_rad[NEAR_TILE];
+    // a barrier of an earlier launch gave up: the state is not the method's
+    // any more, and this launch does nothing (the host reports the time-out)
+    if (*(volatile int *)p.status & 4) return;
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int gw = blockIdx.x * WARPS + wib, nw = gridDim.x * WARPS;
+    const int gt = blockIdx.x * SW_BLOCK + threadIdx.x, nt = gridDim.x * SW_BLOCK;
+    const long long t = *p.t;
+    void *fnew = ((t + 1) & 1) ? p.f1 : p.f0;  // populations of time t+1
+    const volatile unsigned int *ctl = p.bar;
+    if (ctl[3] != 0u || __uint_as_float(ctl[2]) >= 0.5f * NEAR_MARGIN) {
+        // P: near lists, and the centres they were taken at
+        for (int base = blockIdx.x * WARPS; base < p.nmoving; base += nw)
+            phase_pairs_block(p, base, tile_pos, tile_rad);
+        for (int s = gt; s < p.nsolid; s += nt) {
+            DSolid &b = p.S[s];
+            b.tx = b.xo = b.x;
+            b.ty = b.yo = b.y;
+        }
+        if (!grid_sync(p)) return;
+        if (gt == 0) {
+            p.bar[2] = 0u;
+            p.bar[3] = 0u;
+        }
+    }
+    // R
+    for (int m = gw; m < p.nmoving; m += nw) {
+        const int s = p.moving[m];
+        if (solid_ok(p.S[s])) phase_ring(p, s, lane, t, queue[wib], qn[wib]);
+        else if (lane == 0) atomicOr(p.status, 2);
+    }
+    if (!grid_sync(p)) return;
+    if (gt == 0) *p.t = t + 1;  // every block has read t
+    // E: the step's covered and fresh nodes, dealt to every warp of the grid
+    const int nev = min(*(volatile int *)p.ev_len, p.ev_cap);
+    for (int e = gw; e < nev; e += nw) phase_event<P>(p, e, lane, fnew);
+    for (int m = gt; m < p.nmoving; m += nt) advance_solid(p.S[p.moving[m]]);
+}
+
+template <int P, bool LOCAL, bool BND>
+cudaError_t launch_f(const StepParams &p, cudaStream_t st) {
     static int per_sm = -1, sms = 0;
     if (per_sm < 0) {
         int dev = 0;
         cudaError_t e = cudaGetDevice(&dev);
         if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         if (e == cudaSuccess)
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_solids_step<P, LOCAL>,
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_forces<P, LOCAL, BND>,
                                                               SW_BLOCK, 0);
         if (e != cudaSuccess) return e;
     }
-    const int work = p.nsolid > p.nmoving ? p.nsolid : p.nmoving;
-    int blocks = (work + WARPS - 1) / WARPS;
-    const int cap = per_sm * sms;
-    if (blocks > cap) blocks = cap;
+    int blocks = (p.nsolid + WARPS - 1) / WARPS;
+    if (blocks > per_sm * sms) blocks = per_sm * sms;
+    if (blocks < 1) blocks = 1;
+    k_forces<P, LOCAL, BND><<<blocks, SW_BLOCK, 0, st>>>(p);
+    return cudaGetLastError();
+}
+
+template <int P>
+cudaError_t launch_r(const StepParams &p, cudaStream_t st) {
+    static int per_sm = -1, sms = 0;
+    if (per_sm < 0) {
+        int dev = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e == cudaSuccess)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_remask<P>, SW_BLOCK, 0);
+        if (e != cudaSuccess) return e;
+    }
+    // one warp per moving solid for phase R, and at least one block per SM
+    // for the events
+    int blocks = (p.nmoving + WARPS - 1) / WARPS;
+    if (blocks < sms) blocks = sms;
+    if (blocks > per_sm * sms) blocks = per_sm * sms;
     if (blocks < 1) blocks = 1;
     StepParams pp = p;
-    int m = mode;
-    void *args[] = {&pp, &m};
-    return cudaLaunchCooperativeKernel((const void *)k_solids_step<P, LOCAL>, dim3(blocks),
-                                       dim3(SW_BLOCK), args, 0, st);
+    void *args[] = {&pp};
+    return cudaLaunchCooperativeKernel((const void *)k_remask<P>, dim3(blocks), dim3(SW_BLOCK),
+                                       args, 0, st);
 }
 
 // ------------------------------------------------------------- batch
@@ -952,7 +985,7 @@ __global__ void __launch_bounds__(SW_BLOCK)
             continue;
         }
         double acc[6];
-        forces_sum<P, LOCAL>(p, it.y, lane, fcur, wib, WARPS, acc);
+        forces_sum<P, LOCAL, false>(p, it.y, lane, fcur, wib, WARPS, acc);
         if (lane == 0)
             for (int q = 0; q < 6; q++) part[wib][q] = acc[q];
         __syncthreads();
@@ -961,7 +994,8 @@ __global__ void __launch_bounds__(SW_BLOCK)
             if (lane == 0)
                 for (int w = 0; w < WARPS; w++)
                     for (int q = 0; q < 6; q++) tot[q] += part[w][q];
-            record_forces(p, it.y, lane, t, tot);
+            const double none[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};  // resting: no node changes type
+            record_forces(p, it.y, lane, t, tot, none);
         }
         __syncthreads();
     }
@@ -1142,16 +1176,26 @@ cudaError_t launch_batch_converge(const BatchLaunch &b, const BatchState &s, int
     return cudaGetLastError();
 }
 
-cudaError_t launch_solids(const StepParams &p, int mode, cudaStream_t st) {
+cudaError_t launch_forces(const StepParams &p, cudaStream_t st) {
     if (p.nsolid == 0) return cudaSuccess;
-    const bool local = p.rho_w_mode == LBM_RHOW_LOCAL;
+    const bool local = p.rho_w_mode == LBM_RHOW_LOCAL, bnd = p.boundary == LBM_INTERPOLATED;
+#define GBM_F(P)                                                                            \
+    return local ? (bnd ? launch_f<P, true, true>(p, st) : launch_f<P, true, false>(p, st)) \
+                 : (bnd ? launch_f<P, false, true>(p, st) : launch_f<P, false, false>(p, st))
     switch (p.precision) {
-        case LBM_FP64: return local ? launch_sw<LBM_FP64, true>(p, mode, st)
-                                    : launch_sw<LBM_FP64, false>(p, mode, st);
-        case LBM_FP32_DEV: return local ? launch_sw<LBM_FP32_DEV, true>(p, mode, st)
-                                        : launch_sw<LBM_FP32_DEV, false>(p, mode, st);
-        default: return local ? launch_sw<LBM_FP16_DEV, true>(p, mode, st)
-                              : launch_sw<LBM_FP16_DEV, false>(p, mode, st);
+        case LBM_FP64: GBM_F(LBM_FP64);
+        case LBM_FP32_DEV: GBM_F(LBM_FP32_DEV);
+        default: GBM_F(LBM_FP16_DEV);
+    }
+#undef GBM_F
+}
+
+cudaError_t launch_remask(const StepParams &p, cudaStream_t st) {
+    if (p.nmoving == 0) return cudaSuccess;
+    switch (p.precision) {
+        case LBM_FP64: return launch_r<LBM_FP64>(p, st);
+        case LBM_FP32_DEV: return launch_r<LBM_FP32_DEV>(p, st);
+        default: return launch_r<LBM_FP16_DEV>(p, st);
     }
 }
 

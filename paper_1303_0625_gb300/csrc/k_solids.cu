@@ -89,7 +89,6 @@ __global__ void __launch_bounds__(SOLID_BLOCK) k_stamp_finish(const StepParams p
         if (!locate(p.L, bx.x0 + c % bx.w, bx.y0 + c / bx.w, x, y)) continue;
         const long long k = cell_of(p.L, x, y);
         p.flags[k] = node_flags(p.L, p.owner, x, y);
-        p.prev[k] = p.owner[k];
     }
 }
 

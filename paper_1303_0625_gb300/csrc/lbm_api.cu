@@ -23,7 +23,7 @@ struct lbm_ctx {
     int pitch = 0;
     size_t elem = 0;
     void *f[2] = {nullptr, nullptr};
-    uint16_t *owner = nullptr, *prev = nullptr, *flags = nullptr;
+    uint16_t *owner = nullptr, *flags = nullptr;
     DSolid *solids = nullptr;
     int solid_cap = 0;
     int nsolid = 0;
@@ -40,7 +40,14 @@ struct lbm_ctx {
     int ring_cap = 0;      // solids the ring was laid out for
     long long *t_d = nullptr;
     int *status_d = nullptr;
-    unsigned int *bar_d = nullptr;  // grid barrier of the per-solid kernel
+    unsigned int *bar_d = nullptr;  // per-solid control words (barrier, displacement, pair test)
+    uint16_t *near_d = nullptr;     // near lists, [solid_cap][NEAR_CAP]
+    long long spin_limit = 1ll << 24;  // polls of a bounded device wait (about one second)
+    // the force kernel runs on a second stream beside the advection-collision
+    // kernel: fork after the previous step, join before the re-rasterisation
+    cudaStream_t side = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr;
+    bool overlap = true;  // force kernel beside the advection-collision kernel (else before it)
     int64_t t = 0;
     int64_t ring_base = 0; // first step whose force record is valid
     std::string err;
@@ -101,7 +108,6 @@ StepParams params(const lbm_ctx *c) {
     p.f0 = c->f[0];
     p.f1 = c->f[1];
     p.owner = c->owner;
-    p.prev = c->prev;
     p.flags = c->flags;
     p.S = c->solids;
     p.nsolid = c->nsolid;
@@ -148,6 +154,8 @@ StepParams params(const lbm_ctx *c) {
     p.wall_ux1_f = (float)g.wall_ux[1];
     p.umax_f = (float)g.inflow_umax;
     p.bar = c->bar_d;
+    p.spin_limit = c->spin_limit;
+    p.near_id = c->near_d;
     return p;
 }
 
@@ -160,10 +168,13 @@ void release(lbm_ctx *c) {
     if (!c) return;
     drop_graph(c);
     for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
-    void *bufs[] = {c->f[0], c->f[1], c->owner, c->prev, c->flags, c->solids, c->moving_d,
-                    c->ring, c->t_d, c->status_d, c->bar_d, c->scratch, c->bnd_d, c->ev_d};
+    void *bufs[] = {c->f[0], c->f[1], c->owner, c->flags, c->solids, c->moving_d, c->ring,
+                    c->t_d, c->status_d, c->bar_d, c->scratch, c->bnd_d, c->ev_d, c->near_d};
     for (void *b : bufs)
         if (b) cudaFree(b);
+    if (c->fork) cudaEventDestroy(c->fork);
+    if (c->join) cudaEventDestroy(c->join);
+    if (c->side) cudaStreamDestroy(c->side);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
     delete c;
 }
@@ -214,9 +225,22 @@ lbm_status upload_moving(lbm_ctx *c) {
     return LBM_OK;
 }
 
-// One step t -> t+1: the advection-collision kernel, then the per-solid work
-// (link sums and force record of time t, motion, t += 1, re-rasterisation).
+// One step t -> t+1: the force kernel (force record of time t, motion) on the
+// side stream beside the advection-collision kernel, both after the previous
+// step; then the re-rasterisation of the moving solids, which advances t (or
+// a clock tick when no solid moves).
 lbm_status enqueue_step(lbm_ctx *c, const StepParams &p, bool timed) {
+    const bool fork = p.nsolid > 0 && c->overlap;
+    if (fork) {
+        CK(c, cudaEventRecord(c->fork, c->stream));
+        CK(c, cudaStreamWaitEvent(c->side, c->fork, 0));
+        CK(c, gbm::launch_forces(p, c->side));
+        CK(c, cudaEventRecord(c->join, c->side));
+        c->launches++;
+    } else if (p.nsolid > 0) {
+        CK(c, gbm::launch_forces(p, c->stream));
+        c->launches++;
+    }
     if (timed) {
         if (c->ev_used + 2 > c->ev.size()) {
             for (int k = 0; k < 2; k++) {
@@ -236,7 +260,8 @@ lbm_status enqueue_step(lbm_ctx *c, const StepParams &p, bool timed) {
         CK(c, gbm::launch_open_columns(p, c->stream));
         c->launches++;
     }
-    if (p.nsolid > 0) CK(c, gbm::launch_solids(p, p.nmoving > 0 ? gbm::SOLIDS_REMASK : 0, c->stream));
+    if (fork) CK(c, cudaStreamWaitEvent(c->stream, c->join, 0));
+    if (p.nmoving > 0) CK(c, gbm::launch_remask(p, c->stream));
     else CK(c, gbm::launch_tick(p, c->stream));
     c->launches += gbm::stream_collide_launches(p) + 1;
     return LBM_OK;
@@ -259,13 +284,13 @@ lbm_status check_status(lbm_ctx *c) {
     int st = 0;
     CK(c, cudaMemcpyAsync(&st, c->status_d, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
     CK(c, cudaStreamSynchronize(c->stream));
+    // a grid barrier that gave up leaves its arrival count behind: clear it
+    // whatever else was raised, so that a restored state steps cleanly
+    if (st & 4) CK(c, cudaMemsetAsync(c->bar_d, 0, 2 * sizeof(unsigned int), c->stream));
     if (st & 1) return fail(c, LBM_EUNSTABLE, "non-finite or non-positive density produced");
     if (st & 2) return fail(c, LBM_EUNSTABLE, "a solid reached a non-finite state");
-    if (st & 4) {
-        // a grid barrier gave up: reset it so that later launches start clean
-        cudaMemsetAsync(c->bar_d, 0, 2 * sizeof(unsigned int), c->stream);
-        return fail(c, LBM_ETIMEOUT, "a grid-wide barrier of the per-solid kernel timed out");
-    }
+    if (st & 4)
+        return fail(c, LBM_ETIMEOUT, "a grid-wide barrier of the re-rasterisation kernel gave up");
     if (st & 8)
         return fail(c, LBM_ESTATE,
                     "a solid covered or uncovered more nodes in one step than its event queue "
@@ -348,14 +373,19 @@ lbm_status lbm_create(const lbm_config *cfg, lbm_ctx **out) {
     for (int b = 0; b < 2 && e == cudaSuccess; b++)  // row padding stays zero
         e = cudaMemsetAsync(c->f[b], 0, 9 * plane * c->elem, c->stream);
     if (e == cudaSuccess) e = cudaMalloc(&c->owner, plane * sizeof(uint16_t));
-    if (e == cudaSuccess) e = cudaMalloc(&c->prev, plane * sizeof(uint16_t));
     if (e == cudaSuccess) e = cudaMalloc(&c->flags, plane * sizeof(uint16_t));
     if (e == cudaSuccess) e = cudaMalloc(&c->t_d, sizeof(long long));
     if (e == cudaSuccess) e = cudaMalloc(&c->status_d, sizeof(int));
-    if (e == cudaSuccess) e = cudaMalloc(&c->bar_d, 2 * sizeof(unsigned int));
-    if (e == cudaSuccess) e = cudaMemsetAsync(c->bar_d, 0, 2 * sizeof(unsigned int), c->stream);
+    if (e == cudaSuccess) e = cudaMalloc(&c->bar_d, 4 * sizeof(unsigned int));
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->bar_d, 0, 4 * sizeof(unsigned int), c->stream);
+    if (e == cudaSuccess) {
+        int lo = 0, hi = 0;  // the force kernel's stream at the highest priority
+        e = cudaDeviceGetStreamPriorityRange(&lo, &hi);
+        if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&c->side, cudaStreamNonBlocking, hi);
+    }
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->join, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->owner, 0xFF, plane * sizeof(uint16_t), c->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(c->prev, 0xFF, plane * sizeof(uint16_t), c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->t_d, 0, sizeof(long long), c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->status_d, 0, sizeof(int), c->stream);
     if (e == cudaSuccess) {
@@ -416,6 +446,9 @@ lbm_status lbm_add_solid(lbm_ctx *c, const lbm_disk *d, int32_t *id_out) {
         CK(c, cudaStreamSynchronize(c->stream));
         if (c->solids) CK(c, cudaFree(c->solids));
         c->solids = ns;
+        if (c->near_d) CK(c, cudaFree(c->near_d));  // rebuilt by the next pair test
+        c->near_d = nullptr;
+        CK(c, cudaMalloc(&c->near_d, (size_t)cap * gbm::NEAR_CAP * sizeof(uint16_t)));
         c->solid_cap = cap;
     }
     if (c->nsolid + 1 > c->ring_cap) {
@@ -439,8 +472,10 @@ lbm_status lbm_add_solid(lbm_ctx *c, const lbm_disk *d, int32_t *id_out) {
     s.r = d->r;
     s.rho_s = d->rho_s;
     s.ta = c->t;
-    s.pend_t = -1;
-    s.near = 1;  // until the first pair test: assume a neighbour
+    s.xo = s.tx = s.x;
+    s.yo = s.ty = s.y;
+    s.ev_t = -1;
+    s.near_n = -1;  // until the next pair test: every solid is a neighbour
     s.vxf = (float)d->vx;
     s.vyf = (float)d->vy;
     s.omf = (float)d->omega;
@@ -472,6 +507,7 @@ lbm_status lbm_add_solid(lbm_ctx *c, const lbm_disk *d, int32_t *id_out) {
         CK(c, cudaMemsetAsync(c->bnd_d, 0, 2 * sizeof(int), c->stream));
         c->bnd_cap = (int)cap;
     }
+    CK(c, cudaMemsetAsync(c->bar_d + 3, 1, sizeof(unsigned int), c->stream));  // pair test
     StepParams p = params(c);
     CK(c, gbm::launch_stamp_solid(p, id, c->stream));
     c->launches += 2;
@@ -629,6 +665,168 @@ lbm_status lbm_fields_static(lbm_ctx *c, double *rho, double *ux, double *uy) {
     return lbm_sync(c);
 }
 
+}  // extern "C"
+
+// ---------------------------------------------------------- checkpoints
+
+namespace {
+
+constexpr uint32_t STATE_MAGIC = 0x534D424Cu;  // "LBMS"
+constexpr uint32_t STATE_VERSION = 1;
+
+// Leading block of a saved state; the arrays follow in the order of
+// state_parts.  The configuration is kept with its stream and device cleared.
+struct StateHeader {
+    uint32_t magic, version;
+    uint32_t solid_bytes, reserved;
+    lbm_config cfg;
+    int64_t t, ring_base;
+    int32_t pitch, nsolid, ev_len, pad;
+};
+
+struct Part {
+    char *host;        // position in the caller's buffer
+    void *dev;         // device array
+    size_t bytes;
+};
+
+lbm_config comparable(lbm_config g) {
+    g.stream = nullptr;
+    g.device = 0;
+    return g;
+}
+
+int64_t state_bytes(const lbm_ctx *c, int ev_len) {
+    const size_t plane = (size_t)c->cfg.ny * c->pitch;
+    return (int64_t)(sizeof(StateHeader) + 9 * plane * c->elem + 2 * plane * sizeof(uint16_t) +
+                     (size_t)c->nsolid * sizeof(DSolid) +
+                     (size_t)(c->cfg.force_ring + 1) * 2 * c->nsolid * 3 * sizeof(double) +
+                     (size_t)ev_len * (sizeof(int2) + 6 * sizeof(double)) + (size_t)c->nsolid);
+}
+
+// The device arrays of a state, laid out after the header at base.
+std::vector<Part> state_parts(lbm_ctx *c, char *base, int ev_len) {
+    const size_t plane = (size_t)c->cfg.ny * c->pitch;
+    const StepParams p = params(c);
+    char *at = base + sizeof(StateHeader);
+    std::vector<Part> v;
+    auto add = [&](void *dev, size_t bytes) {
+        v.push_back(Part{at, dev, bytes});
+        at += bytes;
+    };
+    add((c->t & 1) ? c->f[1] : c->f[0], 9 * plane * c->elem);  // populations of time t
+    add(c->owner, plane * sizeof(uint16_t));
+    add(c->flags, plane * sizeof(uint16_t));
+    add(c->solids, (size_t)c->nsolid * sizeof(DSolid));
+    add(c->ring, (size_t)(c->cfg.force_ring + 1) * 2 * c->nsolid * 3 * sizeof(double));
+    add(p.ev, (size_t)ev_len * sizeof(int2));
+    add(p.ev_mom, (size_t)ev_len * 6 * sizeof(double));
+    return v;
+}
+
+lbm_status event_count(lbm_ctx *c, int *n) {
+    *n = 0;
+    if (c->ev_d) {
+        CK(c, cudaMemcpyAsync(n, c->ev_d, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+        CK(c, cudaStreamSynchronize(c->stream));
+        if (*n > c->ev_cap) *n = c->ev_cap;
+    }
+    return LBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+lbm_status lbm_state_size(lbm_ctx *c, int64_t *bytes) {
+    if (!c || !bytes) return LBM_EINVAL;
+    CK(c, cudaSetDevice(c->cfg.device));
+    int n = 0;
+    lbm_status st = event_count(c, &n);
+    if (st != LBM_OK) return st;
+    *bytes = state_bytes(c, n);
+    return LBM_OK;
+}
+
+lbm_status lbm_save(lbm_ctx *c, void *buf, int64_t bytes) {
+    if (!c || !buf) return LBM_EINVAL;
+    if (c->batch) return fail(c, LBM_EINVAL, "a case of a batch is saved with its batch");
+    CK(c, cudaSetDevice(c->cfg.device));
+    lbm_status st = lbm_sync(c);  // a state with a raised status is not worth keeping
+    if (st != LBM_OK) return st;
+    int n = 0;
+    st = event_count(c, &n);
+    if (st != LBM_OK) return st;
+    if (bytes < state_bytes(c, n))
+        return fail(c, LBM_EINVAL, "buffer of %lld bytes, the state needs %lld", (long long)bytes,
+                    (long long)state_bytes(c, n));
+    char *base = static_cast<char *>(buf);
+    StateHeader h{};
+    h.magic = STATE_MAGIC;
+    h.version = STATE_VERSION;
+    h.solid_bytes = sizeof(DSolid);
+    h.cfg = comparable(c->cfg);
+    h.t = c->t;
+    h.ring_base = c->ring_base;
+    h.pitch = c->pitch;
+    h.nsolid = c->nsolid;
+    h.ev_len = n;
+    std::memcpy(base, &h, sizeof h);
+    std::vector<Part> parts = state_parts(c, base, n);
+    for (const Part &q : parts)
+        if (q.bytes) CK(c, cudaMemcpyAsync(q.host, q.dev, q.bytes, cudaMemcpyDeviceToHost, c->stream));
+    char *mv = parts.back().host + parts.back().bytes;
+    for (int s = 0; s < c->nsolid; s++) mv[s] = (char)c->is_moving[s];
+    CK(c, cudaStreamSynchronize(c->stream));
+    return LBM_OK;
+}
+
+lbm_status lbm_load(lbm_ctx *c, const void *buf, int64_t bytes) {
+    if (!c || !buf || bytes < (int64_t)sizeof(StateHeader)) return LBM_EINVAL;
+    if (c->batch) return fail(c, LBM_EINVAL, "a case of a batch is loaded with its batch");
+    StateHeader h;
+    std::memcpy(&h, buf, sizeof h);
+    if (h.magic != STATE_MAGIC || h.version != STATE_VERSION || h.solid_bytes != sizeof(DSolid))
+        return fail(c, LBM_EINVAL, "not a state saved by this library");
+    const lbm_config want = comparable(c->cfg);
+    if (std::memcmp(&h.cfg, &want, sizeof want) != 0 || h.pitch != c->pitch)
+        return fail(c, LBM_EINVAL, "the state was saved with another configuration");
+    if (h.nsolid != c->nsolid)
+        return fail(c, LBM_EINVAL, "the state has %d solids, the context %d", h.nsolid, c->nsolid);
+    if (h.ev_len < 0 || bytes < state_bytes(c, h.ev_len))
+        return fail(c, LBM_EINVAL, "truncated state");
+    CK(c, cudaSetDevice(c->cfg.device));
+    CK(c, cudaStreamSynchronize(c->stream));
+    drop_graph(c);
+    lbm_status st = harvest_timing(c);
+    if (st != LBM_OK) return st;
+    const char *base = static_cast<const char *>(buf);
+    const char *mv = base + state_bytes(c, h.ev_len) - c->nsolid;
+    for (int s = 0; s < c->nsolid; s++) c->is_moving[s] = mv[s] ? 1 : 0;
+    st = upload_moving(c);  // also sizes the event list
+    if (st != LBM_OK) return st;
+    if (h.ev_len > c->ev_cap) return fail(c, LBM_EINVAL, "the state's event list does not fit");
+    c->t = h.t;
+    c->ring_base = h.ring_base;
+    std::vector<Part> parts = state_parts(c, const_cast<char *>(base), h.ev_len);
+    for (const Part &q : parts)
+        if (q.bytes) CK(c, cudaMemcpyAsync(q.dev, q.host, q.bytes, cudaMemcpyHostToDevice, c->stream));
+    const long long t = h.t;
+    CK(c, cudaMemcpyAsync(c->t_d, &t, sizeof t, cudaMemcpyHostToDevice, c->stream));
+    if (c->ev_d) CK(c, cudaMemcpyAsync(c->ev_d, &h.ev_len, sizeof(int), cudaMemcpyHostToDevice, c->stream));
+    // clean control words: status, barrier, displacement; a pair test first
+    const unsigned int ctl[4] = {0u, 0u, 0u, 1u};
+    CK(c, cudaMemcpyAsync(c->bar_d, ctl, sizeof ctl, cudaMemcpyHostToDevice, c->stream));
+    CK(c, cudaMemsetAsync(c->status_d, 0, sizeof(int), c->stream));
+    if (c->bnd_d) CK(c, cudaMemsetAsync(c->bnd_d, 0, 2 * sizeof(int), c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    return LBM_OK;
+}
+
+}  // extern "C"
+
+extern "C" {
+
 lbm_status lbm_get_populations(lbm_ctx *c, double *f, int32_t on_device) {
     if (!c || !f) return LBM_EINVAL;
     CK(c, cudaSetDevice(c->cfg.device));
@@ -727,8 +925,8 @@ lbm_status lbm_set_solid(lbm_ctx *c, int32_t id, const double *state) {
     CK(c, cudaStreamSynchronize(c->stream));
     if (state[0] != s.x || state[1] != s.y)
         return fail(c, LBM_EINVAL, "lbm_set_solid changes velocities only; position must match");
-    s.xa = s.xn = s.x;
-    s.ya = s.yn = s.y;
+    s.xa = s.xn = s.xo = s.x;
+    s.ya = s.yn = s.yo = s.y;
     s.ta = c->t;
     s.vx = s.vxn = state[2];
     s.vy = s.vyn = state[3];
@@ -737,6 +935,7 @@ lbm_status lbm_set_solid(lbm_ctx *c, int32_t id, const double *state) {
     s.vyf = (float)state[3];
     s.omf = (float)state[4];
     CK(c, cudaMemcpyAsync(c->solids + id, &s, sizeof s, cudaMemcpyHostToDevice, c->stream));
+    CK(c, cudaMemsetAsync(c->bar_d + 3, 1, sizeof(unsigned int), c->stream));  // pair test
     drop_graph(c);
     c->is_moving[id] = translates(s) ? 1 : 0;
     return upload_moving(c);
@@ -803,6 +1002,14 @@ const char *lbm_status_string(lbm_status st) {
     return "unknown status";
 }
 
+lbm_status lbm_set_wait_limit(lbm_ctx *c, int64_t polls) {
+    if (!c || polls < 0) return LBM_EINVAL;
+    if (c->batch) return fail(c, LBM_EINVAL, "a case of a batch is stepped by its batch");
+    c->spin_limit = polls;
+    drop_graph(c);  // captured launches carry the old limit
+    return LBM_OK;
+}
+
 lbm_status lbm_set_graph(lbm_ctx *c, int32_t steps_per_graph) {
     if (!c || steps_per_graph < 0) return LBM_EINVAL;
     if (steps_per_graph > 1 && !c->own_stream && c->stream == nullptr)
@@ -844,42 +1051,60 @@ lbm_status lbm_set_kernel_variant(lbm_ctx *c, int32_t variant) {
 
 int32_t lbm_kernel_variant(const lbm_ctx *c) { return c ? c->sc_variant : -1; }
 
+lbm_status lbm_set_force_overlap(lbm_ctx *c, int32_t on) {
+    if (!c || (on != 0 && on != 1)) return LBM_EINVAL;
+    drop_graph(c);
+    c->overlap = on != 0;
+    return LBM_OK;
+}
+
+int32_t lbm_force_overlap(const lbm_ctx *c) { return c ? (c->overlap ? 1 : 0) : -1; }
+
 lbm_status lbm_autotune(lbm_ctx *c, int32_t steps, int32_t *best) {
     if (!c || steps < 1) return LBM_EINVAL;
     if (c->batch) return fail(c, LBM_EINVAL, "a case of a batch is tuned by lbm_batch_autotune");
+    CK(c, cudaSetDevice(c->cfg.device));
     const bool was_timing = c->timing;
-    const double keep_ms = c->timed_ms;
-    const int64_t keep_n = c->timed_launches;
+    const int keep_graph = c->graph_steps;
     lbm_status st = harvest_timing(c);
     if (st != LBM_OK) return st;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    CK(c, cudaEventCreate(&e0));
+    CK(c, cudaEventCreate(&e1));
+    c->timing = false;
+    c->graph_steps = 0;
     double best_ms = 0.0;
     int best_v = 0;
-    for (int v = 0; v < gbm::KERNEL_VARIANTS; v++) {
-        c->sc_variant = v;
-        drop_graph(c);
-        if (c->bnd_d) CK(c, cudaMemsetAsync(c->bnd_d, 0, 2 * sizeof(int), c->stream));
-        c->timing = true;
-        c->timed_ms = 0.0;
-        c->timed_launches = 0;
-        st = lbm_step(c, 1);  // first launch of a variant is not timed
-        if (st == LBM_OK) st = harvest_timing(c);
-        c->timed_ms = 0.0;
-        c->timed_launches = 0;
-        if (st == LBM_OK) st = lbm_step(c, steps);
-        if (st == LBM_OK) st = harvest_timing(c);
-        if (st != LBM_OK) return st;
-        const double ms = c->timed_ms / (c->timed_launches ? c->timed_launches : 1);
-        if (v == 0 || ms < best_ms) {
-            best_ms = ms;
-            best_v = v;
+    bool best_o = true;
+    for (int o = 1; o >= 0 && st == LBM_OK; o--) {
+        for (int v = 0; v < gbm::KERNEL_VARIANTS && st == LBM_OK; v++) {
+            c->sc_variant = v;
+            c->overlap = o != 0;
+            drop_graph(c);
+            if (c->bnd_d) CK(c, cudaMemsetAsync(c->bnd_d, 0, 2 * sizeof(int), c->stream));
+            st = lbm_step(c, 1);  // the first step of a shape is not timed
+            if (st == LBM_OK && cudaEventRecord(e0, c->stream) != cudaSuccess) st = LBM_ECUDA;
+            if (st == LBM_OK) st = lbm_step(c, steps);
+            if (st == LBM_OK && cudaEventRecord(e1, c->stream) != cudaSuccess) st = LBM_ECUDA;
+            if (st == LBM_OK) st = lbm_sync(c);
+            float ms = 0.f;
+            if (st == LBM_OK && cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) st = LBM_ECUDA;
+            if (st == LBM_OK && ((o == 1 && v == 0) || ms < best_ms)) {
+                best_ms = ms;
+                best_v = v;
+                best_o = o != 0;
+            }
         }
     }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
     c->sc_variant = best_v;
+    c->overlap = best_o;
     drop_graph(c);
-    if (c->bnd_d) CK(c, cudaMemsetAsync(c->bnd_d, 0, 2 * sizeof(int), c->stream));
+    if (c->bnd_d) cudaMemsetAsync(c->bnd_d, 0, 2 * sizeof(int), c->stream);
     c->timing = was_timing;
-    c->timed_ms = keep_ms;
-    c->timed_launches = keep_n;
+    c->graph_steps = keep_graph;
+    if (st != LBM_OK) return st == LBM_ECUDA ? fail(c, st, "autotuner: event timing failed") : st;
     if (best) *best = best_v;
     return LBM_OK;
 }

@@ -37,24 +37,36 @@ __host__ __device__ constexpr C wgt(int i) {
 struct DSolid {
     double xa, ya;     // position when added (prescribed motion)
     double x, y;       // centre R(t)
-    double xn, yn;     // centre R(t+1), written during the step
+    double xn, yn;     // centre R(t+1), written by the force kernel of the step
     double xw, yw;     // R(t) reduced into the domain along periodic axes
     double xnw, ynw;   // R(t+1) reduced likewise
     double vx, vy, om; // V(t), Omega(t)
     double vxn, vyn, omn;
     double r, rho_s;
-    double pend[6];    // momentum booked by the node-type changes into time pend_t:
-                       // [Fx, Fy, T] for the Eq. 4 record, then for the Eq. 5 record
-    long long pend_t;  // time whose force record carries pend
+    double xo, yo;     // R(t) kept through the re-rasterisation (R(t) itself becomes R(t+1)
+                       // there); equal to x, y between steps
+    double tx, ty;     // centre at the last pair test
+    long long ev_t;    // record (time) into which the segment ev_off, ev_n books its momenta
     long long ta;      // time when added
     float vxf, vyf, omf;  // FP32 copies of vx, vy, om for the FP32 kernels
     float xf, yf, xnf, ynf;  // FP32 copies of x, y, xn, yn for the pair test
     int xwi, ywi;      // integer part of (xw, yw) ...
     float xwr, ywr;    // ... and the FP32 remainder, for FP32 lever arms
     int motion;
-    int near;          // another disk may share a node with this one at t or t+1
-    int ev_off, ev_n;  // this step's segment of the covered/fresh event list
+    int near_n;        // entries of the solid's near list (-1: too many; every solid is tested)
+    int ev_off, ev_n;  // the solid's segment of the covered/fresh event list
 };
+
+// Near list: the solids that can own a node within NEAR_REACH (lattice
+// units) of a disk's surface at t or t+1 are those whose centres are closer
+// than r_s + r_q + NEAR_REACH; the list is built with a further NEAR_MARGIN
+// and stays valid while every solid has moved less than NEAR_MARGIN / 2 from
+// its centre at the test.  NEAR_REACH covers the re-rasterisation ring
+// (within one node of the surface, plus one step of motion) and the refill's
+// extrapolation nodes (three links, 3 sqrt(2) < 4.5, from a fresh node).
+constexpr int NEAR_CAP = 32;
+constexpr float NEAR_REACH = 4.5f;
+constexpr float NEAR_MARGIN = 4.0f;
 
 // covered/fresh nodes one solid can queue per step
 constexpr int SOLID_EVENTS = 256;
@@ -68,7 +80,7 @@ struct Lattice {
 struct StepParams {
     Lattice L;
     void *f0, *f1;            // population buffers; buffer (t & 1) holds time t
-    uint16_t *owner, *prev, *flags;
+    uint16_t *owner, *flags;
     DSolid *S;
     int nsolid;
     const int *moving;        // ids of solids that translate (or are free)
@@ -91,7 +103,11 @@ struct StepParams {
     int sc_variant;           // node width per thread of the advection-collision kernel
     float omega_f, body_xf, body_yf, rho0_f;  // FP32 copies for the FP32 kernels
     float wall_ux0_f, wall_ux1_f, umax_f;
-    unsigned int *bar;        // grid barrier of the per-solid kernel: {count, generation}
+    unsigned int *bar;        // per-solid control words: grid barrier {count, generation},
+                              // largest displacement since the pair test (FP32 bits), pair
+                              // test requested
+    long long spin_limit;     // polls of a bounded device wait (0: give up at once)
+    uint16_t *near_id;        // [nsolid][NEAR_CAP] near lists
     int2 *ev;                 // covered/fresh events of the step: {node code, solid}
     double *ev_mom;           // [6] momentum and torque of each event: Eq. 4, Eq. 5 booking
     int *ev_len;              // events published this step (cleared after use)
@@ -352,11 +368,13 @@ cudaError_t launch_open_columns(const StepParams &p, cudaStream_t st);
 // k_stream_collide_batch.cu
 cudaError_t launch_stream_collide_batch(const BatchLaunch &b, cudaStream_t st);
 int tile_nodes(int precision, int variant);  // nodes along x of one tile
-// k_solid_step.cu: per-solid work of a step in one cooperative launch (force
-// record of time t, motion, t += 1; with SOLIDS_REMASK also re-rasterisation
-// of the moving solids).
-constexpr int SOLIDS_REMASK = 1;
-cudaError_t launch_solids(const StepParams &p, int mode, cudaStream_t st);
+// k_solid_step.cu: per-solid work of a step t -> t+1.  launch_forces: force
+// record of time t and motion t -> t+1 of every solid (it only reads what the
+// advection-collision kernel of the step reads, so it may run beside it);
+// launch_remask, after both: re-rasterisation of the moving solids, refill,
+// t += 1 (one cooperative launch).
+cudaError_t launch_forces(const StepParams &p, cudaStream_t st);
+cudaError_t launch_remask(const StepParams &p, cudaStream_t st);
 // batch: force record of every resting solid of every active case, t += 1
 cudaError_t launch_solids_batch(const BatchLaunch &b, cudaStream_t st);
 // batch: BATCH_TEST retires the active cases whose drag (Eq. 5 Fx summed

@@ -94,6 +94,12 @@ _SIGNATURES = {
     "lbm_last_error": (ctypes.c_char_p, [_P]),
     "lbm_status_string": (ctypes.c_char_p, [_I32]),
     "lbm_set_graph": (_I32, [_P, _I32]),
+    "lbm_set_wait_limit": (_I32, [_P, _I64]),
+    "lbm_set_force_overlap": (_I32, [_P, _I32]),
+    "lbm_force_overlap": (_I32, [_P]),
+    "lbm_state_size": (_I32, [_P, ctypes.POINTER(_I64)]),
+    "lbm_save": (_I32, [_P, _P, _I64]),
+    "lbm_load": (_I32, [_P, _P, _I64]),
     "lbm_set_timing": (_I32, [_P, _I32]),
     "lbm_get_timing": (_I32, [_P, _D, ctypes.POINTER(_I64)]),
     "lbm_launch_count": (_I64, [_P]),
@@ -275,6 +281,33 @@ def lbm_status_string(st: int) -> str:
 
 def lbm_set_graph(ctx, steps: int):
     _check(load().lbm_set_graph(ctx, int(steps)), ctx)
+
+
+def lbm_set_force_overlap(ctx, on: bool):
+    _check(load().lbm_set_force_overlap(ctx, int(bool(on))), ctx)
+
+
+def lbm_force_overlap(ctx) -> int:
+    return load().lbm_force_overlap(ctx)
+
+
+def lbm_set_wait_limit(ctx, polls: int):
+    _check(load().lbm_set_wait_limit(ctx, int(polls)), ctx)
+
+
+def lbm_state_size(ctx) -> int:
+    n = _I64()
+    _check(load().lbm_state_size(ctx, ctypes.byref(n)), ctx)
+    return n.value
+
+
+def lbm_save(ctx, buf):
+    """Save the context's state into buf (a writable host array of uint8)."""
+    _check(load().lbm_save(ctx, _ptr(buf), int(buf.nbytes)), ctx)
+
+
+def lbm_load(ctx, buf):
+    _check(load().lbm_load(ctx, _ptr(buf), int(buf.nbytes)), ctx)
 
 
 def lbm_set_timing(ctx, enable: bool):
@@ -673,6 +706,24 @@ class Lattice:
 
     def set_graph(self, steps: int):
         lbm_set_graph(self._h, steps)
+
+    def set_force_overlap(self, on: bool):
+        lbm_set_force_overlap(self._h, on)
+
+    def force_overlap(self) -> int:
+        return lbm_force_overlap(self._h)
+
+    def set_wait_limit(self, polls: int):
+        lbm_set_wait_limit(self._h, polls)
+
+    def save(self) -> np.ndarray:
+        """The context's state (lbm_save) as a host array of bytes."""
+        buf = np.empty(lbm_state_size(self._h), dtype=np.uint8)
+        lbm_save(self._h, buf)
+        return buf
+
+    def load(self, state: np.ndarray):
+        lbm_load(self._h, np.ascontiguousarray(state, dtype=np.uint8))
 
     def set_timing(self, enable: bool):
         lbm_set_timing(self._h, enable)

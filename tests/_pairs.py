@@ -51,6 +51,32 @@ def force_rel(got, ref, radii, rho0=1.0):
     return worst
 
 
+def force_rel_own(got, ref):
+    """Worst error of each solid's force and torque relative to that solid's
+    own series maximum (no floor): the error of the net force itself, which
+    force_rel may scale by the larger link-sum size.  Returns a list over
+    solids of (Fx/Fy error, torque error)."""
+    got = np.asarray(got)
+    ref = np.asarray(ref)
+    out = []
+    for s in range(ref.shape[1]):
+        row = []
+        for comp in (slice(0, 2), slice(2, 3)):
+            a = ref[:, s, :, comp]
+            scale = np.abs(a).max()
+            row.append(float(np.abs(got[:, s, :, comp] - a).max() / scale) if scale > 0 else 0.0)
+        out.append(tuple(row))
+    return out
+
+
+def describe(got, ref, radii):
+    """Failure text: the force-scale error and each solid's own-scale error."""
+    own = force_rel_own(got, ref)
+    worst = max(max(r) for r in own) if own else 0.0
+    return (f"force rel err {force_rel(got, ref, radii):.3e} (force scale); "
+            f"worst solid relative to its own series {worst:.3e}")
+
+
 def seeded_f(w, seed, amp=0.01):
     """Equilibrium at u0 times a seeded multiplicative perturbation."""
     import workloads as WL

@@ -84,5 +84,23 @@ def test_variant_range_and_autotune():
         g.set_kernel_variant(6)
     best = g.autotune(2)
     assert 0 <= best < 6 and g.kernel_variant() == best
+    assert g.force_overlap() in (0, 1)
     g.sync()
     g.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "fp16"])
+def test_force_kernel_beside_or_before_gives_the_same_results(precision):
+    """The force kernel reads only what the advection-collision kernel of the
+    step reads, so running it beside that kernel (second stream) or before it
+    changes nothing, bit for bit."""
+    w = CASES["walls"]
+    runs = []
+    for on in (True, False):
+        g = make_gpu(w, precision, ring=64)
+        g.set_force_overlap(on)
+        g.set_f(seeded_f(w, 3))
+        runs.append((g.step_record(40), g.get_f(), g.owner(), g.solids()))
+        g.close()
+    for x, y in zip(*runs):
+        assert np.array_equal(x, y)
