@@ -33,9 +33,12 @@
 // the warp's lanes, each lane fetching several nodes before it processes
 // them; every decision is taken by the exact test.
 //
-// Precision: per-link products are in the arithmetic precision of the
-// storage mode (FP32 in the deviation modes); every sum over links and
-// across lanes, the booked momenta and the motion are FP64, in a fixed order.
+// Precision: per-link products and each lane's running sum over its links
+// (a handful) are in the arithmetic precision of the storage mode (FP32 in the
+// deviation modes); the sums across lanes, the booked momenta and the motion
+// are FP64, in a fixed order.  (GB300 runs FP64 at about two fused
+// multiply-adds per clock per SM: FP64 lane sums would cost the force kernel
+// about 100 us per step on 2000 disks.)
 #include "lbm_internal.cuh"
 
 namespace gbm {
@@ -88,8 +91,8 @@ __device__ bool grid_sync(const StepParams &p) {
 
 // ------------------------------------------------------------- helpers
 
-template <int N>
-__device__ __forceinline__ void warp_sum(double (&v)[N]) {
+template <class T, int N>
+__device__ __forceinline__ void warp_sum(T (&v)[N]) {
 #pragma unroll
     for (int k = 0; k < N; k++)
         for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_down_sync(FULL, v[k], o);
@@ -113,12 +116,25 @@ __device__ __forceinline__ float cvt_s(__half v) { return __half2float(v); }
 struct Centre {
     int xi, yi;
     float fx, fy;
+    __device__ __forceinline__ Centre(int xi_, int yi_, float fx_, float fy_)
+        : xi(xi_), yi(yi_), fx(fx_), fy(fy_) {}
     __device__ __forceinline__ Centre(double X, double Y) {
         const double a = floor(X), b = floor(Y);
         xi = (int)a;
         yi = (int)b;
         fx = (float)(X - a);
         fy = (float)(Y - b);
+    }
+    // The integers of row j within rr of the centre, [a, b] (a > b: none),
+    // from the FP32 chord; false when the row misses the circle.
+    __device__ __forceinline__ bool chord(int j, float rr, int &a, int &b) const {
+        const float dy = (float)(j - yi) - fy;
+        const float h2 = rr * rr - dy * dy;
+        if (h2 < 0.f) return false;
+        const float h = sqrtf(h2);
+        a = xi + (int)ceilf(fx - h);
+        b = xi + (int)floorf(fx + h);
+        return true;
     }
     // Unwrapped x-range [a, b] containing every node of row j within rr of
     // the centre (one node of margin on each side); false if none can be.
@@ -149,28 +165,74 @@ __device__ __forceinline__ int neighbour(const Lattice &L, int x, int y, int dx,
     return y * L.pitch + x;
 }
 
+// Unwrapped node coordinates near one disk -> domain nodes, without integer
+// division: along a periodic axis the nodes within WRAP_REACH of the centre
+// lie within one period of the image offset taken once per disk (the domain
+// is wider than 2 r + 8).
+constexpr int WRAP_REACH = 8;
+__host__ __device__ __forceinline__ int floor_div(int a, int n) {
+    return a >= 0 ? a / n : -((n - 1 - a) / n);
+}
+struct Wrap {
+    int ox, oy, nx, ny;
+    bool px, py;
+    // ix, iy = floor of the centre, rc = ceil(r)
+    __device__ __forceinline__ Wrap(const Lattice &L, int ix, int iy, int rc) {
+        nx = L.nx;
+        ny = L.ny;
+        px = L.bc_x == LBM_PERIODIC;
+        py = L.bc_y == LBM_PERIODIC;
+        ox = px ? nx * floor_div(ix - rc - WRAP_REACH, nx) : 0;
+        oy = py ? ny * floor_div(iy - rc - WRAP_REACH, ny) : 0;
+    }
+    __device__ __forceinline__ bool operator()(int i, int j, int &x, int &y) const {
+        x = i - ox;
+        y = j - oy;
+        if (px) {
+            while (x >= nx) x -= nx;  // at most twice
+        } else if ((unsigned)x >= (unsigned)nx) {
+            return false;
+        }
+        if (py) {
+            while (y >= ny) y -= ny;
+        } else if ((unsigned)y >= (unsigned)ny) {
+            return false;
+        }
+        return true;
+    }
+};
+
 // Up to two x-ranges of a row; the second is empty when a1 > b1.
 struct Ranges {
     int a0, b0, a1, b1;
 };
 
 // Nodes of row j that can lie inside exactly one of two disks of radius r
-// centred at c0 and c1: near the two left chord ends and the two right ends.
-__device__ __forceinline__ bool ring_ranges(const Centre &c0, const Centre &c1, float rr, int j,
+// centred at c0 and c1: between the chord ends of radius r + RING_EPS (a
+// superset of each disk's nodes in the row) and those of r - RING_EPS (a
+// subset), at the left and at the right.  RING_EPS is far above the FP32
+// rounding of a chord end (a few 1e-3 where the chord is short), so the exact
+// boundary node of each disk lies between the two; the exact test decides.
+constexpr float RING_EPS = 0.05f;
+__device__ __forceinline__ bool ring_ranges(const Centre &c0, const Centre &c1, float r, int j,
                                             Ranges &R) {
-    int a0, b0, a1, b1;
-    const bool h0 = c0.span(j, rr, a0, b0), h1 = c1.span(j, rr, a1, b1);
+    int a0, b0, a1, b1, p0, q0, p1, q1;
+    bool h0 = c0.chord(j, r + RING_EPS, a0, b0), h1 = c1.chord(j, r + RING_EPS, a1, b1);
+    h0 = h0 && a0 <= b0;
+    h1 = h1 && a1 <= b1;
     if (!h0 && !h1) return false;
-    if (!h0 || !h1) {
-        R.a0 = h0 ? a0 : a1;
-        R.b0 = h0 ? b0 : b1;
-        R.a1 = 1;
-        R.b1 = 0;
+    R.a1 = 1;
+    R.b1 = 0;
+    const bool i0 = h0 && c0.chord(j, r - RING_EPS, p0, q0) && p0 <= q0;
+    const bool i1 = h1 && c1.chord(j, r - RING_EPS, p1, q1) && p1 <= q1;
+    if (!i0 || !i1) {  // the row is near the top or bottom of a disk: the whole union
+        R.a0 = h0 ? (h1 ? min(a0, a1) : a0) : a1;
+        R.b0 = h0 ? (h1 ? max(b0, b1) : b0) : b1;
         return true;
     }
     R.a0 = min(a0, a1);
-    R.b0 = max(a0, a1) + 2;
-    R.a1 = min(b0, b1) - 2;
+    R.b0 = max(p0, p1) - 1;  // left: first node of the outer chords .. last before the inner
+    R.a1 = min(q0, q1) + 1;  // right: after the inner chords .. last of the outer
     R.b1 = max(b0, b1);
     if (R.a1 <= R.b0 + 1) {  // the two ends meet: one range
         R.b0 = R.b1;
@@ -204,6 +266,13 @@ __device__ __forceinline__ bool annulus_ranges(const Centre &c, float r, int j, 
     return true;
 }
 
+// Rows a disk can touch at either of two centres (floor iy0, iy1; rc =
+// ceil(r)), with a margin of g: a superset of rows_of's.
+__device__ __forceinline__ void rows_of_i(int iy0, int iy1, int rc, int g, int &j0, int &j1) {
+    j0 = min(iy0, iy1) - rc - g;
+    j1 = max(iy0, iy1) + rc + 1 + g;
+}
+
 // Rows a disk of radius r at Y0 (and Y1) can touch, with a margin of g.
 __device__ __forceinline__ void rows_of(double Y0, double Y1, double r, int g, int &j0, int &j1) {
     j0 = (int)floor(fmin(Y0, Y1) - r) - g;
@@ -225,7 +294,7 @@ __device__ __forceinline__ void warp_nodes_n(int j0, int j1, int lane, RF &&rng,
         R.a0 = R.a1 = 0;
         int n0 = 0, n1 = 0;
         if (j <= j1 && rng(j, R)) {
-            n0 = R.b0 - R.a0 + 1;
+            n0 = R.b0 >= R.a0 ? R.b0 - R.a0 + 1 : 0;
             n1 = R.b1 >= R.a1 ? R.b1 - R.a1 + 1 : 0;
         }
         int inc = n0 + n1;
@@ -281,9 +350,13 @@ __device__ __forceinline__ double lub_mag(double kappa, double zeta, double gap)
     return kappa * q * q;
 }
 
+// R(t+1) split, reduced into the domain (through the integer part: no FP64
+// division) and in FP32.
 __device__ __forceinline__ void set_next_centre(const Lattice &L, DSolid &b) {
-    b.xnw = wrap_coord(b.xn, L.nx, L.bc_x == LBM_PERIODIC);
-    b.ynw = wrap_coord(b.yn, L.ny, L.bc_y == LBM_PERIODIC);
+    split_coord(b.xn, b.ix1, b.fx1);
+    split_coord(b.yn, b.iy1, b.fy1);
+    b.xnw = L.bc_x == LBM_PERIODIC ? b.xn - (double)(L.nx * floor_div(b.ix1, L.nx)) : b.xn;
+    b.ynw = L.bc_y == LBM_PERIODIC ? b.yn - (double)(L.ny * floor_div(b.iy1, L.ny)) : b.yn;
     b.xnf = (float)b.xn;
     b.ynf = (float)b.yn;
 }
@@ -357,26 +430,31 @@ __device__ void move_solid(const StepParams &p, int s, int lane, long long t, co
 // Eq. 5 = (e_i - v) f_i - (e_opp - v) f_bb, torque (x_s - R) x F (Eq. 7).
 // BND: the interpolated boundary, whose links return the interpolated
 // population and use the velocity and lever arm at the cut.  A candidate
-// node's flags, its 9 populations and its 8 neighbours' owners are loaded
-// together.
+// node's flags and its 9 populations are loaded together, with its 8
+// neighbours' owners unless lists_ok and the solid has no other solid within
+// reach (then every solid neighbour of the annulus is the solid's own: a
+// solid q holding a node within r_s + 4 of s's centre is in s's near list).
 template <int P, bool LOCAL, bool BND>
 __device__ void forces_sum(const StepParams &p, int s, int lane, const void *f, int wi, int nw,
-                           double (&acc)[6]) {
+                           bool lists_ok, double (&acc)[6]) {
     using C = typename Prec<P>::C;
     using S = typename Prec<P>::S;
-    constexpr int UF = 2;
+    constexpr int UF = sizeof(S) == 8 ? 2 : 4;  // candidates a lane fetches at once
     const DSolid &b = p.S[s];
     const Lattice &L = p.L;
     const S *fs = static_cast<const S *>(f);
     const double X = b.x, Y = b.y;
-    const Centre c(X, Y);
+    const Centre c(b.ix0, b.iy0, b.fx0, b.fy0);
     const C vx = pick<C>(b.vx, b.vxf), vy = pick<C>(b.vy, b.vyf), om = pick<C>(b.om, b.omf);
     const C rho0 = pick<C>(p.rho0, p.rho0_f);
     const int plane = (int)L.plane;
     const float r = (float)b.r;
+    const bool owners = !lists_ok || b.near_n != 0;
+    const bool px = L.bc_x == LBM_PERIODIC, py = L.bc_y == LBM_PERIODIC;
+    const Wrap wrap(L, b.ix0, b.iy0, b.rc);
     int j0, j1;
-    rows_of(Y, Y, b.r, 3, j0, j1);
-    double lacc[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};  // this lane's links
+    rows_of_i(b.iy0, b.iy0, b.rc, 3, j0, j1);
+    C lacc[6] = {0, 0, 0, 0, 0, 0};  // this lane's links
     int ii[UF], jj[UF];
     uint16_t fl[UF];
     uint16_t own[UF][9];
@@ -385,17 +463,19 @@ __device__ void forces_sum(const StepParams &p, int s, int lane, const void *f, 
         j0, j1, lane, [&](int j, Ranges &R) { return annulus_ranges(c, r, j, R); },
         [&](int iu, int j, int u) {
             int x, y;
-            if (!locate(L, iu, j, x, y)) return false;
+            if (!wrap(iu, j, x, y)) return false;
             const int k = (int)cell_of(L, x, y);
             ii[u] = iu;
             jj[u] = j;
             fl[u] = p.flags[k];
 #pragma unroll
             for (int q = 0; q < 9; q++) fv[u][q] = fs[q * plane + k];
+            if (owners) {
 #pragma unroll
-            for (int i = 1; i < 9; i++) {
-                const int kb = neighbour(L, x, y, cx(i), cy(i));
-                own[u][i] = kb >= 0 ? p.owner[kb] : FLUID;
+                for (int i = 1; i < 9; i++) {
+                    const int kb = neighbour(L, x, y, cx(i), cy(i));
+                    own[u][i] = kb >= 0 ? p.owner[kb] : FLUID;
+                }
             }
             return true;
         },
@@ -412,7 +492,13 @@ __device__ void forces_sum(const StepParams &p, int s, int lane, const void *f, 
             }
 #pragma unroll
             for (int i = 1; i < 9; i++) {
-                if (!((m >> opp(i)) & 1u) || own[u][i] != (uint16_t)s) continue;
+                if (!((m >> opp(i)) & 1u)) continue;  // x_f + e_i is not solid
+                if (owners) {
+                    if (own[u][i] != (uint16_t)s) continue;
+                } else if ((!px && (unsigned)(iu + cx(i)) >= (unsigned)L.nx) ||
+                           (!py && (unsigned)(j + cy(i)) >= (unsigned)L.ny)) {
+                    continue;  // beyond a wall, not a solid
+                }
                 C dx, dy, ux, uy, fbb;
                 C fi = (C)cvt_s(fv[u][i]);
                 if (Prec<P>::dev) fi += wgt<C>(i);
@@ -461,17 +547,17 @@ __device__ void forces_sum(const StepParams &p, int s, int lane, const void *f, 
                 const C cmy = (C)cy(i) * fi - (C)cy(opp(i)) * fbb;
                 const C gmx = ((C)cx(i) - ux) * fi - ((C)cx(opp(i)) - ux) * fbb;
                 const C gmy = ((C)cy(i) - uy) * fi - ((C)cy(opp(i)) - uy) * fbb;
-                lacc[0] += (double)cmx;
-                lacc[1] += (double)cmy;
-                lacc[2] += (double)(dx * cmy - dy * cmx);
-                lacc[3] += (double)gmx;
-                lacc[4] += (double)gmy;
-                lacc[5] += (double)(dx * gmy - dy * gmx);
+                lacc[0] += cmx;
+                lacc[1] += cmy;
+                lacc[2] += dx * cmy - dy * cmx;
+                lacc[3] += gmx;
+                lacc[4] += gmy;
+                lacc[5] += dx * gmy - dy * gmx;
             }
         },
         wi, nw);
 #pragma unroll
-    for (int q = 0; q < 6; q++) acc[q] = lacc[q];
+    for (int q = 0; q < 6; q++) acc[q] = (double)lacc[q];
     warp_sum(acc);
 }
 
@@ -496,13 +582,16 @@ __device__ void record_forces(const StepParams &p, int s, int lane, long long t,
 
 // One warp per solid (see the top of the file).
 template <int P, bool LOCAL, bool BND>
-__global__ void __launch_bounds__(SW_BLOCK) k_forces(const StepParams p) {
+__global__ void __launch_bounds__(SW_BLOCK, 2) k_forces(const StepParams p) {
     __shared__ float disp[WARPS];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int gw = blockIdx.x * WARPS + wib, nw = gridDim.x * WARPS;
     float dmax = 0.f;  // lane 0: the largest displacement of this warp's solids
     const long long t = *p.t;
     const void *fcur = (t & 1) ? p.f1 : p.f0;  // populations of time t
+    // the near lists hold at t unless a solid was added or changed since the
+    // last pair test
+    const bool lists_ok = p.near_id && ((volatile unsigned int *)p.bar)[3] == 0u;
     // the previous step's events are reached through the solids' segments;
     // the list fills again in this step's re-rasterisation
     if (gw == 0 && lane == 0 && p.ev_len) *p.ev_len = 0;
@@ -513,16 +602,20 @@ __global__ void __launch_bounds__(SW_BLOCK) k_forces(const StepParams p) {
             continue;
         }
         double acc[6];
-        forces_sum<P, LOCAL, BND>(p, s, lane, fcur, 0, 1, acc);
+        forces_sum<P, LOCAL, BND>(p, s, lane, fcur, 0, 1, lists_ok, acc);
         double booked[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
         if (lane == 0 && b.ev_t == t)
             for (int e = b.ev_off; e < b.ev_off + b.ev_n; e++)
                 for (int q = 0; q < 6; q++) booked[q] += p.ev_mom[6 * e + q];
         record_forces(p, s, lane, t, acc, booked);
         if (lane == 0) {
-            // distance from the centre at the last pair test, at t and t+1
-            const double d0 = hypot(b.x - b.tx, b.y - b.ty), d1 = hypot(b.xn - b.tx, b.yn - b.ty);
-            dmax = fmaxf(dmax, __double2float_ru(fmax(d0, d1)));
+            // distance from the centre at the last pair test, at t and t+1 (FP32
+            // from the split centres, with a slack above its rounding)
+            const float d0 = hypotf((float)(b.ix0 - b.ixt) + (b.fx0 - b.fxt),
+                                    (float)(b.iy0 - b.iyt) + (b.fy0 - b.fyt));
+            const float d1 = hypotf((float)(b.ix1 - b.ixt) + (b.fx1 - b.fxt),
+                                    (float)(b.iy1 - b.iyt) + (b.fy1 - b.fyt));
+            dmax = fmaxf(dmax, fmaxf(d0, d1) + 1e-3f);
         }
     }
     if (lane == 0) disp[wib] = dmax;
@@ -540,8 +633,9 @@ __global__ void __launch_bounds__(SW_BLOCK) k_forces(const StepParams p) {
 // (whole blocks call it; base + warp index may be >= nmoving).  The centres
 // at t and t+1 of every solid are staged in shared memory one tile at a time.
 // FP32 distances with a slack far above their rounding.
-constexpr int NEAR_TILE = 1024;
-__device__ void phase_pairs_block(const StepParams &p, int base, float4 *pos, float *rad) {
+constexpr int NEAR_TILE = 512;
+__device__ void phase_pairs_block(const StepParams &p, int base, int4 *ipos, float4 *fpos,
+                                  float *rad) {
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int m = base + wib;
     const bool mine = m < p.nmoving;
@@ -549,14 +643,14 @@ __device__ void phase_pairs_block(const StepParams &p, int base, float4 *pos, fl
     const Lattice &L = p.L;
     const bool px = L.bc_x == LBM_PERIODIC, py = L.bc_y == LBM_PERIODIC;
     const float nxf = (float)L.nx, nyf = (float)L.ny;
-    float rb = 0.f, bx = 0.f, by = 0.f, bxn = 0.f, byn = 0.f;
+    int4 bi = make_int4(0, 0, 0, 0);
+    float4 bf = make_float4(0.f, 0.f, 0.f, 0.f);
+    float rb = 0.f;
     if (mine) {
         const DSolid &b = p.S[s];
-        rb = (float)b.r;
-        bx = b.xf;
-        by = b.yf;
-        bxn = b.xnf;
-        byn = b.ynf;
+        rb = sqrtf(b.r2f);
+        bi = make_int4(b.ix0, b.iy0, b.ix1, b.iy1);
+        bf = make_float4(b.fx0, b.fy0, b.fx1, b.fy1);
     }
     uint16_t *out = mine ? p.near_id + (long long)s * NEAR_CAP : nullptr;
     int cnt = 0;
@@ -565,8 +659,9 @@ __device__ void phase_pairs_block(const StepParams &p, int base, float4 *pos, fl
         __syncthreads();
         for (int q = threadIdx.x; q < n; q += blockDim.x) {
             const DSolid &B = p.S[t0 + q];
-            pos[q] = make_float4(B.xf, B.yf, B.xnf, B.ynf);
-            rad[q] = (float)B.r;
+            ipos[q] = make_int4(B.ix0, B.iy0, B.ix1, B.iy1);
+            fpos[q] = make_float4(B.fx0, B.fy0, B.fx1, B.fy1);
+            rad[q] = sqrtf(B.r2f);
         }
         __syncthreads();
         if (!mine) continue;
@@ -574,9 +669,13 @@ __device__ void phase_pairs_block(const StepParams &p, int base, float4 *pos, fl
             const int q = q0 + lane;
             bool hit = false;
             if (q < n && t0 + q != s) {
-                const float4 c = pos[q];
+                const int4 ci = ipos[q];
+                const float4 cf = fpos[q];
                 const float lim = rb + rad[q] + NEAR_REACH + NEAR_MARGIN + 0.05f;
-                float dx = bx - c.x, dy = by - c.y, ex = bxn - c.z, ey = byn - c.w;
+                float dx = (float)(bi.x - ci.x) + (bf.x - cf.x);
+                float dy = (float)(bi.y - ci.y) + (bf.y - cf.y);
+                float ex = (float)(bi.z - ci.z) + (bf.z - cf.z);
+                float ey = (float)(bi.w - ci.w) + (bf.w - cf.w);
                 if (px) {
                     dx -= nxf * rintf(dx / nxf);
                     ex -= nxf * rintf(ex / nxf);
@@ -603,9 +702,11 @@ __device__ void phase_pairs_block(const StepParams &p, int base, float4 *pos, fl
 // rasterisation of the disk decides it.
 __device__ __forceinline__ bool inside_at(const Lattice &L, int x, int y, double X, double Y,
                                           double r) {
+    // the image shift in FP32: it only has to be right for nodes within r + 1
+    // of the centre, far from the half-period where it could round either way
     int i = x, j = y;
-    if (L.bc_x == LBM_PERIODIC) i += L.nx * (int)floor((X - (double)x) / (double)L.nx + 0.5);
-    if (L.bc_y == LBM_PERIODIC) j += L.ny * (int)floor((Y - (double)y) / (double)L.ny + 0.5);
+    if (L.bc_x == LBM_PERIODIC) i += L.nx * (int)rintf((float)(X - (double)x) / (float)L.nx);
+    if (L.bc_y == LBM_PERIODIC) j += L.ny * (int)rintf((float)(Y - (double)y) / (float)L.ny);
     const float dx = (float)((double)i - X), dy = (float)((double)j - Y), rr = (float)r + 1.0f;
     if (dx * dx + dy * dy > rr * rr) return false;
     return inside_disk(i, j, X, Y, r);
@@ -629,11 +730,10 @@ __device__ void near_owners(const StepParams &p, const DSolid &b, int s, int x, 
     }
 }
 
-// Was the domain node (x, y) inside a solid at t?  Only solid s (a solid
-// with an event this step) and its near list can have held it, for a node
-// within NEAR_REACH of s's surface.  Centres at t: xo, yo (phase E).
-__device__ bool solid_at_t(const StepParams &p, const DSolid &b, int s, int x, int y) {
-    if (inside_at(p.L, x, y, b.xo, b.yo, b.r)) return true;
+// Was the domain node (x, y) inside a solid of s's near list at t?  Only
+// those (and s itself, tested by the caller) can have held a node within
+// NEAR_REACH of s's surface.  Centres at t: xo, yo (phase E).
+__device__ bool near_at_t(const StepParams &p, const DSolid &b, int s, int x, int y) {
     const int nn = b.near_n;
     if (nn == 0) return false;
     const uint16_t *nl = p.near_id + (long long)s * NEAR_CAP;
@@ -652,30 +752,35 @@ constexpr int EVENTS = SOLID_EVENTS;
 // Ring of solid s (phase R): owner and flags of every node whose owner
 // changes, and the covered and fresh nodes of s, queued per warp in lane
 // order and published as the solid's segment of the step's event list (to be
-// booked into the force record of t+1).  No memory is read per node: the
-// owners come from the geometry.
-__device__ void phase_ring(const StepParams &p, int s, int lane, long long t, int *queue,
+// booked into the force record of t+1), each with its unwrapped coordinates
+// in the solid's frame.  No memory is read per node: the owners come from the
+// geometry.
+__device__ void phase_ring(const StepParams &p, int s, int lane, long long t, int2 *queue,
                            int &qn) {
     DSolid &b = p.S[s];
     const Lattice &L = p.L;
-    const DiskTest in0(b.x, b.y, b.r), in1(b.xn, b.yn, b.r);
-    const Centre c0(b.x, b.y), c1(b.xn, b.yn);
-    const float rr = (float)b.r + 0.01f;
+    const DiskTest in0(b.x, b.y, b.r, b.ix0, b.iy0, b.fx0, b.fy0, b.r2f, b.rmf);
+    const DiskTest in1(b.xn, b.yn, b.r, b.ix1, b.iy1, b.fx1, b.fy1, b.r2f, b.rmf);
+    const Centre c0(b.ix0, b.iy0, b.fx0, b.fy0), c1(b.ix1, b.iy1, b.fx1, b.fy1);
+    const Wrap wrap(L, b.ix0, b.iy0, b.rc);
+    const float rf = sqrtf(b.r2f);
     int j0, j1;
-    rows_of(b.y, b.yn, b.r, 1, j0, j1);
+    rows_of_i(b.iy0, b.iy1, b.rc, 1, j0, j1);
     if (lane == 0) qn = 0;
     __syncwarp();
     constexpr int UR = 2;  // nothing is loaded per node: a short batch suffices
-    int kk[UR];
+    int kk[UR], iu[UR], ju[UR];
     bool w0[UR];  // on the ring the node is inside s at t (true) or at t+1 (false)
     warp_nodes_n<UR>(
-        j0, j1, lane, [&](int j, Ranges &R) { return ring_ranges(c0, c1, rr, j, R); },
+        j0, j1, lane, [&](int j, Ranges &R) { return ring_ranges(c0, c1, rf, j, R); },
         [&](int i, int j, int u) {
             const bool a = in0(i, j);
             if (a == in1(i, j)) return false;
             int x, y;
-            if (!locate(L, i, j, x, y)) return false;
+            if (!wrap(i, j, x, y)) return false;
             kk[u] = (int)cell_of(L, x, y);
+            iu[u] = i;
+            ju[u] = j;
             w0[u] = a;
             return true;
         },
@@ -695,7 +800,7 @@ __device__ void phase_ring(const StepParams &p, int s, int lane, long long t, in
 #pragma unroll
                         for (int d = 1; d < 9; d++) {
                             int xn, yn;
-                            if (locate(L, x + cx(d), y + cy(d), xn, yn))
+                            if (wrap(iu[u] + cx(d), ju[u] + cy(d), xn, yn))
                                 flag_bit(p.flags, cell_of(L, xn, yn), d, sn);
                         }
                     }
@@ -712,7 +817,12 @@ __device__ void phase_ring(const StepParams &p, int s, int lane, long long t, in
             if (lane == 0) qn = base + __popc(want);
             if (covered || fresh) {
                 const int pos = base + __popc(want & ((1u << lane) - 1u));
-                if (pos < EVENTS) queue[pos] = (k << 1) | (fresh ? 1 : 0);
+                // node code, and its unwrapped coordinates relative to floor(R)
+                if (pos < EVENTS)
+                    queue[pos] = make_int2(
+                        (k << 1) | (fresh ? 1 : 0),
+                        (int)((unsigned)(iu[u] - c0.xi + 32768) |
+                              ((unsigned)(ju[u] - c0.yi + 32768) << 16)));
                 else atomicOr(p.status, 8);
             }
             __syncwarp();
@@ -725,7 +835,12 @@ __device__ void phase_ring(const StepParams &p, int s, int lane, long long t, in
     off = __shfl_sync(FULL, off, 0);
     const bool fits = off + n <= p.ev_cap;
     for (int e = lane; e < n; e += 32) {
-        if (fits) p.ev[off + e] = make_int2(queue[e], s);
+        if (fits) {
+            const int2 q = queue[e];
+            const unsigned d = (unsigned)q.y;
+            p.ev[off + e] = make_int4(q.x, s, c0.xi + (int)(d & 0xFFFFu) - 32768,
+                                      c0.yi + (int)(d >> 16) - 32768);
+        }
     }
     if (lane == 0) {
         if (!fits) atomicOr(p.status, 8);
@@ -734,6 +849,10 @@ __device__ void phase_ring(const StepParams &p, int s, int lane, long long t, in
         b.ev_t = t + 1;
         b.xo = b.x;
         b.yo = b.y;
+        b.ixo = b.ix0;
+        b.iyo = b.iy0;
+        b.fxo = b.fx0;
+        b.fyo = b.fy0;
     }
     __syncwarp();
 }
@@ -751,21 +870,27 @@ __device__ void phase_event(const StepParams &p, int e, int lane, void *fnew) {
     const Lattice &L = p.L;
     const S *fsn = static_cast<const S *>(fnew);
     const int pl = (int)L.plane;
-    const int2 ev = p.ev[e];
-    const int code = ev.x;
-    const DSolid &b = p.S[ev.y];
+    const int4 ev = p.ev[e];
+    const int code = ev.x, s = ev.y;
+    const DSolid &b = p.S[s];
     double acc[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
     {
         const int k = code >> 1;
         const int x = k % L.pitch, y = k / L.pitch;
         if (code & 1) {
-            // fresh: refill (Sec. IV.B).  Lane 3(i-1)+(d-1) tests x + d e_i.
+            // fresh: refill (Sec. IV.B).  Lane 3(i-1)+(d-1) tests x + d e_i: a
+            // node fluid at t+1 (owner map) that no solid held at t (the
+            // solid's own disk at t in its frame, and its near list)
             bool use = false;
             if (lane < 24) {
                 const int i = lane / 3 + 1, d = lane % 3 + 1;
                 const int kp = neighbour(L, x, y, d * cx(i), d * cy(i));
-                use = kp >= 0 && p.owner[kp] == FLUID &&
-                      !solid_at_t(p, b, ev.y, kp % L.pitch, kp / L.pitch);
+                if (kp >= 0 && p.owner[kp] == FLUID) {
+                    const DiskTest old(b.xo, b.yo, b.r, b.ixo, b.iyo, b.fxo, b.fyo, b.r2f,
+                                       b.rmf);
+                    use = !old(ev.z + d * cx(i), ev.w + d * cy(i)) &&
+                          !near_at_t(p, b, s, kp % L.pitch, kp / L.pitch);
+                }
             }
             const unsigned um = __ballot_sync(FULL, use);
             unsigned d3 = 0, d2 = 0, d1 = 0;  // directions old-fluid up to distance 3, 2, 1
@@ -819,26 +944,36 @@ __device__ void phase_event(const StepParams &p, int e, int lane, void *fnew) {
             }
             __syncwarp();
         }
-        // momentum and mass of the node (post-collision if covered, refilled if fresh)
-        double jm[3] = {0.0, 0.0, 0.0};
+        // momentum and mass of the node (post-collision if covered, refilled if
+        // fresh), summed in the arithmetic precision of the storage mode
+        C jm[3] = {0, 0, 0};
         if (lane < 9) {
-            const double v = f64<P>(fnew, L.plane, lane, k);
-            jm[0] = cx(lane) * v;
-            jm[1] = cy(lane) * v;
+            C v = (C)ldc(fsn + lane * pl + k);
+            if (Prec<P>::dev) v += wgt<C>(lane);
+            jm[0] = (C)cx(lane) * v;
+            jm[1] = (C)cy(lane) * v;
             jm[2] = v;
         }
         warp_sum(jm);
         if (lane == 0) {
             const double sgn = (code & 1) ? -1.0 : 1.0;  // fresh: from the solid; covered: to it
+            const double mx = (double)jm[0], my = (double)jm[1], mm = (double)jm[2];
             double ux, uy, dx, dy;
-            point_velocity(L, b.xn, b.yn, b.vxn, b.vyn, b.omn, (double)x, (double)y, ux, uy, dx,
-                           dy);
-            acc[0] += sgn * jm[0];
-            acc[1] += sgn * jm[1];
-            acc[2] += sgn * (dx * jm[1] - dy * jm[0]);
+            if (P == LBM_FP64) {  // from the domain node at the nearest periodic image
+                point_velocity(L, b.xn, b.yn, b.vxn, b.vyn, b.omn, (double)x, (double)y, ux, uy,
+                               dx, dy);
+            } else {  // the node's unwrapped coordinates are in the centre's frame
+                dx = (double)ev.z - b.xn;
+                dy = (double)ev.w - b.yn;
+                ux = b.vxn - b.omn * dy;
+                uy = b.vyn + b.omn * dx;
+            }
+            acc[0] += sgn * mx;
+            acc[1] += sgn * my;
+            acc[2] += sgn * (dx * my - dy * mx);
             // the Eq. 5 record's booking: the same, or relative to the boundary, m (u - v)
-            const double rx = p.relative_changes ? jm[0] - jm[2] * ux : jm[0];
-            const double ry = p.relative_changes ? jm[1] - jm[2] * uy : jm[1];
+            const double rx = p.relative_changes ? mx - mm * ux : mx;
+            const double ry = p.relative_changes ? my - mm * uy : my;
             acc[3] += sgn * rx;
             acc[4] += sgn * ry;
             acc[5] += sgn * (dx * ry - dy * rx);
@@ -851,16 +986,19 @@ __device__ void phase_event(const StepParams &p, int e, int lane, void *fnew) {
 
 // The state of a moving solid becomes that of t+1 (xo, yo keep R(t) for the
 // events of the step).
-__device__ __forceinline__ void advance_solid(DSolid &b) {
+__device__ __forceinline__ void advance_solid(const Lattice &L, DSolid &b) {
     b.x = b.xn;
     b.y = b.yn;
     b.xw = b.xnw;
     b.yw = b.ynw;
-    const double fxw = floor(b.xw), fyw = floor(b.yw);
-    b.xwi = (int)fxw;
-    b.ywi = (int)fyw;
-    b.xwr = (float)(b.xw - fxw);
-    b.ywr = (float)(b.yw - fyw);
+    b.ix0 = b.ix1;
+    b.iy0 = b.iy1;
+    b.fx0 = b.fx1;
+    b.fy0 = b.fy1;
+    b.xwi = L.bc_x == LBM_PERIODIC ? b.ix1 - L.nx * floor_div(b.ix1, L.nx) : b.ix1;
+    b.ywi = L.bc_y == LBM_PERIODIC ? b.iy1 - L.ny * floor_div(b.iy1, L.ny) : b.iy1;
+    b.xwr = b.fx1;
+    b.ywr = b.fy1;
     b.vx = b.vxn;
     b.vy = b.vyn;
     b.om = b.omn;
@@ -873,9 +1011,10 @@ __device__ __forceinline__ void advance_solid(DSolid &b) {
 
 template <int P>
 __global__ void __launch_bounds__(SW_BLOCK, 3) k_remask(const StepParams p) {
-    __shared__ int queue[WARPS][EVENTS];
+    __shared__ int2 queue[WARPS][EVENTS];
     __shared__ int qn[WARPS];
-    __shared__ float4 tile_pos[NEAR_TILE];
+    __shared__ int4 tile_ipos[NEAR_TILE];
+    __shared__ float4 tile_fpos[NEAR_TILE];
     __shared__ float tile_rad[NEAR_TILE];
     // a barrier of an earlier launch gave up: the state is not the method's
     // any more, and this launch does nothing (the host reports the time-out)
@@ -889,11 +1028,15 @@ __global__ void __launch_bounds__(SW_BLOCK, 3) k_remask(const StepParams p) {
     if (ctl[3] != 0u || __uint_as_float(ctl[2]) >= 0.5f * NEAR_MARGIN) {
         // P: near lists, and the centres they were taken at
         for (int base = blockIdx.x * WARPS; base < p.nmoving; base += nw)
-            phase_pairs_block(p, base, tile_pos, tile_rad);
+            phase_pairs_block(p, base, tile_ipos, tile_fpos, tile_rad);
         for (int s = gt; s < p.nsolid; s += nt) {
             DSolid &b = p.S[s];
-            b.tx = b.xo = b.x;
-            b.ty = b.yo = b.y;
+            b.xo = b.x;
+            b.yo = b.y;
+            b.ixt = b.ixo = b.ix0;
+            b.iyt = b.iyo = b.iy0;
+            b.fxt = b.fxo = b.fx0;
+            b.fyt = b.fyo = b.fy0;
         }
         if (!grid_sync(p)) return;
         if (gt == 0) {
@@ -912,7 +1055,7 @@ __global__ void __launch_bounds__(SW_BLOCK, 3) k_remask(const StepParams p) {
     // E: the step's covered and fresh nodes, dealt to every warp of the grid
     const int nev = min(*(volatile int *)p.ev_len, p.ev_cap);
     for (int e = gw; e < nev; e += nw) phase_event<P>(p, e, lane, fnew);
-    for (int m = gt; m < p.nmoving; m += nt) advance_solid(p.S[p.moving[m]]);
+    for (int m = gt; m < p.nmoving; m += nt) advance_solid(p.L, p.S[p.moving[m]]);
 }
 
 template <int P, bool LOCAL, bool BND>
@@ -945,11 +1088,9 @@ cudaError_t launch_r(const StepParams &p, cudaStream_t st) {
             e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_remask<P>, SW_BLOCK, 0);
         if (e != cudaSuccess) return e;
     }
-    // one warp per moving solid for phase R, and at least one block per SM
-    // for the events
-    int blocks = (p.nmoving + WARPS - 1) / WARPS;
-    if (blocks < sms) blocks = sms;
-    if (blocks > per_sm * sms) blocks = per_sm * sms;
+    // every resident block: phase R takes one warp per moving solid, the
+    // events go to every warp
+    int blocks = per_sm * sms;
     if (blocks < 1) blocks = 1;
     StepParams pp = p;
     void *args[] = {&pp};
@@ -985,7 +1126,7 @@ __global__ void __launch_bounds__(SW_BLOCK)
             continue;
         }
         double acc[6];
-        forces_sum<P, LOCAL, false>(p, it.y, lane, fcur, wib, WARPS, acc);
+        forces_sum<P, LOCAL, false>(p, it.y, lane, fcur, wib, WARPS, false, acc);
         if (lane == 0)
             for (int q = 0; q < 6; q++) part[wib][q] = acc[q];
         __syncthreads();

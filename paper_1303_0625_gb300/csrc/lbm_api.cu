@@ -29,7 +29,7 @@ struct lbm_ctx {
     int nsolid = 0;
     int *moving_d = nullptr;
     int moving_cap = 0;
-    void *ev_d = nullptr;  // covered/fresh events: {length, pad}, int2 list, 3 doubles each
+    void *ev_d = nullptr;  // covered/fresh events: {length, pad}, int4 list, 6 doubles each
     int ev_cap = 0;
     int *bnd_d = nullptr;  // deferred per-node path: {length by step parity, list}
     int bnd_cap = 0;
@@ -141,9 +141,9 @@ StepParams params(const lbm_ctx *c) {
     p.bnd = c->bnd_d;
     p.bnd_cap = c->bnd_cap;
     p.ev_len = static_cast<int *>(c->ev_d);
-    p.ev = c->ev_d ? reinterpret_cast<int2 *>(static_cast<char *>(c->ev_d) + 16) : nullptr;
+    p.ev = c->ev_d ? reinterpret_cast<int4 *>(static_cast<char *>(c->ev_d) + 16) : nullptr;
     p.ev_mom = c->ev_d ? reinterpret_cast<double *>(static_cast<char *>(c->ev_d) + 16 +
-                                                    (size_t)c->ev_cap * sizeof(int2))
+                                                    (size_t)c->ev_cap * sizeof(int4))
                        : nullptr;
     p.ev_cap = c->ev_cap;
     p.omega_f = (float)(1.0 / g.tau);
@@ -191,6 +191,18 @@ lbm_status ensure_scratch(lbm_ctx *c, size_t bytes) {
 
 bool translates(const DSolid &s) { return s.motion == LBM_FREE || s.vx != 0.0 || s.vy != 0.0; }
 
+// Split centres of a solid at rest between steps (R(t) = R(t+1)): at t, at
+// t+1, the copy kept through the re-rasterisation and the pair test's
+// reference.
+void split_centres(DSolid &s) {
+    gbm::split_coord(s.x, s.ix0, s.fx0);
+    gbm::split_coord(s.y, s.iy0, s.fy0);
+    s.ix1 = s.ixo = s.ixt = s.ix0;
+    s.iy1 = s.iyo = s.iyt = s.iy0;
+    s.fx1 = s.fxo = s.fxt = s.fx0;
+    s.fy1 = s.fyo = s.fyt = s.fy0;
+}
+
 lbm_status upload_moving(lbm_ctx *c) {
     c->moving.clear();
     for (int s = 0; s < c->nsolid; s++)
@@ -217,7 +229,7 @@ lbm_status upload_moving(lbm_ctx *c) {
         if (c->ev_d) CK(c, cudaFree(c->ev_d));
         c->ev_d = nullptr;
         c->ev_cap = 0;
-        CK(c, cudaMalloc(&c->ev_d, 16 + (size_t)cap * (sizeof(int2) + 6 * sizeof(double))));
+        CK(c, cudaMalloc(&c->ev_d, 16 + (size_t)cap * (sizeof(int4) + 6 * sizeof(double))));
         CK(c, cudaMemsetAsync(c->ev_d, 0, 16, c->stream));
         c->ev_cap = (int)cap;
     }
@@ -472,8 +484,12 @@ lbm_status lbm_add_solid(lbm_ctx *c, const lbm_disk *d, int32_t *id_out) {
     s.r = d->r;
     s.rho_s = d->rho_s;
     s.ta = c->t;
-    s.xo = s.tx = s.x;
-    s.yo = s.ty = s.y;
+    s.xo = s.x;
+    s.yo = s.y;
+    split_centres(s);
+    s.rc = (int)std::ceil(d->r);
+    s.r2f = (float)(d->r * d->r);
+    s.rmf = 1e-5f * s.r2f + 1e-5f;
     s.ev_t = -1;
     s.near_n = -1;  // until the next pair test: every solid is a neighbour
     s.vxf = (float)d->vx;
@@ -701,7 +717,7 @@ int64_t state_bytes(const lbm_ctx *c, int ev_len) {
     return (int64_t)(sizeof(StateHeader) + 9 * plane * c->elem + 2 * plane * sizeof(uint16_t) +
                      (size_t)c->nsolid * sizeof(DSolid) +
                      (size_t)(c->cfg.force_ring + 1) * 2 * c->nsolid * 3 * sizeof(double) +
-                     (size_t)ev_len * (sizeof(int2) + 6 * sizeof(double)) + (size_t)c->nsolid);
+                     (size_t)ev_len * (sizeof(int4) + 6 * sizeof(double)) + (size_t)c->nsolid);
 }
 
 // The device arrays of a state, laid out after the header at base.
@@ -719,7 +735,7 @@ std::vector<Part> state_parts(lbm_ctx *c, char *base, int ev_len) {
     add(c->flags, plane * sizeof(uint16_t));
     add(c->solids, (size_t)c->nsolid * sizeof(DSolid));
     add(c->ring, (size_t)(c->cfg.force_ring + 1) * 2 * c->nsolid * 3 * sizeof(double));
-    add(p.ev, (size_t)ev_len * sizeof(int2));
+    add(p.ev, (size_t)ev_len * sizeof(int4));
     add(p.ev_mom, (size_t)ev_len * 6 * sizeof(double));
     return v;
 }
@@ -927,6 +943,7 @@ lbm_status lbm_set_solid(lbm_ctx *c, int32_t id, const double *state) {
         return fail(c, LBM_EINVAL, "lbm_set_solid changes velocities only; position must match");
     s.xa = s.xn = s.xo = s.x;
     s.ya = s.yn = s.yo = s.y;
+    split_centres(s);
     s.ta = c->t;
     s.vx = s.vxn = state[2];
     s.vy = s.vyn = state[3];

@@ -45,7 +45,6 @@ struct DSolid {
     double r, rho_s;
     double xo, yo;     // R(t) kept through the re-rasterisation (R(t) itself becomes R(t+1)
                        // there); equal to x, y between steps
-    double tx, ty;     // centre at the last pair test
     long long ev_t;    // record (time) into which the segment ev_off, ev_n books its momenta
     long long ta;      // time when added
     float vxf, vyf, omf;  // FP32 copies of vx, vy, om for the FP32 kernels
@@ -55,7 +54,22 @@ struct DSolid {
     int motion;
     int near_n;        // entries of the solid's near list (-1: too many; every solid is tested)
     int ev_off, ev_n;  // the solid's segment of the covered/fresh event list
+    // Centres split into floor() and the FP32 remainder, for FP32 geometry
+    // without FP64 arithmetic in the per-solid kernels: R(t), R(t+1), R(t) kept
+    // through the re-rasterisation (as xo, yo), and the centre at the last
+    // pair test.
+    int ix0, iy0, ix1, iy1, ixo, iyo, ixt, iyt;
+    float fx0, fy0, fx1, fy1, fxo, fyo, fxt, fyt;
+    int rc;            // ceil(r)
+    float r2f, rmf;    // (float)(r * r) and the exact test's band, 1e-5 r^2 + 1e-5
 };
+
+// floor(X) and the FP32 remainder X - floor(X) (host and device).
+__host__ __device__ inline void split_coord(double X, int &i, float &f) {
+    const double a = floor(X);
+    i = (int)a;
+    f = (float)(X - a);
+}
 
 // Near list: the solids that can own a node within NEAR_REACH (lattice
 // units) of a disk's surface at t or t+1 are those whose centres are closer
@@ -108,7 +122,8 @@ struct StepParams {
                               // test requested
     long long spin_limit;     // polls of a bounded device wait (0: give up at once)
     uint16_t *near_id;        // [nsolid][NEAR_CAP] near lists
-    int2 *ev;                 // covered/fresh events of the step: {node code, solid}
+    int4 *ev;                 // covered/fresh events of the step: {node code (cell << 1 |
+                              // fresh), solid, unwrapped x, y in the solid's frame}
     double *ev_mom;           // [6] momentum and torque of each event: Eq. 4, Eq. 5 booking
     int *ev_len;              // events published this step (cleared after use)
     int ev_cap;
@@ -191,8 +206,9 @@ __device__ __forceinline__ Box disk_box(double X, double Y, double r, int g) {
 // A solid whose centre is not finite (or absurdly far away) would give a
 // meaningless box; per-solid kernels skip it and raise status bit 1.
 __device__ __forceinline__ bool solid_ok(const DSolid &b) {
-    return fabs(b.x) < 1e9 && fabs(b.y) < 1e9 && fabs(b.xn) < 1e9 && fabs(b.yn) < 1e9 &&
-           b.r > 0.0 && b.r < 1e6;
+    // the FP32 copies of the centres (a NaN fails every comparison)
+    return fabsf(b.xf) < 1e9f && fabsf(b.yf) < 1e9f && fabsf(b.xnf) < 1e9f &&
+           fabsf(b.ynf) < 1e9f && b.r2f > 0.f && b.r2f < 1e12f;
 }
 
 __device__ __forceinline__ Box box_union(Box a, Box b) {
@@ -253,6 +269,10 @@ struct DiskTest {
     double X, Y, r;
     int xi, yi;
     float fx, fy, r2, margin;
+    // from a centre already split (split_coord) and the solid's r2f, rmf
+    __device__ __forceinline__ DiskTest(double X_, double Y_, double r_, int xi_, int yi_,
+                                        float fx_, float fy_, float r2_, float margin_)
+        : X(X_), Y(Y_), r(r_), xi(xi_), yi(yi_), fx(fx_), fy(fy_), r2(r2_), margin(margin_) {}
     __device__ __forceinline__ DiskTest(double X_, double Y_, double r_) : X(X_), Y(Y_), r(r_) {
         const double fxd = floor(X), fyd = floor(Y);
         xi = (int)fxd;
