@@ -87,6 +87,16 @@ lbm_status lbm_unet_train_step(lbm_unet *net, const float *in, const float *targ
 lbm_status lbm_unet_input(lbm_unet *net, const int32_t *owner_device, double reynolds,
                           float *in_device);
 
+/* Network input of the case held by ctx (the warm start's learned part; the
+ * paper has no counterpart), [8][ny][nx] device floats at in_device, from its
+ * solid table and Reynolds number: 0 the solid mask, 1 Re / 100,
+ * 2 log10(Re) / 2, 3 the signed distance to the nearest disk surface / 16
+ * (clipped to [-1, 4]), 4 the axial distance from that disk's centre in its
+ * radii / 8 (clipped to [-1, 4], positive downstream), 5 the channel's
+ * parabola 4 y'(ny - y') / ny^2 with y' = y + 1/2, 6 x / nx, 7 y' / ny - 1/2.
+ * Enqueued on the context's stream.  LBM_EINVAL for Re <= 0. */
+lbm_status lbm_case_input(lbm_ctx *ctx, double reynolds, float *in_device);
+
 /* Initial state of ctx from a network output [3][H][W] (device floats):
  * at every fluid node f = f^eq(rho, u) (Eq. 8) with
  *   rho = 1 + rho_scale p0, u = u_scale (p1, p2)                      (base 0)

@@ -282,18 +282,26 @@ __device__ __forceinline__ void rows_of(double Y0, double Y1, double r, int g, i
 // Deals the nodes of rows j0..j1 (the ranges that rng(j, R) gives for each
 // row) to the lanes of the warp, U nodes per lane at a time: fetch(i, j, u)
 // is called for all U nodes of a lane first (to issue their loads together),
-// then process(u, ok) for each, on every lane of the warp together (ok is
-// false for items past the end and for nodes fetch rejected).  With nw > 1
-// warps sharing the rows, this warp (wi) takes the 32-row blocks wi, wi + nw ...
-template <int NB, class RF, class FF, class PF>
+// then mid(ok) once (loads that depend on what fetch loaded, for all U nodes
+// together), then process(u, ok) for each, on every lane of the warp together
+// (ok is false for items past the end and for nodes fetch rejected).  Rows come in
+// blocks of RB <= 32 (lane l < RB takes row l of a block); with nw > 1 warps
+// sharing the rows, this warp (wi) takes the blocks wi, wi + nw ...
+struct NoMid {
+    template <int NB>
+    __device__ __forceinline__ void operator()(const bool (&)[NB]) const {}
+};
+
+template <int NB, int RB = 32, class RF, class FF, class PF, class MF = NoMid>
 __device__ __forceinline__ void warp_nodes_n(int j0, int j1, int lane, RF &&rng, FF &&fetch,
-                                             PF &&process, int wi = 0, int nw = 1) {
-    for (int jb = j0 + 32 * wi; jb <= j1; jb += 32 * nw) {
+                                             PF &&process, int wi = 0, int nw = 1,
+                                             MF &&mid = MF()) {
+    for (int jb = j0 + RB * wi; jb <= j1; jb += RB * nw) {
         const int j = jb + lane;
         Ranges R;
         R.a0 = R.a1 = 0;
         int n0 = 0, n1 = 0;
-        if (j <= j1 && rng(j, R)) {
+        if (lane < RB && j <= j1 && rng(j, R)) {
             n0 = R.b0 >= R.a0 ? R.b0 - R.a0 + 1 : 0;
             n1 = R.b1 >= R.a1 ? R.b1 - R.a1 + 1 : 0;
         }
@@ -324,6 +332,7 @@ __device__ __forceinline__ void warp_nodes_n(int j0, int j1, int lane, RF &&rng,
                 const int i = tt < qn0 ? qa0 + tt : qa1 + (tt - qn0);
                 ok[u] = e < total && fetch(i, jb + q, u);
             }
+            mid(ok);
 #pragma unroll
             for (int u = 0; u < NB; u++) process(u, ok[u]);
         }
@@ -439,7 +448,11 @@ __device__ void forces_sum(const StepParams &p, int s, int lane, const void *f, 
                            bool lists_ok, double (&acc)[6]) {
     using C = typename Prec<P>::C;
     using S = typename Prec<P>::S;
-    constexpr int UF = sizeof(S) == 8 ? 2 : 4;  // candidates a lane fetches at once
+    constexpr int UF = 2;  // candidates a lane takes at once
+    // with rho_w = rho0 and the half-way boundary a link needs only f_i of its
+    // own direction: the flags come first and only the bounced directions'
+    // populations (and owners) are read; otherwise all nine with the flags
+    constexpr bool SPARSE = !LOCAL && !BND;
     const DSolid &b = p.S[s];
     const Lattice &L = p.L;
     const S *fs = static_cast<const S *>(f);
@@ -448,18 +461,26 @@ __device__ void forces_sum(const StepParams &p, int s, int lane, const void *f, 
     const C vx = pick<C>(b.vx, b.vxf), vy = pick<C>(b.vy, b.vyf), om = pick<C>(b.om, b.omf);
     const C rho0 = pick<C>(p.rho0, p.rho0_f);
     const int plane = (int)L.plane;
-    const float r = (float)b.r;
+    const float r = sqrtf(b.r2f);
     const bool owners = !lists_ok || b.near_n != 0;
     const bool px = L.bc_x == LBM_PERIODIC, py = L.bc_y == LBM_PERIODIC;
     const Wrap wrap(L, b.ix0, b.iy0, b.rc);
     int j0, j1;
     rows_of_i(b.iy0, b.iy0, b.rc, 3, j0, j1);
     C lacc[6] = {0, 0, 0, 0, 0, 0};  // this lane's links
-    int ii[UF], jj[UF];
+    int ii[UF], jj[UF], kk[UF];
     uint16_t fl[UF];
     uint16_t own[UF][9];
     S fv[UF][9];
-    warp_nodes_n<UF>(
+    // is x_f + e_i (in the domain) a node of solid s?  own holds the owners
+    // when they were read; else the flag bit suffices (no other solid in reach)
+    auto linked = [&](int u, int i) -> bool {
+        if (!((fl[u] >> opp(i)) & 1u)) return false;  // x_f + e_i is not solid
+        if (owners) return own[u][i] == (uint16_t)s;
+        return (px || (unsigned)(ii[u] + cx(i)) < (unsigned)L.nx) &&
+               (py || (unsigned)(jj[u] + cy(i)) < (unsigned)L.ny);  // not beyond a wall
+    };
+    warp_nodes_n<UF, 16>(
         j0, j1, lane, [&](int j, Ranges &R) { return annulus_ranges(c, r, j, R); },
         [&](int iu, int j, int u) {
             int x, y;
@@ -467,14 +488,17 @@ __device__ void forces_sum(const StepParams &p, int s, int lane, const void *f, 
             const int k = (int)cell_of(L, x, y);
             ii[u] = iu;
             jj[u] = j;
+            kk[u] = k;
             fl[u] = p.flags[k];
+            if (!SPARSE) {
 #pragma unroll
-            for (int q = 0; q < 9; q++) fv[u][q] = fs[q * plane + k];
-            if (owners) {
+                for (int q = 0; q < 9; q++) fv[u][q] = fs[q * plane + k];
+                if (owners) {
 #pragma unroll
-                for (int i = 1; i < 9; i++) {
-                    const int kb = neighbour(L, x, y, cx(i), cy(i));
-                    own[u][i] = kb >= 0 ? p.owner[kb] : FLUID;
+                    for (int i = 1; i < 9; i++) {
+                        const int kb = neighbour(L, x, y, cx(i), cy(i));
+                        own[u][i] = kb >= 0 ? p.owner[kb] : FLUID;
+                    }
                 }
             }
             return true;
@@ -492,13 +516,7 @@ __device__ void forces_sum(const StepParams &p, int s, int lane, const void *f, 
             }
 #pragma unroll
             for (int i = 1; i < 9; i++) {
-                if (!((m >> opp(i)) & 1u)) continue;  // x_f + e_i is not solid
-                if (owners) {
-                    if (own[u][i] != (uint16_t)s) continue;
-                } else if ((!px && (unsigned)(iu + cx(i)) >= (unsigned)L.nx) ||
-                           (!py && (unsigned)(j + cy(i)) >= (unsigned)L.ny)) {
-                    continue;  // beyond a wall, not a solid
-                }
+                if (!linked(u, i)) continue;
                 C dx, dy, ux, uy, fbb;
                 C fi = (C)cvt_s(fv[u][i]);
                 if (Prec<P>::dev) fi += wgt<C>(i);
@@ -555,7 +573,27 @@ __device__ void forces_sum(const StepParams &p, int s, int lane, const void *f, 
                 lacc[5] += dx * gmy - dy * gmx;
             }
         },
-        wi, nw);
+        wi, nw,
+        [&](const bool (&ok)[UF]) {
+            if (!SPARSE) return;
+            // the bounced directions of every fluid candidate, for all of them together
+#pragma unroll
+            for (int u = 0; u < UF; u++) {
+                const uint16_t m = fl[u];
+                if (!ok[u] || (m & 1u) || !(m & 0x1FEu)) continue;
+                int x = 0, y = 0;
+                if (owners) wrap(ii[u], jj[u], x, y);
+#pragma unroll
+                for (int i = 1; i < 9; i++) {
+                    if (!((m >> opp(i)) & 1u)) continue;
+                    fv[u][i] = fs[i * plane + kk[u]];
+                    if (owners) {
+                        const int kb = neighbour(L, x, y, cx(i), cy(i));
+                        own[u][i] = kb >= 0 ? p.owner[kb] : FLUID;
+                    }
+                }
+            }
+        });
 #pragma unroll
     for (int q = 0; q < 6; q++) acc[q] = (double)lacc[q];
     warp_sum(acc);
@@ -580,51 +618,228 @@ __device__ void record_forces(const StepParams &p, int s, int lane, long long t,
     move_solid(p, s, lane, t, fg);
 }
 
-// One warp per solid (see the top of the file).
+// ------------------------------------------------- force kernel (block)
+
+// One block per solid: thread t takes the annulus candidates t, t + FB, ...
+// (a candidate node x_f can have a link into the disk when r - eps < |x_f - R|
+// <= r + sqrt 2 + eps: between the outer chord of each row and the inner one).
+// A candidate's flags are read first, then only the populations of its
+// bounced directions (all nine when rho_w is local or the boundary is
+// interpolated) and, unless the solid's near list is empty, the owners of
+// those directions.  Sums: per thread and over each warp's tree in the
+// arithmetic precision of the storage mode, then across the block's warps in
+// FP64, in warp order.  Warp 0 then records the force and moves the solid.
+constexpr int FB = 128;                  // threads per solid
+constexpr int FW = FB / 32;
+constexpr float ANN_EPS = 0.05f;         // above the FP32 rounding of a chord end
+
 template <int P, bool LOCAL, bool BND>
-__global__ void __launch_bounds__(SW_BLOCK, 2) k_forces(const StepParams p) {
-    __shared__ float disp[WARPS];
-    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    const int gw = blockIdx.x * WARPS + wib, nw = gridDim.x * WARPS;
-    float dmax = 0.f;  // lane 0: the largest displacement of this warp's solids
+__global__ void __launch_bounds__(FB, 6) k_forces(const StepParams p) {
+    using C = typename Prec<P>::C;
+    using S = typename Prec<P>::S;
+    constexpr bool SPARSE = !LOCAL && !BND;
+    __shared__ int s_cnt[FB];          // the chunk's rows: exclusive prefix of their candidates
+    __shared__ int s_lo[FB], s_i0[FB], s_i1[FB];  // row: [lo, hi] minus the inner chord [i0, i1]
+    __shared__ double s_part[FW][6];
+    __shared__ float s_disp;
+    const int tid = threadIdx.x, lane = tid & 31, wib = tid >> 5;
+    const Lattice &L = p.L;
     const long long t = *p.t;
-    const void *fcur = (t & 1) ? p.f1 : p.f0;  // populations of time t
+    const S *fs = static_cast<const S *>((t & 1) ? p.f1 : p.f0);  // populations of time t
+    const int plane = (int)L.plane;
+    const bool px = L.bc_x == LBM_PERIODIC, py = L.bc_y == LBM_PERIODIC;
     // the near lists hold at t unless a solid was added or changed since the
     // last pair test
     const bool lists_ok = p.near_id && ((volatile unsigned int *)p.bar)[3] == 0u;
     // the previous step's events are reached through the solids' segments;
     // the list fills again in this step's re-rasterisation
-    if (gw == 0 && lane == 0 && p.ev_len) *p.ev_len = 0;
-    for (int s = gw; s < p.nsolid; s += nw) {
+    if (blockIdx.x == 0 && tid == 0 && p.ev_len) *p.ev_len = 0;
+    if (tid == 0) s_disp = 0.f;
+    for (int s = blockIdx.x; s < p.nsolid; s += gridDim.x) {
         DSolid &b = p.S[s];
         if (!solid_ok(b)) {
-            if (lane == 0) atomicOr(p.status, 2);
+            if (tid == 0) atomicOr(p.status, 2);
             continue;
         }
-        double acc[6];
-        forces_sum<P, LOCAL, BND>(p, s, lane, fcur, 0, 1, lists_ok, acc);
-        double booked[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
-        if (lane == 0 && b.ev_t == t)
-            for (int e = b.ev_off; e < b.ev_off + b.ev_n; e++)
-                for (int q = 0; q < 6; q++) booked[q] += p.ev_mom[6 * e + q];
-        record_forces(p, s, lane, t, acc, booked);
-        if (lane == 0) {
-            // distance from the centre at the last pair test, at t and t+1 (FP32
-            // from the split centres, with a slack above its rounding)
-            const float d0 = hypotf((float)(b.ix0 - b.ixt) + (b.fx0 - b.fxt),
-                                    (float)(b.iy0 - b.iyt) + (b.fy0 - b.fyt));
-            const float d1 = hypotf((float)(b.ix1 - b.ixt) + (b.fx1 - b.fxt),
-                                    (float)(b.iy1 - b.iyt) + (b.fy1 - b.fyt));
-            dmax = fmaxf(dmax, fmaxf(d0, d1) + 1e-3f);
+        const Centre c(b.ix0, b.iy0, b.fx0, b.fy0);
+        const Wrap wrap(L, b.ix0, b.iy0, b.rc);
+        const float r = sqrtf(b.r2f);
+        const bool owners = !lists_ok || b.near_n != 0;
+        const C vx = pick<C>(b.vx, b.vxf), vy = pick<C>(b.vy, b.vyf), om = pick<C>(b.om, b.omf);
+        const C rho0 = pick<C>(p.rho0, p.rho0_f);
+        int j0, j1;
+        rows_of_i(b.iy0, b.iy0, b.rc, 3, j0, j1);
+        C lacc[6] = {0, 0, 0, 0, 0, 0};
+        for (int jc = j0; jc <= j1; jc += FB) {  // rows in chunks of FB
+            // candidates of row jc + tid
+            int lo = 1, hi = 0, i0 = 1, i1 = 0, n = 0;
+            const int j = jc + tid;
+            if (j <= j1 && c.chord(j, r + 1.4143f + ANN_EPS, lo, hi) && lo <= hi) {
+                n = hi - lo + 1;
+                if (c.chord(j, r - ANN_EPS, i0, i1) && i0 <= i1) n -= i1 - i0 + 1;
+            }
+            // exclusive prefix over the block
+            int inc = n;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int v = __shfl_up_sync(FULL, inc, o);
+                if (lane >= o) inc += v;
+            }
+            if (lane == 31) s_cnt[wib] = inc;
+            __syncthreads();
+            if (tid < 32) {
+                int w = tid < FW ? s_cnt[tid] : 0;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int v = __shfl_up_sync(FULL, w, o);
+                    if (lane >= o) w += v;
+                }
+                if (tid < FW) s_cnt[tid] = w;  // inclusive over warps
+            }
+            __syncthreads();
+            const int excl = (wib ? s_cnt[wib - 1] : 0) + inc - n;
+            const int total = s_cnt[FW - 1];
+            __syncthreads();
+            s_cnt[tid] = excl;
+            s_lo[tid] = lo;
+            s_i0[tid] = i0 <= i1 ? i0 : 1;  // an empty inner chord: i0 > i1
+            s_i1[tid] = i0 <= i1 ? i1 : 0;
+            __syncthreads();
+            // candidate e -> row (binary search over the prefix) and column
+            for (int e = tid; e < total; e += FB) {
+                int q = 0;
+#pragma unroll
+                for (int step = FB / 2; step > 0; step >>= 1)
+                    if (q + step < FB && s_cnt[q + step] <= e) q += step;
+                const int jj = jc + q;
+                int iu = s_lo[q] + (e - s_cnt[q]);
+                const int a = s_i0[q], bb = s_i1[q];
+                if (a <= bb && iu >= a) iu += bb - a + 1;  // step over the inner chord
+                int x, y;
+                if (!wrap(iu, jj, x, y)) continue;
+                const int k = (int)cell_of(L, x, y);
+                const uint16_t m = p.flags[k];
+                if ((m & 1u) || !(m & 0x1FEu)) continue;  // solid, or no bounced population
+                S fv[9];
+                uint16_t own[9];
+#pragma unroll
+                for (int i = 1; i < 9; i++) {
+                    const bool bounced = (m >> opp(i)) & 1u;  // x_f + e_i is solid
+                    if (!SPARSE || bounced) fv[i] = fs[i * plane + k];
+                    if (owners && bounced) {
+                        const int kb = neighbour(L, x, y, cx(i), cy(i));
+                        own[i] = kb >= 0 ? p.owner[kb] : FLUID;
+                    }
+                }
+                if (!SPARSE) fv[0] = fs[k];
+                C rho_w = rho0;
+                if (LOCAL) {
+                    C a9 = 0;
+#pragma unroll
+                    for (int q9 = 0; q9 < 9; q9++) a9 += (C)cvt_s(fv[q9]);
+                    rho_w = Prec<P>::dev ? (C)1 + a9 : a9;
+                }
+#pragma unroll
+                for (int i = 1; i < 9; i++) {
+                    if (!((m >> opp(i)) & 1u)) continue;  // x_f + e_i is not solid
+                    if (owners) {
+                        if (own[i] != (uint16_t)s) continue;
+                    } else if ((!px && (unsigned)(iu + cx(i)) >= (unsigned)L.nx) ||
+                               (!py && (unsigned)(jj + cy(i)) >= (unsigned)L.ny)) {
+                        continue;  // beyond a wall, not a solid
+                    }
+                    C dx, dy, ux, uy, fbb;
+                    C fi = (C)cvt_s(fv[i]);
+                    if (Prec<P>::dev) fi += wgt<C>(i);
+                    if (BND) {
+                        // the cut at fraction q of the link, and the population that
+                        // returns to x_f along e_opp by the fused kernel's
+                        // interpolation (full populations; M = 6 w rho_w (e_opp . v))
+                        const double qf = link_fraction(L, b, x, y, i);
+                        double vxd, vyd, ddx, ddy;
+                        point_velocity(L, b.x, b.y, b.vx, b.vy, b.om, (double)x + qf * cx(i),
+                                       (double)y + qf * cy(i), vxd, vyd, ddx, ddy);
+                        dx = (C)ddx;
+                        dy = (C)ddy;
+                        ux = (C)vxd;
+                        uy = (C)vyd;
+                        const C mw =
+                            -(C)6 * wgt<C>(i) * rho_w * ((C)cx(i) * ux + (C)cy(i) * uy);
+                        C fo = (C)cvt_s(fv[opp(i)]);
+                        if (Prec<P>::dev) fo += wgt<C>(i);
+                        if (qf >= 0.5) {
+                            fbb = (fi + mw) / (C)(2.0 * qf) +
+                                  (C)((2.0 * qf - 1.0) / (2.0 * qf)) * fo;
+                        } else if (!((m >> i) & 1u)) {  // x_f - e_i is a fluid node
+                            int xn, yn;
+                            locate(L, x - cx(i), y - cy(i), xn, yn);
+                            C fn = (C)cvt_s(fs[i * plane + (int)cell_of(L, xn, yn)]);
+                            if (Prec<P>::dev) fn += wgt<C>(i);
+                            fbb = (C)(2.0 * qf) * fi + (C)(1.0 - 2.0 * qf) * fn + mw;
+                        } else {
+                            fbb = fi + mw;
+                        }
+                    } else {
+                        // x_s = x_f + e_i / 2 relative to R, from the unwrapped coordinate
+                        if (Prec<P>::dev) {
+                            dx = (C)(iu - c.xi) + (C)(0.5f * cx(i)) - (C)c.fx;
+                            dy = (C)(jj - c.yi) + (C)(0.5f * cy(i)) - (C)c.fy;
+                        } else {
+                            dx = (C)(((double)iu + 0.5 * cx(i)) - b.x);
+                            dy = (C)(((double)jj + 0.5 * cy(i)) - b.y);
+                        }
+                        ux = vx - om * dy;
+                        uy = vy + om * dx;
+                        fbb = fi - (C)6 * wgt<C>(i) * rho_w * ((C)cx(i) * ux + (C)cy(i) * uy);
+                    }
+                    const C cmx = (C)cx(i) * fi - (C)cx(opp(i)) * fbb;
+                    const C cmy = (C)cy(i) * fi - (C)cy(opp(i)) * fbb;
+                    const C gmx = ((C)cx(i) - ux) * fi - ((C)cx(opp(i)) - ux) * fbb;
+                    const C gmy = ((C)cy(i) - uy) * fi - ((C)cy(opp(i)) - uy) * fbb;
+                    lacc[0] += cmx;
+                    lacc[1] += cmy;
+                    lacc[2] += dx * cmy - dy * cmx;
+                    lacc[3] += gmx;
+                    lacc[4] += gmy;
+                    lacc[5] += dx * gmy - dy * gmx;
+                }
+            }
+            __syncthreads();  // the chunk's tables are reused
         }
+        warp_sum(lacc);
+        if (lane == 0)
+            for (int q = 0; q < 6; q++) s_part[wib][q] = (double)lacc[q];
+        __syncthreads();
+        if (wib == 0) {
+            // lane q < 6 sums component q over the warps and over the booked
+            // events, each in order; lane 0 gathers them
+            double aq = 0.0, bq = 0.0;
+            if (lane < 6) {
+                for (int w = 0; w < FW; w++) aq += s_part[w][lane];
+                if (b.ev_t == t)
+                    for (int e = b.ev_off; e < b.ev_off + b.ev_n; e++) bq += p.ev_mom[6 * e + lane];
+            }
+            double acc[6], booked[6];
+#pragma unroll
+            for (int q = 0; q < 6; q++) {
+                acc[q] = __shfl_sync(FULL, aq, q);
+                booked[q] = __shfl_sync(FULL, bq, q);
+            }
+            record_forces(p, s, lane, t, acc, booked);
+            if (lane == 0) {
+                // distance from the centre at the last pair test, at t and t+1 (FP32
+                // from the split centres, with a slack above its rounding)
+                const float d0 = hypotf((float)(b.ix0 - b.ixt) + (b.fx0 - b.fxt),
+                                        (float)(b.iy0 - b.iyt) + (b.fy0 - b.fyt));
+                const float d1 = hypotf((float)(b.ix1 - b.ixt) + (b.fx1 - b.fxt),
+                                        (float)(b.iy1 - b.iyt) + (b.fy1 - b.fyt));
+                s_disp = fmaxf(s_disp, fmaxf(d0, d1) + 1e-3f);
+            }
+        }
+        __syncthreads();  // s_part is reused
     }
-    if (lane == 0) disp[wib] = dmax;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        float m = 0.f;
-        for (int w = 0; w < WARPS; w++) m = fmaxf(m, disp[w]);
-        if (m > 0.f) atomicMax(p.bar + 2, __float_as_uint(m));  // non-negative: bits order as values
-    }
+    if (tid == 0 && s_disp > 0.f)  // non-negative: bits order as values
+        atomicMax(p.bar + 2, __float_as_uint(s_disp));
 }
 
 // ----------------------------------------------------- re-rasterisation
@@ -877,6 +1092,7 @@ __device__ void phase_event(const StepParams &p, int e, int lane, void *fnew) {
     {
         const int k = code >> 1;
         const int x = k % L.pitch, y = k / L.pitch;
+        C fj = 0;  // lane j < 9: population j of the node (a fresh node's as stored)
         if (code & 1) {
             // fresh: refill (Sec. IV.B).  Lane 3(i-1)+(d-1) tests x + d e_i: a
             // node fluid at t+1 (owner map) that no solid held at t (the
@@ -929,8 +1145,9 @@ __device__ void phase_event(const StepParams &p, int e, int lane, void *fnew) {
                 }
                 C v = wd * sum;
                 v += __shfl_down_sync(FULL, v, 1) + __shfl_down_sync(FULL, v, 2);
-                if (lane < 27 && lane % 3 == 0)
-                    st(static_cast<S *>(fnew) + j * pl + k, v / (C)__popc(dirs));
+                v = stored(fsn, v / (C)__popc(dirs));
+                if (lane < 27 && lane % 3 == 0) st(static_cast<S *>(fnew) + j * pl + k, v);
+                fj = __shfl_sync(FULL, v, 3 * (lane < 9 ? lane : 0));  // lane j <- lane 3j
             } else if (lane < 9) {
                 // no old-fluid neighbour: equilibrium at rho0 and the solid's velocity
                 double ux, uy, ddx, ddy;
@@ -939,16 +1156,18 @@ __device__ void phase_event(const StepParams &p, int e, int lane, void *fnew) {
                 const double eu = cx(lane) * ux + cy(lane) * uy, uu = ux * ux + uy * uy;
                 const double fe =
                     p.rho0 * wgt<double>(lane) * (1.0 + 3.0 * eu + 4.5 * eu * eu - 1.5 * uu);
-                st(static_cast<S *>(fnew) + lane * pl + k,
-                   (C)(Prec<P>::dev ? fe - wgt<double>(lane) : fe));
+                fj = stored(fsn, (C)(Prec<P>::dev ? fe - wgt<double>(lane) : fe));
+                st(static_cast<S *>(fnew) + lane * pl + k, fj);
             }
             __syncwarp();
+        } else if (lane < 9) {
+            fj = (C)ldc(fsn + lane * pl + k);  // covered: its post-collision populations
         }
         // momentum and mass of the node (post-collision if covered, refilled if
         // fresh), summed in the arithmetic precision of the storage mode
         C jm[3] = {0, 0, 0};
         if (lane < 9) {
-            C v = (C)ldc(fsn + lane * pl + k);
+            C v = fj;
             if (Prec<P>::dev) v += wgt<C>(lane);
             jm[0] = (C)cx(lane) * v;
             jm[1] = (C)cy(lane) * v;
@@ -1010,7 +1229,7 @@ __device__ __forceinline__ void advance_solid(const Lattice &L, DSolid &b) {
 }
 
 template <int P>
-__global__ void __launch_bounds__(SW_BLOCK, 3) k_remask(const StepParams p) {
+__global__ void __launch_bounds__(SW_BLOCK, 4) k_remask(const StepParams p) {
     __shared__ int2 queue[WARPS][EVENTS];
     __shared__ int qn[WARPS];
     __shared__ int4 tile_ipos[NEAR_TILE];
@@ -1067,13 +1286,13 @@ cudaError_t launch_f(const StepParams &p, cudaStream_t st) {
         if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         if (e == cudaSuccess)
             e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_forces<P, LOCAL, BND>,
-                                                              SW_BLOCK, 0);
+                                                              FB, 0);
         if (e != cudaSuccess) return e;
     }
-    int blocks = (p.nsolid + WARPS - 1) / WARPS;
-    if (blocks > per_sm * sms) blocks = per_sm * sms;
+    int blocks = p.nsolid;  // one solid per block, looped beyond the resident blocks
+    if (blocks > 8 * per_sm * sms) blocks = 8 * per_sm * sms;
     if (blocks < 1) blocks = 1;
-    k_forces<P, LOCAL, BND><<<blocks, SW_BLOCK, 0, st>>>(p);
+    k_forces<P, LOCAL, BND><<<blocks, FB, 0, st>>>(p);
     return cudaGetLastError();
 }
 

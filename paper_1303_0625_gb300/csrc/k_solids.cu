@@ -143,6 +143,40 @@ __global__ void k_warm_start(const StepParams p, const float *pred, double U, do
     }
 }
 
+// Network input of a case, [8][ny][nx] floats: 0 the solid mask, 1 Re / 100,
+// 2 log10(Re) / 2, 3 the signed distance to the nearest disk surface / 16
+// (clipped to [-1, 4]), 4 the axial distance from that disk's centre in its
+// radii / 8 (clipped to [-1, 4]; positive downstream), 5 the channel's
+// parabola 4 y'(ny - y') / ny^2 (y' = y + 1/2), 6 x / nx, 7 y' / ny - 1/2.
+// Geometry from the solid table, centres at the current time.
+__global__ void k_case_features(const StepParams p, float re, float *in) {
+    const Lattice &L = p.L;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
+    if (x >= L.nx) return;
+    const long long n = (long long)L.nx * L.ny, o = (long long)y * L.nx + x;
+    float dmin = 1e30f, ax = 0.f;
+    for (int s = 0; s < p.nsolid; s++) {
+        const DSolid &b = p.S[s];
+        const float dx = (float)((double)x - b.x), dy = (float)((double)y - b.y);
+        const float r = sqrtf(b.r2f);
+        const float d = sqrtf(dx * dx + dy * dy) - r;
+        if (d < dmin) {
+            dmin = d;
+            ax = dx / (8.f * r);
+        }
+    }
+    if (p.nsolid == 0) dmin = 64.f;
+    const float h = (float)L.ny, yy = (float)y + 0.5f;
+    in[o] = p.owner[cell_of(L, x, y)] != FLUID ? 1.f : 0.f;
+    in[n + o] = re / 100.f;
+    in[2 * n + o] = log10f(re) / 2.f;
+    in[3 * n + o] = fminf(fmaxf(dmin / 16.f, -1.f), 4.f);
+    in[4 * n + o] = fminf(fmaxf(ax, -1.f), 4.f);
+    in[5 * n + o] = 4.f * yy * (h - yy) / (h * h);
+    in[6 * n + o] = (float)x / (float)L.nx;
+    in[7 * n + o] = yy / h - 0.5f;
+}
+
 __global__ void k_export_owner(const StepParams p, int32_t *out) {
     const Lattice &L = p.L;
     const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
@@ -249,6 +283,11 @@ cudaError_t launch_warm_start(const StepParams &p, const float *pred, double u_s
         case LBM_FP32_DEV: k_warm_start<LBM_FP32_DEV><<<g, 128, 0, st>>>(p, pred, u_scale, rho_scale, base); break;
         default: k_warm_start<LBM_FP16_DEV><<<g, 128, 0, st>>>(p, pred, u_scale, rho_scale, base);
     }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_case_features(const StepParams &p, double re, float *in, cudaStream_t st) {
+    k_case_features<<<cell_grid(p.L), 128, 0, st>>>(p, (float)re, in);
     return cudaGetLastError();
 }
 

@@ -892,6 +892,14 @@ lbm_status lbm_warm_start(lbm_ctx *c, const float *pred, double u_scale, double 
     return LBM_OK;
 }
 
+lbm_status lbm_case_input(lbm_ctx *c, double reynolds, float *in) {
+    if (!c || !in || !(reynolds > 0.0) || !std::isfinite(reynolds)) return LBM_EINVAL;
+    CK(c, cudaSetDevice(c->cfg.device));
+    CK(c, gbm::launch_case_features(params(c), reynolds, in, c->stream));
+    c->launches++;
+    return LBM_OK;
+}
+
 lbm_status lbm_get_owner(lbm_ctx *c, int32_t *owner, int32_t on_device) {
     if (!c || !owner) return LBM_EINVAL;
     CK(c, cudaSetDevice(c->cfg.device));

@@ -169,6 +169,12 @@ __device__ __forceinline__ void st(double *p, double v) { *p = v; }
 __device__ __forceinline__ void st(float *p, float v) { *p = v; }
 __device__ __forceinline__ void st(__half *p, float v) { *p = __float2half_rn(v); }
 __device__ __forceinline__ void st(float *p, double v) { *p = (float)v; }
+// v rounded to the storage type S, as st() stores it, in the arithmetic type
+__device__ __forceinline__ double stored(const double *, double v) { return v; }
+__device__ __forceinline__ float stored(const float *, float v) { return v; }
+__device__ __forceinline__ float stored(const __half *, float v) {
+    return __half2float(__float2half_rn(v));
+}
 __device__ __forceinline__ void st(__half *p, double v) { *p = __double2half(v); }
 
 // Population i of cell k as an FP64 value f_i (undoing the deviation storage).
@@ -417,6 +423,7 @@ cudaError_t launch_import_populations(const StepParams &p, const double *in, cud
 cudaError_t launch_warm_start(const StepParams &p, const float *pred, double u_scale,
                               double rho_scale, int base, cudaStream_t st);
 cudaError_t launch_export_owner(const StepParams &p, int32_t *out, cudaStream_t st);
+cudaError_t launch_case_features(const StepParams &p, double re, float *in, cudaStream_t st);
 cudaError_t launch_fields(const StepParams &p, double *rho, double *ux, double *uy,
                           cudaStream_t st);
 cudaError_t launch_link_masks(const StepParams &p, uint8_t *mask, cudaStream_t st);

@@ -133,6 +133,7 @@ _SIGNATURES = {
     "lbm_unet_gradients": (_I32, [_P, _P, _P, _P, _I32, _P, _D, _I32]),
     "lbm_unet_train_step": (_I32, [_P, _P, _P, _P, _I32, ctypes.c_float, _D, _I32]),
     "lbm_unet_input": (_I32, [_P, _P, ctypes.c_double, _P]),
+    "lbm_case_input": (_I32, [_P, ctypes.c_double, _P]),
     "lbm_warm_start": (_I32, [_P, _P, ctypes.c_double, ctypes.c_double, _I32]),
 }
 
@@ -487,6 +488,11 @@ def lbm_unet_train_step(net, x, target, fluid, batch: int, lr: float, on_device:
     _ncheck(load().lbm_unet_train_step(net, _ptr(x), _ptr(target), _ptr(fluid), int(batch),
                                        float(lr), ctypes.byref(loss), int(on_device)), net)
     return float(loss.value)
+
+
+def lbm_case_input(ctx, reynolds: float, in_dev):
+    """Network input [8][ny][nx] of the case held by ctx (device tensor)."""
+    _check(load().lbm_case_input(ctx, float(reynolds), _ptr(in_dev)), ctx)
 
 
 def lbm_unet_input(net, owner_dev, reynolds: float, in_dev):

@@ -7,8 +7,10 @@ device buffers.
 
   steady(cases)          run a batch of cases to a steady state (drag change
                          below tol per `every` steps) and collect the fields
-  dataset(cases, runs)   network inputs (solid mask, Re / 100), targets
-                         (scaled rho - 1 and u) and fluid masks
+                         and each case's network input (lbm_case_input: the
+                         solid mask, Re and geometric features)
+  dataset(cases, runs)   network inputs, targets (scaled residuals of rho
+                         and u) and fluid masks
   train(net, data, ...)  mini-batch Adam on the masked MSE
   time_to_drag(...)      steps and wall time until every case's drag is within
                          rel of its converged value, from the plain (cold)
@@ -51,11 +53,25 @@ def _batch(cases, precision, device, stream, ring=4):
                                   stream=stream)
 
 
+def inputs(b, cases, device=0):
+    """Network inputs [N][8][ny][nx] (device tensor) of the cases of batch b."""
+    import torch
+
+    ny, nx = cases[0]["ny"], cases[0]["nx"]
+    x = torch.empty((len(cases), 8, ny, nx), dtype=torch.float32,
+                    device=torch.device("cuda", device))
+    for k in range(len(cases)):
+        L.lbm_case_input(b.case(k).handle, cases[k]["re"], x[k])
+    return x
+
+
 def steady(cases, *, precision=L.LBM_FP32_DEV, tol=1e-7, every=100, cap=300_000, chunk=1000,
            device=0, stream=None, fields=True):
     """Run every case to a steady state; returns dict with state, steps,
-    drag and (with fields) rho, ux, uy [N][ny][nx] (NaN at solids)."""
+    drag and (with fields) rho, ux, uy [N][ny][nx] (NaN at solids) and the
+    network inputs x [N][8][ny][nx]."""
     b = _batch(cases, precision, device, stream)
+    xin = inputs(b, cases, device).cpu().numpy() if fields else None
     b.set_convergence(every=every, tol=tol, max_steps=cap)
     t0 = time.perf_counter()
     while b.run(chunk) > 0:
@@ -73,7 +89,7 @@ def steady(cases, *, precision=L.LBM_FP32_DEV, tol=1e-7, every=100, cap=300_000,
                 rho[k] = ux[k] = uy[k] = np.nan
             else:
                 rho[k], ux[k], uy[k] = b.case(k).fields()
-        out.update(rho=rho, ux=ux, uy=uy)
+        out.update(rho=rho, ux=ux, uy=uy, x=xin)
     b.close()
     return out
 
@@ -81,19 +97,18 @@ def steady(cases, *, precision=L.LBM_FP32_DEV, tol=1e-7, every=100, cap=300_000,
 def dataset(cases, runs, mirror=False):
     """Inputs [N][8][H][W], targets [N][3][H][W], fluid [N][H][W] (float32) of
     the cases that reached a steady state; with mirror, each also mirrored
-    about the channel's centre line (y -> ny - 1 - y, u_y -> -u_y), which the
-    walls and the inlet profile leave invariant."""
+    about the channel's centre line (y -> ny - 1 - y, u_y -> -u_y, and the
+    input's antisymmetric coordinate plane negated), which the walls and the
+    inlet profile leave invariant."""
     keep = np.flatnonzero(runs["state"] == L.LBM_CASE_CONVERGED)
     n = len(keep)
     ny, nx = cases[0]["ny"], cases[0]["nx"]
-    x = np.zeros((n, 8, ny, nx), dtype=np.float32)
+    x = np.ascontiguousarray(runs["x"][keep], dtype=np.float32)
     y = np.zeros((n, 3, ny, nx), dtype=np.float32)
     f = np.zeros((n, ny, nx), dtype=np.float32)
     for j, k in enumerate(keep):
         solid = np.isnan(runs["rho"][k])
         U = cases[k]["u_scale"]
-        x[j, 0] = solid
-        x[j, 1] = cases[k]["re"] / 100.0
         f[j] = ~solid
         rp, up = poiseuille(cases[k])
         y[j, 0] = np.where(solid, 0.0, (runs["rho"][k] - rp) / rho_scale(cases[k]))
@@ -101,6 +116,7 @@ def dataset(cases, runs, mirror=False):
         y[j, 2] = np.where(solid, 0.0, runs["uy"][k] / U)
     if mirror:
         xm, ym, fm = x[:, :, ::-1].copy(), y[:, :, ::-1].copy(), f[:, ::-1].copy()
+        xm[:, 7] *= -1.0
         ym[:, 2] *= -1.0
         x, y, f = np.concatenate([x, xm]), np.concatenate([y, ym]), np.concatenate([f, fm])
     return dict(x=x, y=y, fluid=f, index=keep)
@@ -177,11 +193,8 @@ def time_to_drag(cases, d_star, *, net=None, rel=1e-4, precision=L.LBM_FP32_DEV,
     fallback = np.zeros(n, dtype=bool)
     mass0 = None
     if net is not None:
-        owner = torch.empty((ny, nx), dtype=torch.int32, device=dev)
-        xin = torch.empty((n, 8, ny, nx), dtype=torch.float32, device=dev)
-        for k in range(n):
-            L.lbm_get_owner(b.case(k).handle, owner, on_device=True)
-            L.lbm_unet_input(net.handle, owner, cases[k]["re"], xin[k])
+        xin = inputs(b, cases, device)
+        torch.cuda.synchronize()
         out = torch.empty((n, 3, ny, nx), dtype=torch.float32, device=dev)
         for s in range(0, n, net.max_batch):
             e = min(n, s + net.max_batch)
