@@ -70,6 +70,12 @@ def parse():
     ap.add_argument("--ws-train", type=int, default=1024)
     ap.add_argument("--ws-test", type=int, default=256)
     ap.add_argument("--ws-epochs", type=int, default=100)
+    ap.add_argument("--ws-save", type=str, default="",
+                    help="with --warm-start: write the trained parameters here (npz)")
+    ap.add_argument("--ws-load", type=str, default="",
+                    help="with --warm-start: evaluate these parameters instead of training")
+    ap.add_argument("--ws-bench-cases", type=int, default=96,
+                    help="held-out channels of the default line's time-to-drag entry")
     ap.add_argument("--batch-converge", type=int, default=0, metavar="STEPS",
                     help="run the 512-channel sweep until every case retires or STEPS steps")
     ap.add_argument("--unet", action="store_true",
@@ -379,6 +385,7 @@ def run_ours(a, ws, rank, local):
         line["batch"] = run_batch(a, local, stream, peak)
         line["sedimentation"] = run_sedimentation(a, local, stream, peak)
         line["precision_study"] = run_precision_study(a, w, local, stream)
+        line["warm_start"] = run_warm_start_bench(a, local)
         line["cpu_baseline"] = run_cpu_baseline(a, w, a.cpu_seconds)
     elif rank == 0:
         line["e2e"] = None
@@ -521,10 +528,18 @@ def run_precision_study(a, w, local, stream):
     fmag = np.abs(ref).max(axis=0, keepdims=True)
     scale[..., :2] = np.maximum(fmag[..., :2], f0[None, :, None, None])
     scale[..., 2:] = np.maximum(fmag[..., 2:], (f0 * radii)[None, :, None, None])
-    out = {"reference": "fp64 mode on the GPU", "horizons": horizons}
+    # each force's error relative to its own series' largest magnitude (no
+    # floor): the error of the net force itself; median and worst over solids
+    own = np.abs(ref).max(axis=0, keepdims=True)
+    out = {"reference": "fp64 mode on the GPU", "horizons": horizons,
+           "scale": "larger of the series' magnitude and 2 rho0 r / 3 (torque: times r)"}
     for prec in ("fp32", "fp16"):
         err = np.abs(rec[prec] - ref) / scale
         out[prec] = [float("%.3g" % err[h - 1].max()) for h in horizons]
+        rel_own = np.abs(rec[prec] - ref) / np.where(own > 0, own, 1.0)
+        per_solid = [rel_own[:h].max(axis=(0, 2, 3)) for h in horizons]  # worst up to h
+        out[prec + "_own_scale_median_worst"] = [
+            [float("%.3g" % np.median(v)), float("%.3g" % v.max())] for v in per_solid]
     return out
 
 
@@ -566,10 +581,11 @@ def run_batch_converge(a, local):
             "batch_steps": done, "wall_s": round(wall, 2),
             "converged": int(conv.sum()), "active": int((st == G.LBM_CASE_ACTIVE).sum()),
             "unstable": int((st == G.LBM_CASE_UNSTABLE).sum()),
+            "capped": int((st == G.LBM_CASE_CAPPED).sum()),
             "steps_to_converge_pct_0_50_90_100": [int(np.percentile(s1[conv], q)) for q in (0, 50, 90, 100)]
             if conv.any() else None,
             "aggregate_mlups": round(upd / wall / 1e6, 1),
-            "active_after_steps": marks}
+            "active_after_steps": marks[::10] + ([marks[-1]] if len(marks) % 10 != 1 else [])}
 
 
 def run_unet(a, local, H=128, W=256, B=16, levels=4, base=32):
@@ -629,14 +645,54 @@ def run_unet(a, local, H=128, W=256, B=16, levels=4, base=32):
             **res}
 
 
+WS_WEIGHTS = os.path.join(ROOT, "paper_1303_0625_gb300", "weights", "unet_channels_256x128.npz")
+
+
+def evaluate_warm_start(net, test_all, local):
+    """Time to converged drag on held-out channels, warm (net) against cold:
+    steps and wall time (inference included) until every case's drag is within
+    1e-4 of the drag its plain run converges to (1e-7 per 100 steps), same
+    batch engine and GPU; cases without a steady state are left out and
+    counted; prediction error on the held-out steady fields."""
+    import numpy as np
+
+    import paper_1303_0625_gb300 as G
+    from paper_1303_0625_gb300 import warmstart as WS
+
+    ref = WS.steady(test_all, device=local)
+    keep = np.flatnonzero(ref["state"] == G.LBM_CASE_CONVERGED)
+    test = [test_all[k] for k in keep]
+    d_star = ref["drag"][keep]
+    cold = WS.time_to_drag(test, d_star, device=local)
+    warm = WS.time_to_drag(test, d_star, net=net, device=local)
+    tdata = WS.dataset(test_all, ref)
+    pred = WS.predict(net, tdata["x"]).cpu().numpy()
+    m = tdata["fluid"][:, None]
+    err = float(np.sqrt(((pred - tdata["y"]) ** 2 * m).sum() / ((tdata["y"] ** 2) * m).sum()))
+    steps_c, steps_w = cold["steps"].astype(float), warm["steps"].astype(float)
+    return {"test_cases": len(test_all), "test_steady": len(test),
+            "excluded_unsteady": int(len(test_all) - len(test)),
+            "cold": {"wall_s": round(cold["wall"], 3), "batch_steps": int(cold["batch_steps"]),
+                     "median_case_steps": float(np.median(steps_c))},
+            "warm": {"wall_s": round(warm["wall"], 3), "batch_steps": int(warm["batch_steps"]),
+                     "median_case_steps": float(np.median(steps_w)),
+                     "fallbacks": int(warm["fallback"].sum()),
+                     "settled_elsewhere": int(warm["elsewhere"].sum())},
+            "prediction_rel_l2": round(err, 4),
+            "wall_speedup": round(cold["wall"] / warm["wall"], 3),
+            "median_step_speedup": round(float(np.median(steps_c / np.maximum(steps_w, 1))), 3)}
+
+
+WS_WORKLOAD = ("256x128 channels, 1-4 fixed disks r 6-16, Re 1..100, tau from Re (>= 0.53), "
+               "velocity inlet / pressure outlet, fp32 batch engine")
+
+
 def run_warm_start(a, local):
     """Learned warm start on 256 x 128 channels with 1-4 fixed disks and Re
     in 1..100: train the U-Net on steady fields the batch engine computes for
-    a training set, then on held-out cases measure the steps and the wall
-    time (inference included) until every case's drag is within 1e-4 of its
-    converged cold-start value, warm against cold, same batch engine and GPU.
-    Cases without a steady state within the step cap are left out and
-    counted."""
+    a training set (or load parameters), then evaluate_warm_start on held-out
+    cases.  --ws-save writes the trained parameters (FP16) with their
+    provenance."""
     import numpy as np
     import torch
 
@@ -645,47 +701,64 @@ def run_warm_start(a, local):
     from paper_1303_0625_gb300 import warmstart as WS
 
     torch.cuda.set_device(local)
-    t0 = time.time()
-    train_cases = W.warm_start_channels(a.ws_train, seed_offset=5)
-    runs = WS.steady(train_cases, device=local)
-    data = WS.dataset(train_cases, runs, mirror=True)
-    t_data = time.time() - t0
     net = G.UNet(128, 256, levels=4, base=32, max_batch=16, seed=3, device=local)
-    t1 = time.time()
-    losses = WS.train(net, data, epochs=a.ws_epochs, batch=16, lr=1e-3, lr_end=1e-5)
-    t_train = time.time() - t1
+    out = {"metric": "time-to-drag at 1e-4 rel err, warm vs cold start", "workload": WS_WORKLOAD}
+    if a.ws_load:
+        net.set_params(np.load(a.ws_load)["params"].astype(np.float32))
+        out["parameters"] = a.ws_load
+    else:
+        t0 = time.time()
+        train_cases = W.warm_start_channels(a.ws_train, seed_offset=5)
+        runs = WS.steady(train_cases, device=local)
+        data = WS.dataset(train_cases, runs, mirror=True)
+        t_data = time.time() - t0
+        t1 = time.time()
+        losses = WS.train(net, data, epochs=a.ws_epochs, batch=16, lr=1e-3, lr_end=1e-5)
+        out.update({"train_unstable": int((runs["state"] == G.LBM_CASE_UNSTABLE).sum()),
+                    "train_capped": int((runs["state"] == G.LBM_CASE_CAPPED).sum()),
+                    "train_cases": len(train_cases), "train_steady": int(len(data["index"])),
+                    "train_samples": int(data["x"].shape[0]),
+                    "data_seconds": round(t_data, 1), "train_seconds": round(time.time() - t1, 1),
+                    "epochs": a.ws_epochs, "final_loss": float("%.4g" % losses[-1])})
+        if a.ws_save:
+            os.makedirs(os.path.dirname(os.path.abspath(a.ws_save)), exist_ok=True)
+            np.savez(a.ws_save, params=net.params().astype(np.float16), levels=4, base=32,
+                     height=128, width=256, inputs="lbm_case_input",
+                     trained_on=f"{len(train_cases)} channels (seed offset 5), "
+                                f"{int(data['x'].shape[0])} samples with mirrors, "
+                                f"{a.ws_epochs} epochs, Adam 1e-3 -> 1e-5",
+                     command=" ".join(sys.argv))
+            out["saved"] = a.ws_save
     test_all = W.warm_start_channels(a.ws_test, seed_offset=6)
-    ref = WS.steady(test_all, device=local)
-    keep = np.flatnonzero(ref["state"] == G.LBM_CASE_CONVERGED)
-    test = [test_all[k] for k in keep]
-    d_star = ref["drag"][keep]
-    cold = WS.time_to_drag(test, d_star, device=local)
-    warm = WS.time_to_drag(test, d_star, net=net, device=local)
-    # prediction error on the held-out steady fields
-    tdata = WS.dataset(test_all, ref)
-    pred = WS.predict(net, tdata["x"]).cpu().numpy()
-    m = tdata["fluid"][:, None]
-    err = float(np.sqrt(((pred - tdata["y"]) ** 2 * m).sum() / ((tdata["y"] ** 2) * m).sum()))
-    steps_c, steps_w = cold["steps"].astype(float), warm["steps"].astype(float)
-    return {"metric": "time-to-drag at 1e-4 rel err, warm vs cold start",
-            "train_unstable": int((runs["state"] == G.LBM_CASE_UNSTABLE).sum()),
-            "train_capped": int((runs["state"] == G.LBM_CASE_CAPPED).sum()),
-            "workload": "256x128 channels, 1-4 fixed disks r 6-16, Re 1..100, tau from Re "
-                        "(>= 0.53), velocity inlet / pressure outlet, fp32 batch engine",
-            "train_cases": len(train_cases), "train_steady": int(len(data["index"])),
-            "train_samples": int(data["x"].shape[0]),
-            "data_seconds": round(t_data, 1), "train_seconds": round(t_train, 1),
-            "epochs": a.ws_epochs, "final_loss": float("%.4g" % losses[-1]),
-            "test_cases": len(test_all), "test_steady": len(test),
-            "excluded_unsteady": int(len(test_all) - len(test)),
-            "cold": {"wall_s": round(cold["wall"], 3), "batch_steps": int(cold["batch_steps"]),
-                     "median_case_steps": float(np.median(steps_c))},
-            "warm": {"wall_s": round(warm["wall"], 3), "batch_steps": int(warm["batch_steps"]),
-                     "median_case_steps": float(np.median(steps_w)),
-                     "fallbacks": int(warm["fallback"].sum())},
-            "prediction_rel_l2": round(err, 4),
-            "wall_speedup": round(cold["wall"] / warm["wall"], 3),
-            "median_step_speedup": round(float(np.median(steps_c / np.maximum(steps_w, 1))), 3)}
+    out.update(evaluate_warm_start(net, test_all, local))
+    net.close()
+    return out
+
+
+def run_warm_start_bench(a, local):
+    """The default line's time-to-drag entry: the shipped network parameters
+    against the plain run on the first ws_bench_cases held-out channels."""
+    import numpy as np
+    import torch
+
+    import paper_1303_0625_gb300 as G
+    import workloads as W
+
+    if not os.path.exists(WS_WEIGHTS):
+        return {"unavailable": "no trained network parameters in the package"}
+    torch.cuda.set_device(local)
+    z = np.load(WS_WEIGHTS)
+    net = G.UNet(int(z["height"]), int(z["width"]), levels=int(z["levels"]), base=int(z["base"]),
+                 max_batch=16, seed=0, device=local)
+    net.set_params(z["params"].astype(np.float32))
+    t0 = time.time()
+    out = {"metric": "time-to-drag at 1e-4 rel err, warm vs cold start", "workload": WS_WORKLOAD,
+           "parameters": os.path.relpath(WS_WEIGHTS, ROOT), "trained_on": str(z["trained_on"])}
+    out.update(evaluate_warm_start(net, W.warm_start_channels(a.ws_bench_cases, seed_offset=6),
+                                   local))
+    out["seconds"] = round(time.time() - t0, 1)
+    net.close()
+    return out
 
 
 def run_e2e(a, w, local, stream):
@@ -703,6 +776,12 @@ def run_e2e(a, w, local, stream):
     f0 = torch.empty((9, ny, nx), dtype=torch.float64, pin_memory=True)
     lat.step(1)
     L.lbm_get_populations(lat.handle, f0.numpy())  # a valid state to upload
+    if a.variant >= 0:  # the launch shape of the main measurement
+        lat.set_kernel_variant(a.variant)
+        if a.overlap >= 0:
+            lat.set_force_overlap(a.overlap)
+    else:
+        lat.autotune(4)
     ns = lat.nsolid
     block = 50
     out = torch.empty((2, block, ns, 3), dtype=torch.float64, pin_memory=True)

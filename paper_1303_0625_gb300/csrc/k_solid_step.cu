@@ -705,8 +705,10 @@ __global__ void __launch_bounds__(FB, 6) k_forces(const StepParams p) {
             s_i0[tid] = i0 <= i1 ? i0 : 1;  // an empty inner chord: i0 > i1
             s_i1[tid] = i0 <= i1 ? i1 : 0;
             __syncthreads();
-            // candidate e -> row (binary search over the prefix) and column
-            for (int e = tid; e < total; e += FB) {
+            // candidate e -> row (binary search over the prefix) and column; every
+            // thread runs the same iterations (the list append is warp-wide)
+            for (int base = 0; base < total; base += FB) {
+                const int e = base + tid;
                 int q = 0;
 #pragma unroll
                 for (int step = FB / 2; step > 0; step >>= 1)
@@ -715,11 +717,25 @@ __global__ void __launch_bounds__(FB, 6) k_forces(const StepParams p) {
                 int iu = s_lo[q] + (e - s_cnt[q]);
                 const int a = s_i0[q], bb = s_i1[q];
                 if (a <= bb && iu >= a) iu += bb - a + 1;  // step over the inner chord
-                int x, y;
-                if (!wrap(iu, jj, x, y)) continue;
-                const int k = (int)cell_of(L, x, y);
-                const uint16_t m = p.flags[k];
-                if ((m & 1u) || !(m & 0x1FEu)) continue;  // solid, or no bounced population
+                int x = 0, y = 0;
+                const bool here = e < total && wrap(iu, jj, x, y);
+                const int k = here ? (int)cell_of(L, x, y) : 0;
+                const uint16_t m = here ? p.flags[k] : (uint16_t)1u;
+                const bool bounced_node = !(m & 1u) && (m & 0x1FEu);
+                if (p.list_by_forces) {
+                    // the node goes to the deferred per-node path's list of step t
+                    const unsigned want = __ballot_sync(FULL, bounced_node);
+                    if (want) {
+                        int at = 0;
+                        if (lane == 0) at = atomicAdd(p.bnd + (t & 1), __popc(want));
+                        at = __shfl_sync(FULL, at, 0) + __popc(want & ((1u << lane) - 1u));
+                        if (bounced_node) {
+                            if (at < p.bnd_cap) p.bnd[2 + at] = k;
+                            else atomicOr(p.status, 16);
+                        }
+                    }
+                }
+                if (!bounced_node) continue;  // solid, or no bounced population
                 S fv[9];
                 uint16_t own[9];
 #pragma unroll

@@ -15,63 +15,17 @@ __global__ void __launch_bounds__(SC_BLOCK_X) k_stream_collide(const StepParams 
 
 // With the per-node path deferred (variants 3-5), the nodes k_stream_collide
 // leaves to the per-node update (update_node) are computed from the same
-// populations after it, in two kernels:
-//   k_boundary_scan    one block per disk tests the nodes of the disk's box
-//                      against the ring r - 1 <= |x - R| <= r + 2, which holds
-//                      every fluid node with a link into the disk (fluid nodes
-//                      lie outside r, links are at most sqrt 2 long), gathers
-//                      the ring's fluid nodes with a bounced population in
-//                      shared memory and appends them to a device list (one
-//                      atomic per block and chunk);
-//   k_boundary_update  one thread per node of the list, then of the first and
-//                      last columns and, where the vector path does not take
-//                      them, of the wall rows.
-// The list's length is kept per step parity; the update kernel of step t
-// clears the slot of step t + 1.  A node next to two disks (or a disk and an
-// edge) is computed twice, with identical results.  Inline in the vector path
-// these nodes run with one or two active lanes per warp; which way is faster
-// depends on the workload (the autotuner measures both).
-constexpr int BN_BLOCK = 256, BN_CHUNK = 2048;
-
-template <int P, bool LOCAL>
-__global__ void __launch_bounds__(BN_BLOCK) k_boundary_scan(const StepParams p) {
-    __shared__ int list[BN_CHUNK];
-    __shared__ int count, gbase;
-    const Lattice &L = p.L;
-    const DSolid &b = p.S[blockIdx.x];
-    if (!solid_ok(b)) return;  // flagged by the per-solid kernel
-    const long long t = *p.t;
-    int *len = p.bnd + (t & 1);
-    int *out = p.bnd + 2;
-    const int xi = (int)floor(b.x), yi = (int)floor(b.y);
-    const float fx = (float)(b.x - xi), fy = (float)(b.y - yi);
-    const float ro = (float)b.r + 2.f, ri = (float)b.r - 1.f;
-    const float ro2 = ro * ro, ri2 = ri > 0.f ? ri * ri : 0.f;
-    const int h = boundary_half(b.r), bw = 2 * h + 1, n = bw * bw;
-    for (int c0 = 0; c0 < n; c0 += BN_CHUNK) {
-        if (threadIdx.x == 0) count = 0;
-        __syncthreads();
-        const int c1 = min(n, c0 + BN_CHUNK);
-        for (int q = c0 + (int)threadIdx.x; q < c1; q += BN_BLOCK) {
-            const int di = q % bw - h, dj = q / bw - h;
-            const float dx = (float)di - fx, dy = (float)dj - fy, d2 = dx * dx + dy * dy;
-            int x, y;
-            if (d2 >= ri2 && d2 <= ro2 && locate(L, xi + di, yi + dj, x, y)) {
-                const uint16_t fl = p.flags[cell_of(L, x, y)];
-                if (!(fl & 1u) && (fl & 0x1FEu)) list[atomicAdd(&count, 1)] = y * L.pitch + x;
-            }
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) gbase = count ? atomicAdd(len, count) : 0;
-        __syncthreads();
-        const int m = count, g0 = gbase;
-        for (int e = (int)threadIdx.x; e < m; e += BN_BLOCK) {
-            if (g0 + e < p.bnd_cap) out[g0 + e] = list[e];
-            else atomicOr(p.status, 16);
-        }
-        __syncthreads();  // list and count are reused by the next chunk
-    }
-}
+// populations after it, by k_boundary_update: one thread per node of the
+// step's list of fluid nodes next to solids, then of the first and last
+// columns and, where the vector path does not take them, of the wall rows.
+// The force kernel of the step fills the list: it visits every fluid node
+// with a link into its solid (one atomic per warp and list chunk).  The
+// list's length is kept per step parity; the update kernel of step t clears
+// the slot of step t + 1.  A node next to two disks is computed twice, with
+// identical results.  Inline in the vector path these nodes run with one or
+// two active lanes per warp; which way is faster depends on the workload (the
+// autotuner measures both).
+constexpr int BN_BLOCK = 256;
 
 template <int P, bool FORCE, bool LOCAL>
 __host__ __device__ long long boundary_edge_nodes(const Lattice &L) {
@@ -122,6 +76,9 @@ __global__ void k_open_columns(const StepParams p) {
     open_row<P, FORCE>(p, static_cast<R *>((t & 1) ? p.f0 : p.f1), y);
 }
 
+template <int P, bool FORCE, bool LOCAL>
+cudaError_t launch_update(const StepParams &p, cudaStream_t st);
+
 // Walled domains (y walls) with rho_w = rho0 in FP32/FP64 take the kernel
 // whose vector path also covers the wall rows.
 template <int P, int V, bool FORCE, bool LOCAL, bool DEFER>
@@ -133,12 +90,16 @@ cudaError_t launch_sc(const StepParams &p, cudaStream_t st) {
     else
         k_stream_collide<P, V, FORCE, LOCAL, false, DEFER><<<grid, SC_BLOCK_X, 0, st>>>(p);
     cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess || !DEFER) return e;
-    if (p.nsolid > 0) {
-        k_boundary_scan<P, LOCAL><<<p.nsolid, BN_BLOCK, 0, st>>>(p);
-        e = cudaGetLastError();
-        if (e != cudaSuccess) return e;
-    }
+    // with solids, the force kernel lists the nodes next to them and the
+    // host launches the update after it (launch_deferred_update)
+    if (e != cudaSuccess || !DEFER || p.list_by_forces) return e;
+    return launch_update<P, FORCE, LOCAL>(p, st);
+}
+
+// The update kernel of the deferred per-node path, over the list of step t.
+template <int P, bool FORCE, bool LOCAL>
+cudaError_t launch_update(const StepParams &p, cudaStream_t st) {
+    cudaError_t e = cudaSuccess;
     static int sms = 0;
     if (!sms) {
         int dev = 0;
@@ -170,7 +131,7 @@ cudaError_t launch_sc_v(const StepParams &p, cudaStream_t st) {
 
 // Node widths per thread: variant 0 = one 16-byte word per population,
 // variant 1 = 8 bytes, variant 2 = 4 bytes; variants 3-5 the same widths
-// with the per-node path deferred to k_boundary_scan / k_boundary_update.
+// with the per-node path deferred to k_boundary_update.
 // MRT: one launch shape, 8-byte words per population plane, slow nodes inline.
 template <int P, bool LOCAL, bool BND>
 cudaError_t launch_mrt_b(const StepParams &p, cudaStream_t st) {
@@ -215,6 +176,20 @@ cudaError_t launch_stream_collide(const StepParams &p, cudaStream_t st) {
         case LBM_FP32_DEV: return launch_sc_p<LBM_FP32_DEV>(p, st);
         default: return launch_sc_p<LBM_FP16_DEV>(p, st);
     }
+}
+
+cudaError_t launch_deferred_update(const StepParams &p, cudaStream_t st) {
+    const bool force = p.body_x != 0.0 || p.body_y != 0.0;
+    const bool local = p.rho_w_mode == LBM_RHOW_LOCAL;
+#define GBM_U(P)                                                                            \
+    return force ? (local ? launch_update<P, true, true>(p, st) : launch_update<P, true, false>(p, st)) \
+                 : (local ? launch_update<P, false, true>(p, st) : launch_update<P, false, false>(p, st))
+    switch (p.precision) {
+        case LBM_FP64: GBM_U(LBM_FP64);
+        case LBM_FP32_DEV: GBM_U(LBM_FP32_DEV);
+        default: GBM_U(LBM_FP16_DEV);
+    }
+#undef GBM_U
 }
 
 cudaError_t launch_open_columns(const StepParams &p, cudaStream_t st) {

@@ -140,6 +140,9 @@ StepParams params(const lbm_ctx *c) {
     p.sc_variant = c->sc_variant;
     p.bnd = c->bnd_d;
     p.bnd_cap = c->bnd_cap;
+    // with solids on the deferred per-node path, the force kernel lists the
+    // nodes next to them (it visits them anyway)
+    p.list_by_forces = c->nsolid > 0 && c->bnd_d && gbm::deferred_path(p) ? 1 : 0;
     p.ev_len = static_cast<int *>(c->ev_d);
     p.ev = c->ev_d ? reinterpret_cast<int4 *>(static_cast<char *>(c->ev_d) + 16) : nullptr;
     p.ev_mom = c->ev_d ? reinterpret_cast<double *>(static_cast<char *>(c->ev_d) + 16 +
@@ -264,6 +267,10 @@ lbm_status enqueue_step(lbm_ctx *c, const StepParams &p, bool timed) {
         CK(c, cudaEventRecord(c->ev[c->ev_used], c->stream));
     }
     CK(c, gbm::launch_stream_collide(p, c->stream));
+    if (p.list_by_forces) {  // the slow nodes' update, once the force kernel has listed them
+        if (fork) CK(c, cudaStreamWaitEvent(c->stream, c->join, 0));
+        CK(c, gbm::launch_deferred_update(p, c->stream));
+    }
     if (timed) {
         CK(c, cudaEventRecord(c->ev[c->ev_used + 1], c->stream));
         c->ev_used += 2;
@@ -272,7 +279,7 @@ lbm_status enqueue_step(lbm_ctx *c, const StepParams &p, bool timed) {
         CK(c, gbm::launch_open_columns(p, c->stream));
         c->launches++;
     }
-    if (fork) CK(c, cudaStreamWaitEvent(c->stream, c->join, 0));
+    if (fork && !p.list_by_forces) CK(c, cudaStreamWaitEvent(c->stream, c->join, 0));
     if (p.nmoving > 0) CK(c, gbm::launch_remask(p, c->stream));
     else CK(c, gbm::launch_tick(p, c->stream));
     c->launches += gbm::stream_collide_launches(p) + 1;

@@ -129,11 +129,13 @@ struct StepParams {
     int ev_cap;
     int *bnd;                 // deferred per-node path: {length at even t, at odd t, list...}
     int bnd_cap;              // capacity of the list
+    int list_by_forces;       // the force kernel fills the deferred list; the fused pass
+                              // leaves the update to launch_deferred_update
 };
 
-// Half-width of the box around floor(R) that holds the ring r - 1 <= |x - R|
-// <= r + 2 of a disk (R within one node of floor(R)); the box has
-// (2 h + 1)^2 nodes, which bounds the disk's entries in the deferred list.
+// Half-width of a box around floor(R) that holds every fluid node with a
+// link into a disk (within r + sqrt 2 of R, R within one node of floor(R));
+// the box's (2 h + 1)^2 nodes bound the disk's entries in the deferred list.
 __host__ __device__ inline int boundary_half(double r) { return (int)ceil(r) + 3; }
 
 template <class C> __device__ __forceinline__ C pick(double d, float f);
@@ -382,12 +384,15 @@ struct BatchState {
 // the fused advection-collision kernel, and with variants 3-5 the pass over
 // the nodes it leaves to the per-node update
 constexpr int KERNEL_VARIANTS = 6;
+inline bool deferred_path(const StepParams &p) {
+    return p.collision != LBM_MRT && (p.sc_variant >= 3 || p.boundary == LBM_INTERPOLATED);
+}
 inline int stream_collide_launches(const StepParams &p) {
-    if (p.collision == LBM_MRT) return 1;  // MRT keeps the slow nodes inline
-    const bool deferred = p.sc_variant >= 3 || p.boundary == LBM_INTERPOLATED;
-    return deferred ? (p.nsolid > 0 ? 3 : 2) : 1;
+    return deferred_path(p) ? 2 : 1;  // MRT keeps the slow nodes inline
 }
 cudaError_t launch_stream_collide(const StepParams &p, cudaStream_t st);
+// the update of the deferred per-node path, when list_by_forces
+cudaError_t launch_deferred_update(const StepParams &p, cudaStream_t st);
 // open channel: columns 0 and nx-1 of the populations just written (t+1)
 cudaError_t launch_open_columns(const StepParams &p, cudaStream_t st);
 

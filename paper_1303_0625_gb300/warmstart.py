@@ -3,7 +3,9 @@
 Host-side orchestration only: every step runs in the library's kernels (the
 batch engine for the lattice-Boltzmann runs, the U-Net kernels for training
 and inference, ``lbm_warm_start`` for the initial state).  PyTorch supplies
-device buffers.
+device buffers.  The library's contexts and the network run on streams of
+their own: every hand-over of device data between them and PyTorch's stream
+waits for the producer (torch.cuda.synchronize).
 
   steady(cases)          run a batch of cases to a steady state (drag change
                          below tol per `every` steps) and collect the fields
@@ -60,8 +62,10 @@ def inputs(b, cases, device=0):
     ny, nx = cases[0]["ny"], cases[0]["nx"]
     x = torch.empty((len(cases), 8, ny, nx), dtype=torch.float32,
                     device=torch.device("cuda", device))
+    torch.cuda.synchronize(device)  # x is allocated on PyTorch's stream
     for k in range(len(cases)):
         L.lbm_case_input(b.case(k).handle, cases[k]["re"], x[k])
+    torch.cuda.synchronize(device)  # written on the batch's stream
     return x
 
 
@@ -142,6 +146,7 @@ def train(net, data, *, epochs=20, batch=16, lr=1e-3, lr_end=1e-4, seed=0, log=N
         for s in range(0, n - batch + 1, batch):
             idx = torch.from_numpy(order[s:s + batch]).to(dev)
             xb, yb, fb = X[idx].contiguous(), Y[idx].contiguous(), F[idx].contiguous()
+            torch.cuda.current_stream(dev).synchronize()  # gathered on PyTorch's stream
             rate = lr * (lr_end / lr) ** (k / steps)
             tot += L.lbm_unet_train_step(net.handle, xb, yb, fb, batch, rate, on_device=True)
             cnt += 1
@@ -159,9 +164,12 @@ def predict(net, data_x, batch=16):
     dev = torch.device("cuda", net.cfg.device)
     X = torch.from_numpy(data_x).to(dev)
     out = torch.empty((X.shape[0], 3, X.shape[2], X.shape[3]), dtype=torch.float32, device=dev)
-    for s in range(0, X.shape[0], batch):
-        e = min(X.shape[0], s + batch)
-        L.lbm_unet_forward(net.handle, X[s:e].contiguous(), out[s:e], e - s, on_device=True)
+    chunks = [X[s:min(X.shape[0], s + batch)].contiguous() for s in range(0, X.shape[0], batch)]
+    torch.cuda.synchronize(dev)  # uploaded on PyTorch's stream
+    for k, xc in enumerate(chunks):
+        s = k * batch
+        L.lbm_unet_forward(net.handle, xc, out[s:s + xc.shape[0]], xc.shape[0], on_device=True)
+    torch.cuda.synchronize(dev)  # written on the network's stream
     return out
 
 
@@ -174,13 +182,20 @@ def _mass(ctx):
 
 
 def time_to_drag(cases, d_star, *, net=None, rel=1e-4, precision=L.LBM_FP32_DEV, every=100,
-                 cap=300_000, drift_steps=200, drift_mass=1e-2, device=0, stream=None):
+                 cap=300_000, drift_steps=200, drift_mass=1e-2, settle=1e-7, device=0,
+                 stream=None):
     """Steps and wall time until every case's Eq. 5 drag is within rel of
     d_star (the converged drag of the plain run), starting cold (net None)
-    or warm from the network's prediction.  Warm cases are checked after
-    drift_steps: an unstable state, a non-finite drag or a total-mass change
-    above drift_mass (relative) restarts that case cold.  The wall time
-    covers input assembly, inference and every step."""
+    or warm from the network's prediction.  The plain run is the judge, and
+    a warm case falls back to it (a cold restart in a batch of its own,
+    charged with the steps it has taken):
+      - after drift_steps, when its state is unstable, its drag not finite or
+        its total mass has moved by more than drift_mass (relative);
+      - whenever its drag has settled (changed by less than settle, relative,
+        over `every` steps, the steady-state test of the plain run) away from
+        d_star: it has reached another steady state.
+    A case stops stepping once it is within rel of d_star.  The wall time
+    covers input assembly, inference, every step and the cold restarts."""
     import torch
 
     dev = torch.device("cuda", device)
@@ -191,6 +206,7 @@ def time_to_drag(cases, d_star, *, net=None, rel=1e-4, precision=L.LBM_FP32_DEV,
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     fallback = np.zeros(n, dtype=bool)
+    elsewhere = np.zeros(n, dtype=bool)
     mass0 = None
     if net is not None:
         xin = inputs(b, cases, device)
@@ -206,33 +222,53 @@ def time_to_drag(cases, d_star, *, net=None, rel=1e-4, precision=L.LBM_FP32_DEV,
         mass0 = np.array([_mass(b.case(k)) for k in range(n)])
     done = np.full(n, -1, dtype=np.int64)
     drift = None
+    prev = np.full(n, np.nan)
     steps = 0
+
+    def restart_cold(ids, at, st):
+        # the plain run of those cases, in a batch of their own; they leave this one
+        sub = [cases[k] for k in ids]
+        r = time_to_drag(sub, d_star[ids], rel=rel, precision=precision, every=every, cap=cap,
+                         device=device, stream=stream)
+        done[ids] = np.where(r["steps"] >= 0, r["steps"] + at, -1)
+        fallback[ids] = True
+        still = ids[st[ids] == L.LBM_CASE_ACTIVE]  # an unstable case has retired already
+        if len(still):
+            b.retire(still)
+
     while steps < cap:
         b.run(every)
         steps += every
         st, stp, drag = b.state()
+        active = (done < 0) & ~fallback & (st == L.LBM_CASE_ACTIVE)
         if net is not None and steps == drift_steps:
             drift = np.zeros(n)
+            bad = []
             for k in range(n):
                 m = _mass(b.case(k))
                 drift[k] = abs(m - mass0[k]) / abs(mass0[k]) if np.isfinite(m) else np.inf
                 if st[k] == L.LBM_CASE_UNSTABLE or not np.isfinite(drag[k]) or \
                         not drift[k] <= drift_mass:
-                    fallback[k] = True
-            if fallback.any():  # those cases start again, cold, in a batch of their own
-                sub = [cases[k] for k in np.flatnonzero(fallback)]
-                r = time_to_drag(sub, d_star[fallback], rel=rel, precision=precision, every=every,
-                                 cap=cap, device=device, stream=stream)
-                done[fallback] = r["steps"] + steps
+                    bad.append(k)
+            if bad:
+                restart_cold(np.array(bad), steps, st)
+                active &= ~fallback
         ok = np.abs(drag - d_star) <= rel * np.abs(d_star)
-        newly = ok & (done < 0) & ~fallback & (st == L.LBM_CASE_ACTIVE)
+        newly = ok & active
         done[newly] = steps
         if newly.any():  # the case has reached its drag: it stops stepping
             b.retire(np.flatnonzero(newly))
+        if net is not None and steps > drift_steps:
+            settled = np.abs(drag - prev) < settle * np.abs(drag)
+            away = settled & ~ok & active
+            if away.any():
+                elsewhere |= away
+                restart_cold(np.flatnonzero(away), steps, st)
+        prev = drag.copy()
         if (done >= 0).all():
             break
     torch.cuda.synchronize()
     wall = time.perf_counter() - t0
     b.close()
-    return dict(steps=done, wall=wall, fallback=fallback, batch_steps=steps,
+    return dict(steps=done, wall=wall, fallback=fallback, elsewhere=elsewhere, batch_steps=steps,
                 drift=drift if net is not None and steps >= drift_steps else None)
