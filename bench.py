@@ -94,6 +94,9 @@ def parse():
     ap.add_argument("--galilean-density", type=float, default=1.5,
                     help="solid/fluid density ratio of --galilean (the paper's 1.003 and 1.03 "
                          "need the interpolated boundary)")
+    ap.add_argument("--precision-full", type=int, default=0, metavar="STEPS",
+                    help="precision study to STEPS steps on a 2048 x 1024 variant of the workload "
+                         "whose disks share one velocity (no overlaps)")
     ap.add_argument("--batch-only", action="store_true",
                     help="measure only the cylinder-sweep batch and print its record")
     ap.add_argument("--batch-warmup", type=int, default=100)
@@ -543,6 +546,54 @@ def run_precision_study(a, w, local, stream):
     return out
 
 
+def run_precision_full(a, local):
+    """Force error of the FP32 and FP16 deviation modes against the FP64 mode
+    up to a.precision_full steps, on the precision-study recipe with one
+    shared disk velocity (no overlaps, so every horizon is computable):
+    horizons 1, 10, 100, 1000 and on to the last; same error scales as
+    run_precision_study."""
+    import numpy as np
+    import torch
+
+    import paper_1303_0625_gb300 as G
+    import workloads as W
+
+    torch.cuda.set_device(local)
+    stream = torch.cuda.Stream()
+    w = W.precision_study_common_velocity()
+    n = a.precision_full
+    horizons = sorted({h for h in (1, 10, 100, 1000, 5000, 10000, n) if h <= n})
+    radii = np.array([s["r"] for s in w["solids"]])
+    f0 = 2.0 * radii / 3.0
+    t0 = time.time()
+    recs = {}
+    for prec in ("fp64", "fp32", "fp16"):
+        lat = G.Lattice.from_workload(w, precision=G.PRECISION_NAMES[prec], device=local,
+                                      stream=stream.cuda_stream, force_ring=1024)
+        lat.set_graph(100)
+        rows, done = [], 0
+        for h in horizons:  # the record of each horizon's step
+            lat.step(h - done - 1)
+            rows.append(lat.step_record(1)[0])
+            done = h
+        lat.sync()
+        lat.close()
+        recs[prec] = np.array(rows)  # [horizons][nsolid][2][3]
+    ref = recs["fp64"]
+    out = {"workload": f"{w['nx']}x{w['ny']} periodic, {len(w['solids'])} disks r 8-20 sharing "
+                       f"one velocity, tau {w['tau']:.6f}",
+           "reference": "fp64 mode on the GPU", "horizons": horizons,
+           "seconds": round(time.time() - t0, 1)}
+    for prec in ("fp32", "fp16"):
+        err = np.abs(recs[prec] - ref)
+        scale = np.empty_like(ref)
+        fmag = np.abs(ref).max(axis=0, keepdims=True)
+        scale[..., :2] = np.maximum(fmag[..., :2], f0[None, :, None, None])
+        scale[..., 2:] = np.maximum(fmag[..., 2:], (f0 * radii)[None, :, None, None])
+        out[prec] = [float("%.3g" % (err[k] / scale[0]).max()) for k in range(len(horizons))]
+    return out
+
+
 def run_batch_converge(a, local):
     """The 512-channel sweep run the way it is meant to be used: 100-step
     graph blocks with the convergence test (drag change below 1e-7 per 100
@@ -727,7 +778,8 @@ def run_warm_start(a, local):
                      trained_on=f"{len(train_cases)} channels (seed offset 5), "
                                 f"{int(data['x'].shape[0])} samples with mirrors, "
                                 f"{a.ws_epochs} epochs, Adam 1e-3 -> 1e-5",
-                     command=" ".join(sys.argv))
+                     command=f"python bench.py --warm-start --ws-train {a.ws_train} "
+                             f"--ws-test {a.ws_test} --ws-epochs {a.ws_epochs} --ws-save <path>")
             out["saved"] = a.ws_save
     test_all = W.warm_start_channels(a.ws_test, seed_offset=6)
     out.update(evaluate_warm_start(net, test_all, local))
@@ -967,6 +1019,9 @@ def main():
     elif a.galilean:
         if rank == 0:
             print(json.dumps(run_galilean(a, local)), flush=True)
+    elif a.precision_full:
+        if rank == 0:
+            print(json.dumps(run_precision_full(a, local)), flush=True)
     elif a.warm_start:
         if rank == 0:
             print(json.dumps(run_warm_start(a, local)), flush=True)

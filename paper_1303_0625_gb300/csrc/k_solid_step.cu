@@ -47,7 +47,6 @@ namespace {
 
 constexpr int SW_BLOCK = 256;
 constexpr int WARPS = SW_BLOCK / 32;
-constexpr int U = 4;                        // nodes a lane fetches at once
 constexpr double PI = 3.14159265358979323846;
 constexpr unsigned FULL = 0xffffffffu;
 
@@ -273,12 +272,6 @@ __device__ __forceinline__ void rows_of_i(int iy0, int iy1, int rc, int g, int &
     j1 = max(iy0, iy1) + rc + 1 + g;
 }
 
-// Rows a disk of radius r at Y0 (and Y1) can touch, with a margin of g.
-__device__ __forceinline__ void rows_of(double Y0, double Y1, double r, int g, int &j0, int &j1) {
-    j0 = (int)floor(fmin(Y0, Y1) - r) - g;
-    j1 = (int)ceil(fmax(Y0, Y1) + r) + g;
-}
-
 // Deals the nodes of rows j0..j1 (the ranges that rng(j, R) gives for each
 // row) to the lanes of the warp, U nodes per lane at a time: fetch(i, j, u)
 // is called for all U nodes of a lane first (to issue their loads together),
@@ -339,11 +332,6 @@ __device__ __forceinline__ void warp_nodes_n(int j0, int j1, int lane, RF &&rng,
     }
 }
 
-template <class RF, class FF, class PF>
-__device__ __forceinline__ void warp_nodes(int j0, int j1, int lane, RF &&rng, FF &&fetch,
-                                           PF &&process) {
-    warp_nodes_n<U>(j0, j1, lane, rng, fetch, process);
-}
 
 // ------------------------------------------------------------- forces
 
@@ -1191,27 +1179,38 @@ __device__ void phase_event(const StepParams &p, int e, int lane, void *fnew) {
         }
         warp_sum(jm);
         if (lane == 0) {
-            const double sgn = (code & 1) ? -1.0 : 1.0;  // fresh: from the solid; covered: to it
-            const double mx = (double)jm[0], my = (double)jm[1], mm = (double)jm[2];
-            double ux, uy, dx, dy;
-            if (P == LBM_FP64) {  // from the domain node at the nearest periodic image
-                point_velocity(L, b.xn, b.yn, b.vxn, b.vyn, b.omn, (double)x, (double)y, ux, uy,
-                               dx, dy);
-            } else {  // the node's unwrapped coordinates are in the centre's frame
-                dx = (double)ev.z - b.xn;
-                dy = (double)ev.w - b.yn;
-                ux = b.vxn - b.omn * dy;
-                uy = b.vyn + b.omn * dx;
+            // fresh: from the solid; covered: to it.  The node's momentum, its
+            // velocity relative to the boundary and its lever about the new
+            // centre in the arithmetic precision C (the FP64 mode from the
+            // domain node at the nearest periodic image; the deviation modes
+            // from the node's unwrapped coordinates and the split centre)
+            const C sgn = (code & 1) ? (C)-1 : (C)1;
+            const C mx = jm[0], my = jm[1], mm = jm[2];
+            C ux, uy, dx, dy;
+            if (P == LBM_FP64) {
+                double vx, vy, ddx, ddy;
+                point_velocity(L, b.xn, b.yn, b.vxn, b.vyn, b.omn, (double)x, (double)y, vx, vy,
+                               ddx, ddy);
+                ux = (C)vx;
+                uy = (C)vy;
+                dx = (C)ddx;
+                dy = (C)ddy;
+            } else {
+                dx = (C)(ev.z - b.ix1) - (C)b.fx1;
+                dy = (C)(ev.w - b.iy1) - (C)b.fy1;
+                const C vxn = (C)b.vxn, vyn = (C)b.vyn, omn = (C)b.omn;
+                ux = vxn - omn * dy;
+                uy = vyn + omn * dx;
             }
-            acc[0] += sgn * mx;
-            acc[1] += sgn * my;
-            acc[2] += sgn * (dx * my - dy * mx);
             // the Eq. 5 record's booking: the same, or relative to the boundary, m (u - v)
-            const double rx = p.relative_changes ? mx - mm * ux : mx;
-            const double ry = p.relative_changes ? my - mm * uy : my;
-            acc[3] += sgn * rx;
-            acc[4] += sgn * ry;
-            acc[5] += sgn * (dx * ry - dy * rx);
+            const C rx = p.relative_changes ? mx - mm * ux : mx;
+            const C ry = p.relative_changes ? my - mm * uy : my;
+            acc[0] = (double)(sgn * mx);
+            acc[1] = (double)(sgn * my);
+            acc[2] = (double)(sgn * (dx * my - dy * mx));
+            acc[3] = (double)(sgn * rx);
+            acc[4] = (double)(sgn * ry);
+            acc[5] = (double)(sgn * (dx * ry - dy * rx));
         }
     }
     if (lane == 0)

@@ -219,14 +219,6 @@ __device__ __forceinline__ bool solid_ok(const DSolid &b) {
            fabsf(b.ynf) < 1e9f && b.r2f > 0.f && b.r2f < 1e12f;
 }
 
-__device__ __forceinline__ Box box_union(Box a, Box b) {
-    Box u;
-    u.x0 = min(a.x0, b.x0);
-    u.y0 = min(a.y0, b.y0);
-    u.w = max(a.x0 + a.w, b.x0 + b.w) - u.x0;
-    u.h = max(a.y0 + a.h, b.y0 + b.h) - u.y0;
-    return u;
-}
 
 // (i - X)^2 + (j - Y)^2 <= r^2, each operation rounded once (no contraction)
 __device__ __forceinline__ bool inside_disk(int i, int j, double X, double Y, double r) {
@@ -251,22 +243,6 @@ __device__ __forceinline__ bool locate(const Lattice &L, int x, int y, int &xo, 
     xo = x;
     yo = y;
     return true;
-}
-
-// Coordinate reduced into [0, n) along a periodic axis.
-__device__ __forceinline__ double wrap_coord(double X, int n, bool periodic) {
-    if (!periodic) return X;
-    return X - (double)n * floor(X / (double)n);
-}
-
-// Separation from a centre already reduced into the domain to a point of the
-// domain, taken to the nearest periodic image by one conditional shift.
-__device__ __forceinline__ double near_image(double d, int n, bool periodic) {
-    if (periodic) {
-        if (d > 0.5 * n) d -= n;
-        else if (d < -0.5 * n) d += n;
-    }
-    return d;
 }
 
 // Inside test of node (i, j) for the disk (X, Y, r), decided exactly as the

@@ -187,15 +187,16 @@ def time_to_drag(cases, d_star, *, net=None, rel=1e-4, precision=L.LBM_FP32_DEV,
     """Steps and wall time until every case's Eq. 5 drag is within rel of
     d_star (the converged drag of the plain run), starting cold (net None)
     or warm from the network's prediction.  The plain run is the judge, and
-    a warm case falls back to it (a cold restart in a batch of its own,
-    charged with the steps it has taken):
+    a warm case falls back to it: its populations are reset to the plain
+    initial state in place (it keeps stepping in the batch, its count of
+    steps goes on):
       - after drift_steps, when its state is unstable, its drag not finite or
         its total mass has moved by more than drift_mass (relative);
       - whenever its drag has settled (changed by less than settle, relative,
         over `every` steps, the steady-state test of the plain run) away from
         d_star: it has reached another steady state.
     A case stops stepping once it is within rel of d_star.  The wall time
-    covers input assembly, inference, every step and the cold restarts."""
+    covers input assembly, inference and every step."""
     import torch
 
     dev = torch.device("cuda", device)
@@ -209,9 +210,14 @@ def time_to_drag(cases, d_star, *, net=None, rel=1e-4, precision=L.LBM_FP32_DEV,
     elsewhere = np.zeros(n, dtype=bool)
     mass0 = None
     if net is not None:
-        xin = inputs(b, cases, device)
+        # the plain initial state of every case, for the cold restarts
+        f_cold = torch.empty((n, 9, ny, nx), dtype=torch.float64, device=dev)
         torch.cuda.synchronize()
+        for k in range(n):
+            L.lbm_get_populations(b.case(k).handle, f_cold[k], on_device=True)
+        xin = inputs(b, cases, device)
         out = torch.empty((n, 3, ny, nx), dtype=torch.float32, device=dev)
+        torch.cuda.synchronize()
         for s in range(0, n, net.max_batch):
             e = min(n, s + net.max_batch)
             L.lbm_unet_forward(net.handle, xin[s:e], out[s:e], e - s, on_device=True)
@@ -225,22 +231,17 @@ def time_to_drag(cases, d_star, *, net=None, rel=1e-4, precision=L.LBM_FP32_DEV,
     prev = np.full(n, np.nan)
     steps = 0
 
-    def restart_cold(ids, at, st):
-        # the plain run of those cases, in a batch of their own; they leave this one
-        sub = [cases[k] for k in ids]
-        r = time_to_drag(sub, d_star[ids], rel=rel, precision=precision, every=every, cap=cap,
-                         device=device, stream=stream)
-        done[ids] = np.where(r["steps"] >= 0, r["steps"] + at, -1)
+    def restart_cold(ids):
+        for k in ids:
+            L.lbm_set_populations(b.case(k).handle, f_cold[k], on_device=True)
+        torch.cuda.synchronize()
         fallback[ids] = True
-        still = ids[st[ids] == L.LBM_CASE_ACTIVE]  # an unstable case has retired already
-        if len(still):
-            b.retire(still)
 
     while steps < cap:
         b.run(every)
         steps += every
         st, stp, drag = b.state()
-        active = (done < 0) & ~fallback & (st == L.LBM_CASE_ACTIVE)
+        active = (done < 0) & (st == L.LBM_CASE_ACTIVE)
         if net is not None and steps == drift_steps:
             drift = np.zeros(n)
             bad = []
@@ -250,9 +251,17 @@ def time_to_drag(cases, d_star, *, net=None, rel=1e-4, precision=L.LBM_FP32_DEV,
                 if st[k] == L.LBM_CASE_UNSTABLE or not np.isfinite(drag[k]) or \
                         not drift[k] <= drift_mass:
                     bad.append(k)
-            if bad:
-                restart_cold(np.array(bad), steps, st)
-                active &= ~fallback
+            bad = np.array(bad, dtype=np.int64)
+            if len(bad):
+                unstable = bad[st[bad] == L.LBM_CASE_UNSTABLE]
+                if len(unstable):  # retired by the batch: its plain run, in a batch of its own
+                    r = time_to_drag([cases[k] for k in unstable], d_star[unstable], rel=rel,
+                                     precision=precision, every=every, cap=cap, device=device,
+                                     stream=stream)
+                    done[unstable] = np.where(r["steps"] >= 0, r["steps"] + steps, -1)
+                    fallback[unstable] = True
+                restart_cold(bad[st[bad] == L.LBM_CASE_ACTIVE])
+                continue  # the restarted cases' drag is not yet meaningful
         ok = np.abs(drag - d_star) <= rel * np.abs(d_star)
         newly = ok & active
         done[newly] = steps
@@ -260,10 +269,10 @@ def time_to_drag(cases, d_star, *, net=None, rel=1e-4, precision=L.LBM_FP32_DEV,
             b.retire(np.flatnonzero(newly))
         if net is not None and steps > drift_steps:
             settled = np.abs(drag - prev) < settle * np.abs(drag)
-            away = settled & ~ok & active
+            away = settled & ~ok & active & ~fallback
             if away.any():
                 elsewhere |= away
-                restart_cold(np.flatnonzero(away), steps, st)
+                restart_cold(np.flatnonzero(away))
         prev = drag.copy()
         if (done >= 0).all():
             break

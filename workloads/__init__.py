@@ -108,6 +108,22 @@ def precision_study(nx=8192, ny=4096, ndisk=2000, *, tau=None, seed_offset=2, rm
                 body_force=(0.0, 0.0), rho_w_mode=RHOW_CONST, refill=1, solids=solids)
 
 
+def precision_study_common_velocity(nx=2048, ny=1024, ndisk=125, *, seed_offset=2, rmin=8.0,
+                                    rmax=20.0, vmax=0.05):
+    """The precision-study recipe with every disk given one velocity, drawn
+    with components uniform in [-vmax, vmax]: the disks keep their distances,
+    so none overlaps at any horizon (the independent velocities of
+    precision_study make disks overlap and trap fluid between them within a
+    few hundred steps).  Default: the disk density of the 8192 x 4096 /
+    2000-disk domain on a 2048 x 1024 domain."""
+    w = precision_study(nx, ny, ndisk, seed_offset=seed_offset, rmin=rmin, rmax=rmax, vmax=vmax)
+    rng = np.random.default_rng(BASE_SEED + seed_offset + 200)
+    vx, vy = (float(v) for v in rng.uniform(-vmax, vmax, size=2))
+    for d in w["solids"]:
+        d.update(vx=vx, vy=vy)
+    return w
+
+
 def perturbation(shape, seed, amplitude):
     """Seeded uniform noise in [-amplitude, amplitude] of the given shape."""
     rng = np.random.default_rng(BASE_SEED + 7919 * int(seed))
