@@ -55,6 +55,16 @@ lbm_status lbm_unet_create(const lbm_unet_config *cfg, lbm_unet **out);
 lbm_status lbm_unet_destroy(lbm_unet *net);
 const char *lbm_unet_last_error(const lbm_unet *net);
 
+/* Polls of an mbarrier before a wait of the tensor-core convolutions gives
+ * up (default 2^24; 0 gives up at the first wait).  A CTA whose wait gave up
+ * issues no further MMA, waits (at most 2^24 polls) for the MMAs it issued,
+ * frees its tensor memory and stores nothing; the next call that
+ * synchronises (a host-array forward, lbm_unet_gradients,
+ * lbm_unet_train_step with a loss) returns LBM_ETIMEOUT once and clears the
+ * flag.  The outputs and parameters of the calls since are then undefined:
+ * set them again.  LBM_EINVAL for polls < 0. */
+lbm_status lbm_unet_set_wait_limit(lbm_unet *net, int64_t polls);
+
 /* Number of floats in the parameter vector, and its FP32 master copy. */
 int64_t lbm_unet_param_count(const lbm_unet *net);
 lbm_status lbm_unet_get_params(lbm_unet *net, float *params, int32_t on_device);

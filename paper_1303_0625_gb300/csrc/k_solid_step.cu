@@ -1,32 +1,35 @@
-// Per-solid work of one step t -> t+1, in two launches.
+// Per-solid work of one step t -> t+1, in three launches.
 //
-// k_forces runs beside the advection-collision kernel of the step (both only
-// read the populations of time t, the owner map and the node flags), one warp
-// per solid: the momentum booked by the node-type changes of the previous
-// step (the solid's segment of the event list), the link sums of Eq. 4 and
-// Eq. 5 over every fluid-solid link of time t (Eq. 6 and Eq. 7) -> the force
-// record of t; the motion t -> t+1 (prescribed, or Newton-Euler on the Eq. 5
-// force; Eq. 4 when the context selects it for comparison); the largest
-// displacement of any solid since the last pair test.
-//
-// k_remask follows both, in one cooperative launch:
+// k_forces, one block per solid, and then k_ring run beside the
+// advection-collision kernel of the step: they read the populations of time
+// t, the owner map and the node flags (which that kernel also only reads),
+// and write nothing that it reads.
+//   k_forces: the momentum booked by the node-type changes of the previous
+//      step (the solid's segment of the event list), the link sums of Eq. 4
+//      and Eq. 5 over every fluid-solid link of time t (Eq. 6 and Eq. 7) ->
+//      the force record of t; the motion t -> t+1 (prescribed, or
+//      Newton-Euler on the Eq. 5 force; Eq. 4 when the context selects it for
+//      comparison); the largest displacement of any solid since the last
+//      pair test.
+//   k_ring, one warp per moving solid:
 //   P  only when some solid may have come within reach of another one since
-//      the last test: the near list of every moving solid, the solids whose
-//      centres are closer than r_s + r_q + NEAR_REACH + NEAR_MARGIN at t or
-//      t+1
-//   R  on the ring (old disk XOR new disk) of every moving solid: the owner
-//      at t and at t+1 from the geometry of the solid and of its near list
-//      (lowest id where disks overlap), so that no map of the old owners is
-//      kept; the owner map and the node flags of every node whose owner
-//      changed; covered and fresh nodes queued per warp in lane order and
-//      published as the solid's segment of the step's event list
-//   E  every warp of the grid takes events from the list: a fresh node is
-//      refilled by extrapolation (Sec. IV.B) from nodes fluid at t and at
-//      t+1; each event's momentum and torque go to its own slot; the moving
-//      solids' state becomes t+1; the clock advances.
-// The phases are separated by a grid-wide barrier whose wait is bounded.  A
-// node on the rings of several solids is written by each of their warps with
-// the same owner; flag bits are set and cleared atomically.
+//      the last test: the solid's near list, the solids whose centres are
+//      closer than r_s + r_q + NEAR_REACH + NEAR_MARGIN at t or t+1
+//   R  on the ring (old disk XOR new disk): the owner at t and at t+1 from
+//      the geometry of the solid and of its near list (lowest id where disks
+//      overlap), so that no map of the old owners is kept; every node whose
+//      owner changes goes to the step's change list; covered and fresh nodes
+//      are queued per warp in lane order and published as the solid's
+//      segment of the step's event list.
+// k_remask follows all three, in one cooperative launch:
+//   A  the change list into the owner map and the node flags (a node on the
+//      rings of several solids is listed by each with the same owner; flag
+//      bits are set and cleared atomically)
+//   E  after a grid-wide barrier whose wait is bounded: every warp of the grid
+//      takes events from the list: a fresh node is refilled by extrapolation
+//      (Sec. IV.B) from nodes fluid at t and at t+1; each event's momentum and
+//      torque go to its own slot; the moving solids' state becomes t+1; the
+//      clock advances.
 //
 // Work per solid follows its perimeter: the nodes near the ends of the disk's
 // chord in every row (FP32 bounds with a one-node margin) are dealt out to
@@ -641,7 +644,10 @@ __global__ void __launch_bounds__(FB, 6) k_forces(const StepParams p) {
     const bool lists_ok = p.near_id && ((volatile unsigned int *)p.bar)[3] == 0u;
     // the previous step's events are reached through the solids' segments;
     // the list fills again in this step's re-rasterisation
-    if (blockIdx.x == 0 && tid == 0 && p.ev_len) *p.ev_len = 0;
+    if (blockIdx.x == 0 && tid == 0 && p.ev_len) {
+        *p.ev_len = 0;
+        *p.chg_len = 0;
+    }
     if (tid == 0) s_disp = 0.f;
     for (int s = blockIdx.x; s < p.nsolid; s += gridDim.x) {
         DSolid &b = p.S[s];
@@ -968,12 +974,12 @@ __device__ bool near_at_t(const StepParams &p, const DSolid &b, int s, int x, in
 
 constexpr int EVENTS = SOLID_EVENTS;
 
-// Ring of solid s (phase R): owner and flags of every node whose owner
-// changes, and the covered and fresh nodes of s, queued per warp in lane
-// order and published as the solid's segment of the step's event list (to be
-// booked into the force record of t+1), each with its unwrapped coordinates
-// in the solid's frame.  No memory is read per node: the owners come from the
-// geometry.
+// Ring of solid s (phase R): every node whose owner changes, into the
+// step's change list, and the covered and fresh nodes of s, queued per warp
+// in lane order and published as the solid's segment of the step's event
+// list (to be booked into the force record of t+1), each with its unwrapped
+// coordinates in the solid's frame.  No memory is read per node: the owners
+// come from the geometry.
 __device__ void phase_ring(const StepParams &p, int s, int lane, long long t, int2 *queue,
                            int &qn) {
     DSolid &b = p.S[s];
@@ -1004,28 +1010,34 @@ __device__ void phase_ring(const StepParams &p, int s, int lane, long long t, in
             return true;
         },
         [&](int u, bool ok) {
-            bool covered = false, fresh = false;
+            bool covered = false, fresh = false, changed = false;
+            int2 chg;
             const int k = kk[u];
             if (ok) {
                 uint16_t was = w0[u] ? (uint16_t)s : FLUID, now = w0[u] ? FLUID : (uint16_t)s;
                 const int x = k % L.pitch, y = k / L.pitch;
                 near_owners(p, b, s, x, y, was, now);
                 if (was != now) {
-                    p.owner[k] = now;
+                    // the new owner; bit 16: the node's solidity flips, bit 17: to solid
                     const bool sn = now != FLUID;
-                    if (sn != (was != FLUID)) {
-                        // bit 0 of the node, bit d of the neighbour x + e_d
-                        flag_bit(p.flags, k, 0, sn);
-#pragma unroll
-                        for (int d = 1; d < 9; d++) {
-                            int xn, yn;
-                            if (wrap(iu[u] + cx(d), ju[u] + cy(d), xn, yn))
-                                flag_bit(p.flags, cell_of(L, xn, yn), d, sn);
-                        }
-                    }
+                    chg = make_int2(k, (int)now | (sn != (was != FLUID) ? (sn ? 0x30000 : 0x10000)
+                                                                         : 0));
+                    changed = true;
                 }
                 covered = was == FLUID && now == (uint16_t)s;
                 fresh = was == (uint16_t)s && now == FLUID;
+            }
+            // the change list, one atomic per warp
+            const unsigned cm = __ballot_sync(FULL, changed);
+            if (cm) {
+                int cb = 0;
+                if (lane == 0) cb = atomicAdd(p.chg_len, __popc(cm));
+                cb = __shfl_sync(FULL, cb, 0);
+                if (changed) {
+                    const int at = cb + __popc(cm & ((1u << lane) - 1u));
+                    if (at < p.chg_cap) p.chg[at] = chg;
+                    else atomicOr(p.status, 8);
+                }
             }
             // queue the covered and fresh nodes in lane order
             __syncwarp();
@@ -1243,8 +1255,8 @@ __device__ __forceinline__ void advance_solid(const Lattice &L, DSolid &b) {
     b.yf = b.ynf;
 }
 
-template <int P>
-__global__ void __launch_bounds__(SW_BLOCK, 4) k_remask(const StepParams p) {
+// P and R (beside the advection-collision kernel), one warp per moving solid.
+__global__ void __launch_bounds__(SW_BLOCK, 2) k_ring(const StepParams p) {
     __shared__ int2 queue[WARPS][EVENTS];
     __shared__ int qn[WARPS];
     __shared__ int4 tile_ipos[NEAR_TILE];
@@ -1254,42 +1266,68 @@ __global__ void __launch_bounds__(SW_BLOCK, 4) k_remask(const StepParams p) {
     // any more, and this launch does nothing (the host reports the time-out)
     if (*(volatile int *)p.status & 4) return;
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const long long t = *p.t;
+    const volatile unsigned int *ctl = p.bar;
+    // nothing changes the control words between the force kernel and k_remask
+    const bool pairs = ctl[3] != 0u || __uint_as_float(ctl[2]) >= 0.5f * NEAR_MARGIN;
+    if (pairs) phase_pairs_block(p, blockIdx.x * WARPS, tile_ipos, tile_fpos, tile_rad);
+    const int m = blockIdx.x * WARPS + wib;
+    if (m >= p.nmoving) return;
+    const int s = p.moving[m];
+    DSolid &b = p.S[s];
+    if (pairs && lane == 0) {  // the centres the near list was taken at
+        b.ixt = b.ix0;
+        b.iyt = b.iy0;
+        b.fxt = b.fx0;
+        b.fyt = b.fy0;
+    }
+    __syncwarp();
+    if (solid_ok(b)) phase_ring(p, s, lane, t, queue[wib], qn[wib]);
+    else if (lane == 0) atomicOr(p.status, 2);
+}
+
+// A and E (after the advection-collision kernel and k_ring), one cooperative
+// launch.
+template <int P>
+__global__ void __launch_bounds__(SW_BLOCK, 4) k_remask(const StepParams p) {
+    if (*(volatile int *)p.status & 4) return;
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int gw = blockIdx.x * WARPS + wib, nw = gridDim.x * WARPS;
     const int gt = blockIdx.x * SW_BLOCK + threadIdx.x, nt = gridDim.x * SW_BLOCK;
+    const Lattice &L = p.L;
     const long long t = *p.t;
     void *fnew = ((t + 1) & 1) ? p.f1 : p.f0;  // populations of time t+1
-    const volatile unsigned int *ctl = p.bar;
-    if (ctl[3] != 0u || __uint_as_float(ctl[2]) >= 0.5f * NEAR_MARGIN) {
-        // P: near lists, and the centres they were taken at
-        for (int base = blockIdx.x * WARPS; base < p.nmoving; base += nw)
-            phase_pairs_block(p, base, tile_ipos, tile_fpos, tile_rad);
-        for (int s = gt; s < p.nsolid; s += nt) {
-            DSolid &b = p.S[s];
-            b.xo = b.x;
-            b.yo = b.y;
-            b.ixt = b.ixo = b.ix0;
-            b.iyt = b.iyo = b.iy0;
-            b.fxt = b.fxo = b.fx0;
-            b.fyt = b.fyo = b.fy0;
+    // A: owners and flags of t+1
+    const int nchg = min(*(volatile int *)p.chg_len, p.chg_cap);
+    for (int c = gt; c < nchg; c += nt) {
+        const int2 q = p.chg[c];
+        const int k = q.x;
+        p.owner[k] = (uint16_t)(q.y & 0xFFFF);
+        if (q.y & 0x10000) {
+            // bit 0 of the node, bit d of the neighbour x + e_d
+            const bool sn = (q.y & 0x20000) != 0;
+            const int x = k % L.pitch, y = k / L.pitch;
+            flag_bit(p.flags, k, 0, sn);
+#pragma unroll
+            for (int d = 1; d < 9; d++) {
+                const int kn = neighbour(L, x, y, cx(d), cy(d));
+                if (kn >= 0) flag_bit(p.flags, kn, d, sn);
+            }
         }
-        if (!grid_sync(p)) return;
-        if (gt == 0) {
-            p.bar[2] = 0u;
-            p.bar[3] = 0u;
-        }
-    }
-    // R
-    for (int m = gw; m < p.nmoving; m += nw) {
-        const int s = p.moving[m];
-        if (solid_ok(p.S[s])) phase_ring(p, s, lane, t, queue[wib], qn[wib]);
-        else if (lane == 0) atomicOr(p.status, 2);
     }
     if (!grid_sync(p)) return;
-    if (gt == 0) *p.t = t + 1;  // every block has read t
+    if (gt == 0) {
+        *p.t = t + 1;  // every block has read t
+        volatile unsigned int *ctl = p.bar;
+        if (ctl[3] != 0u || __uint_as_float(ctl[2]) >= 0.5f * NEAR_MARGIN) {
+            ctl[2] = 0u;  // the pair test of this step has run
+            ctl[3] = 0u;
+        }
+    }
     // E: the step's covered and fresh nodes, dealt to every warp of the grid
     const int nev = min(*(volatile int *)p.ev_len, p.ev_cap);
     for (int e = gw; e < nev; e += nw) phase_event<P>(p, e, lane, fnew);
-    for (int m = gt; m < p.nmoving; m += nt) advance_solid(p.L, p.S[p.moving[m]]);
+    for (int m = gt; m < p.nmoving; m += nt) advance_solid(L, p.S[p.moving[m]]);
 }
 
 template <int P, bool LOCAL, bool BND>
@@ -1322,8 +1360,8 @@ cudaError_t launch_r(const StepParams &p, cudaStream_t st) {
             e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_remask<P>, SW_BLOCK, 0);
         if (e != cudaSuccess) return e;
     }
-    // every resident block: phase R takes one warp per moving solid, the
-    // events go to every warp
+    // every resident block: the changes go to every thread, the events to
+    // every warp
     int blocks = per_sm * sms;
     if (blocks < 1) blocks = 1;
     StepParams pp = p;
@@ -1563,6 +1601,12 @@ cudaError_t launch_forces(const StepParams &p, cudaStream_t st) {
         default: GBM_F(LBM_FP16_DEV);
     }
 #undef GBM_F
+}
+
+cudaError_t launch_ring(const StepParams &p, cudaStream_t st) {
+    if (p.nmoving == 0) return cudaSuccess;
+    k_ring<<<(p.nmoving + WARPS - 1) / WARPS, SW_BLOCK, 0, st>>>(p);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_remask(const StepParams &p, cudaStream_t st) {

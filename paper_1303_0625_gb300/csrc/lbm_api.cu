@@ -149,6 +149,12 @@ StepParams params(const lbm_ctx *c) {
                                                     (size_t)c->ev_cap * sizeof(int4))
                        : nullptr;
     p.ev_cap = c->ev_cap;
+    // the change list after the event list: twice its capacity
+    p.chg_len = c->ev_d ? static_cast<int *>(c->ev_d) + 1 : nullptr;
+    p.chg = c->ev_d ? reinterpret_cast<int2 *>(static_cast<char *>(c->ev_d) + 16 +
+                                               (size_t)c->ev_cap * (sizeof(int4) + 6 * sizeof(double)))
+                    : nullptr;
+    p.chg_cap = 2 * c->ev_cap;
     p.omega_f = (float)(1.0 / g.tau);
     p.body_xf = (float)g.body_force[0];
     p.body_yf = (float)g.body_force[1];
@@ -222,7 +228,8 @@ lbm_status upload_moving(lbm_ctx *c) {
     if (!c->moving.empty())
         CK(c, cudaMemcpyAsync(c->moving_d, c->moving.data(), c->moving.size() * sizeof(int),
                               cudaMemcpyHostToDevice, c->stream));
-    // event list of the per-solid kernel: SOLID_EVENTS per moving solid
+    // event list of the per-solid kernels: SOLID_EVENTS per moving solid (and
+    // the change list, twice as long)
     const long long need = (long long)c->moving.size() * gbm::SOLID_EVENTS;
     if (need > c->ev_cap) {
         long long cap = c->ev_cap ? c->ev_cap : 64LL * gbm::SOLID_EVENTS;
@@ -232,7 +239,8 @@ lbm_status upload_moving(lbm_ctx *c) {
         if (c->ev_d) CK(c, cudaFree(c->ev_d));
         c->ev_d = nullptr;
         c->ev_cap = 0;
-        CK(c, cudaMalloc(&c->ev_d, 16 + (size_t)cap * (sizeof(int4) + 6 * sizeof(double))));
+        CK(c, cudaMalloc(&c->ev_d, 16 + (size_t)cap * (sizeof(int4) + 6 * sizeof(double) +
+                                                     2 * sizeof(int2))));
         CK(c, cudaMemsetAsync(c->ev_d, 0, 16, c->stream));
         c->ev_cap = (int)cap;
     }
@@ -240,21 +248,25 @@ lbm_status upload_moving(lbm_ctx *c) {
     return LBM_OK;
 }
 
-// One step t -> t+1: the force kernel (force record of time t, motion) on the
-// side stream beside the advection-collision kernel, both after the previous
-// step; then the re-rasterisation of the moving solids, which advances t (or
-// a clock tick when no solid moves).
+// One step t -> t+1: the force kernel (force record of time t, motion) and
+// the ring kernel (the moving solids' owner changes and covered/fresh nodes,
+// listed) on the side stream beside the advection-collision kernel, all after
+// the previous step; then the re-rasterisation of the moving solids (the
+// changes applied, refill), which advances t (or a clock tick when no solid
+// moves).
 lbm_status enqueue_step(lbm_ctx *c, const StepParams &p, bool timed) {
     const bool fork = p.nsolid > 0 && c->overlap;
     if (fork) {
         CK(c, cudaEventRecord(c->fork, c->stream));
         CK(c, cudaStreamWaitEvent(c->side, c->fork, 0));
         CK(c, gbm::launch_forces(p, c->side));
+        CK(c, gbm::launch_ring(p, c->side));
         CK(c, cudaEventRecord(c->join, c->side));
-        c->launches++;
+        c->launches += p.nmoving > 0 ? 2 : 1;
     } else if (p.nsolid > 0) {
         CK(c, gbm::launch_forces(p, c->stream));
-        c->launches++;
+        CK(c, gbm::launch_ring(p, c->stream));
+        c->launches += p.nmoving > 0 ? 2 : 1;
     }
     if (timed) {
         if (c->ev_used + 2 > c->ev.size()) {

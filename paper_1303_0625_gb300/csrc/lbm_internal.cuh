@@ -127,6 +127,10 @@ struct StepParams {
     double *ev_mom;           // [6] momentum and torque of each event: Eq. 4, Eq. 5 booking
     int *ev_len;              // events published this step (cleared after use)
     int ev_cap;
+    int2 *chg;                // owner changes of the step: {cell, new owner | bit 16: the
+                              // solidity flips | bit 17: to solid}
+    int *chg_len;             // changes listed this step (cleared with ev_len)
+    int chg_cap;
     int *bnd;                 // deferred per-node path: {length at even t, at odd t, list...}
     int bnd_cap;              // capacity of the list
     int list_by_forces;       // the force kernel fills the deferred list; the fused pass
@@ -376,11 +380,14 @@ cudaError_t launch_open_columns(const StepParams &p, cudaStream_t st);
 cudaError_t launch_stream_collide_batch(const BatchLaunch &b, cudaStream_t st);
 int tile_nodes(int precision, int variant);  // nodes along x of one tile
 // k_solid_step.cu: per-solid work of a step t -> t+1.  launch_forces: force
-// record of time t and motion t -> t+1 of every solid (it only reads what the
-// advection-collision kernel of the step reads, so it may run beside it);
-// launch_remask, after both: re-rasterisation of the moving solids, refill,
-// t += 1 (one cooperative launch).
+// record of time t and motion t -> t+1 of every solid; launch_ring after it:
+// near lists when due, the moving solids' owner changes and covered/fresh
+// nodes, listed (both only read what the advection-collision kernel of the
+// step reads and write nothing it reads, so they may run beside it);
+// launch_remask, after all three: the owner changes applied, refill, t += 1
+// (one cooperative launch).
 cudaError_t launch_forces(const StepParams &p, cudaStream_t st);
+cudaError_t launch_ring(const StepParams &p, cudaStream_t st);
 cudaError_t launch_remask(const StepParams &p, cudaStream_t st);
 // batch: force record of every resting solid of every active case, t += 1
 cudaError_t launch_solids_batch(const BatchLaunch &b, cudaStream_t st);

@@ -292,11 +292,12 @@ struct WgradOp {
 // tcgen05.mma.kind::f16 (M = 128, N = BN, K = 16; BF16 in, FP32 accumulate)
 // and commits them to the stage's mbarrier.  TC_STAGES stages: the copies of
 // the next blocks are in flight while the tensor cores work.  Every mbarrier
-// wait is bounded; a wait that runs out sets *err and the tile's results are
-// not stored.
+// wait is bounded (by the network's wait limit, a number of polls); a wait
+// that runs out stops the pipeline, the CTA waits (bounded by TC_SPIN) for the
+// MMAs it has issued, frees its tensor memory, sets *err and stores nothing.
 constexpr int TC_M = 128, TC_K = 64, TC_THREADS = 256, TC_STAGES = 3;
 constexpr int TC_TABLE_MAX = 8192;  // bytes of the A operand's K table (K up to 8192)
-constexpr int TC_SPIN = 1 << 24;
+constexpr long long TC_SPIN = 1 << 24;
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
     return (uint32_t)__cvta_generic_to_shared(p);
@@ -312,9 +313,9 @@ __device__ __forceinline__ uint64_t tc_desc(uint32_t addr) {
     return d;
 }
 
-__device__ __forceinline__ bool tc_wait(uint32_t mbar, uint32_t parity) {
+__device__ __forceinline__ bool tc_wait(uint32_t mbar, uint32_t parity, long long limit) {
     uint32_t done = 0;
-    for (int it = 0; it < TC_SPIN && !done; it++)
+    for (long long it = 0; it < limit && !done; it++)
         asm volatile(
             "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
             "selp.u32 %0, 1, 0, p;\n}\n"
@@ -335,14 +336,20 @@ __device__ __forceinline__ void cp16(uint32_t dst, const void *src, const void *
 // filled with cp.async by every thread (stage(i, addr) copies K block i; it is
 // called for i = 0, 1, 2, ... in order), one thread issuing a block's four
 // K = 16 MMAs (mma(addr, accumulate)) and committing them to the stage's
-// mbarrier, which is waited for (bounded) before the stage is refilled.  The
-// block of iteration j completes phase j / TC_STAGES of barrier j % TC_STAGES,
-// and every barrier has at most one phase outstanding when it is waited for.
-// Returns false when a wait gave up.
+// mbarrier, which is waited for (at most `limit` polls) before the stage is
+// refilled.  The block of iteration j completes phase j / TC_STAGES of barrier
+// j % TC_STAGES, and every barrier has at most one phase outstanding when it
+// is waited for.  A wait that gives up in any thread ends the pipeline before
+// the next MMA (no stage is refilled while the tensor cores may read it);
+// the issuing thread then commits once more to the drain barrier
+// mbar[TC_STAGES], which completes when every MMA it issued has, and the CTA
+// waits for that (at most TC_SPIN polls) before its tensor memory is read or
+// freed.  Returns false, in every thread, when a wait gave up.
 template <int STAGE, class StageFn, class MmaFn>
 __device__ __forceinline__ bool tc_pipeline(int nk, uint32_t base, uint64_t *mbar, int tid,
-                                            StageFn &&stage, MmaFn &&mma) {
+                                            long long limit, StageFn &&stage, MmaFn &&mma) {
     bool ok = true;
+    int issued = 0;  // K blocks whose MMAs were issued (the same in every thread)
 #pragma unroll
     for (int st = 0; st < TC_STAGES - 1; st++) {
         if (st < nk) stage(st, base + st * STAGE);
@@ -352,7 +359,7 @@ __device__ __forceinline__ bool tc_pipeline(int nk, uint32_t base, uint64_t *mba
         const int s = kt % TC_STAGES;
         asm volatile("cp.async.wait_group %0;\n" ::"n"(TC_STAGES - 2) : "memory");
         asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-        __syncthreads();
+        if (__syncthreads_or(!ok)) break;
         if (tid == 0) {
             asm volatile("tcgen05.fence::after_thread_sync;\n");
             mma(base + s * STAGE, kt > 0);
@@ -360,17 +367,29 @@ __device__ __forceinline__ bool tc_pipeline(int nk, uint32_t base, uint64_t *mba
                 "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
                     smem_u32(&mbar[s])));
         }
+        issued = kt + 1;
         // refill the stage of block kt - 1 once its MMAs are done
         const int nxt = kt + TC_STAGES - 1;
         if (nxt < nk) {
-            if (kt > 0) ok &= tc_wait(smem_u32(&mbar[(kt - 1) % TC_STAGES]), ((kt - 1) / TC_STAGES) & 1);
-            stage(nxt, base + (nxt % TC_STAGES) * STAGE);
+            if (kt > 0)
+                ok &= tc_wait(smem_u32(&mbar[(kt - 1) % TC_STAGES]), ((kt - 1) / TC_STAGES) & 1,
+                              limit);
+            if (ok) stage(nxt, base + (nxt % TC_STAGES) * STAGE);
         }
         asm volatile("cp.async.commit_group;\n" ::: "memory");
     }
     // blocks max(nk - TC_STAGES, 0) .. nk - 1 have not been waited for
-    for (int j = nk > TC_STAGES ? nk - TC_STAGES : 0; j < nk; j++)
-        ok &= tc_wait(smem_u32(&mbar[j % TC_STAGES]), (j / TC_STAGES) & 1);
+    if (issued == nk)
+        for (int j = nk > TC_STAGES ? nk - TC_STAGES : 0; j < nk; j++)
+            ok &= tc_wait(smem_u32(&mbar[j % TC_STAGES]), (j / TC_STAGES) & 1, limit);
+    ok = __syncthreads_and(ok);
+    if (!ok) {
+        if (tid == 0)
+            asm volatile(
+                "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                    smem_u32(&mbar[TC_STAGES])));
+        tc_wait(smem_u32(&mbar[TC_STAGES]), 0, TC_SPIN);
+    }
     asm volatile("cp.async.wait_group 0;\n" ::: "memory");
     asm volatile("tcgen05.fence::after_thread_sync;\n");
     return ok;
@@ -384,7 +403,7 @@ __device__ __forceinline__ void tc_alloc(uint32_t *slot, uint64_t *mbar, int nco
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
     }
     if (tid == 0) {
-        for (int s = 0; s < TC_STAGES; s++)
+        for (int s = 0; s <= TC_STAGES; s++)
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&mbar[s])));
         asm volatile("fence.mbarrier_init.release.cluster;\n");
     }
@@ -441,10 +460,10 @@ __device__ __forceinline__ void conv_table(const ConvOp &op, int2 *tab, int nent
 }
 
 template <int BN>
-__global__ void __launch_bounds__(TC_THREADS) k_conv_tc(const ConvOp op, int *err) {
+__global__ void __launch_bounds__(TC_THREADS) k_conv_tc(const ConvOp op, long long limit, int *err) {
     extern __shared__ __align__(1024) unsigned char smem[];
     __shared__ uint32_t tmem_base;
-    __shared__ __align__(8) uint64_t mbar[TC_STAGES];
+    __shared__ __align__(8) uint64_t mbar[TC_STAGES + 1];  // the stages' and the drain barrier
     constexpr int STAGE = TC_M * TC_K * 2 + BN * TC_K * 2;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int m0 = blockIdx.x * TC_M, n0 = blockIdx.y * BN;
@@ -500,7 +519,7 @@ __global__ void __launch_bounds__(TC_THREADS) k_conv_tc(const ConvOp op, int *er
             tc_mma(tmem, tc_desc(sa + ks * 256), tc_desc(sb + ks * 256), idesc,
                    (accumulate || ks > 0) ? 1u : 0u);
     };
-    const bool ok = tc_pipeline<STAGE>(nk, base, mbar, tid, stage, mma);
+    const bool ok = tc_pipeline<STAGE>(nk, base, mbar, tid, limit, stage, mma);
     if (!ok) atomicOr(err, 1);
     // epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31, columns of half w / 4
     const int row = m0 + (warp & 3) * 32 + lane, cb = (warp >> 2) * (BN / 2);
@@ -529,10 +548,10 @@ struct WgradTc {
 };
 
 template <int BN>
-__global__ void __launch_bounds__(TC_THREADS) k_wgrad_tc(const WgradTc op, int *err) {
+__global__ void __launch_bounds__(TC_THREADS) k_wgrad_tc(const WgradTc op, long long limit, int *err) {
     extern __shared__ __align__(1024) unsigned char smem[];
     __shared__ uint32_t tmem_base;
-    __shared__ __align__(8) uint64_t mbar[TC_STAGES];
+    __shared__ __align__(8) uint64_t mbar[TC_STAGES + 1];  // the stages' and the drain barrier
     constexpr int STAGE = TC_M * TC_K * 2 + BN * TC_K * 2;
     constexpr int AG = TC_M * TC_K / 8 / TC_THREADS, BG = BN * TC_K / 8 / TC_THREADS;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -607,7 +626,7 @@ __global__ void __launch_bounds__(TC_THREADS) k_wgrad_tc(const WgradTc op, int *
             tc_mma(tmem, ad, bd, idesc, (accumulate || ks > 0) ? 1u : 0u);
         }
     };
-    const bool ok = tc_pipeline<STAGE>(nk, base, mbar, tid, stage, mma);
+    const bool ok = tc_pipeline<STAGE>(nk, base, mbar, tid, limit, stage, mma);
     if (!ok) atomicOr(err, 1);
     const int m = m0 + (warp & 3) * 32 + lane, cb = (warp >> 2) * (BN / 2);
 #pragma unroll
@@ -946,6 +965,7 @@ struct lbm_unet {
     float *cnt = nullptr;
     double *loss = nullptr;
     int *err_d = nullptr;    // bit 0: a bounded wait of a tensor-core kernel ran out
+    long long wait_limit = nn::TC_SPIN;  // polls of an mbarrier before a wait gives up
     int sms = 0;             // streaming multiprocessors of the device
     long long adam_t = 0;
     std::string err;
@@ -1024,7 +1044,7 @@ cudaError_t launch_tc(lbm_unet *n, const nn::ConvOp &op) {
         attr = true;
     }
     const dim3 grid((op.M + nn::TC_M - 1) / nn::TC_M, (op.N + BN - 1) / BN);
-    nn::k_conv_tc<BN><<<grid, nn::TC_THREADS, stages + table, n->stream>>>(op, n->err_d);
+    nn::k_conv_tc<BN><<<grid, nn::TC_THREADS, stages + table, n->stream>>>(op, n->wait_limit, n->err_d);
     return cudaGetLastError();
 }
 
@@ -1089,7 +1109,7 @@ cudaError_t launch_wg(lbm_unet *n, const nn::WgradTc &op, int z) {
         attr = true;
     }
     const dim3 grid((op.M + nn::TC_M - 1) / nn::TC_M, (op.N + BN - 1) / BN, z);
-    nn::k_wgrad_tc<BN><<<grid, nn::TC_THREADS, smem, n->stream>>>(op, n->err_d);
+    nn::k_wgrad_tc<BN><<<grid, nn::TC_THREADS, smem, n->stream>>>(op, n->wait_limit, n->err_d);
     return cudaGetLastError();
 }
 
@@ -1455,6 +1475,12 @@ lbm_status lbm_unet_destroy(lbm_unet *n) {
 }
 
 const char *lbm_unet_last_error(const lbm_unet *n) { return n ? n->err.c_str() : g_nn_error.c_str(); }
+
+lbm_status lbm_unet_set_wait_limit(lbm_unet *n, int64_t polls) {
+    if (!n || polls < 0) return LBM_EINVAL;
+    n->wait_limit = (long long)polls;
+    return LBM_OK;
+}
 
 int64_t lbm_unet_param_count(const lbm_unet *n) {
     if (!n) return -1;

@@ -125,6 +125,7 @@ _SIGNATURES = {
     "lbm_batch_last_error": (ctypes.c_char_p, [_P]),
     "lbm_unet_create": (_I32, [ctypes.POINTER(lbm_unet_config), ctypes.POINTER(_P)]),
     "lbm_unet_destroy": (_I32, [_P]),
+    "lbm_unet_set_wait_limit": (_I32, [_P, _I64]),
     "lbm_unet_last_error": (ctypes.c_char_p, [_P]),
     "lbm_unet_param_count": (_I64, [_P]),
     "lbm_unet_get_params": (_I32, [_P, _P, _I32]),
@@ -460,6 +461,10 @@ def lbm_unet_destroy(net):
     _ncheck(load().lbm_unet_destroy(net), net)
 
 
+def lbm_unet_set_wait_limit(net, polls: int):
+    _ncheck(load().lbm_unet_set_wait_limit(net, int(polls)), net)
+
+
 def lbm_unet_param_count(net) -> int:
     return int(load().lbm_unet_param_count(net))
 
@@ -533,6 +538,9 @@ class UNet:
     @property
     def nparam(self) -> int:
         return lbm_unet_param_count(self._h)
+
+    def set_wait_limit(self, polls: int):
+        lbm_unet_set_wait_limit(self._h, polls)
 
     def params(self) -> np.ndarray:
         out = np.empty(self.nparam, dtype=np.float32)

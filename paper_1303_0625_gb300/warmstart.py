@@ -35,6 +35,14 @@ import numpy as np
 from . import lbm as L
 
 
+# The reference of the time-to-drag measurement: the plain run converged to
+# REF_TOL relative drag change per 100 steps (with an exponential approach of
+# decay time T its drag is then within REF_TOL * T / 100 of the steady value:
+# 1e-4 for T up to 1e6 steps), at most REF_CAP steps.
+REF_TOL = 1e-8
+REF_CAP = 600_000
+
+
 def poiseuille(case):
     """(rho_P [ny][nx], u_P [ny]) of the case's empty channel."""
     nx, ny = case["nx"], case["ny"]
@@ -182,8 +190,8 @@ def _mass(ctx):
 
 
 def time_to_drag(cases, d_star, *, net=None, rel=1e-4, precision=L.LBM_FP32_DEV, every=100,
-                 cap=300_000, drift_steps=200, drift_mass=1e-2, settle=1e-7, device=0,
-                 stream=None):
+                 cap=300_000, drift_steps=200, drift_mass=1e-2, settle=1e-7, settle_checks=20,
+                 device=0, stream=None):
     """Steps and wall time until every case's Eq. 5 drag is within rel of
     d_star (the converged drag of the plain run), starting cold (net None)
     or warm from the network's prediction.  The plain run is the judge, and
@@ -192,9 +200,11 @@ def time_to_drag(cases, d_star, *, net=None, rel=1e-4, precision=L.LBM_FP32_DEV,
     steps goes on):
       - after drift_steps, when its state is unstable, its drag not finite or
         its total mass has moved by more than drift_mass (relative);
-      - whenever its drag has settled (changed by less than settle, relative,
-        over `every` steps, the steady-state test of the plain run) away from
-        d_star: it has reached another steady state.
+      - whenever its drag has settled away from d_star (changed by less than
+        settle, relative, over each of the last settle_checks blocks of
+        `every` steps; a single block is not enough: an oscillating drag
+        passes that test at its turning points): it has reached another
+        steady state.
     A case stops stepping once it is within rel of d_star.  The wall time
     covers input assembly, inference and every step."""
     import torch
@@ -229,6 +239,7 @@ def time_to_drag(cases, d_star, *, net=None, rel=1e-4, precision=L.LBM_FP32_DEV,
     done = np.full(n, -1, dtype=np.int64)
     drift = None
     prev = np.full(n, np.nan)
+    calm = np.zeros(n, dtype=np.int64)  # consecutive blocks with a settled drag
     steps = 0
 
     def restart_cold(ids):
@@ -236,6 +247,7 @@ def time_to_drag(cases, d_star, *, net=None, rel=1e-4, precision=L.LBM_FP32_DEV,
             L.lbm_set_populations(b.case(k).handle, f_cold[k], on_device=True)
         torch.cuda.synchronize()
         fallback[ids] = True
+        calm[ids] = 0
 
     while steps < cap:
         b.run(every)
@@ -269,7 +281,8 @@ def time_to_drag(cases, d_star, *, net=None, rel=1e-4, precision=L.LBM_FP32_DEV,
             b.retire(np.flatnonzero(newly))
         if net is not None and steps > drift_steps:
             settled = np.abs(drag - prev) < settle * np.abs(drag)
-            away = settled & ~ok & active & ~fallback
+            calm = np.where(settled, calm + 1, 0)
+            away = (calm >= settle_checks) & ~ok & active & ~fallback
             if away.any():
                 elsewhere |= away
                 restart_cold(np.flatnonzero(away))

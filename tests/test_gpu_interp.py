@@ -54,7 +54,7 @@ def test_interpolated_every_launch_variant_fp64(variant):
     launches = g.launch_count()
     g.step(1)
     g.sync()
-    assert g.launch_count() - launches == 4  # forces, fused, update, re-rasterisation
+    assert g.launch_count() - launches == 5  # forces, ring, fused, update, re-rasterisation
 
 
 @pytest.mark.gpu

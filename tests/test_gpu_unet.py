@@ -141,3 +141,31 @@ def test_warm_start_sets_the_predicted_equilibrium():
     rho, ux, uy = lat.fields()
     assert np.allclose(rho[fl], (rp + R * pred[0])[fl], atol=2e-6)
     assert np.allclose(ux[fl], (up[:, None] + U_ * pred[1])[fl], atol=2e-6)
+
+
+def test_wait_time_out_is_reported_and_the_network_recovers():
+    """A wait limit of 0 makes the mbarrier waits of every tensor-core
+    convolution give up at once: each CTA stops issuing MMAs, waits for the
+    ones it issued, frees its tensor memory and stores nothing; the host gets
+    LBM_ETIMEOUT, and with the limit restored the network computes as
+    before (the forward pass bit for bit; the weight gradients, summed with
+    FP32 atomics across pixel splits, to rounding)."""
+    net, p, x, t, fl = _case(3, 16, 32, 64, 2, seed=11)
+    ref = net.forward(x)
+    loss_ref, g_ref = net.gradients(x, t, fl)
+    net.set_wait_limit(0)
+    with pytest.raises(G.LBMError) as e:
+        net.forward(x)
+    assert e.value.status == G.LBM_ETIMEOUT
+    with pytest.raises(G.LBMError) as e:
+        net.gradients(x, t, fl)
+    assert e.value.status == G.LBM_ETIMEOUT
+    with pytest.raises(G.LBMError) as e:
+        net.set_wait_limit(-1)
+    assert e.value.status == G.LBM_EINVAL
+    net.set_wait_limit(1 << 24)
+    assert np.array_equal(net.forward(x), ref)
+    loss, g = net.gradients(x, t, fl)
+    assert abs(loss - loss_ref) <= 1e-6 * abs(loss_ref)
+    assert _rel(g, g_ref) <= 1e-5
+    net.close()
