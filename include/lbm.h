@@ -361,6 +361,15 @@ lbm_status lbm_batch_add_solid(lbm_batch *b, int32_t k, const lbm_disk *d, int32
  * solids has D = 0 and never converges.  The drag history restarts. */
 lbm_status lbm_batch_set_convergence(lbm_batch *b, int32_t every, double tol, int64_t max_steps);
 
+/* Number of tests in a row whose drag must stay within tol (relative) of the
+ * drag at the test before them for a case to retire as converged (default 1:
+ * the test as stated above).  A single test also passes at a turning point of
+ * an oscillating drag, and in FP32 storage the drag's round-off noise (a few
+ * 1e-7 per 100 steps) decides whether a tolerance below it ever passes; a
+ * band held over many tests does neither.  The drag history restarts.
+ * LBM_EINVAL for tests < 1. */
+lbm_status lbm_batch_set_convergence_window(lbm_batch *b, int32_t tests);
+
 /* Advance every active case by up to `steps` steps (fewer when all cases
  * retire first; the test runs whenever the batch has done `every` steps since
  * the previous one).  *nactive (when not NULL) receives the number of active

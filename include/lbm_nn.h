@@ -107,17 +107,25 @@ lbm_status lbm_unet_input(lbm_unet *net, const int32_t *owner_device, double rey
  * Enqueued on the context's stream.  LBM_EINVAL for Re <= 0. */
 lbm_status lbm_case_input(lbm_ctx *ctx, double reynolds, float *in_device);
 
+/* Flags of lbm_warm_start. */
+enum { LBM_WS_BASE = 1, LBM_WS_FLUX = 2 };
+
 /* Initial state of ctx from a network output [3][H][W] (device floats):
  * at every fluid node f = f^eq(rho, u) (Eq. 8) with
- *   rho = 1 + rho_scale p0, u = u_scale (p1, p2)                      (base 0)
- *   rho = rho_P(x) + rho_scale p0, u = (u_P(y), 0) + u_scale (p1, p2) (base 1)
+ *   rho = 1 + rho_scale p0, u = u_scale (p1, p2)                  (flags 0)
+ *   rho = rho_P(x) + rho_scale p0, u = (u_P(y), 0) + u_scale (p1, p2)
+ *                                                        (LBM_WS_BASE)
  * where (rho_P, u_P) is the empty channel's Poiseuille flow of the context
  * (bc_x = LBM_OPEN): u_P = the inlet parabola, rho_P = rho0 + 24 nu umax
  * (nx - 1 - x) / ny^2 (the pressure drop of that flow, rho0 at the outlet),
- * nu = (tau - 1/2) / 3.  The domain must be H x W; solid nodes keep their
- * state. */
+ * nu = (tau - 1/2) / 3.  With LBM_WS_BASE | LBM_WS_FLUX, u_x of every
+ * column is then scaled so that the column's mass flux sum_y rho u_x over
+ * its fluid nodes equals the inlet's, sum over column 0 of rho u_P (a steady
+ * flow carries that flux through every column).  The domain must be H x W;
+ * solid nodes keep their state.  LBM_EINVAL for other flags, or a base
+ * without an open channel. */
 lbm_status lbm_warm_start(lbm_ctx *ctx, const float *prediction_device, double u_scale,
-                          double rho_scale, int32_t base);
+                          double rho_scale, int32_t flags);
 
 #ifdef __cplusplus
 }

@@ -428,13 +428,12 @@ __device__ void move_solid(const StepParams &p, int s, int lane, long long t, co
 // f~_i(x_f), the bounced f_bb = f_i - 6 w_i rho_w (e_i . v) with v the
 // solid's velocity at x_s = x_f + e_i / 2; Eq. 4 = e_i f_i - e_opp f_bb,
 // Eq. 5 = (e_i - v) f_i - (e_opp - v) f_bb, torque (x_s - R) x F (Eq. 7).
-// BND: the interpolated boundary, whose links return the interpolated
-// population and use the velocity and lever arm at the cut.  A candidate
-// node's flags and its 9 populations are loaded together, with its 8
+// (The batch's disks take the half-way boundary.)  A candidate node's flags
+// and its 9 populations are loaded together, with its 8
 // neighbours' owners unless lists_ok and the solid has no other solid within
 // reach (then every solid neighbour of the annulus is the solid's own: a
 // solid q holding a node within r_s + 4 of s's centre is in s's near list).
-template <int P, bool LOCAL, bool BND>
+template <int P, bool LOCAL>
 __device__ void forces_sum(const StepParams &p, int s, int lane, const void *f, int wi, int nw,
                            bool lists_ok, double (&acc)[6]) {
     using C = typename Prec<P>::C;
@@ -443,7 +442,7 @@ __device__ void forces_sum(const StepParams &p, int s, int lane, const void *f, 
     // with rho_w = rho0 and the half-way boundary a link needs only f_i of its
     // own direction: the flags come first and only the bounced directions'
     // populations (and owners) are read; otherwise all nine with the flags
-    constexpr bool SPARSE = !LOCAL && !BND;
+    constexpr bool SPARSE = !LOCAL;
     const DSolid &b = p.S[s];
     const Lattice &L = p.L;
     const S *fs = static_cast<const S *>(f);
@@ -508,50 +507,19 @@ __device__ void forces_sum(const StepParams &p, int s, int lane, const void *f, 
 #pragma unroll
             for (int i = 1; i < 9; i++) {
                 if (!linked(u, i)) continue;
-                C dx, dy, ux, uy, fbb;
+                C dx, dy;
                 C fi = (C)cvt_s(fv[u][i]);
                 if (Prec<P>::dev) fi += wgt<C>(i);
-                if (BND) {
-                    // the cut at fraction q of the link, and the population that
-                    // returns to x_f along e_opp by the fused kernel's
-                    // interpolation (full populations; M = 6 w rho_w (e_opp . v))
-                    int x, y;
-                    locate(L, iu, j, x, y);
-                    const double q = link_fraction(L, b, x, y, i);
-                    double vxd, vyd, ddx, ddy;
-                    point_velocity(L, b.x, b.y, b.vx, b.vy, b.om, (double)x + q * cx(i),
-                                   (double)y + q * cy(i), vxd, vyd, ddx, ddy);
-                    dx = (C)ddx;
-                    dy = (C)ddy;
-                    ux = (C)vxd;
-                    uy = (C)vyd;
-                    const C mw = -(C)6 * wgt<C>(i) * rho_w * ((C)cx(i) * ux + (C)cy(i) * uy);
-                    C fo = (C)cvt_s(fv[u][opp(i)]);
-                    if (Prec<P>::dev) fo += wgt<C>(i);
-                    if (q >= 0.5) {
-                        fbb = (fi + mw) / (C)(2.0 * q) + (C)((2.0 * q - 1.0) / (2.0 * q)) * fo;
-                    } else if (!((m >> i) & 1u)) {  // x_f - e_i is a fluid node
-                        int xn, yn;
-                        locate(L, x - cx(i), y - cy(i), xn, yn);
-                        C fn = (C)cvt_s(fs[i * plane + (int)cell_of(L, xn, yn)]);
-                        if (Prec<P>::dev) fn += wgt<C>(i);
-                        fbb = (C)(2.0 * q) * fi + (C)(1.0 - 2.0 * q) * fn + mw;
-                    } else {
-                        fbb = fi + mw;
-                    }
+                // x_s = x_f + e_i / 2 relative to R, from the unwrapped coordinate
+                if (Prec<P>::dev) {
+                    dx = (C)(iu - c.xi) + (C)(0.5f * cx(i)) - (C)c.fx;
+                    dy = (C)(j - c.yi) + (C)(0.5f * cy(i)) - (C)c.fy;
                 } else {
-                    // x_s = x_f + e_i / 2 relative to R, from the unwrapped coordinate
-                    if (Prec<P>::dev) {
-                        dx = (C)(iu - c.xi) + (C)(0.5f * cx(i)) - (C)c.fx;
-                        dy = (C)(j - c.yi) + (C)(0.5f * cy(i)) - (C)c.fy;
-                    } else {
-                        dx = (C)(((double)iu + 0.5 * cx(i)) - X);
-                        dy = (C)(((double)j + 0.5 * cy(i)) - Y);
-                    }
-                    ux = vx - om * dy;
-                    uy = vy + om * dx;
-                    fbb = fi - (C)6 * wgt<C>(i) * rho_w * ((C)cx(i) * ux + (C)cy(i) * uy);
+                    dx = (C)(((double)iu + 0.5 * cx(i)) - X);
+                    dy = (C)(((double)j + 0.5 * cy(i)) - Y);
                 }
+                const C ux = vx - om * dy, uy = vy + om * dx;
+                const C fbb = fi - (C)6 * wgt<C>(i) * rho_w * ((C)cx(i) * ux + (C)cy(i) * uy);
                 const C cmx = (C)cx(i) * fi - (C)cx(opp(i)) * fbb;
                 const C cmy = (C)cy(i) * fi - (C)cy(opp(i)) * fbb;
                 const C gmx = ((C)cx(i) - ux) * fi - ((C)cx(opp(i)) - ux) * fbb;
@@ -765,27 +733,38 @@ __global__ void __launch_bounds__(FB, 6) k_forces(const StepParams p) {
                         // the cut at fraction q of the link, and the population that
                         // returns to x_f along e_opp by the fused kernel's
                         // interpolation (full populations; M = 6 w rho_w (e_opp . v))
-                        const double qf = link_fraction(L, b, x, y, i);
-                        double vxd, vyd, ddx, ddy;
-                        point_velocity(L, b.x, b.y, b.vx, b.vy, b.om, (double)x + qf * cx(i),
-                                       (double)y + qf * cy(i), vxd, vyd, ddx, ddy);
-                        dx = (C)ddx;
-                        dy = (C)ddy;
-                        ux = (C)vxd;
-                        uy = (C)vyd;
+                        C qf;
+                        if (Prec<P>::dev) {  // FP32 from the unwrapped offset, split
+                            qf = (C)link_fraction_split(iu - c.xi, jj - c.yi, c.fx, c.fy, b.r,
+                                                        cx(i), cy(i));
+                            dx = ((C)(iu - c.xi) - (C)c.fx) + qf * (C)cx(i);
+                            dy = ((C)(jj - c.yi) - (C)c.fy) + qf * (C)cy(i);
+                            ux = (C)b.vxf - (C)b.omf * dy;
+                            uy = (C)b.vyf + (C)b.omf * dx;
+                        } else {
+                            const double qd = link_fraction(L, b, x, y, i);
+                            double vxd, vyd, ddx, ddy;
+                            point_velocity(L, b.x, b.y, b.vx, b.vy, b.om, (double)x + qd * cx(i),
+                                           (double)y + qd * cy(i), vxd, vyd, ddx, ddy);
+                            qf = (C)qd;
+                            dx = (C)ddx;
+                            dy = (C)ddy;
+                            ux = (C)vxd;
+                            uy = (C)vyd;
+                        }
                         const C mw =
                             -(C)6 * wgt<C>(i) * rho_w * ((C)cx(i) * ux + (C)cy(i) * uy);
                         C fo = (C)cvt_s(fv[opp(i)]);
                         if (Prec<P>::dev) fo += wgt<C>(i);
-                        if (qf >= 0.5) {
-                            fbb = (fi + mw) / (C)(2.0 * qf) +
-                                  (C)((2.0 * qf - 1.0) / (2.0 * qf)) * fo;
+                        const C q2 = (C)2 * qf;
+                        if (q2 >= (C)1) {
+                            fbb = (fi + mw) / q2 + ((q2 - (C)1) / q2) * fo;
                         } else if (!((m >> i) & 1u)) {  // x_f - e_i is a fluid node
                             int xn, yn;
                             locate(L, x - cx(i), y - cy(i), xn, yn);
                             C fn = (C)cvt_s(fs[i * plane + (int)cell_of(L, xn, yn)]);
                             if (Prec<P>::dev) fn += wgt<C>(i);
-                            fbb = (C)(2.0 * qf) * fi + (C)(1.0 - 2.0 * qf) * fn + mw;
+                            fbb = q2 * fi + ((C)1 - q2) * fn + mw;
                         } else {
                             fbb = fi + mw;
                         }
@@ -1398,7 +1377,7 @@ __global__ void __launch_bounds__(SW_BLOCK)
             continue;
         }
         double acc[6];
-        forces_sum<P, LOCAL, false>(p, it.y, lane, fcur, wib, WARPS, false, acc);
+        forces_sum<P, LOCAL>(p, it.y, lane, fcur, wib, WARPS, false, acc);
         if (lane == 0)
             for (int q = 0; q < 6; q++) part[wib][q] = acc[q];
         __syncthreads();
@@ -1461,9 +1440,9 @@ cudaError_t launch_sb(const BatchLaunch &b, cudaStream_t st) {
 // BATCH_GATHER only copies the step counters.  Every mode copies them.
 constexpr int CV_BLOCK = 1024;
 __global__ void __launch_bounds__(CV_BLOCK)
-    k_batch_converge(BatchLaunch b, int ncase, double tol, long long max_steps, int mode,
-                     int *state, double *drag, long long *steps, int *toff, int *ioff,
-                     int tile_w, int tile_h) {
+    k_batch_converge(BatchLaunch b, int ncase, double tol, long long max_steps, int window,
+                     int mode, int *state, double *drag, int *calm, double *anchor,
+                     long long *steps, int *toff, int *ioff, int tile_w, int tile_h) {
     __shared__ int changed;
     __shared__ int wsum[3][CV_BLOCK / 32];
     __shared__ int carry[3];
@@ -1480,6 +1459,8 @@ __global__ void __launch_bounds__(CV_BLOCK)
         if (mode == BATCH_GATHER) continue;
         if (mode == BATCH_REBUILD) {
             drag[c] = __longlong_as_double(0x7ff8000000000000ll);  // no history
+            anchor[c] = drag[c];
+            calm[c] = 0;
             continue;
         }
         if (state[c] != 0) continue;
@@ -1490,10 +1471,17 @@ __global__ void __launch_bounds__(CV_BLOCK)
             const long long slot = (t - 1) % p.ring_len;
             const double *rg = p.ring + (slot * 2 + 1) * p.nsolid * 3;
             for (int s = 0; s < p.nsolid; s++) D += rg[s * 3];
-            const double prev = drag[c];
+            // converged once the drag has stayed within tol of the drag at the
+            // start of `window` tests in a row (window 1: of the previous test)
+            const double a = anchor[c];
             drag[c] = D;
             if (!isfinite(D)) ns = 3;
-            else if (isfinite(prev) && fabs(D - prev) < tol * fabs(D)) ns = 1;
+            else if (isfinite(a) && fabs(D - a) < tol * fabs(D)) {
+                if (++calm[c] >= window) ns = 1;
+            } else {
+                anchor[c] = D;
+                calm[c] = 0;
+            }
         }
         if (ns == 0 && t >= max_steps) ns = 2;
         if (ns != 0) {
@@ -1583,9 +1571,10 @@ cudaError_t launch_solids_batch(const BatchLaunch &b, cudaStream_t st) {
 
 cudaError_t launch_batch_converge(const BatchLaunch &b, const BatchState &s, int mode,
                                   cudaStream_t st) {
-    k_batch_converge<<<1, CV_BLOCK, 0, st>>>(b, s.ncase, s.tol, s.max_steps, mode,
-                                             s.state, s.drag, s.steps, s.toff, s.ioff,
-                                             tile_nodes(b.precision, b.variant), b.tile_h);
+    k_batch_converge<<<1, CV_BLOCK, 0, st>>>(b, s.ncase, s.tol, s.max_steps, s.window, mode,
+                                             s.state, s.drag, s.calm, s.anchor, s.steps, s.toff,
+                                             s.ioff, tile_nodes(b.precision, b.variant),
+                                             b.tile_h);
     return cudaGetLastError();
 }
 

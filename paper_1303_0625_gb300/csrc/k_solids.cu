@@ -143,6 +143,68 @@ __global__ void k_warm_start(const StepParams p, const float *pred, double U, do
     }
 }
 
+// The same with the mass flux of every column made equal to the inlet's
+// (open channel, walls in y): the steady flow carries the inlet's flux
+// sum_y rho u_x through every column, and an error in it relaxes on the
+// slowest scales of the channel.  One block per column x: rho and u_x of its
+// fluid nodes as above (Poiseuille base), Q(x) = sum rho u_x and the inlet's
+// Q_in = sum over column 0 of rho u_P (FP64, fixed tree), then
+// u_x -> u_x Q_in / Q(x) and f = f^eq.
+constexpr int WS_BLOCK = 128;
+
+__device__ double block_sum_ws(double v, double *sh) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) sh[w] = v;
+    __syncthreads();
+    double t = 0.0;
+    for (int k = 0; k < WS_BLOCK / 32; k++) t += sh[k];
+    return t;
+}
+
+template <int P>
+__global__ void __launch_bounds__(WS_BLOCK) k_warm_start_flux(const StepParams p, const float *pred,
+                                                              double U, double R) {
+    __shared__ double sh[WS_BLOCK / 32];
+    const Lattice &L = p.L;
+    const int x = blockIdx.x;
+    const long long n = (long long)L.nx * L.ny;
+    const long long t = *p.t;
+    void *f = (t & 1) ? p.f1 : p.f0;
+    const double h = (double)L.ny, nu = (p.tau - 0.5) / 3.0;
+    auto rho_at = [&](int xx, int y) {
+        return p.rho0 + R * (double)pred[(long long)y * L.nx + xx] +
+               24.0 * nu * p.umax * (double)(L.nx - 1 - xx) / (h * h);
+    };
+    auto up_at = [&](int y) {
+        const double yy = (double)y + 0.5;
+        return 4.0 * p.umax * yy * (h - yy) / (h * h);
+    };
+    double q = 0.0, qin = 0.0;
+    for (int y = threadIdx.x; y < L.ny; y += WS_BLOCK) {
+        if (!(p.flags[cell_of(L, 0, y)] & 1u)) qin += rho_at(0, y) * up_at(y);
+        if (!(p.flags[cell_of(L, x, y)] & 1u))
+            q += rho_at(x, y) * (up_at(y) + U * (double)pred[n + (long long)y * L.nx + x]);
+    }
+    q = block_sum_ws(q, sh);
+    qin = block_sum_ws(qin, sh);
+    const double scale = q > 0.0 ? qin / q : 1.0;
+    for (int y = threadIdx.x; y < L.ny; y += WS_BLOCK) {
+        const long long k = cell_of(L, x, y), o = (long long)y * L.nx + x;
+        if (p.flags[k] & 1u) continue;
+        const double rho = rho_at(x, y);
+        const double ux = (up_at(y) + U * (double)pred[n + o]) * scale;
+        const double uy = U * (double)pred[2 * n + o];
+        const double uu = ux * ux + uy * uy;
+        for (int i = 0; i < 9; i++) {
+            const double eu = cx(i) * ux + cy(i) * uy;
+            put64<P>(f, L.plane, i, k, rho * wgt<double>(i) * (1.0 + 3.0 * eu + 4.5 * eu * eu - 1.5 * uu));
+        }
+    }
+}
+
 // Network input of a case, [8][ny][nx] floats: 0 the solid mask, 1 Re / 100,
 // 2 log10(Re) / 2, 3 the signed distance to the nearest disk surface / 16
 // (clipped to [-1, 4]), 4 the axial distance from that disk's centre in its
@@ -277,6 +339,14 @@ cudaError_t launch_import_populations(const StepParams &p, const double *in, cud
 
 cudaError_t launch_warm_start(const StepParams &p, const float *pred, double u_scale,
                               double rho_scale, int base, cudaStream_t st) {
+    if (base & 2) {  // the column flux made equal to the inlet's (with the Poiseuille base)
+        switch (p.precision) {
+            case LBM_FP64: k_warm_start_flux<LBM_FP64><<<p.L.nx, WS_BLOCK, 0, st>>>(p, pred, u_scale, rho_scale); break;
+            case LBM_FP32_DEV: k_warm_start_flux<LBM_FP32_DEV><<<p.L.nx, WS_BLOCK, 0, st>>>(p, pred, u_scale, rho_scale); break;
+            default: k_warm_start_flux<LBM_FP16_DEV><<<p.L.nx, WS_BLOCK, 0, st>>>(p, pred, u_scale, rho_scale);
+        }
+        return cudaGetLastError();
+    }
     const dim3 g = cell_grid(p.L);
     switch (p.precision) {
         case LBM_FP64: k_warm_start<LBM_FP64><<<g, 128, 0, st>>>(p, pred, u_scale, rho_scale, base); break;

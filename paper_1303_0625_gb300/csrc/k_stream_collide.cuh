@@ -131,20 +131,42 @@ __device__ __forceinline__ void bounce(const StepParams &p, const typename Raw<P
                 // M = 6 w_i rho_w (e_i . v), v at the cut x - q e_i; half-way
                 // value where x + e_i is not a fluid node
                 const DSolid &b = p.S[o];
-                const double q = link_fraction(L, b, x, y, opp(i));
-                double ux, uy, ddx, ddy;
-                point_velocity(L, b.x, b.y, b.vx, b.vy, b.om, (double)x - q * cx(i),
-                               (double)y - q * cy(i), ux, uy, ddx, ddy);
-                const C m = (C)6 * wgt<C>(i) * rho_w * ((C)cx(i) * (C)ux + (C)cy(i) * (C)uy);
+                C q, ux, uy;
+                if (Prec<P>::dev) {
+                    // FP32: the offset from the centre's nearest image, split
+                    int di = x - b.xwi, dj = y - b.ywi;
+                    if (L.bc_x == LBM_PERIODIC) {
+                        if (2 * di > L.nx) di -= L.nx;
+                        else if (2 * di < -L.nx) di += L.nx;
+                    }
+                    if (L.bc_y == LBM_PERIODIC) {
+                        if (2 * dj > L.ny) dj -= L.ny;
+                        else if (2 * dj < -L.ny) dj += L.ny;
+                    }
+                    q = (C)link_fraction_split(di, dj, b.xwr, b.ywr, b.r, -cx(i), -cy(i));
+                    const C ddx = ((C)di - (C)b.xwr) - q * (C)cx(i);
+                    const C ddy = ((C)dj - (C)b.ywr) - q * (C)cy(i);
+                    ux = (C)b.vxf - (C)b.omf * ddy;
+                    uy = (C)b.vyf + (C)b.omf * ddx;
+                } else {
+                    const double qd = link_fraction(L, b, x, y, opp(i));
+                    double vxd, vyd, ddx, ddy;
+                    point_velocity(L, b.x, b.y, b.vx, b.vy, b.om, (double)x - qd * cx(i),
+                                   (double)y - qd * cy(i), vxd, vyd, ddx, ddy);
+                    q = (C)qd;
+                    ux = (C)vxd;
+                    uy = (C)vyd;
+                }
+                const C m = (C)6 * wgt<C>(i) * rho_w * ((C)cx(i) * ux + (C)cy(i) * uy);
                 const C back = cvt(fin[opp(i) * plane + k]);
-                if (q >= 0.5) {
-                    g[i] = (back + m) / (C)(2.0 * q) +
-                           (C)((2.0 * q - 1.0) / (2.0 * q)) * cvt(fin[i * plane + k]);
+                const C q2 = (C)2 * q;
+                if (q2 >= (C)1) {
+                    g[i] = (back + m) / q2 + ((q2 - (C)1) / q2) * cvt(fin[i * plane + k]);
                 } else if (!((fl >> opp(i)) & 1u)) {
                     int xn, yn;
                     locate(L, x + cx(i), y + cy(i), xn, yn);
-                    g[i] = (C)(2.0 * q) * back +
-                           (C)(1.0 - 2.0 * q) * cvt(fin[opp(i) * plane + yn * L.pitch + xn]) + m;
+                    g[i] = q2 * back +
+                           ((C)1 - q2) * cvt(fin[opp(i) * plane + yn * L.pitch + xn]) + m;
                 } else {
                     g[i] = back + m;
                 }

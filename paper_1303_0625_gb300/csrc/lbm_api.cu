@@ -900,11 +900,15 @@ lbm_status lbm_set_populations(lbm_ctx *c, const double *f, int32_t on_device) {
 }
 
 lbm_status lbm_warm_start(lbm_ctx *c, const float *pred, double u_scale, double rho_scale,
-                          int32_t base) {
-    if (!c || !pred || !std::isfinite(u_scale) || !std::isfinite(rho_scale) || base < 0 || base > 1)
+                          int32_t flags) {
+    if (!c || !pred || !std::isfinite(u_scale) || !std::isfinite(rho_scale) || flags < 0 ||
+        flags > (LBM_WS_BASE | LBM_WS_FLUX))
         return LBM_EINVAL;
-    if (base && c->cfg.bc_x != LBM_OPEN)
+    if (flags && c->cfg.bc_x != LBM_OPEN)
         return fail(c, LBM_EINVAL, "a Poiseuille base needs an open channel");
+    if ((flags & LBM_WS_FLUX) && !(flags & LBM_WS_BASE))
+        return fail(c, LBM_EINVAL, "the column flux correction works on the Poiseuille base");
+    const int base = flags;
     CK(c, cudaSetDevice(c->cfg.device));
     CK(c, gbm::launch_warm_start(params(c), pred, u_scale, rho_scale, base, c->stream));
     c->launches++;
@@ -1192,6 +1196,9 @@ struct lbm_batch {
     unsigned int *ticket_d = nullptr;
     int *state_d = nullptr;
     double *drag_d = nullptr;
+    int *calm_d = nullptr;       // tests in a row within tol of the anchor, per case
+    double *anchor_d = nullptr;  // drag at the start of that run, per case
+    int window = 1;              // tests in a row within tol that retire a case
     long long *steps_d = nullptr;
     int *toff_d = nullptr, *ioff_d = nullptr;
     long long tile_cap = 0, item_cap = 0;
@@ -1262,6 +1269,9 @@ gbm::BatchState bstate(const lbm_batch *b) {
     s.max_steps = b->max_steps;
     s.state = b->state_d;
     s.drag = b->drag_d;
+    s.window = b->window;
+    s.calm = b->calm_d;
+    s.anchor = b->anchor_d;
     s.steps = b->steps_d;
     s.toff = b->toff_d;
     s.ioff = b->ioff_d;
@@ -1282,7 +1292,8 @@ void brelease(lbm_batch *b) {
         release(c);
     }
     void *bufs[] = {b->cases_d, b->tiles_d, b->items_d, b->counts_d, b->active_d, b->ticket_d,
-                    b->state_d, b->drag_d, b->steps_d, b->toff_d, b->ioff_d};
+                    b->state_d, b->drag_d, b->calm_d, b->anchor_d, b->steps_d, b->toff_d,
+                    b->ioff_d};
     for (void *p : bufs)
         if (p) cudaFree(p);
     if (b->nactive_h) cudaFreeHost(b->nactive_h);
@@ -1475,6 +1486,9 @@ lbm_status lbm_batch_create(const lbm_config *configs, int32_t ncase, lbm_batch 
     if (e == cudaSuccess) e = cudaMalloc(&b->ticket_d, sizeof(unsigned int));
     if (e == cudaSuccess) e = cudaMalloc(&b->state_d, n * sizeof(int));
     if (e == cudaSuccess) e = cudaMalloc(&b->drag_d, n * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&b->calm_d, n * sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc(&b->anchor_d, n * sizeof(double));
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->calm_d, 0, n * sizeof(int), b->stream);
     if (e == cudaSuccess) e = cudaMalloc(&b->steps_d, n * sizeof(long long));
     if (e == cudaSuccess) e = cudaMalloc(&b->toff_d, n * sizeof(int));
     if (e == cudaSuccess) e = cudaMalloc(&b->ioff_d, n * sizeof(int));
@@ -1532,6 +1546,14 @@ lbm_status lbm_batch_set_convergence(lbm_batch *b, int32_t every, double tol, in
     b->every = every;
     b->tol = tol;
     b->max_steps = max_steps;
+    b->dirty = true;
+    bdrop_graph(b);
+    return LBM_OK;
+}
+
+lbm_status lbm_batch_set_convergence_window(lbm_batch *b, int32_t tests) {
+    if (!b || tests < 1) return LBM_EINVAL;
+    b->window = tests;
     b->dirty = true;
     bdrop_graph(b);
     return LBM_OK;

@@ -324,6 +324,30 @@ __device__ __forceinline__ double link_fraction(const Lattice &L, const DSolid &
     return q;
 }
 
+// The same fraction for the FP32 kernels, from the node's offset from the
+// centre split as an integer part minus an FP32 remainder, (di - fx, dj - fy),
+// along (ex, ey): the offset and c = |p - R|^2 - r^2 in FP64 without a
+// division (the offset is exact, c to rounding), the root in FP32 by the
+// conjugate form q = c / (-h + sqrt(h^2 - a c)), which loses no digits when
+// the node lies close to the circle.  GB300 runs FP64 division and square
+// root at a small fraction of its FP32 rate; these are the only ones this
+// replaces.
+__device__ __forceinline__ float link_fraction_split(int di, int dj, float fx, float fy, double r,
+                                                     int ex, int ey) {
+    const double px = (double)di - (double)fx, py = (double)dj - (double)fy;
+    const double c = fma(px, px, fma(py, py, -r * r));  // > 0: the node is outside
+    const float a = (float)(ex * ex + ey * ey), h = (float)(px * ex + py * ey);
+    const float cf = (float)c, disc = h * h - a * cf;
+    float q = 0.5f;
+    if (disc > 0.f) {
+        const float den = -h + sqrtf(disc);
+        q = den > 0.f ? cf / den : 0.f;
+    }
+    if (!(q > 0.f)) q = 0.f;
+    if (q > 1.f) q = 1.f;
+    return q;
+}
+
 __device__ __forceinline__ long long cell_of(const Lattice &L, int x, int y) {
     return (long long)y * L.pitch + x;
 }
@@ -356,6 +380,9 @@ struct BatchState {
     long long max_steps;
     int *state;               // 0 active, 1 converged, 2 step cap, 3 unstable
     double *drag;             // drag at the previous test (NaN: none yet)
+    int window;               // tests in a row within tol of the first that retire a case
+    int *calm;                // tests in a row within tol of the anchor so far
+    double *anchor;           // drag at the start of the current run of calm tests
     long long *steps;         // step counter of each case at the last test
     int *toff, *ioff;         // offsets of each active case in the tile and item lists
 };

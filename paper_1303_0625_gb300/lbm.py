@@ -112,6 +112,7 @@ _SIGNATURES = {
     "lbm_batch_case": (_I32, [_P, _I32, ctypes.POINTER(_P)]),
     "lbm_batch_add_solid": (_I32, [_P, _I32, ctypes.POINTER(lbm_disk), ctypes.POINTER(_I32)]),
     "lbm_batch_set_convergence": (_I32, [_P, _I32, ctypes.c_double, _I64]),
+    "lbm_batch_set_convergence_window": (_I32, [_P, _I32]),
     "lbm_batch_run": (_I32, [_P, _I64, ctypes.POINTER(_I32)]),
     "lbm_batch_state": (_I32, [_P, _P, _P, _P]),
     "lbm_batch_retire": (_I32, [_P, _P, _I32]),
@@ -384,6 +385,10 @@ def lbm_batch_set_convergence(b, every: int, tol: float, max_steps: int):
     _bcheck(load().lbm_batch_set_convergence(b, int(every), float(tol), int(max_steps)), b)
 
 
+def lbm_batch_set_convergence_window(b, tests: int):
+    _bcheck(load().lbm_batch_set_convergence_window(b, int(tests)), b)
+
+
 def lbm_batch_run(b, steps: int) -> int:
     na = _I32()
     _bcheck(load().lbm_batch_run(b, int(steps), ctypes.byref(na)), b)
@@ -504,9 +509,14 @@ def lbm_unet_input(net, owner_dev, reynolds: float, in_dev):
     _ncheck(load().lbm_unet_input(net, _ptr(owner_dev), float(reynolds), _ptr(in_dev)), net)
 
 
-def lbm_warm_start(ctx, prediction_dev, u_scale: float, rho_scale: float, base: bool = False):
+LBM_WS_BASE, LBM_WS_FLUX = 1, 2
+
+
+def lbm_warm_start(ctx, prediction_dev, u_scale: float, rho_scale: float, base: bool = False,
+                   flux: bool = False):
+    flags = (LBM_WS_BASE if base else 0) | (LBM_WS_FLUX if flux else 0)
     _check(load().lbm_warm_start(ctx, _ptr(prediction_dev), float(u_scale), float(rho_scale),
-                                 int(bool(base))), ctx)
+                                 flags), ctx)
 
 
 class UNet:
@@ -806,8 +816,9 @@ class Batch:
     def add_disk(self, k: int, cx, cy, r) -> int:
         return lbm_batch_add_solid(self._h, k, lbm_disk(cx=cx, cy=cy, r=r))
 
-    def set_convergence(self, every=100, tol=1e-7, max_steps=2_000_000):
+    def set_convergence(self, every=100, tol=1e-7, max_steps=2_000_000, window=1):
         lbm_batch_set_convergence(self._h, every, tol, max_steps)
+        lbm_batch_set_convergence_window(self._h, window)
 
     def run(self, steps: int) -> int:
         """Advance the active cases by up to ``steps``; returns the active count."""

@@ -133,6 +133,27 @@ def test_convergence_retires_cases_and_freezes_them():
         assert steps2[k] == steps[k] + 2 * every or st2[k] != L.LBM_CASE_ACTIVE
 
 
+def test_convergence_window_needs_consecutive_calm_tests():
+    """With a tolerance every test passes (tol 10), a case retires at the
+    first test that finds the drag within tol of the previous one (the second
+    test: the first has no history), or, with a window of w tests, after w
+    such tests in a row; a window needs w >= 1."""
+    ws = _sweep(3, seed=59)
+    every = 10
+    for window, expect in ((1, 2 * every), (4, 5 * every)):
+        b = _batch(ws, "fp32", ring=4)
+        b.set_convergence(every=every, tol=10.0, max_steps=10**6, window=window)
+        assert b.run(1000) == 0
+        st, steps, _ = b.state()
+        assert (st == L.LBM_CASE_CONVERGED).all() and (steps == expect).all(), (window, steps)
+        b.close()
+    b = _batch(ws, "fp32", ring=4)
+    with pytest.raises(G.LBMError) as e:
+        L.lbm_batch_set_convergence_window(b.handle, 0)
+    assert e.value.status == G.LBM_EINVAL
+    b.close()
+
+
 def test_step_cap_and_all_retired():
     ws = _sweep(3, seed=53)
     b = _batch(ws, "fp32", ring=4)

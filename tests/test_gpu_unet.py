@@ -141,6 +141,38 @@ def test_warm_start_sets_the_predicted_equilibrium():
     rho, ux, uy = lat.fields()
     assert np.allclose(rho[fl], (rp + R * pred[0])[fl], atol=2e-6)
     assert np.allclose(ux[fl], (up[:, None] + U_ * pred[1])[fl], atol=2e-6)
+    with pytest.raises(G.LBMError):  # the flux correction works on the base
+        L.lbm_warm_start(lat.handle, dev, U_, R, flux=True)
+
+
+def test_warm_start_column_flux_equals_the_inlet_flux():
+    """With the column flux correction every column of the initial state
+    carries the inlet's mass flux sum_y rho u_P over column 0, u_x of each
+    column scaled by one factor (FP64 storage: to rounding); rho and u_y as
+    without it."""
+    import torch
+    H, W = 32, 64
+    lat = G.Lattice(W, H, 0.7, bc_x=G.LBM_OPEN, bc_y=G.LBM_WALL, inflow_umax=0.05,
+                    precision=G.LBM_FP64)
+    lat.add_disk(30.3, 15.8, 6.2)
+    lat.add_disk(48.0, 9.5, 3.5)
+    rng = np.random.default_rng(5)
+    pred = rng.normal(0.0, 0.3, (3, H, W)).astype(np.float32)
+    U_, R = 0.05, 3e-3
+    L.lbm_warm_start(lat.handle, torch.from_numpy(pred).cuda(), U_, R, base=True, flux=True)
+    rho, ux, uy = lat.fields()
+    fl = lat.owner() < 0
+    from paper_1303_0625_gb300 import warmstart as WS
+    rp, up = WS.poiseuille(dict(nx=W, ny=H, tau=0.7, inflow_umax=0.05, rho0=1.0))
+    rho_p = rp + R * pred[0].astype(np.float64)
+    ux_p = up[:, None] + U_ * pred[1].astype(np.float64)
+    q_in = (np.where(fl[:, 0], rho_p[:, 0] * up, 0.0)).sum()
+    q = np.where(fl, rho * ux, 0.0).sum(axis=0)
+    assert np.abs(q / q_in - 1.0).max() <= 1e-12
+    scale = q_in / np.where(fl, rho_p * ux_p, 0.0).sum(axis=0)
+    assert np.allclose(ux[fl], (ux_p * scale[None, :])[fl], rtol=0, atol=1e-13)
+    assert np.allclose(rho[fl], rho_p[fl], rtol=0, atol=1e-13)
+    assert np.allclose(uy[fl], (U_ * pred[2].astype(np.float64))[fl], rtol=0, atol=1e-13)
 
 
 def test_wait_time_out_is_reported_and_the_network_recovers():
