@@ -75,6 +75,9 @@ def parse():
     ap.add_argument("--ws-epochs", type=int, default=100)
     ap.add_argument("--ws-save", type=str, default="",
                     help="with --warm-start: write the trained parameters here (npz)")
+    ap.add_argument("--ws-rho-weight", type=float, default=1.0,
+                    help="weight of the density channel in the training loss (the target is "
+                         "scaled by it)")
     ap.add_argument("--ws-load", type=str, default="",
                     help="with --warm-start: evaluate these parameters instead of training")
     ap.add_argument("--ws-bench-cases", type=int, default=96,
@@ -705,7 +708,7 @@ def run_unet(a, local, H=128, W=256, B=16, levels=4, base=32):
 WS_WEIGHTS = os.path.join(ROOT, "paper_1303_0625_gb300", "weights", "unet_channels_256x128.npz")
 
 
-def evaluate_warm_start(net, test_all, local):
+def evaluate_warm_start(net, test_all, local, rho_weight=1.0):
     """Time to converged drag on held-out channels, warm (net) against cold:
     steps and wall time (inference included) until every case's drag is within
     1e-4 of the drag its plain run converges to (within 1e-5 of one value
@@ -725,11 +728,16 @@ def evaluate_warm_start(net, test_all, local):
     test = [test_all[k] for k in keep]
     d_star = ref["drag"][keep]
     cold = WS.time_to_drag(test, d_star, cap=WS.REF_CAP, device=local)
-    warm = WS.time_to_drag(test, d_star, net=net, cap=WS.REF_CAP, device=local)
-    tdata = WS.dataset(test_all, ref)
+    warm = WS.time_to_drag(test, d_star, net=net, cap=WS.REF_CAP, rho_weight=rho_weight,
+                           device=local)
+    tdata = WS.dataset(test_all, ref, rho_weight=rho_weight)
     pred = WS.predict(net, tdata["x"]).cpu().numpy()
     m = tdata["fluid"][:, None]
     err = float(np.sqrt(((pred - tdata["y"]) ** 2 * m).sum() / ((tdata["y"] ** 2) * m).sum()))
+    # per channel (independent of the channels' scales)
+    err_c = [round(float(np.sqrt(((pred[:, c] - tdata["y"][:, c]) ** 2 * m[:, 0]).sum()
+                                 / ((tdata["y"][:, c] ** 2) * m[:, 0]).sum())), 4)
+             for c in range(3)]
     steps_c, steps_w = cold["steps"].astype(float), warm["steps"].astype(float)
     return {"test_cases": len(test_all), "test_steady": len(test),
             "excluded_unsteady": int(len(test_all) - len(test)),
@@ -739,7 +747,7 @@ def evaluate_warm_start(net, test_all, local):
                      "median_case_steps": float(np.median(steps_w)),
                      "fallbacks": int(warm["fallback"].sum()),
                      "settled_elsewhere": int(warm["elsewhere"].sum())},
-            "prediction_rel_l2": round(err, 4),
+            "prediction_rel_l2": round(err, 4), "prediction_rel_l2_rho_ux_uy": err_c,
             "wall_speedup": round(cold["wall"] / warm["wall"], 3),
             "median_step_speedup": round(float(np.median(steps_c / np.maximum(steps_w, 1))), 3)}
 
@@ -764,14 +772,17 @@ def run_warm_start(a, local):
     torch.cuda.set_device(local)
     net = G.UNet(128, 256, levels=4, base=32, max_batch=16, seed=3, device=local)
     out = {"metric": "time-to-drag at 1e-4 rel err, warm vs cold start", "workload": WS_WORKLOAD}
+    rho_weight = a.ws_rho_weight
     if a.ws_load:
-        net.set_params(np.load(a.ws_load)["params"].astype(np.float32))
+        z = np.load(a.ws_load)
+        net.set_params(z["params"].astype(np.float32))
+        rho_weight = float(z["rho_weight"]) if "rho_weight" in z.files else 1.0
         out["parameters"] = a.ws_load
     else:
         t0 = time.time()
         train_cases = W.warm_start_channels(a.ws_train, seed_offset=5)
         runs = WS.steady(train_cases, device=local)
-        data = WS.dataset(train_cases, runs, mirror=True)
+        data = WS.dataset(train_cases, runs, mirror=True, rho_weight=rho_weight)
         t_data = time.time() - t0
         t1 = time.time()
         losses = WS.train(net, data, epochs=a.ws_epochs, batch=16, lr=1e-3, lr_end=1e-5)
@@ -780,19 +791,21 @@ def run_warm_start(a, local):
                     "train_cases": len(train_cases), "train_steady": int(len(data["index"])),
                     "train_samples": int(data["x"].shape[0]),
                     "data_seconds": round(t_data, 1), "train_seconds": round(time.time() - t1, 1),
-                    "epochs": a.ws_epochs, "final_loss": float("%.4g" % losses[-1])})
+                    "epochs": a.ws_epochs, "final_loss": float("%.4g" % losses[-1]),
+                    "rho_weight": rho_weight})
         if a.ws_save:
             os.makedirs(os.path.dirname(os.path.abspath(a.ws_save)), exist_ok=True)
             np.savez(a.ws_save, params=net.params().astype(np.float16), levels=4, base=32,
-                     height=128, width=256, inputs="lbm_case_input",
+                     height=128, width=256, inputs="lbm_case_input", rho_weight=rho_weight,
                      trained_on=f"{len(train_cases)} channels (seed offset 5), "
                                 f"{int(data['x'].shape[0])} samples with mirrors, "
                                 f"{a.ws_epochs} epochs, Adam 1e-3 -> 1e-5",
                      command=f"python bench.py --warm-start --ws-train {a.ws_train} "
-                             f"--ws-test {a.ws_test} --ws-epochs {a.ws_epochs} --ws-save <path>")
+                             f"--ws-test {a.ws_test} --ws-epochs {a.ws_epochs} "
+                             f"--ws-rho-weight {rho_weight} --ws-save <path>")
             out["saved"] = a.ws_save
     test_all = W.warm_start_channels(a.ws_test, seed_offset=6)
-    out.update(evaluate_warm_start(net, test_all, local))
+    out.update(evaluate_warm_start(net, test_all, local, rho_weight))
     net.close()
     return out
 
@@ -816,8 +829,9 @@ def run_warm_start_bench(a, local):
     t0 = time.time()
     out = {"metric": "time-to-drag at 1e-4 rel err, warm vs cold start", "workload": WS_WORKLOAD,
            "parameters": os.path.relpath(WS_WEIGHTS, ROOT), "trained_on": str(z["trained_on"])}
+    rho_weight = float(z["rho_weight"]) if "rho_weight" in z.files else 1.0
     out.update(evaluate_warm_start(net, W.warm_start_channels(a.ws_bench_cases, seed_offset=6),
-                                   local))
+                                   local, rho_weight))
     out["seconds"] = round(time.time() - t0, 1)
     net.close()
     return out

@@ -112,12 +112,14 @@ def steady(cases, *, precision=L.LBM_FP32_DEV, tol=1e-7, every=100, cap=300_000,
     return out
 
 
-def dataset(cases, runs, mirror=False):
+def dataset(cases, runs, mirror=False, rho_weight=1.0):
     """Inputs [N][8][H][W], targets [N][3][H][W], fluid [N][H][W] (float32) of
     the cases that reached a steady state; with mirror, each also mirrored
     about the channel's centre line (y -> ny - 1 - y, u_y -> -u_y, and the
     input's antisymmetric coordinate plane negated), which the walls and the
-    inlet profile leave invariant."""
+    inlet profile leave invariant.  The density target is multiplied by
+    rho_weight (its weight in the squared-error loss is rho_weight^2;
+    time_to_drag divides it out again)."""
     keep = np.flatnonzero(runs["state"] == L.LBM_CASE_CONVERGED)
     n = len(keep)
     ny, nx = cases[0]["ny"], cases[0]["nx"]
@@ -129,7 +131,7 @@ def dataset(cases, runs, mirror=False):
         U = cases[k]["u_scale"]
         f[j] = ~solid
         rp, up = poiseuille(cases[k])
-        y[j, 0] = np.where(solid, 0.0, (runs["rho"][k] - rp) / rho_scale(cases[k]))
+        y[j, 0] = np.where(solid, 0.0, (runs["rho"][k] - rp) * rho_weight / rho_scale(cases[k]))
         y[j, 1] = np.where(solid, 0.0, (runs["ux"][k] - up[:, None]) / U)
         y[j, 2] = np.where(solid, 0.0, runs["uy"][k] / U)
     if mirror:
@@ -197,12 +199,13 @@ def _mass(ctx):
 
 def time_to_drag(cases, d_star, *, net=None, rel=1e-4, precision=L.LBM_FP32_DEV, every=100,
                  cap=300_000, drift_steps=200, drift_mass=1e-2, settle=REF_TOL,
-                 settle_checks=REF_WINDOW, flux=True, device=0, stream=None):
+                 settle_checks=REF_WINDOW, flux=True, rho_weight=1.0, device=0, stream=None):
     """Steps and wall time until every case's Eq. 5 drag is within rel of
     d_star (the converged drag of the plain run), starting cold (net None)
     or warm from the network's prediction (on the channel's Poiseuille flow,
     with each column's mass flux made equal to the inlet's unless flux is
-    False: lbm_warm_start).  The plain run is the judge, and
+    False: lbm_warm_start; the network's density channel in units of
+    rho_scale / rho_weight).  The plain run is the judge, and
     a warm case falls back to it: its populations are reset to the plain
     initial state in place (it keeps stepping in the batch, its count of
     steps goes on):
@@ -240,8 +243,8 @@ def time_to_drag(cases, d_star, *, net=None, rel=1e-4, precision=L.LBM_FP32_DEV,
             L.lbm_unet_forward(net.handle, xin[s:e], out[s:e], e - s, on_device=True)
         torch.cuda.synchronize()
         for k in range(n):
-            L.lbm_warm_start(b.case(k).handle, out[k], cases[k]["u_scale"], rho_scale(cases[k]),
-                             base=True, flux=flux)
+            L.lbm_warm_start(b.case(k).handle, out[k], cases[k]["u_scale"],
+                             rho_scale(cases[k]) / rho_weight, base=True, flux=flux)
         mass0 = np.array([_mass(b.case(k)) for k in range(n)])
     done = np.full(n, -1, dtype=np.int64)
     drift = None
