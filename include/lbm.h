@@ -160,9 +160,10 @@ lbm_status lbm_step(lbm_ctx *ctx, int64_t nsteps);
  * LBM_EUNSTABLE for a non-finite or non-positive density or a non-finite
  * solid state; LBM_ETIMEOUT when a grid barrier of the per-solid kernel gave
  * up; LBM_ESTATE when a solid covered or uncovered more than 256 nodes in one
- * step (its event queue) or the deferred list of nodes next to solids
- * overflowed (the step's momentum booking or slow-node update is then
- * incomplete).  These conditions persist: every later waiting call returns
+ * step (its event queue), the step's owner changes overflowed their list
+ * (twice the event lists' room), or the deferred list of nodes next to
+ * solids overflowed (the step's momentum booking, re-rasterisation or
+ * slow-node update is then incomplete).  These conditions persist: every later waiting call returns
  * them until lbm_load restores a saved state. */
 lbm_status lbm_sync(lbm_ctx *ctx);
 

@@ -325,7 +325,8 @@ lbm_status check_status(lbm_ctx *c) {
     if (st & 8)
         return fail(c, LBM_ESTATE,
                     "a solid covered or uncovered more nodes in one step than its event queue "
-                    "holds (%d)", gbm::SOLID_EVENTS);
+                    "holds (%d), or the step's owner changes overflowed their list",
+                    gbm::SOLID_EVENTS);
     if (st & 16) return fail(c, LBM_ESTATE, "the list of nodes next to solids overflowed");
     return LBM_OK;
 }
