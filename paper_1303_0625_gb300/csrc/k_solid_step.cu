@@ -593,7 +593,7 @@ constexpr int FW = FB / 32;
 constexpr float ANN_EPS = 0.05f;         // above the FP32 rounding of a chord end
 
 template <int P, bool LOCAL, bool BND>
-__global__ void __launch_bounds__(FB, 6) k_forces(const StepParams p) {
+__global__ void __launch_bounds__(FB, 8) k_forces(const StepParams p) {
     using C = typename Prec<P>::C;
     using S = typename Prec<P>::S;
     constexpr bool SPARSE = !LOCAL && !BND;
@@ -1235,7 +1235,7 @@ __device__ __forceinline__ void advance_solid(const Lattice &L, DSolid &b) {
 }
 
 // P and R (beside the advection-collision kernel), one warp per moving solid.
-__global__ void __launch_bounds__(SW_BLOCK, 2) k_ring(const StepParams p) {
+__global__ void __launch_bounds__(SW_BLOCK, 4) k_ring(const StepParams p) {
     __shared__ int2 queue[WARPS][EVENTS];
     __shared__ int qn[WARPS];
     __shared__ int4 tile_ipos[NEAR_TILE];
