@@ -1357,7 +1357,7 @@ cudaError_t launch_r(const StepParams &p, cudaStream_t st) {
 // active case and swaps its population buffers (batch convention: f0 holds
 // the current time), after every block has read them.
 template <int P, bool LOCAL>
-__global__ void __launch_bounds__(SW_BLOCK)
+__global__ void __launch_bounds__(SW_BLOCK, 2)
     k_solids_batch(StepParams *cases, const int2 *__restrict__ items,
                    const int *__restrict__ nitems, const int *__restrict__ active,
                    const int *__restrict__ nactive, unsigned int *ticket) {
