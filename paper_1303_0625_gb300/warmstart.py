@@ -189,6 +189,15 @@ def predict(net, data_x, batch=16):
     return out
 
 
+def band_step(anchor, calm, drag, tol):
+    """One test of the steady band: a case whose drag is within tol
+    (relative) of its anchor counts one more calm test; any other case starts
+    a new run at its current drag.  Returns the new (anchor, calm) arrays;
+    NaN anchors start a run."""
+    near = np.abs(drag - anchor) < tol * np.abs(drag)
+    return np.where(near, anchor, drag), np.where(near, calm + 1, 0)
+
+
 def _mass(ctx):
     """Total fluid mass of a case, or NaN once its state is unusable."""
     try:
@@ -291,9 +300,7 @@ def time_to_drag(cases, d_star, *, net=None, rel=1e-4, precision=L.LBM_FP32_DEV,
         if newly.any():  # the case has reached its drag: it stops stepping
             b.retire(np.flatnonzero(newly))
         if net is not None and steps > drift_steps:
-            near = np.abs(drag - anchor) < settle * np.abs(drag)
-            calm = np.where(near, calm + 1, 0)
-            anchor = np.where(near, anchor, drag)
+            anchor, calm = band_step(anchor, calm, drag, settle)
             away = (calm >= settle_checks) & ~ok & active & ~fallback
             if away.any():
                 elsewhere |= away
